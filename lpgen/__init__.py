@@ -1,0 +1,286 @@
+"""Seeded synthetic LP generators shared by the tests, the benchmark and the oracle checks.
+
+This module builds problem data only.  It holds none of the solver's arithmetic: no PDHG
+step, no projection, no residual.  Every LP it returns is in the form of Section 2.1
+(Eq. prob:primal): ``min c^T x  s.t.  lc <= A x <= uc,  lv <= x <= uv`` with ``A`` stored
+as CSR (int64 row pointers, int32 column indices sorted inside each row, float64 values).
+
+Row types follow the constraint-type codes of the C ABI: 0 is an equality row
+(``lc = uc = b``), 1 a ``<=`` row (``lc = -inf, uc = b``), 2 a ``>=`` row
+(``lc = b, uc = +inf``).
+
+Feasible instances are built from a primal-dual pair ``(x*, y*, z*)`` that satisfies the
+KKT conditions of the LP by construction, so the optimal value ``p* = c^T x*`` is known
+without solving anything:
+
+* ``x*`` sits at its lower bound, its upper bound, or strictly inside;
+* ``<=`` rows get a positive slack and ``y* = 0``; equality rows get ``y* ~ N(0, 1)``;
+* the reduced cost ``z*`` is positive at a lower bound, negative at an upper bound and
+  zero inside (strict complementarity, with a 0.1 floor);
+* ``c = A^T y* + z*``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+EQ, LE, GE = 0, 1, 2
+
+
+@dataclasses.dataclass
+class LP:
+    """A sparse LP in CSR form, plus the optimal pair it was built from (if any)."""
+
+    n: int
+    m: int
+    c: np.ndarray
+    row_ptr: np.ndarray  # int64 [m+1]
+    col: np.ndarray  # int32 [Z]
+    val: np.ndarray  # float64 [Z]
+    lc: np.ndarray  # float64 [m], -inf allowed
+    uc: np.ndarray  # float64 [m], +inf allowed
+    lv: np.ndarray  # float64 [n], -inf allowed
+    uv: np.ndarray  # float64 [n], +inf allowed
+    ctype: np.ndarray | None = None  # int8 [m] when every row is one of EQ/LE/GE
+    b: np.ndarray | None = None  # float64 [m], the finite side of each typed row
+    x_star: np.ndarray | None = None
+    y_star: np.ndarray | None = None
+    z_star: np.ndarray | None = None
+    name: str = "lp"
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    @property
+    def p_star(self) -> float | None:
+        if self.x_star is None:
+            return None
+        return float(np.dot(self.c, self.x_star))
+
+
+def bounds_from_types(ctype: np.ndarray, b: np.ndarray):
+    """Row bounds (lc, uc) from constraint-type codes and right-hand sides."""
+    lc = np.where(ctype == LE, -np.inf, b).astype(np.float64)
+    uc = np.where(ctype == GE, np.inf, b).astype(np.float64)
+    return lc, uc
+
+
+def _csr_from_coo(m: int, n: int, rows: np.ndarray, cols: np.ndarray, vals: np.ndarray):
+    """CSR arrays with columns sorted inside each row; (row, col) pairs must be distinct."""
+    order = np.lexsort((cols, rows))
+    rows = rows[order]
+    cols = cols[order]
+    vals = vals[order]
+    counts = np.bincount(rows, minlength=m)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    return row_ptr, cols.astype(np.int32), vals.astype(np.float64)
+
+
+def _csr_matvec(row_ptr, col, val, x):
+    """A x for building right-hand sides (construction only, not solver arithmetic)."""
+    m = row_ptr.shape[0] - 1
+    rows = np.repeat(np.arange(m), np.diff(row_ptr))
+    return np.bincount(rows, weights=val * x[col], minlength=m)
+
+
+def _csr_rmatvec(row_ptr, col, val, y, n):
+    m = row_ptr.shape[0] - 1
+    rows = np.repeat(np.arange(m), np.diff(row_ptr))
+    return np.bincount(col, weights=val * y[rows], minlength=n)
+
+
+def _planted_optimum(rng, n, m, row_ptr, col, val, ctype):
+    """Bounds, x*, y*, z*, b and c for a feasible LP with a known optimum."""
+    lv = np.zeros(n)
+    uv = np.full(n, np.inf)
+    finite_u = rng.random(n) < 0.5
+    uv[finite_u] = rng.uniform(1.0, 10.0, size=int(finite_u.sum()))
+    # Category per variable: 0 at lower bound, 1 at upper bound, 2 interior.
+    # Finite-u variables: 40 % lower / 40 % upper / 20 % inside; the others 40 % / 0 / 60 %,
+    # so over all variables 40 % sit at 0 and 20 % at u.
+    r = rng.random(n)
+    cat = np.where(r < 0.4, 0, np.where(finite_u & (r < 0.8), 1, 2))
+    x_star = np.zeros(n)
+    x_star[cat == 1] = uv[cat == 1]
+    inside = cat == 2
+    hi = np.where(np.isfinite(uv), uv, 10.0)
+    x_star[inside] = rng.uniform(0.0, 1.0, size=int(inside.sum())) * hi[inside]
+    z_star = np.zeros(n)
+    z_star[cat == 0] = rng.uniform(0.1, 1.0, size=int((cat == 0).sum()))
+    z_star[cat == 1] = -rng.uniform(0.1, 1.0, size=int((cat == 1).sum()))
+    ax = _csr_matvec(row_ptr, col, val, x_star)
+    b = ax.copy()
+    le = ctype == LE
+    b[le] += rng.uniform(0.0, 1.0, size=int(le.sum()))
+    y_star = np.zeros(m)
+    eq = ctype == EQ
+    y_star[eq] = rng.standard_normal(int(eq.sum()))
+    c = _csr_rmatvec(row_ptr, col, val, y_star, n) + z_star
+    return lv, uv, x_star, y_star, z_star, b, c
+
+
+def small_random_lp(seed: int = 0, n: int = 2000, m: int = 1000, nnz_per_col: int = 8,
+                    n_eq: int | None = None) -> LP:
+    """Small feasible LP: every column holds ``nnz_per_col`` distinct rows drawn uniformly,
+    values N(0, 1); the first 60 % of rows are equalities and the rest ``<=`` rows.
+
+    With the defaults this is the 2,000-variable, 1,000-row workload (600 equality rows,
+    400 ``<=`` rows, 16,000 nonzeros).
+    """
+    rng = np.random.default_rng(seed)
+    if n_eq is None:
+        n_eq = (m * 6) // 10
+    k = min(nnz_per_col, m)
+    rows = np.argpartition(rng.random((n, m)), k - 1, axis=1)[:, :k].reshape(-1) if m > 0 \
+        else np.zeros(0, dtype=np.int64)
+    cols = np.repeat(np.arange(n), k) if m > 0 else np.zeros(0, dtype=np.int64)
+    vals = rng.standard_normal(rows.shape[0])
+    row_ptr, col, val = _csr_from_coo(m, n, rows.astype(np.int64), cols.astype(np.int64), vals)
+    ctype = np.where(np.arange(m) < n_eq, EQ, LE).astype(np.int8)
+    lv, uv, xs, ys, zs, b, c = _planted_optimum(rng, n, m, row_ptr, col, val, ctype)
+    lc, uc = bounds_from_types(ctype, b)
+    return LP(n, m, c, row_ptr, col, val, lc, uc, lv, uv, ctype, b, xs, ys, zs,
+              name=f"small_random_lp(seed={seed},n={n},m={m})")
+
+
+def _pareto_row_lengths(rng, m: int, target_nnz: int, cap: int, alpha: float = 1.5):
+    """Row lengths L_i = min(cap, ceil(L0 * U^(-1/alpha))) with L0 chosen by bisection so
+    that sum(L) is within 0.1 % of ``target_nnz`` (Pareto tail of index ``alpha``)."""
+    u = 1.0 - rng.random(m)  # in (0, 1]
+    base = u ** (-1.0 / alpha)
+
+    def total(l0):
+        return int(np.minimum(cap, np.ceil(l0 * base)).sum())
+
+    lo, hi = 1e-3, float(target_nnz) / m * 4 + 1.0
+    while total(hi) < target_nnz and hi < 1e9:
+        hi *= 2
+    l0 = hi
+    for _ in range(100):
+        mid = 0.5 * (lo + hi)
+        t = total(mid)
+        if abs(t - target_nnz) <= max(1, target_nnz // 1000):
+            l0 = mid
+            break
+        if t < target_nnz:
+            lo = mid
+        else:
+            hi = mid
+            l0 = mid
+    lengths = np.minimum(cap, np.ceil(l0 * base)).astype(np.int64)
+    return lengths, l0
+
+
+def powerlaw_lp(seed: int = 1, n: int = 4_000_000, m: int = 2_000_000,
+                target_nnz: int = 40_000_000, cap: int = 100_000, eq_frac: float = 0.6,
+                alpha: float = 1.5) -> LP:
+    """Large irregular LP with power-law row lengths.
+
+    Row lengths follow a Pareto tail of index 1.5 capped at ``cap`` (a few rows are dense and
+    stress load balance); each row picks distinct columns uniformly at random; values are
+    +-1 with probability 0.7 and +-lognormal(0, 1) otherwise; ``eq_frac`` of the rows
+    (chosen at random) are equalities and the others ``<=`` rows; bounds and the planted
+    optimum are built as in :func:`small_random_lp`.
+
+    With the defaults this is the 4M-variable, 2M-row, ~40M-nonzero workload.
+    """
+    rng = np.random.default_rng(seed)
+    cap = min(cap, n)
+    lengths, _ = _pareto_row_lengths(rng, m, target_nnz, cap, alpha)
+    rows = np.repeat(np.arange(m, dtype=np.int64), lengths)
+    cols = rng.integers(0, n, size=rows.shape[0], dtype=np.int64)
+    key = rows * n + cols
+    del rows, cols
+    key.sort()  # by (row, col); then drop repeated draws inside a row
+    keep = np.empty(key.shape[0], dtype=bool)
+    keep[:1] = True
+    np.not_equal(key[1:], key[:-1], out=keep[1:])
+    key = key[keep]
+    del keep
+    rows = key // n
+    cols = (key - rows * n).astype(np.int32)
+    del key
+    z = rows.shape[0]
+    mag = np.where(rng.random(z) < 0.7, 1.0, rng.lognormal(0.0, 1.0, size=z))
+    vals = np.where(rng.random(z) < 0.5, -mag, mag)
+    del mag
+    counts = np.bincount(rows, minlength=m)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    del rows
+    ctype = np.where(rng.random(m) < eq_frac, EQ, LE).astype(np.int8)
+    lv, uv, xs, ys, zs, b, c = _planted_optimum(rng, n, m, row_ptr, cols, vals, ctype)
+    lc, uc = bounds_from_types(ctype, b)
+    return LP(n, m, c, row_ptr, cols, vals, lc, uc, lv, uv, ctype, b, xs, ys, zs,
+              name=f"powerlaw_lp(seed={seed},n={n},m={m},nnz~{target_nnz})")
+
+
+def tiny_bounded_lp(seed: int, n: int = 4, m: int = 3, density: float = 0.7) -> LP:
+    """Tiny dense-ish LP with finite variable bounds (a polytope), mixed row types and an
+    interior feasible point, for brute-force vertex enumeration."""
+    rng = np.random.default_rng(seed)
+    dense = rng.standard_normal((m, n)) * (rng.random((m, n)) < density)
+    for i in range(m):  # no empty rows
+        if not dense[i].any():
+            dense[i, rng.integers(n)] = rng.standard_normal() or 1.0
+    lv = -rng.uniform(0.0, 2.0, size=n)
+    uv = rng.uniform(0.5, 3.0, size=n)
+    xf = lv + (uv - lv) * rng.uniform(0.2, 0.8, size=n)
+    ax = dense @ xf
+    ctype = rng.integers(0, 3, size=m).astype(np.int8)
+    slack = rng.uniform(0.1, 1.0, size=m)
+    b = np.where(ctype == EQ, ax, np.where(ctype == LE, ax + slack, ax - slack))
+    lc, uc = bounds_from_types(ctype, b)
+    c = rng.standard_normal(n)
+    rr, cc = np.nonzero(dense)
+    row_ptr, col, val = _csr_from_coo(m, n, rr.astype(np.int64), cc.astype(np.int64), dense[rr, cc])
+    return LP(n, m, c, row_ptr, col, val, lc, uc, lv, uv, ctype, b, name=f"tiny_bounded_lp({seed})")
+
+
+def from_dense(A: np.ndarray, c, lc, uc, lv, uv, name="dense") -> LP:
+    """Wrap a small dense matrix as an LP in CSR form (structural zeros dropped)."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    rr, cc = np.nonzero(A)
+    row_ptr, col, val = _csr_from_coo(m, n, rr.astype(np.int64), cc.astype(np.int64), A[rr, cc])
+    f = lambda v, k: np.asarray(v, dtype=np.float64).reshape(k)
+    return LP(n, m, f(c, n), row_ptr, col, val, f(lc, m), f(uc, m), f(lv, n), f(uv, n), name=name)
+
+
+def row_length_stress_lp(seed: int, lengths, n: int) -> LP:
+    """LP whose rows have exactly the given lengths (distinct uniform columns, N(0,1) values),
+    mixed row types and a planted optimum: used to stress SpMV load balancing (empty rows,
+    single long rows, rows that straddle tile boundaries)."""
+    rng = np.random.default_rng(seed)
+    lengths = np.asarray(lengths, dtype=np.int64)
+    m = lengths.shape[0]
+    rows_l, cols_l = [], []
+    for i, L in enumerate(lengths):
+        if L == 0:
+            continue
+        L = int(min(L, n))
+        cols_l.append(rng.choice(n, size=L, replace=False))
+        rows_l.append(np.full(L, i, dtype=np.int64))
+    rows = np.concatenate(rows_l) if rows_l else np.zeros(0, np.int64)
+    cols = np.concatenate(cols_l).astype(np.int64) if cols_l else np.zeros(0, np.int64)
+    vals = rng.standard_normal(rows.shape[0])
+    row_ptr, col, val = _csr_from_coo(m, n, rows, cols, vals)
+    ctype = rng.integers(0, 3, size=m).astype(np.int8)
+    ctype[ctype == GE] = LE  # planted optimum uses EQ / LE rows
+    lv, uv, xs, ys, zs, b, c = _planted_optimum(rng, n, m, row_ptr, col, val, ctype)
+    lc, uc = bounds_from_types(ctype, b)
+    return LP(n, m, c, row_ptr, col, val, lc, uc, lv, uv, ctype, b, xs, ys, zs,
+              name=f"row_length_stress_lp({seed})")
+
+
+def scaled_powerlaw_lp(seed: int, scale: float) -> LP:
+    """The power-law workload shrunk by ``scale`` in n, m and nnz (same recipe, cap scaled)."""
+    n = max(2, int(round(4_000_000 * scale)))
+    m = max(1, int(round(2_000_000 * scale)))
+    z = max(m, int(round(40_000_000 * scale)))
+    cap = max(1, min(n, int(round(100_000 * math.sqrt(scale)))))
+    return powerlaw_lp(seed=seed, n=n, m=m, target_nnz=z, cap=cap)

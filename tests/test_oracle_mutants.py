@@ -1,0 +1,175 @@
+"""Planted mistakes in the oracle must each be caught by one of its pins.
+
+Every mutant below is a plausible slip (a dropped term, a wrong sign, a swapped bound, a
+transposed operand, the garbled printed grouping of the Halpern step).  The test patches
+the mutant into the oracle module on the CPU and runs the pins of
+``test_oracle_pins.py``: at least one must fail.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import pdhg as O
+import test_oracle_pins as pins
+
+ALL_CHECKS = [
+    pins.check_pdhg_hand, pins.check_dual_step_closed_forms, pins.check_halpern_fixed_point,
+    pins.check_planted_optimum_is_fixed, pins.check_p_norm_dense, pins.check_kkt_hand,
+    pins.check_kkt_zero_at_planted, pins.check_power_iteration, pins.check_restart_rules,
+    pins.check_pid, pins.check_box_only, pins.check_knapsack,
+    lambda: pins.check_brute_force(seeds=range(2)),
+]
+
+
+def _orig(name):
+    return getattr(O, name)
+
+
+def m_primal_sign(lp, x, y, tau, sigma):
+    g = lp.c + lp.ATy(y)  # wrong sign of A^T y
+    xh = O.proj_X(x - tau * g, lp.lv, lp.uv)
+    xbar = 2.0 * xh - x
+    z = lp.Ax(xbar)
+    w = y / sigma - z
+    return xh, sigma * (w - O.proj_negS(w, lp.lc, lp.uc)), xbar, z
+
+
+def m_no_reflection(lp, x, y, tau, sigma):
+    g = lp.c - lp.ATy(y)
+    xh = O.proj_X(x - tau * g, lp.lv, lp.uv)
+    xbar = xh  # dropped 2 x^{k+1} - x^k
+    z = lp.Ax(xbar)
+    w = y / sigma - z
+    return xh, sigma * (w - O.proj_negS(w, lp.lc, lp.uc)), xbar, z
+
+
+def m_transposed(lp, x, y, tau, sigma):
+    g = lp.c - lp.Ax(y) if lp.m == lp.n else lp.c - lp.A.T.T @ np.resize(y, lp.n)[: lp.n]
+    xh = O.proj_X(x - tau * g, lp.lv, lp.uv)
+    xbar = 2.0 * xh - x
+    z = lp.Ax(xbar)
+    w = y / sigma - z
+    return xh, sigma * (w - O.proj_negS(w, lp.lc, lp.uc)), xbar, z
+
+
+def m_dual_sign(lp, x, y, tau, sigma):
+    g = lp.c - lp.ATy(y)
+    xh = O.proj_X(x - tau * g, lp.lv, lp.uv)
+    xbar = 2.0 * xh - x
+    z = lp.Ax(xbar)
+    w = y / sigma + z  # wrong sign of z
+    return xh, sigma * (w - O.proj_negS(w, lp.lc, lp.uc)), xbar, z
+
+
+def m_proj_S_not_negated(v, lc, uc):
+    return np.minimum(np.maximum(v, lc), uc)
+
+
+def m_halpern_printed(zh, z, z0, k, gamma):
+    return (1.0 + gamma) * (k + 1.0) / (k + 2.0) * zh - gamma * z + z0 / (k + 2.0)
+
+
+def m_halpern_swapped(zh, z, z0, k, gamma):
+    return (1.0 / (k + 2.0)) * ((1.0 + gamma) * zh - gamma * z) + ((k + 1.0) / (k + 2.0)) * z0
+
+
+def m_pnorm_sign(dx, dy, adx, omega, eta):
+    return ((omega / eta) * float(np.dot(dx, dx)) + (1.0 / (eta * omega)) * float(np.dot(dy, dy))
+            - 2.0 * float(np.dot(adx, dy)))
+
+
+def m_pnorm_swapped(dx, dy, adx, omega, eta):
+    return ((1.0 / (eta * omega)) * float(np.dot(dx, dx)) + (omega / eta) * float(np.dot(dy, dy))
+            + 2.0 * float(np.dot(adx, dy)))
+
+
+def _kkt_variant(rdual_tau=True, dual_obj_sign=-1.0):
+    def f(lp, x, y, tau, bnorm=None, cnorm=None):
+        if bnorm is None:
+            bnorm = O.finite_bound_norm(lp.lc, lp.uc)
+        if cnorm is None:
+            cnorm = float(np.linalg.norm(lp.c))
+        ax = lp.Ax(x)
+        r_p = float(np.linalg.norm(ax - O.proj_S(ax, lp.lc, lp.uc))) / (1.0 + bnorm)
+        g = lp.c - lp.ATy(y)
+        xt = x - tau * g
+        px = O.proj_X(xt, lp.lv, lp.uv)
+        r_d = float(np.linalg.norm(px - x)) / (tau if rdual_tau else 1.0) / (1.0 + cnorm)
+        s = (px - xt) / tau
+        obj_p = float(np.dot(lp.c, x))
+        obj_d = dual_obj_sign * O.p_fun(-y, lp.lc, lp.uc) + float(np.dot(s, x))
+        r_g = abs(obj_p - obj_d) / (1.0 + max(abs(obj_p), abs(obj_d)))
+        return dict(r_primal=r_p, r_dual=r_d, r_gap=r_g, obj_p=obj_p, obj_d=obj_d)
+    return f
+
+
+def m_pfun_swapped(y, l, u):
+    return _orig_pfun(y, u, l)
+
+
+_orig_pfun = O.p_fun
+
+
+def m_pid_sign(omega, d_x, d_y, e_sum, e_prev, kp, ki, kd):
+    if not (d_x > 0.0 and d_y > 0.0):
+        return omega, e_sum, e_prev
+    e = -math.log(math.sqrt(omega) * d_x / (d_y / math.sqrt(omega)))
+    e_sum = e_sum + e
+    de = 0.0 if e_prev is None else e - e_prev
+    return math.exp(math.log(omega) - (kp * e + ki * e_sum + kd * de)), e_sum, e
+
+
+def m_necessary_strict(r, r_anchor, r_prev, first_check, k, T, bs, bn, ba):
+    if r <= bs * r_anchor:
+        return 1
+    if (not first_check) and r <= bn * r_anchor and r >= r_prev:
+        return 2
+    if k >= ba * T:
+        return 3
+    return 0
+
+
+def m_power_no_sqrt(lp, iters=200, tol=1e-8):
+    return _orig_power(lp, iters, tol) ** 2
+
+
+_orig_power = O.power_sigma_max
+
+
+def m_proj_X_unbounded_above(v, lv, uv):
+    return np.maximum(v, lv)
+
+
+MUTANTS = {
+    "primal step sign of A^T y": ("pdhg_step", m_primal_sign),
+    "dropped reflection 2x+ - x": ("pdhg_step", m_no_reflection),
+    "transposed operand in primal step": ("pdhg_step", m_transposed),
+    "dual step sign of z": ("pdhg_step", m_dual_sign),
+    "dual projection onto S instead of -S": ("proj_negS", m_proj_S_not_negated),
+    "Halpern with the printed grouping": ("halpern", m_halpern_printed),
+    "Halpern weights swapped": ("halpern", m_halpern_swapped),
+    "P-norm cross term sign": ("p_norm_sq", m_pnorm_sign),
+    "P-norm diagonal blocks swapped": ("p_norm_sq", m_pnorm_swapped),
+    "r_dual without the 1/tau": ("kkt", _kkt_variant(rdual_tau=False)),
+    "dual objective sign of p(-y)": ("kkt", _kkt_variant(dual_obj_sign=1.0)),
+    "p() with l and u swapped": ("p_fun", m_pfun_swapped),
+    "PID error sign": ("pid_omega", m_pid_sign),
+    "necessary decay with >= instead of >": ("restart_decision", m_necessary_strict),
+    "power iteration returns sigma^2": ("power_sigma_max", m_power_no_sqrt),
+    "box projection ignores upper bound": ("proj_X", m_proj_X_unbounded_above),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, monkeypatch):
+    attr, fn = MUTANTS[name]
+    monkeypatch.setattr(O, attr, fn)
+    caught = None
+    for check in ALL_CHECKS:  # cheapest first; one failing pin is enough
+        try:
+            check()
+        except Exception as e:  # AssertionError, or a shape error from a wrong operand
+            caught = (getattr(check, "__name__", "check"), type(e).__name__)
+            break
+    assert caught, f"no pin caught the planted mistake: {name}"
