@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark of the single-GPU PDHG hot path (one JSON line on stdout).
+
+Workload: the power-law LP (n = 4,000,000 variables, m = 2,000,000 rows, ~40M nonzeros,
+Pareto row lengths capped at 100k, seed 1), FP64.  One step = one body of the solver's CUDA
+graph: 64 fused PDHG iterations (primal kernel + dual kernel each) and one check (KKT,
+fixed-point residual, restart, PID).  ``value`` is PDHG iterations per second with the LP
+resident in HBM; ``e2e`` is the same metric through the C ABI with host buffers (pinned):
+each step uploads the start point, runs 64 iterations from it and reads the solution back.
+
+``--impl reference`` times the CPU oracle on the same workload and metric (one PDHG
+iteration per step, on the host cores).  With torchrun (N > 1) every rank solves its own
+copy (replicas, no collective on the data path); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-8 rel. KKT & PDHG iters/s; SpMV HBM GB/s vs peak; plain vs chosen form"
+WORKLOAD = "powerlaw LP n=4,000,000 m=2,000,000 nnz~40M (Pareto-1.5 rows capped 100k, seed 1), FP64"
+K_CHECK = 64
+FP64_FMA_PER_CLK_SM = 2  # GB300 FP64 issue rate (measured: 1.90 FMA/clk/SM)
+N_SM = 152
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="powerlaw", choices=["powerlaw", "powerlaw_quarter", "small"])
+    p.add_argument("--e2e-steps", type=int, default=20)
+    p.add_argument("--tol-runs", default="small", choices=["none", "small", "all"],
+                   help="time-to-tolerance runs: small LP only (default), both LPs, or none")
+    p.add_argument("--cpu-sample-iters", type=int, default=10)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--host-loop", action="store_true",
+                   help="launch the iteration kernels from a host loop instead of the CUDA graph "
+                        "(same kernels; for profilers that do not descend into graph loops)")
+    return p.parse_args()
+
+
+def make_lp(workload):
+    import lpgen
+
+    if workload == "powerlaw":
+        return lpgen.powerlaw_lp(1)
+    if workload == "powerlaw_quarter":  # same recipe at 1/4 size, for profiler captures
+        return lpgen.scaled_powerlaw_lp(1, 0.25)
+    return lpgen.small_random_lp(0)
+
+
+def workload_name(workload):
+    if workload == "powerlaw":
+        return WORKLOAD
+    if workload == "powerlaw_quarter":
+        return "powerlaw LP at 1/4 size: n=1,000,000 m=500,000 nnz~10M (cap 50k, seed 1), FP64"
+    return "small random LP n=2,000 m=1,000 (600 '=', 400 '<='), 16,000 nnz, seed 0, FP64"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "internal.h"):
+        with open(os.path.join(ROOT, "paper_2601_07628_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic_powerlaw_4Mx2M.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    kv = {}
+    for ln in lines:
+        if "=" in ln and not ln.startswith("#"):
+            k, v = ln.split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    v = kv.get(f"{kernel}_dram_bytes_per_launch")
+    return float(v) if v else None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = sorted(float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit())
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4)
+                          if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx[0] if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline_subprocess(workload, iters):
+    """Time the CPU oracle on a bounded sample (``iters`` PDHG iterations of the same LP),
+    single-threaded, in a spawned process (no fork after CUDA init)."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+import bench
+from oracle import pdhg as O
+lp = bench.make_lp({workload!r})
+o = O.OracleLP.from_lpgen(lp)
+eta = 1.0 / float(np.linalg.norm(lp.val))
+st = O.solve(o, eps=0.0, max_iter=1, params=dict(eta=eta)).state
+t0 = time.perf_counter()
+r = O.solve(o, eps=0.0, max_iter=1 + {iters}, params=dict(eta=eta), state=st)
+dt = time.perf_counter() - t0
+print(json.dumps(dict(iters={iters}, seconds=dt)))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=1800)
+    if out.returncode != 0:
+        return {"value": None, "unit": "iter/s", "cores": 1, "kind": "oracle",
+                "sample": "failed: " + out.stderr.strip().splitlines()[-1] if out.stderr else "failed"}
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": d["iters"] / d["seconds"], "unit": "iter/s", "cores": 1, "kind": "oracle",
+            "sample": f"{d['iters']} oracle PDHG iterations (no check among them) of the same LP "
+                      f"in {d['seconds']:.1f} s, 1 thread (scipy CSR products, numpy)"}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if os.environ.get("BENCH_GLOO") is None else "gloo")
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    """The CPU oracle on the same workload and metric: one PDHG iteration per step."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    from oracle import pdhg as O
+
+    lp = make_lp(args.workload)
+    o = O.OracleLP.from_lpgen(lp)
+    eta = 1.0 / float(np.linalg.norm(lp.val))
+    params = dict(eta=eta)
+    st = O.solve(o, eps=0.0, max_iter=0, params=params).state
+    T = 0
+    for _ in range(args.warmup):
+        T += 1
+        st = O.solve(o, eps=0.0, max_iter=T, params=params, state=st).state
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        T += 1
+        st = O.solve(o, eps=0.0, max_iter=T, params=params, state=st).state
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", "0") or 0) or 1
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iter/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(args.workload),
+                       "step": "1 PDHG iteration of the CPU oracle (numpy/scipy FP64)",
+                       "parallelism": "host"},
+            "cpu_baseline": {"value": v, "unit": "iter/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} oracle PDHG iterations after {args.warmup} warm-up"},
+            "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_to_tol(Solver, lp, tol, max_iter, stream):
+    import torch
+
+    s = Solver(torch.cuda.current_device())
+    s.set_stream(stream)
+    s.load(lp)
+    s.solve(tol, 64)  # power iteration and graph build outside the timed solve
+    t0 = time.perf_counter()
+    st = s.solve(tol, max_iter)
+    dt = time.perf_counter() - t0
+    k = s.kkt()
+    s.close()
+    return {"tol": tol, "status": st, "seconds": dt, "iterations": k["iterations"],
+            "restarts": k["restarts"], "rel_kkt": max(k["r_primal"], k["r_dual"], k["r_gap"])}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import numpy as np
+    import torch
+
+    from paper_2601_07628_gb300 import build
+    from paper_2601_07628_gb300.costmodel import kernel_bytes
+    from paper_2601_07628_gb300.dpdlp import Solver
+
+    if rank == 0:
+        build()
+    if world > 1:
+        torch.distributed.barrier()
+    build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream().cuda_stream
+    dev = torch.cuda.current_device()
+
+    lp = make_lp(args.workload)
+    s = Solver(dev)
+    s.set_stream(stream)
+    s.load(lp)
+    info = s.info()
+    s.set_param("resume", 1)
+    if args.host_loop:
+        s.set_param("use_graph", 0)
+    T = 0
+    for _ in range(max(args.warmup, 3)):  # the first step also runs the power iteration
+        T += K_CHECK
+        s.solve(0.0, T)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        T += K_CHECK
+        s.solve(0.0, T)
+    ev1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    iters_all = args.steps * K_CHECK * world
+    value = iters_all / (ms / 1e3)
+
+    # ---- dominant kernel: average launch time with CUDA events on the solver's stream
+    kb = kernel_bytes(lp.n, lp.m, lp.nnz)
+    kt = {k: s.time_kernel(k, 50) for k in ("primal", "dual")}
+    dom = max(kt, key=kt.get)
+    peak, peak_kind = peaks()
+    ach = kb[dom] / (kt[dom] * 1e-3) / 1e9
+    # FP64 issue slots per launch: one FMA per nonzero plus the per-column / per-row updates
+    fp64_ops = {"primal": lp.nnz + 8 * lp.n, "dual": lp.nnz + 9 * lp.m}
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    fp64_peak = N_SM * FP64_FMA_PER_CLK_SM * sm_mhz * 1e6 / 1e9  # G ops / s
+    traffic = recorded_traffic(dom)
+    roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": traffic, "kernel": dom, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6800 GB/s",
+                "bytes_per_launch": kb[dom], "ms_per_launch": kt[dom]}
+    kernels = {k: {"ms": kt[k], "GB/s": kb[k] / (kt[k] * 1e-3) / 1e9,
+                   "hbm_frac": kb[k] / (kt[k] * 1e-3) / 1e9 / peak,
+                   "fp64_Gops": fp64_ops[k] / (kt[k] * 1e-3) / 1e9,
+                   "fp64_frac": fp64_ops[k] / (kt[k] * 1e-3) / 1e9 / fp64_peak}
+               for k in kt}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    xh = torch.empty(lp.n, dtype=torch.float64, pin_memory=True).numpy()
+    yh = torch.empty(lp.m, dtype=torch.float64, pin_memory=True).numpy()
+    xs, ys = s.solution()
+    xh[:], yh[:] = xs, ys
+    s.set_param("resume", 0)
+    s.set_start(xh, yh)
+    s.solve(0.0, K_CHECK)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.e2e_steps):
+        s.set_start(xh, yh)
+        s.solve(0.0, K_CHECK)
+        s.solution(xh, yh)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e = {"value": args.e2e_steps * K_CHECK * world / (e2e_ms / 1e3), "unit": "iter/s",
+           "h2d_bytes_per_step": 8 * (lp.n + lp.m), "d2h_bytes_per_step": 8 * (lp.n + lp.m),
+           "step": "set_start(host x,y) + 64 iterations from it + get_solution(host)"}
+    s.close()
+
+    # ---- time to tolerance
+    ttt = {}
+    if args.tol_runs != "none" and rank == 0:
+        import lpgen
+
+        small = lpgen.small_random_lp(0)
+        ttt["small_lp_1e-4"] = time_to_tol(Solver, small, 1e-4, 1_000_000, stream)
+        ttt["small_lp_1e-8"] = time_to_tol(Solver, small, 1e-8, 1_000_000, stream)
+        if args.tol_runs == "all":
+            ttt["powerlaw_1e-4"] = time_to_tol(Solver, lp, 1e-4, 400_000, stream)
+            ttt["powerlaw_1e-8"] = time_to_tol(Solver, lp, 1e-8, 400_000, stream)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_subprocess(args.workload, args.cpu_sample_iters)
+
+    if rank != 0:
+        return
+    launches_per_step = 2 * K_CHECK + 6
+    line = {
+        "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.workload),
+                   "step": f"{K_CHECK} fused PDHG iterations + 1 KKT/restart/PID check (one CUDA-graph body)",
+                   "l2": "inputs larger than L2 (matrix CSR+CSC ~1 GB)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "block_permute": 1, "tiles_csr": info["tiles_csr"], "tiles_csc": info["tiles_csc"]},
+        "clocks": clk, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+        "roofline": roofline, "kernels": kernels,
+        "fp64_peak_Gops": fp64_peak, "time_to_tol": ttt, "preprocess_ms": info["preprocess_ms"],
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

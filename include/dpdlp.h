@@ -1,0 +1,209 @@
+/*
+ * dpdlp.h -- C ABI of libdpdlp, a single-GPU (GB300, sm_103a) restarted reflected-Halpern
+ * PDHG solver for sparse linear programs.
+ *
+ * The method is the PDLP iteration of "D-PDLP: Scaling PDLP to Distributed Multi-GPU
+ * Systems" (arXiv 2601.07628), run on one device:
+ *   - problem (Section 2.1, Eq. prob:primal):  min c^T x  s.t.  lc <= A x <= uc,
+ *     lv <= x <= uv, with A sparse (m rows, n columns);
+ *   - PDHG step (Section 2.2; Algorithm 1, steps 1-2):
+ *       x^ = proj_X(x - tau (c - A^T y)),  z = A (2 x^ - x),
+ *       y^ = y - sigma z - sigma proj_{-S}(y / sigma - z),   tau = eta/omega, sigma = eta*omega;
+ *   - reflected Halpern step (Appendix B.1; Algorithm 1, step 3);
+ *   - every check_every iterations: relative KKT error (Appendix B.4), fixed-point residual
+ *     in the P-norm (Appendix B, D.2.1), adaptive restart (Appendix B.2) and the PID primal
+ *     weight (Appendix B.3).
+ * The paper's 2D device grid and its AllReduces are not used: everything runs on one GPU;
+ * its block-wise random permutation (Section 4.2) and nonzero-aware partitioning
+ * (Section 4.3) are used to balance nonzeros across thread blocks.
+ *
+ * Conventions for every entry point:
+ *   - Return value: >= 0 on success (dpdlp_solve returns a solve status), < 0 an error code
+ *     (DPDLP_ERR_*).  After an error, dpdlp_last_error(h) describes it.
+ *   - Arrays are plain C arrays in the caller's index order (the library permutes
+ *     internally and undoes it on output).  Sizes: n = number of variables (columns of A),
+ *     m = number of rows.
+ *   - Pointer location: dpdlp_load_lp and dpdlp_set_row_bounds take HOST pointers.  Vector
+ *     arguments of dpdlp_set_start, dpdlp_get_solution, dpdlp_get_state, dpdlp_set_state,
+ *     dpdlp_apply_A and dpdlp_apply_AT are HOST pointers by default and DEVICE pointers
+ *     (on the handle's device) after dpdlp_set_param(h, "ptr_mode_device", 1).
+ *   - Ownership: inputs are copied; the caller keeps and frees its buffers.  Outputs are
+ *     written into caller-owned buffers of the stated length.  The handle owns all device
+ *     memory it allocates and frees it in dpdlp_destroy.
+ *   - Concurrency: handles are independent; one handle must not be used from two host
+ *     threads at once.  All device work of a handle is ordered on its stream.
+ */
+#ifndef DPDLP_H
+#define DPDLP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Solve status (non-negative return of dpdlp_solve). */
+#define DPDLP_CONVERGED 0     /* max(r_primal, r_dual, r_gap) <= tol at a check */
+#define DPDLP_MAX_ITER 1      /* iteration limit reached without convergence */
+#define DPDLP_NUMERICAL 2     /* a non-finite iterate or residual was detected at a check */
+
+/* Error codes (negative returns). */
+#define DPDLP_ERR_INVALID (-1)    /* invalid argument: bad CSR, lv > uv, lc > uc, NaN input... */
+#define DPDLP_ERR_OOM (-2)        /* device or host allocation failed */
+#define DPDLP_ERR_CUDA (-3)       /* a CUDA runtime call failed */
+#define DPDLP_ERR_NOT_LOADED (-4) /* no LP loaded on this handle */
+#define DPDLP_ERR_TIMEOUT (-5)    /* a bounded device wait gave up */
+
+typedef struct dpdlp dpdlp_t; /* opaque solver handle, one LP per handle */
+
+/* Convergence report of the last solve (Appendix B.4 quantities at the final check). */
+typedef struct dpdlp_kkt {
+  double r_primal;   /* ||Ax - proj_S(Ax)|| / (1 + ||[lc,uc]||_finite) */
+  double r_dual;     /* ||proj_X(x - tau(c - A^T y)) - x|| / tau / (1 + ||c||) */
+  double r_gap;      /* |obj_p - obj_d| / (1 + max(|obj_p|, |obj_d|)) */
+  double obj_p;      /* c^T x */
+  double obj_d;      /* -p(-y; lc, uc) + s^T x */
+  double r_fp;       /* fixed-point residual ||z - PDHG(z)||_P at the final check */
+  double omega;      /* primal weight */
+  double eta;        /* step size */
+  double tau, sigma; /* eta / omega, eta * omega */
+  int64_t iterations;
+  int64_t restarts;
+  int64_t checks;
+  int32_t status;    /* DPDLP_CONVERGED / DPDLP_MAX_ITER / DPDLP_NUMERICAL, -1 before a solve */
+  int32_t spmv_mode; /* 0: FP64 matrix values */
+} dpdlp_kkt_t;
+
+/* One record per check, kept in a device ring of the last trace_capacity checks. */
+typedef struct dpdlp_trace {
+  int64_t T;        /* total iterations at the check */
+  int64_t k;        /* iterations since the last restart, after this check's iteration */
+  double r_primal, r_dual, r_gap, obj_p, obj_d;
+  double r_fp;      /* fixed-point residual */
+  double omega;     /* primal weight used by this check's iteration */
+  int32_t restart;  /* 0 none, 1 sufficient decay, 2 necessary decay, 3 artificial */
+  int32_t pad;
+} dpdlp_trace_t;
+
+/* Scalar part of a checkpoint (the vector part is x, y, x0, y0). */
+typedef struct dpdlp_scalar_state {
+  int64_t T, k, restarts, checks;
+  double eta, omega;
+  double r_anchor, r_prev; /* restart references; has_anchor = 0 means "unset" */
+  double e_sum, e_prev;    /* PID integral and last error; has_e_prev = 0 means "unset" */
+  int32_t has_anchor, has_e_prev;
+} dpdlp_scalar_state_t;
+
+/* Sizes and layout facts of the loaded LP. */
+typedef struct dpdlp_info {
+  int32_t n, m;
+  int64_t nnz;
+  int64_t nnz_padded_csr, nnz_padded_csc;
+  int32_t tiles_csr, tiles_csc;
+  int32_t long_rows, long_cols;
+  int64_t device_bytes;
+  double preprocess_ms;
+} dpdlp_info_t;
+
+/* Create a handle bound to CUDA device `device`.  Work goes to a stream the handle creates
+ * unless dpdlp_set_stream supplies one.  Errors: DPDLP_ERR_INVALID (bad device),
+ * DPDLP_ERR_CUDA, DPDLP_ERR_OOM. */
+int dpdlp_create(dpdlp_t** h, int device);
+
+/* Free the handle and every device buffer it owns.  Safe on NULL. */
+void dpdlp_destroy(dpdlp_t* h);
+
+/* Description of the last error on this handle ("" if none); valid until the next call. */
+const char* dpdlp_last_error(const dpdlp_t* h);
+
+/* Use `cuda_stream` (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream) for
+ * all later work of the handle; NULL restores the handle's own stream.  The caller keeps
+ * the stream alive while the handle uses it. */
+int dpdlp_set_stream(dpdlp_t* h, void* cuda_stream);
+
+/* Load an LP (Section 2.1, Eq. prob:primal) from HOST arrays.
+ *   c[n]                objective
+ *   row_ptr[m+1]        CSR row pointers, row_ptr[0] = 0, non-decreasing, row_ptr[m] = nnz
+ *   col_idx[nnz]        CSR column indices in [0, n)
+ *   val[nnz]            CSR values (finite)
+ *   b[m], ctype[m]      row type 0: lc = uc = b ('='), 1: lc = -inf, uc = b ('<='),
+ *                       2: lc = b, uc = +inf ('>=').  Both may be NULL (rows free until
+ *                       dpdlp_set_row_bounds).
+ *   lv[n], uv[n]        variable bounds, -INFINITY / +INFINITY allowed, lv <= uv
+ * Validates the input (DPDLP_ERR_INVALID on failure), then on the host builds the CSC copy
+ * of A, the optional block-wise random permutation (Section 4.2) and the nonzero-balanced
+ * tiles (Section 4.3), and copies everything to the device.  Replaces any LP loaded before
+ * and resets the solver state. */
+int dpdlp_load_lp(dpdlp_t* h, int32_t n, int32_t m, const double* c, const int64_t* row_ptr,
+                  const int32_t* col_idx, const double* val, const double* b,
+                  const double* lv, const double* uv, const int8_t* ctype);
+
+/* Replace the row bounds with general ranges lc[m] <= A x <= uc[m] (HOST arrays, +-inf
+ * allowed, lc <= uc, no NaN).  Resets the solver state. */
+int dpdlp_set_row_bounds(dpdlp_t* h, const double* lc, const double* uc);
+
+/* Set a named parameter.  Keys (default):
+ *   eta (0 = power iteration, 0.998 / sigma_max(A)), eta_safety (0.998), power_iters (200),
+ *   power_tol (1e-8), omega0 (0 = ||c|| / ||b_finite||), gamma (1.0), halpern (1),
+ *   check_every (64, 1..1024), restart (1), beta_sufficient (0.2), beta_necessary (0.8),
+ *   beta_artificial (0.36), pid (1), pid_kp (0.99), pid_ki (0.01), pid_kd (0.0),
+ *   block_permute (1), perm_block (256), perm_seed (1), use_graph (1),
+ *   ptr_mode_device (0), resume (0: each solve starts from the start point; 1: continue
+ *   from the current state), trace_capacity (4096).
+ * Load-time keys (block_permute, perm_block, perm_seed) take effect at the next
+ * dpdlp_load_lp.  Unknown key or out-of-range value: DPDLP_ERR_INVALID. */
+int dpdlp_set_param(dpdlp_t* h, const char* key, double v);
+
+/* Read a parameter's current value. */
+int dpdlp_get_param(const dpdlp_t* h, const char* key, double* v);
+
+/* Warm start: x0[n], y0[m] (host or device per ptr_mode_device; either may be NULL for the
+ * default x = proj_X(0), y = 0).  Used by the next non-resumed solve. */
+int dpdlp_set_start(dpdlp_t* h, const double* x0, const double* y0);
+
+/* Run PDHG until max(r_primal, r_dual, r_gap) <= tol at a check, or until the total
+ * iteration count reaches max_iter.  The loop runs on the device (one CUDA graph with a
+ * conditional while node); the host waits once at the end.  Returns DPDLP_CONVERGED,
+ * DPDLP_MAX_ITER or DPDLP_NUMERICAL, or an error code. */
+int dpdlp_solve(dpdlp_t* h, double tol, int64_t max_iter);
+
+/* The returned point: (x^, y^), the PDHG output at the final check, x[n] and y[m]
+ * (either may be NULL). */
+int dpdlp_get_solution(dpdlp_t* h, double* x, double* y);
+
+/* Residuals and counters of the last solve (HOST struct). */
+int dpdlp_get_kkt(dpdlp_t* h, dpdlp_kkt_t* out);
+
+/* Copy up to `cap` trace records, oldest first, into HOST `out`; *count receives the number
+ * copied. */
+int dpdlp_get_trace(dpdlp_t* h, dpdlp_trace_t* out, int32_t cap, int32_t* count);
+
+/* Checkpoint: the current iterate (x[n], y[m]), anchor (x0[n], y0[m]) and scalars.  After
+ * dpdlp_set_state the next dpdlp_solve resumes from it and reproduces the uninterrupted
+ * solve.  Vector pointers may be NULL to skip them (get) -- set needs all four. */
+int dpdlp_get_state(dpdlp_t* h, double* x, double* y, double* x0, double* y0,
+                    dpdlp_scalar_state_t* s);
+int dpdlp_set_state(dpdlp_t* h, const double* x, const double* y, const double* x0,
+                    const double* y0, const dpdlp_scalar_state_t* s);
+
+/* Parity mode: restart decisions of checks 0..count-1 (0 none, 1..3 restart kinds) are
+ * taken from `kinds` (HOST) instead of the restart test; count = 0 switches it off. */
+int dpdlp_set_schedule(dpdlp_t* h, const int8_t* kinds, int32_t count);
+
+/* Operator application with the solver's SpMV kernels: out[m] = A x[n], out[n] = A^T y[m]. */
+int dpdlp_apply_A(dpdlp_t* h, const double* x, double* out);
+int dpdlp_apply_AT(dpdlp_t* h, const double* y, double* out);
+
+/* Time `reps` back-to-back launches of one iteration kernel ("primal": fused CSC SpMV +
+ * primal update, "dual": fused CSR SpMV + dual update) on the handle's stream with CUDA
+ * events, on the current state (the state is left as it was).  *avg_ms = mean duration of
+ * one launch.  Needs a solve or dpdlp_set_start beforehand. */
+int dpdlp_time_kernel(dpdlp_t* h, const char* which, int32_t reps, double* avg_ms);
+
+/* Sizes and layout of the loaded LP. */
+int dpdlp_get_info(dpdlp_t* h, dpdlp_info_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DPDLP_H */

@@ -1,0 +1,701 @@
+// sm_103a kernels of the PDHG hot path.
+//
+//  tiled_spmv_kernel  one thread block per tile of a row-major sparse matrix (CSR of A for
+//                     A x, CSR of A^T -- the CSC copy -- for A^T y).  Each thread sums 8
+//                     consecutive nonzeros in stored order with one FMA per nonzero (FP64
+//                     issue slots are scarce on GB300, so no shuffle trees on the common
+//                     path); rows that cross thread boundaries are finished by their owner
+//                     thread from per-thread head partials in shared memory.  The row
+//                     results feed an epilogue:
+//                       PrimalEpi  the primal step of Section 2.2 / Algorithm 1 step 1 and the
+//                                  Halpern step of Appendix B.1 (K-A);
+//                       DualEpi    the dual step of Section 2.2 / Algorithm 1 step 2 and the
+//                                  Halpern step (K-B);
+//                       StoreEpi   plain output (KKT products, power iteration, A x / A^T y).
+//  reduce_*_kernel    per-row / per-column terms of the relative KKT error (Appendix B.4)
+//                     and of the fixed-point residual (Appendix D.2.1), block partials in a
+//                     fixed order (deterministic, no floating-point atomics).
+//  control_kernel     one block: final sums, KKT, restart test (Appendix B.2), PID primal
+//                     weight (Appendix B.3), trace record, next Halpern weights, and the
+//                     CUDA-graph loop condition.
+//  apply_kernel       after a check: restart (anchor and iterate <- PDHG output) or the
+//                     Halpern step of the check iteration.
+#include <cuda_runtime.h>
+
+#include "../../include/dpdlp.h"
+#include "internal.h"
+
+namespace pdhg {
+
+// ---------------------------------------------------------------- small device helpers
+// Clamp written with comparisons so that a NaN input stays NaN (fmin/fmax would drop it
+// and hide a diverged iterate from the non-finite check).
+__device__ __forceinline__ double clampd(double v, double lo, double hi) {
+  return v < lo ? lo : (v > hi ? hi : v);
+}
+
+__device__ __forceinline__ unsigned long long l2_evict_first_policy() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// Matrix values and indices are read once per pass and are larger than L2: stream them
+// with an evict-first L2 policy so the gathered vectors (x_bar, y) stay L2-resident.
+__device__ __forceinline__ double2 ld_stream(const double2* p, unsigned long long pol) {
+  double2 r;
+  asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+      : "=d"(r.x), "=d"(r.y)
+      : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ int4 ld_stream(const int4* p, unsigned long long pol) {
+  int4 r;
+  asm("ld.global.nc.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+      : "l"(p), "l"(pol));
+  return r;
+}
+
+// Deterministic block sum (fixed xor-butterfly inside warps, fixed order across warps).
+// The result is valid in thread 0.  `buf` holds TPB/32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* buf) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) buf[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = l < TPB / 32 ? buf[l] : 0.0;
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------- epilogues
+struct StoreEpi1 {
+  double* out0;
+  __device__ bool begin() { return true; }
+  __device__ void apply(int r, const double* s) { out0[r] = s[0]; }
+};
+struct StoreEpi2 {
+  double *out0, *out1;
+  __device__ bool begin() { return true; }
+  __device__ void apply(int r, const double* s) {
+    out0[r] = s[0];
+    out1[r] = s[1];
+  }
+};
+
+// Per-iteration scalars read from device memory by the fused epilogues.
+struct IterScalars {
+  double step, inv_step, w1, w0, gamma;
+  int check, halpern, gamma_one;
+};
+
+__device__ __forceinline__ bool load_iter(const DevScalars* sc, IterPlan p, bool primal,
+                                          IterScalars& o) {
+  if (p.force_regular) {
+    o.check = 0;
+  } else {
+    const long long T = sc->T_base + p.i;
+    if (T >= sc->max_iter) return false;  // past the iteration limit inside this body
+    o.check = (T + 1 == sc->T_check);
+  }
+  o.step = primal ? sc->tau : sc->sigma;
+  o.inv_step = sc->inv_sigma;
+  o.w1 = sc->w1[p.i];
+  o.w0 = sc->w0[p.i];
+  o.gamma = sc->gamma;
+  o.halpern = sc->halpern;
+  o.gamma_one = (sc->gamma == 1.0);
+  return true;
+}
+
+// Primal step per column j, given s = (A^T y)_j:
+//   x^ = proj_X(x - tau (c - s)),  x_bar = 2 x^ - x,
+//   Halpern: x <- w1 ((1+gamma) x^ - gamma x) + w0 x0   (regular iteration),
+//   check iteration: keep x = x^k, store x^ and dx = x^k - x^.
+struct PrimalEpi {
+  const DevScalars* sc;
+  IterPlan plan;
+  const double *c, *lv, *uv, *x0;
+  double *x, *xbar, *xh, *dx;
+  IterScalars q;
+  __device__ bool begin() { return load_iter(sc, plan, true, q); }
+  __device__ void apply(int j, const double* s) {
+    const double g = c[j] - s[0];
+    const double xj = x[j];
+    const double xhj = clampd(fma(-q.step, g, xj), lv[j], uv[j]);
+    const double xb = fma(2.0, xhj, -xj);
+    xbar[j] = xb;
+    if (q.check) {
+      xh[j] = xhj;
+      dx[j] = xj - xhj;
+    } else if (q.halpern) {
+      const double r = q.gamma_one ? xb : fma(1.0 + q.gamma, xhj, -q.gamma * xj);
+      x[j] = fma(q.w1, r, q.w0 * x0[j]);
+    } else {
+      x[j] = xhj;
+    }
+  }
+};
+
+// Dual step per row i, given z = (A x_bar)_i:
+//   w = y / sigma - z,  y^ = sigma (w - proj_{-S}(w)),  -S_i = [lo_i, hi_i] = [-uc_i, -lc_i],
+//   Halpern on y as for x; check iteration: keep y = y^k, store y^.
+struct DualEpi {
+  const DevScalars* sc;
+  IterPlan plan;
+  const double *lo, *hi, *y0;
+  double *y, *yh;
+  IterScalars q;
+  __device__ bool begin() { return load_iter(sc, plan, false, q); }
+  __device__ void apply(int i, const double* s) {
+    const double yi = y[i];
+    const double w = fma(yi, q.inv_step, -s[0]);
+    const double yhi = q.step * (w - clampd(w, lo[i], hi[i]));
+    if (q.check) {
+      yh[i] = yhi;
+    } else if (q.halpern) {
+      const double r = q.gamma_one ? fma(2.0, yhi, -yi) : fma(1.0 + q.gamma, yhi, -q.gamma * yi);
+      y[i] = fma(q.w1, r, q.w0 * y0[i]);
+    } else {
+      y[i] = yhi;
+    }
+  }
+};
+
+// ---------------------------------------------------------------- tiled SpMV
+template <int NV>
+struct GatherVecs {
+  const double* x[NV];
+};
+
+template <int NV, class Epi>
+__global__ void __launch_bounds__(TPB) tiled_spmv_kernel(DevTiled M, GatherVecs<NV> g, Epi epi_in) {
+  __shared__ int srp[TPB + 1];
+  __shared__ double rsum[NV][TPB];
+  __shared__ double head[NV][TPB];
+  __shared__ double red[TPB / 32];
+
+  Epi epi = epi_in;
+  if (!epi.begin()) return;  // uniform over the launch
+
+  const Tile t = M.tiles[blockIdx.x];
+  const int tid = threadIdx.x;
+  const int base = t.e0 + tid * IPT;  // IPT-aligned: 16-byte vector loads below
+  const int nvalid = min(IPT, max(0, t.e1 - base));
+
+  const unsigned long long pol = l2_evict_first_policy();
+  double v[IPT];
+  int ci[IPT];
+  {
+    const double2* vp = reinterpret_cast<const double2*>(M.val + base);
+    const int4* ip = reinterpret_cast<const int4*>(M.idx + base);
+#pragma unroll
+    for (int q = 0; q < IPT / 2; ++q) {
+      const double2 d = ld_stream(vp + q, pol);
+      v[2 * q] = d.x;
+      v[2 * q + 1] = d.y;
+    }
+#pragma unroll
+    for (int q = 0; q < IPT / 4; ++q) {
+      const int4 d = ld_stream(ip + q, pol);
+      ci[4 * q] = d.x;
+      ci[4 * q + 1] = d.y;
+      ci[4 * q + 2] = d.z;
+      ci[4 * q + 3] = d.w;
+    }
+  }
+  double xv[NV][IPT];
+#pragma unroll
+  for (int j = 0; j < IPT; ++j) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) xv[k][j] = (j < nvalid) ? __ldg(g.x[k] + ci[j]) : 0.0;
+  }
+
+  if (t.slot == -1) {
+    // ---- shared tile: whole rows [r0, r1)
+    const int nrows = t.r1 - t.r0;
+    for (int r = tid; r <= nrows; r += TPB) srp[r] = M.ptr[t.r0 + r];
+    if (tid < nrows) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) rsum[k][tid] = 0.0;
+    }
+    __syncthreads();
+    int open_row = -1;  // a row this thread started that continues past its items
+    if (nvalid > 0) {
+      int lo = 0, hi = nrows - 1;  // the row holding item `base`: last r with srp[r] <= base
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (srp[mid] <= base) lo = mid; else hi = mid - 1;
+      }
+      int r = lo;
+      bool owner = srp[r] >= base;
+      int rend = srp[r + 1];
+      double acc[NV];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        if (j < nvalid) {
+          const int e = base + j;
+          while (e >= rend) {  // row r ends before item e
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+              if (owner) rsum[k][r] = acc[k]; else head[k][tid] = acc[k];
+              acc[k] = 0.0;
+            }
+            ++r;
+            rend = srp[r + 1];
+            owner = true;
+          }
+#pragma unroll
+          for (int k = 0; k < NV; ++k) acc[k] = fma(v[j], xv[k][j], acc[k]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        if (owner) rsum[k][r] = acc[k]; else head[k][tid] = acc[k];
+      }
+      if (owner && rend > base + nvalid) open_row = r;
+    }
+    __syncthreads();
+    if (open_row >= 0) {  // add the head partials of the following threads, in order
+      const int t_end = (srp[open_row + 1] - 1 - t.e0) / IPT;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        double s = rsum[k][open_row];
+        for (int tt = tid + 1; tt <= t_end; ++tt) s += head[k][tt];
+        rsum[k][open_row] = s;
+      }
+    }
+    __syncthreads();
+    if (tid < nrows) {
+      double s[NV];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) s[k] = rsum[k][tid];
+      epi.apply(t.r0 + tid, s);
+    }
+    return;
+  }
+
+  // ---- a tile of one long row: block sum, then either finish the row (single chunk) or
+  // publish the chunk sum; the last chunk to arrive adds all chunks in chunk order.
+  double tot[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double a = 0.0;
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) a = fma(v[j], xv[k][j], a);  // zeros beyond nvalid
+    tot[k] = block_sum(a, red);
+  }
+  if (tid != 0) return;
+  if (t.slot == -2) {
+    epi.apply(t.r0, tot);
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) M.lr_partial[k * M.long_chunks + t.slot + t.chunk] = tot[k];
+  __threadfence();
+  const unsigned prev = atomicAdd(&M.lr_count[t.lrow], 1u);
+  if (prev == (unsigned)(t.nchunks - 1)) {
+    __threadfence();
+    double s[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double a = 0.0;
+      for (int c = 0; c < t.nchunks; ++c) a += __ldcg(&M.lr_partial[k * M.long_chunks + t.slot + c]);
+      s[k] = a;
+    }
+    M.lr_count[t.lrow] = 0;  // ready for the next launch
+    epi.apply(t.r0, s);
+  }
+}
+
+template <int NV, class Epi>
+static cudaError_t launch_tiled(const DevTiled& M, GatherVecs<NV> g, Epi epi, cudaStream_t s) {
+  if (M.ntiles == 0) return cudaSuccess;
+  tiled_spmv_kernel<NV, Epi><<<M.ntiles, TPB, 0, s>>>(M, g, epi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_primal(const DevTiled& csc, const DevVecs& v, const DevScalars* sc,
+                          IterPlan p, cudaStream_t s) {
+  PrimalEpi e{sc, p, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, {}};
+  if (csc.ntiles == 0) return cudaSuccess;
+  GatherVecs<1> g{{v.y}};
+  return launch_tiled<1>(csc, g, e, s);
+}
+
+cudaError_t launch_dual(const DevTiled& csr, const DevVecs& v, const DevScalars* sc,
+                        IterPlan p, cudaStream_t s) {
+  DualEpi e{sc, p, v.lo, v.hi, v.y0, v.y, v.yh, {}};
+  GatherVecs<1> g{{v.xbar}};
+  return launch_tiled<1>(csr, g, e, s);
+}
+
+cudaError_t launch_spmv(const DevTiled& M, const double* x0, const double* x1, double* out0,
+                        double* out1, cudaStream_t s) {
+  if (x1) {
+    GatherVecs<2> g{{x0, x1}};
+    return launch_tiled<2>(M, g, StoreEpi2{out0, out1}, s);
+  }
+  GatherVecs<1> g{{x0}};
+  return launch_tiled<1>(M, g, StoreEpi1{out0}, s);
+}
+
+// ---------------------------------------------------------------- check reductions
+int reduction_grid(int len) {
+  const int g = (len + 4095) / 4096;
+  return g < 1 ? 1 : (g > 1024 ? 1024 : g);
+}
+
+// Row terms at (x^, y^): [0] (Ax^ - proj_S(Ax^))^2, [1] the p(-y^; lc, uc) term,
+// [2] (y^k - y^)^2, [3] (A dx)_i (y^k - y^)_i, [4] (y^ - y0)^2.
+__global__ void __launch_bounds__(TPB) reduce_rows_kernel(DevVecs v, int m) {
+  __shared__ double buf[TPB / 32];
+  double q[NRED] = {0, 0, 0, 0, 0};
+  for (int i = blockIdx.x * TPB + threadIdx.x; i < m; i += gridDim.x * TPB) {
+    const double lc = -v.hi[i], uc = -v.lo[i];
+    const double ax = v.axh[i];
+    const double d = ax - clampd(ax, lc, uc);
+    q[0] = fma(d, d, q[0]);
+    const double yh = v.yh[i];
+    double p = 0.0;  // u (-y)^+ - l (-y)^-, a term vanishing when its multiplier is 0
+    if (yh < 0.0) p = uc * (-yh);
+    if (yh > 0.0) p = -(lc * yh);
+    q[1] += p;
+    const double dy = v.y[i] - yh;
+    q[2] = fma(dy, dy, q[2]);
+    q[3] = fma(v.adx[i], dy, q[3]);
+    const double ya = yh - v.y0[i];
+    q[4] = fma(ya, ya, q[4]);
+  }
+#pragma unroll
+  for (int k = 0; k < NRED; ++k) {
+    const double s = block_sum(q[k], buf);
+    if (threadIdx.x == 0) v.red_rows[blockIdx.x * NRED + k] = s;
+  }
+}
+
+// Column terms at (x^, y^) with the current tau: g = c - A^T y^, xt = x^ - tau g,
+// px = proj_X(xt): [0] (px - x^)^2, [1] (px - xt) x^ (= tau s_j x^_j), [2] c x^,
+// [3] dx^2, [4] (x^ - x0)^2.
+__global__ void __launch_bounds__(TPB) reduce_cols_kernel(DevVecs v, int n, const DevScalars* sc) {
+  __shared__ double buf[TPB / 32];
+  const double tau = sc->tau;
+  double q[NRED] = {0, 0, 0, 0, 0};
+  for (int j = blockIdx.x * TPB + threadIdx.x; j < n; j += gridDim.x * TPB) {
+    const double xhj = v.xh[j];
+    const double g = v.c[j] - v.aty[j];
+    const double xt = fma(-tau, g, xhj);
+    const double px = clampd(xt, v.lv[j], v.uv[j]);
+    const double d = px - xhj;
+    q[0] = fma(d, d, q[0]);
+    q[1] = fma(px - xt, xhj, q[1]);
+    q[2] = fma(v.c[j], xhj, q[2]);
+    const double dx = v.dx[j];
+    q[3] = fma(dx, dx, q[3]);
+    const double xa = xhj - v.x0[j];
+    q[4] = fma(xa, xa, q[4]);
+  }
+#pragma unroll
+  for (int k = 0; k < NRED; ++k) {
+    const double s = block_sum(q[k], buf);
+    if (threadIdx.x == 0) v.red_cols[blockIdx.x * NRED + k] = s;
+  }
+}
+
+// Restart criteria of Appendix B.2 (0 none, 1 sufficient, 2 necessary, 3 artificial).
+__device__ int restart_kind(double r, double r_anchor, double r_prev, bool first, long long k,
+                            long long T, const DevScalars& s) {
+  if (r <= s.beta_s * r_anchor) return 1;
+  if (!first && r <= s.beta_n * r_anchor && r > r_prev) return 2;
+  if ((double)k >= s.beta_a * (double)T) return 3;
+  return 0;
+}
+
+__global__ void __launch_bounds__(TPB) control_kernel(DevVecs v, DevScalars* sc,
+                                                      unsigned long long cond, int use_cond) {
+  __shared__ double buf[TPB / 32];
+  __shared__ double S[2][NRED];
+  __shared__ long long kb_next;
+  for (int k = 0; k < NRED; ++k) {
+    double a = 0.0;
+    for (int gi = threadIdx.x; gi < v.g_rows; gi += TPB) a += v.red_rows[gi * NRED + k];
+    a = block_sum(a, buf);
+    double b = 0.0;
+    for (int gi = threadIdx.x; gi < v.g_cols; gi += TPB) b += v.red_cols[gi * NRED + k];
+    b = block_sum(b, buf);
+    if (threadIdx.x == 0) {
+      S[0][k] = a;
+      S[1][k] = b;
+    }
+  }
+  if (threadIdx.x == 0) {
+    DevScalars& s = *sc;
+    const double tau = s.tau, omega = s.omega, eta = s.eta;
+    const double* R = S[0];
+    const double* C = S[1];
+    const double r_p = sqrt(R[0]) / (1.0 + s.bnorm);
+    const double r_d = sqrt(C[0]) / tau / (1.0 + s.cnorm);
+    const double obj_p = C[2];
+    const double obj_d = -R[1] + C[1] / tau;
+    const double r_g = fabs(obj_p - obj_d) / (1.0 + fmax(fabs(obj_p), fabs(obj_d)));
+    const double rsq = (omega / eta) * C[3] + (1.0 / (eta * omega)) * R[2] + 2.0 * R[3];
+    const double r = sqrt(fmax(0.0, rsq));
+    const long long T = s.T_check;
+    const long long k_after = s.k_base + (T - s.T_base);
+    const long long check_idx = s.checks;
+    s.checks += 1;
+    s.r_p = r_p; s.r_d = r_d; s.r_g = r_g; s.obj_p = obj_p; s.obj_d = obj_d; s.r_fp = r;
+    bool finite = isfinite(r) && isfinite(r_p) && isfinite(r_d) && isfinite(r_g);
+    for (int k = 0; k < NRED; ++k) finite = finite && isfinite(R[k]) && isfinite(C[k]);
+    int kind = 0;
+    unsigned go = 0;
+    long long k_next = k_after;
+    s.T_base = T;
+    if (!finite) {
+      s.status = 2;
+      s.apply_mode = 2;
+    } else if (fmax(r_p, fmax(r_d, r_g)) <= s.eps) {
+      s.status = 0;
+      s.apply_mode = 2;
+    } else {
+      const bool first = !s.has_anchor;
+      if (first) {
+        s.r_anchor = r;
+        s.r_prev = r;
+        s.has_anchor = 1;
+      }
+      const int8_t* sched = v.sched;
+      if (s.sched_len > 0) {
+        kind = check_idx < s.sched_len ? (int)sched[check_idx] : 0;
+      } else if (s.restart_enabled) {
+        kind = restart_kind(r, s.r_anchor, s.r_prev, first, k_after, T, s);
+      }
+      s.r_prev = r;
+      if (kind) {
+        s.restarts += 1;
+        if (s.pid_enabled) {
+          const double d_x = sqrt(C[4]), d_y = sqrt(R[4]);
+          if (d_x > 0.0 && d_y > 0.0 && isfinite(d_x) && isfinite(d_y)) {
+            const double so = sqrt(omega);
+            const double e = log((so * d_x) / (d_y / so));
+            s.e_sum += e;
+            const double de = s.has_e_prev ? (e - s.e_prev) : 0.0;
+            const double lw = log(omega) - (s.kp * e + s.ki * s.e_sum + s.kd * de);
+            s.omega = exp(lw);
+            s.e_prev = e;
+            s.has_e_prev = 1;
+          }
+        }
+        s.tau = s.eta / s.omega;
+        s.sigma = s.eta * s.omega;
+        s.inv_sigma = 1.0 / s.sigma;
+        s.has_anchor = 0;
+        k_next = 0;
+        s.apply_mode = 1;
+      } else {
+        const double kc = (double)(k_after - 1);
+        s.w1_check = (kc + 1.0) / (kc + 2.0);
+        s.w0_check = 1.0 / (kc + 2.0);
+        s.apply_mode = 0;
+      }
+      if (T >= s.max_iter) {
+        s.status = 1;
+      } else {
+        s.status = -1;
+        go = 1;
+        s.T_check = T + s.K < s.max_iter ? T + s.K : s.max_iter;
+      }
+    }
+    s.k_base = k_next;
+    kb_next = k_next;
+    if (s.trace_cap > 0) {
+      dpdlp_trace_t* tr = static_cast<dpdlp_trace_t*>(v.trace) + (s.trace_count % s.trace_cap);
+      tr->T = T;
+      tr->k = k_after;
+      tr->r_primal = r_p;
+      tr->r_dual = r_d;
+      tr->r_gap = r_g;
+      tr->obj_p = obj_p;
+      tr->obj_d = obj_d;
+      tr->r_fp = r;
+      tr->omega = omega;
+      tr->restart = kind;
+      tr->pad = 0;
+      s.trace_count += 1;
+    }
+    if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, go);
+  }
+  __syncthreads();
+  const double kb = (double)kb_next;
+  for (int i = threadIdx.x; i < sc->K; i += TPB) {
+    sc->w1[i] = (kb + i + 1.0) / (kb + i + 2.0);
+    sc->w0[i] = 1.0 / (kb + i + 2.0);
+  }
+}
+
+__global__ void __launch_bounds__(TPB) apply_kernel(DevVecs v, const DevScalars* sc) {
+  const int mode = sc->apply_mode;
+  if (mode == 2) return;
+  const int id = blockIdx.x * TPB + threadIdx.x;
+  const double w1 = sc->w1_check, w0 = sc->w0_check, gamma = sc->gamma;
+  const bool g1 = (gamma == 1.0), hal = sc->halpern != 0;
+  if (id < v.n) {
+    const double xh = v.xh[id];
+    if (mode == 1) {
+      v.x[id] = xh;
+      v.x0[id] = xh;
+    } else if (hal) {
+      const double xj = v.x[id];
+      const double r = g1 ? fma(2.0, xh, -xj) : fma(1.0 + gamma, xh, -gamma * xj);
+      v.x[id] = fma(w1, r, w0 * v.x0[id]);
+    } else {
+      v.x[id] = xh;
+    }
+  }
+  if (id < v.m) {
+    const double yh = v.yh[id];
+    if (mode == 1) {
+      v.y[id] = yh;
+      v.y0[id] = yh;
+    } else if (hal) {
+      const double yi = v.y[id];
+      const double r = g1 ? fma(2.0, yh, -yi) : fma(1.0 + gamma, yh, -gamma * yi);
+      v.y[id] = fma(w1, r, w0 * v.y0[id]);
+    } else {
+      v.y[id] = yh;
+    }
+  }
+}
+
+cudaError_t launch_check(const DevTiled& csr, const DevTiled& csc, const DevVecs& v,
+                         DevScalars* sc, unsigned long long cond_handle, int use_cond,
+                         cudaStream_t s) {
+  cudaError_t e;
+  if ((e = launch_spmv(csr, v.xh, v.dx, v.axh, v.adx, s)) != cudaSuccess) return e;
+  if ((e = launch_spmv(csc, v.yh, nullptr, v.aty, nullptr, s)) != cudaSuccess) return e;
+  if (v.m > 0) {
+    reduce_rows_kernel<<<v.g_rows, TPB, 0, s>>>(v, v.m);
+  } else {
+    cudaMemsetAsync(v.red_rows, 0, sizeof(double) * NRED * v.g_rows, s);
+  }
+  if (v.n > 0) {
+    reduce_cols_kernel<<<v.g_cols, TPB, 0, s>>>(v, v.n, sc);
+  } else {
+    cudaMemsetAsync(v.red_cols, 0, sizeof(double) * NRED * v.g_cols, s);
+  }
+  control_kernel<<<1, TPB, 0, s>>>(v, sc, cond_handle, use_cond);
+  const int len = v.n > v.m ? v.n : v.m;
+  if (len > 0) apply_kernel<<<(len + TPB - 1) / TPB, TPB, 0, s>>>(v, sc);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- start point, vectors
+__global__ void fill_start_kernel(DevVecs v, int fresh_x, int fresh_y) {
+  const int id = blockIdx.x * TPB + threadIdx.x;
+  if (id < v.n) {
+    const double x = fresh_x ? clampd(0.0, v.lv[id], v.uv[id]) : v.x[id];  // proj_X(0)
+    v.x[id] = x;
+    v.x0[id] = x;
+    v.xh[id] = x;
+  }
+  if (id < v.m) {
+    const double y = fresh_y ? 0.0 : v.y[id];
+    v.y[id] = y;
+    v.y0[id] = y;
+    v.yh[id] = y;
+  }
+}
+
+cudaError_t launch_fill_start(const DevVecs& v, int fresh_x, int fresh_y, cudaStream_t s) {
+  const int len = v.n > v.m ? v.n : v.m;
+  if (len == 0) return cudaSuccess;
+  fill_start_kernel<<<(len + TPB - 1) / TPB, TPB, 0, s>>>(v, fresh_x, fresh_y);
+  return cudaGetLastError();
+}
+
+__global__ void gather_kernel(const double* in, const int32_t* perm, double* out, int len) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i < len) out[i] = in[perm[i]];
+}
+__global__ void scatter_kernel(const double* in, const int32_t* perm, double* out, int len) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i < len) out[perm[i]] = in[i];
+}
+__global__ void fill_kernel(double* p, double val, int len) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i < len) p[i] = val;
+}
+
+cudaError_t launch_gather(const double* in, const int32_t* perm, double* out, int len,
+                          cudaStream_t s) {
+  if (len == 0) return cudaSuccess;
+  gather_kernel<<<(len + TPB - 1) / TPB, TPB, 0, s>>>(in, perm, out, len);
+  return cudaGetLastError();
+}
+cudaError_t launch_scatter(const double* in, const int32_t* perm, double* out, int len,
+                           cudaStream_t s) {
+  if (len == 0) return cudaSuccess;
+  scatter_kernel<<<(len + TPB - 1) / TPB, TPB, 0, s>>>(in, perm, out, len);
+  return cudaGetLastError();
+}
+cudaError_t launch_fill(double* p, double val, int len, cudaStream_t s) {
+  if (len == 0) return cudaSuccess;
+  fill_kernel<<<(len + TPB - 1) / TPB, TPB, 0, s>>>(p, val, len);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- power iteration
+__global__ void __launch_bounds__(TPB) sumsq_kernel(const double* a, int len, double* part) {
+  __shared__ double buf[TPB / 32];
+  double q = 0.0;
+  for (int i = blockIdx.x * TPB + threadIdx.x; i < len; i += gridDim.x * TPB) q = fma(a[i], a[i], q);
+  q = block_sum(q, buf);
+  if (threadIdx.x == 0) part[blockIdx.x] = q;
+}
+
+__global__ void __launch_bounds__(TPB) power_finish_kernel(const double* pw_part, int gw,
+                                                           const double* pu_part, int gu,
+                                                           double* pw) {
+  __shared__ double buf[TPB / 32];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < gw; i += TPB) a += pw_part[i];
+  a = block_sum(a, buf);
+  double b = 0.0;
+  for (int i = threadIdx.x; i < gu; i += TPB) b += pu_part[i];
+  b = block_sum(b, buf);
+  if (threadIdx.x == 0) {
+    pw[0] = a;
+    pw[1] = sqrt(b);
+    pw[2] = pw[1] > 0.0 ? 1.0 / pw[1] : 0.0;
+  }
+}
+
+__global__ void scale_kernel(double* v, const double* u, const double* pw, int len) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i < len) v[i] = u[i] * pw[2];
+}
+
+cudaError_t launch_power_round(const DevTiled& csr, const DevTiled& csc, const DevVecs& v,
+                               double* vec_v, double* vec_w, double* vec_u, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = launch_spmv(csr, vec_v, nullptr, vec_w, nullptr, s)) != cudaSuccess) return e;
+  if ((e = launch_spmv(csc, vec_w, nullptr, vec_u, nullptr, s)) != cudaSuccess) return e;
+  const int gw = reduction_grid(v.m), gu = reduction_grid(v.n);
+  // partials live in the check-reduction buffers (at least 1024 * NRED doubles each)
+  sumsq_kernel<<<gw, TPB, 0, s>>>(vec_w, v.m, v.red_rows);
+  sumsq_kernel<<<gu, TPB, 0, s>>>(vec_u, v.n, v.red_cols);
+  power_finish_kernel<<<1, TPB, 0, s>>>(v.red_rows, gw, v.red_cols, gu, v.pw);
+  if (v.n > 0) scale_kernel<<<(v.n + TPB - 1) / TPB, TPB, 0, s>>>(vec_v, vec_u, v.pw, v.n);
+  return cudaGetLastError();
+}
+
+}  // namespace pdhg

@@ -1,0 +1,194 @@
+// Host preprocessing of an LP before it goes to the device (runs once per load).
+//
+//  * CSR validation.
+//  * Block-wise random permutation of rows and columns (Section 4.2): contiguous blocks of
+//    B indices (B = 256 by default) are shuffled, the order inside a block is kept.
+//  * The CSC copy of A (the paper keeps both CSR and CSC in device memory so that A^T y
+//    needs no atomics, Appendix E.2), built as the CSR of A^T by a stable counting sort.
+//  * Nonzero-aware partitioning (Section 4.3) at thread-block granularity: consecutive
+//    rows are grouped into tiles of at most TILE_NNZ nonzeros; a row longer than
+//    SOLO_NNZ gets tiles of its own (one per TILE_NNZ chunk).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "internal.h"
+
+namespace pdhg {
+
+// Rows longer than this get their own tile(s) and a block-wide reduction instead of the
+// per-thread walk, which bounds the serial fix-up chain of a shared tile to SOLO_NNZ/IPT.
+constexpr int SOLO_NNZ = 512;
+
+std::string validate_csr(int rows, int cols, const int64_t* ptr, const int32_t* idx,
+                         const double* val) {
+  if (rows < 0 || cols < 0) return "negative dimension";
+  if (!ptr) return "row_ptr is NULL";
+  if (ptr[0] != 0) return "row_ptr[0] != 0";
+  for (int r = 0; r < rows; ++r)
+    if (ptr[r + 1] < ptr[r]) return "row_ptr not non-decreasing at row " + std::to_string(r);
+  const int64_t nnz = ptr[rows];
+  if (nnz > (int64_t)INT32_MAX - 16LL * TILE_NNZ - 8LL * rows)
+    return "too many nonzeros for 32-bit indices";
+  if (nnz > 0 && (!idx || !val)) return "col_idx or val is NULL";
+  for (int64_t e = 0; e < nnz; ++e) {
+    if (idx[e] < 0 || idx[e] >= cols)
+      return "column index out of range at entry " + std::to_string(e);
+    if (!std::isfinite(val[e])) return "non-finite matrix value at entry " + std::to_string(e);
+  }
+  return "";
+}
+
+static inline uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+std::vector<int32_t> block_permutation(int len, int block, uint64_t seed, bool enabled) {
+  std::vector<int32_t> p(len);
+  std::iota(p.begin(), p.end(), 0);
+  if (!enabled || block <= 0 || len <= block) return p;
+  const int nfull = len / block;
+  std::vector<int32_t> order(nfull);
+  std::iota(order.begin(), order.end(), 0);
+  uint64_t s = seed;
+  for (int i = nfull - 1; i > 0; --i) {  // Fisher-Yates over whole blocks
+    const int j = (int)(splitmix64(s) % (uint64_t)(i + 1));
+    std::swap(order[i], order[j]);
+  }
+  for (int b = 0; b < nfull; ++b)
+    for (int t = 0; t < block; ++t) p[(size_t)b * block + t] = order[b] * block + t;
+  return p;  // the trailing partial block keeps its place
+}
+
+void permute_csr(int rows, int cols, const int64_t* ptr, const int32_t* idx, const double* val,
+                 const std::vector<int32_t>& prow, const std::vector<int32_t>& pcol,
+                 std::vector<int64_t>& optr, std::vector<int32_t>& oidx,
+                 std::vector<double>& oval) {
+  std::vector<int32_t> inv_col(cols);
+  for (int j = 0; j < cols; ++j) inv_col[pcol[j]] = j;
+  optr.assign(rows + 1, 0);
+  for (int r = 0; r < rows; ++r) optr[r + 1] = optr[r] + (ptr[prow[r] + 1] - ptr[prow[r]]);
+  const int64_t nnz = optr[rows];
+  oidx.resize(nnz);
+  oval.resize(nnz);
+  std::vector<std::pair<int32_t, double>> buf;
+  for (int r = 0; r < rows; ++r) {
+    const int64_t s = ptr[prow[r]], e = ptr[prow[r] + 1];
+    buf.resize(e - s);
+    bool sorted = true;
+    for (int64_t k = s; k < e; ++k) {
+      buf[k - s] = {inv_col[idx[k]], val[k]};
+      if (k > s && buf[k - s].first < buf[k - s - 1].first) sorted = false;
+    }
+    if (!sorted)
+      std::stable_sort(buf.begin(), buf.end(),
+                       [](const std::pair<int32_t, double>& a,
+                          const std::pair<int32_t, double>& b) { return a.first < b.first; });
+    for (size_t k = 0; k < buf.size(); ++k) {
+      oidx[optr[r] + k] = buf[k].first;
+      oval[optr[r] + k] = buf[k].second;
+    }
+  }
+}
+
+void transpose_csr(int rows, int cols, const std::vector<int64_t>& ptr,
+                   const std::vector<int32_t>& idx, const std::vector<double>& val,
+                   std::vector<int64_t>& tptr, std::vector<int32_t>& tidx,
+                   std::vector<double>& tval) {
+  const int64_t nnz = ptr[rows];
+  tptr.assign(cols + 1, 0);
+  for (int64_t e = 0; e < nnz; ++e) tptr[idx[e] + 1]++;
+  for (int j = 0; j < cols; ++j) tptr[j + 1] += tptr[j];
+  std::vector<int64_t> pos(tptr.begin(), tptr.end() - 1);
+  tidx.resize(nnz);
+  tval.resize(nnz);
+  for (int r = 0; r < rows; ++r)
+    for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) {
+      const int64_t p = pos[idx[e]]++;
+      tidx[p] = r;
+      tval[p] = val[e];
+    }
+}
+
+static inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+void build_tiled(int rows, int cols, const std::vector<int64_t>& ptr,
+                 const std::vector<int32_t>& idx, const std::vector<double>& val,
+                 HostTiled& out) {
+  out.rows = rows;
+  out.cols = cols;
+  out.tiles.clear();
+  out.long_rows = 0;
+  out.long_chunks = 0;
+  // Pass 1: tile plan over the original offsets.
+  struct Plan { int r0, r1; bool solo; };
+  std::vector<Plan> plan;
+  for (int r = 0; r < rows;) {
+    const int64_t L = ptr[r + 1] - ptr[r];
+    if (L > SOLO_NNZ) {
+      plan.push_back({r, r + 1, true});
+      ++r;
+      continue;
+    }
+    int r1 = r;
+    int64_t nz = 0;
+    while (r1 < rows && r1 - r < TPB) {
+      const int64_t Lr = ptr[r1 + 1] - ptr[r1];
+      if (Lr > SOLO_NNZ || nz + Lr > TILE_NNZ) break;
+      nz += Lr;
+      ++r1;
+    }
+    plan.push_back({r, r1, false});
+    r = r1;
+  }
+  // Pass 2: padded arrays and tile descriptors.
+  int64_t padded = 0;
+  for (const Plan& p : plan) padded += round_up(ptr[p.r1] - ptr[p.r0], IPT);
+  out.nnz_padded = padded;
+  out.ptr.assign(rows + 1, 0);
+  out.idx.assign(padded + TILE_NNZ, 0);
+  out.val.assign(padded + TILE_NNZ, 0.0);
+  int64_t pos = 0;
+  for (const Plan& p : plan) {
+    const int64_t e0 = pos;
+    for (int r = p.r0; r < p.r1; ++r) {
+      out.ptr[r] = (int32_t)pos;
+      const int64_t L = ptr[r + 1] - ptr[r];
+      if (L > 0) {
+        std::memcpy(&out.idx[pos], &idx[ptr[r]], L * sizeof(int32_t));
+        std::memcpy(&out.val[pos], &val[ptr[r]], L * sizeof(double));
+      }
+      pos += L;
+    }
+    // explicit zeros appended to the tile's last row keep the next tile IPT-aligned
+    const int64_t end = e0 + round_up(pos - e0, IPT);
+    const int32_t pad_col = pos > e0 ? out.idx[pos - 1] : 0;
+    for (; pos < end; ++pos) {
+      out.idx[pos] = pad_col;
+      out.val[pos] = 0.0;
+    }
+    if (!p.solo) {
+      out.tiles.push_back({p.r0, p.r1, (int)e0, (int)pos, -1, -1, 0, 1});
+    } else {
+      const int nch = (int)((pos - e0 + TILE_NNZ - 1) / TILE_NNZ);
+      if (nch <= 1) {
+        out.tiles.push_back({p.r0, p.r1, (int)e0, (int)pos, -2, -1, 0, 1});
+      } else {
+        for (int c = 0; c < nch; ++c) {
+          const int64_t a = e0 + (int64_t)c * TILE_NNZ;
+          const int64_t b = std::min<int64_t>(a + TILE_NNZ, pos);
+          out.tiles.push_back({p.r0, p.r1, (int)a, (int)b, out.long_chunks, out.long_rows, c, nch});
+        }
+        out.long_chunks += nch;
+        out.long_rows += 1;
+      }
+    }
+  }
+  out.ptr[rows] = (int32_t)pos;
+}
+
+}  // namespace pdhg

@@ -1,0 +1,827 @@
+// C ABI of libdpdlp (declared in include/dpdlp.h): handle, load, solve loop, getters.
+//
+// The solve loop is one CUDA graph: a conditional WHILE node whose body holds
+// check_every iterations (primal kernel, dual kernel) followed by the check kernels; the
+// control kernel of the check sets the loop condition on the device, so the host waits
+// once per solve.  With use_graph = 0 the same kernels are launched from a host loop that
+// reads the status after every check.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/dpdlp.h"
+#include "internal.h"
+
+using namespace pdhg;
+
+namespace {
+
+struct Param {
+  double value, lo, hi;
+  bool integer;
+};
+
+std::map<std::string, Param> default_params() {
+  return {
+      {"eta", {0.0, 0.0, 1e300, false}},
+      {"eta_safety", {0.998, 1e-6, 1.0, false}},
+      {"power_iters", {200, 1, 100000, true}},
+      {"power_tol", {1e-8, 0.0, 1.0, false}},
+      {"omega0", {0.0, 0.0, 1e300, false}},
+      {"gamma", {1.0, 0.0, 1.0, false}},
+      {"halpern", {1, 0, 1, true}},
+      {"check_every", {64, 1, KMAX, true}},
+      {"restart", {1, 0, 1, true}},
+      {"beta_sufficient", {0.2, 0.0, 1.0, false}},
+      {"beta_necessary", {0.8, 0.0, 1.0, false}},
+      {"beta_artificial", {0.36, 0.0, 1.0, false}},
+      {"pid", {1, 0, 1, true}},
+      {"pid_kp", {0.99, -1e3, 1e3, false}},
+      {"pid_ki", {0.01, -1e3, 1e3, false}},
+      {"pid_kd", {0.0, -1e3, 1e3, false}},
+      {"block_permute", {1, 0, 1, true}},
+      {"perm_block", {256, 1, 1 << 30, true}},
+      {"perm_seed", {1, 0, 9007199254740992.0, true}},
+      {"use_graph", {1, 0, 1, true}},
+      {"ptr_mode_device", {0, 0, 1, true}},
+      {"resume", {0, 0, 1, true}},
+      {"trace_capacity", {4096, 0, 1 << 20, true}},
+  };
+}
+
+}  // namespace
+
+struct dpdlp {
+  int device = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  std::map<std::string, Param> params = default_params();
+
+  bool loaded = false;
+  int n = 0, m = 0;
+  int64_t nnz = 0;
+  std::vector<int32_t> prow, pcol;  // internal index -> caller index
+  std::vector<double> h_lc, h_uc;   // caller order
+  DevTiled csr, csc;
+  DevVecs v;
+  double *xs = nullptr, *ys = nullptr;  // warm start (internal order)
+  bool have_start_x = false, have_start_y = false;
+  DevScalars* d_sc = nullptr;
+  DevScalars h_sc{};
+  double bnorm = 0.0, cnorm = 0.0;
+  double eta_cached = 0.0;
+  bool eta_valid = false;
+  bool pending_state = false;
+  bool has_state = false;
+  int trace_cap = 0;
+
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int graph_K = -1;
+
+  std::vector<void*> allocs;
+  int64_t dev_bytes = 0;
+  dpdlp_info_t info{};
+
+  double P(const char* k) const { return params.at(k).value; }
+};
+
+namespace {
+
+int fail(dpdlp* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? DPDLP_ERR_OOM : DPDLP_ERR_CUDA, \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));               \
+  } while (0)
+
+template <class T>
+int dalloc(dpdlp* h, T** p, size_t count) {
+  *p = nullptr;
+  const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(h, DPDLP_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  h->allocs.push_back(*p);
+  h->dev_bytes += bytes;
+  return 0;
+}
+
+void free_graph(dpdlp* h) {
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->exec = nullptr;
+  h->graph = nullptr;
+  h->graph_K = -1;
+}
+
+void free_problem(dpdlp* h) {
+  free_graph(h);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  h->dev_bytes = 0;
+  h->csr = DevTiled{};
+  h->csc = DevTiled{};
+  h->v = DevVecs{};
+  h->xs = h->ys = nullptr;
+  h->d_sc = nullptr;
+  h->loaded = false;
+  h->eta_valid = false;
+  h->pending_state = false;
+  h->has_state = false;
+  h->have_start_x = h->have_start_y = false;
+}
+
+int upload_tiled(dpdlp* h, const HostTiled& H, DevTiled& D) {
+  D.rows = H.rows;
+  D.cols = H.cols;
+  D.ntiles = (int)H.tiles.size();
+  D.long_rows = H.long_rows;
+  D.long_chunks = H.long_chunks;
+  int rc;
+  if ((rc = dalloc(h, &D.ptr, H.ptr.size()))) return rc;
+  if ((rc = dalloc(h, &D.idx, H.idx.size()))) return rc;
+  if ((rc = dalloc(h, &D.val, H.val.size()))) return rc;
+  if ((rc = dalloc(h, &D.tiles, H.tiles.size()))) return rc;
+  if ((rc = dalloc(h, &D.lr_partial, 2 * (size_t)H.long_chunks + 2))) return rc;
+  if ((rc = dalloc(h, &D.lr_count, (size_t)H.long_rows + 1))) return rc;
+  CK(cudaMemcpy(D.ptr, H.ptr.data(), H.ptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(D.idx, H.idx.data(), H.idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(D.val, H.val.data(), H.val.size() * sizeof(double), cudaMemcpyHostToDevice));
+  if (!H.tiles.empty())
+    CK(cudaMemcpy(D.tiles, H.tiles.data(), H.tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+  CK(cudaMemset(D.lr_count, 0, ((size_t)H.long_rows + 1) * sizeof(unsigned)));
+  return 0;
+}
+
+template <class T>
+std::vector<T> permuted(const T* src, const std::vector<int32_t>& p) {
+  std::vector<T> out(p.size());
+  for (size_t i = 0; i < p.size(); ++i) out[i] = src[p[i]];
+  return out;
+}
+
+// ||[lc, uc]|| over finite entries, an equality row counted once (reading of the
+// r_primal denominator of Appendix B.4 and of the initial primal weight).
+double bound_norm(const std::vector<double>& lc, const std::vector<double>& uc) {
+  double s = 0.0;
+  for (size_t i = 0; i < lc.size(); ++i) {
+    const bool lf = std::isfinite(lc[i]), uf = std::isfinite(uc[i]);
+    if (lf && uf && lc[i] == uc[i]) {
+      s += lc[i] * lc[i];
+    } else {
+      if (lf) s += lc[i] * lc[i];
+      if (uf) s += uc[i] * uc[i];
+    }
+  }
+  return std::sqrt(s);
+}
+
+int upload_row_bounds(dpdlp* h) {
+  std::vector<double> lo(h->m), hi(h->m);
+  for (int i = 0; i < h->m; ++i) {
+    const int o = h->prow[i];
+    lo[i] = -h->h_uc[o];
+    hi[i] = -h->h_lc[o];
+  }
+  if (h->m) {
+    CK(cudaMemcpy(h->v.lo, lo.data(), h->m * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->v.hi, hi.data(), h->m * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  h->bnorm = bound_norm(h->h_lc, h->h_uc);
+  return 0;
+}
+
+bool ptr_device(const dpdlp* h) { return h->P("ptr_mode_device") != 0.0; }
+
+// Caller vector (caller order, host or device) -> internal-order device vector `dst`.
+int import_vec(dpdlp* h, const double* src, double* dst, const int32_t* perm, int len,
+               double* staging) {
+  if (len == 0) return 0;
+  const double* dsrc = src;
+  if (!ptr_device(h)) {
+    CK(cudaMemcpyAsync(staging, src, len * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    dsrc = staging;
+  }
+  CK(launch_gather(dsrc, perm, dst, len, h->stream));
+  return 0;
+}
+
+// Internal-order device vector -> caller vector (caller order, host or device).
+int export_vec(dpdlp* h, const double* src, double* dst, const int32_t* perm, int len,
+               double* staging) {
+  if (len == 0 || !dst) return 0;
+  if (ptr_device(h)) {
+    CK(launch_scatter(src, perm, dst, len, h->stream));
+  } else {
+    CK(launch_scatter(src, perm, staging, len, h->stream));
+    CK(cudaMemcpyAsync(dst, staging, len * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return 0;
+}
+
+// eta = eta_safety / sigma_max(A) by power iteration on A^T A (start 1/sqrt(n), stop when
+// the Rayleigh quotient changes by <= power_tol relatively, at most power_iters rounds);
+// eta = 1 when A has no nonzeros.
+int compute_eta(dpdlp* h) {
+  if (h->eta_valid) return 0;
+  const int n = h->n;
+  if (n == 0 || h->nnz == 0) {
+    h->eta_cached = 1.0;
+    h->eta_valid = true;
+    return 0;
+  }
+  double* vv = h->v.tmp_n;
+  double* ww = h->v.tmp_m;
+  double* uu = h->v.tmp_n2;
+  CK(launch_fill(vv, 1.0 / std::sqrt((double)n), n, h->stream));
+  const int iters = (int)h->P("power_iters");
+  const double tol = h->P("power_tol");
+  double lam = 0.0, lam_prev = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    CK(launch_power_round(h->csr, h->csc, h->v, vv, ww, uu, h->stream));
+    double pw[3];
+    CK(cudaMemcpyAsync(pw, h->v.pw, sizeof(pw), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    lam = pw[0];
+    if (pw[1] == 0.0 || lam == 0.0) break;
+    if (std::fabs(lam - lam_prev) <= tol * lam) break;
+    lam_prev = lam;
+  }
+  const double s = std::sqrt(lam);
+  h->eta_cached = s > 0.0 ? h->P("eta_safety") / s : 1.0;
+  h->eta_valid = true;
+  return 0;
+}
+
+void fill_weights(DevScalars& s) {
+  const double kb = (double)s.k_base;
+  for (int i = 0; i < s.K; ++i) {
+    s.w1[i] = (kb + i + 1.0) / (kb + i + 2.0);
+    s.w0[i] = 1.0 / (kb + i + 2.0);
+  }
+}
+
+void copy_params(dpdlp* h, DevScalars& s) {
+  s.gamma = h->P("gamma");
+  s.halpern = (int)h->P("halpern");
+  s.K = (int)h->P("check_every");
+  s.restart_enabled = (int)h->P("restart");
+  s.pid_enabled = (int)h->P("pid");
+  s.beta_s = h->P("beta_sufficient");
+  s.beta_n = h->P("beta_necessary");
+  s.beta_a = h->P("beta_artificial");
+  s.kp = h->P("pid_kp");
+  s.ki = h->P("pid_ki");
+  s.kd = h->P("pid_kd");
+  s.bnorm = h->bnorm;
+  s.cnorm = h->cnorm;
+  s.trace_cap = h->trace_cap;
+}
+
+// Fresh start: x = proj_X(0) (or the warm start), y = 0 (or the warm start), anchor = start.
+int init_fresh(dpdlp* h) {
+  int rc;
+  const double pe = h->P("eta");
+  double eta;
+  if (pe > 0.0) {
+    eta = pe;
+  } else {
+    if ((rc = compute_eta(h))) return rc;
+    eta = h->eta_cached;
+  }
+  const double po = h->P("omega0");
+  const double omega = po > 0.0 ? po : ((h->cnorm > 0.0 && h->bnorm > 0.0) ? h->cnorm / h->bnorm : 1.0);
+  if (h->have_start_x && h->n)
+    CK(cudaMemcpyAsync(h->v.x, h->xs, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  if (h->have_start_y && h->m)
+    CK(cudaMemcpyAsync(h->v.y, h->ys, h->m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  CK(launch_fill_start(h->v, h->have_start_x ? 0 : 1, h->have_start_y ? 0 : 1, h->stream));
+  DevScalars& s = h->h_sc;
+  const int sched = s.sched_len;  // the forced schedule outlives a fresh start
+  std::memset(&s, 0, sizeof(s));
+  s.sched_len = sched;
+  s.eta = eta;
+  s.omega = omega;
+  s.tau = eta / omega;
+  s.sigma = eta * omega;
+  s.inv_sigma = 1.0 / s.sigma;
+  s.status = -1;
+  s.apply_mode = 2;
+  h->has_state = true;
+  return 0;
+}
+
+int build_graph(dpdlp* h, int K) {
+  free_graph(h);
+  CK(cudaGraphCreate(&h->graph, 0));
+  cudaGraphConditionalHandle handle;
+  CK(cudaGraphConditionalHandleCreate(&handle, h->graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, h->graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < K && e == cudaSuccess; ++i) {
+    e = launch_primal(h->csc, h->v, h->d_sc, IterPlan{i, 0}, h->cap_stream);
+    if (e == cudaSuccess) e = launch_dual(h->csr, h->v, h->d_sc, IterPlan{i, 0}, h->cap_stream);
+  }
+  if (e == cudaSuccess)
+    e = launch_check(h->csr, h->csc, h->v, h->d_sc, (unsigned long long)handle, 1, h->cap_stream);
+  cudaGraph_t captured = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &captured);
+  if (e != cudaSuccess) return fail(h, DPDLP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  if (e2 != cudaSuccess) return fail(h, DPDLP_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e2));
+  CK(cudaGraphInstantiate(&h->exec, h->graph, 0));
+  h->graph_K = K;
+  return 0;
+}
+
+int run_host_loop(dpdlp* h) {
+  const int K = h->h_sc.K;
+  for (;;) {
+    for (int i = 0; i < K; ++i) {
+      CK(launch_primal(h->csc, h->v, h->d_sc, IterPlan{i, 0}, h->stream));
+      CK(launch_dual(h->csr, h->v, h->d_sc, IterPlan{i, 0}, h->stream));
+    }
+    CK(launch_check(h->csr, h->csc, h->v, h->d_sc, 0ULL, 0, h->stream));
+    int status = -1;
+    CK(cudaMemcpyAsync(&status, &h->d_sc->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (status != -1) return 0;
+  }
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+int dpdlp_create(dpdlp_t** out, int device) {
+  if (!out) return DPDLP_ERR_INVALID;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+    return DPDLP_ERR_INVALID;
+  dpdlp* h = new (std::nothrow) dpdlp();
+  if (!h) return DPDLP_ERR_OOM;
+  h->device = device;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete h;
+    return DPDLP_ERR_CUDA;
+  }
+  h->stream = h->own_stream;
+  *out = h;
+  return 0;
+}
+
+void dpdlp_destroy(dpdlp_t* h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  free_problem(h);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+const char* dpdlp_last_error(const dpdlp_t* h) { return h ? h->err.c_str() : "null handle"; }
+
+int dpdlp_set_stream(dpdlp_t* h, void* s) {
+  if (!h) return DPDLP_ERR_INVALID;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  h->stream = s ? (cudaStream_t)s : h->own_stream;
+  return 0;
+}
+
+int dpdlp_set_param(dpdlp_t* h, const char* key, double v) {
+  if (!h || !key) return DPDLP_ERR_INVALID;
+  auto it = h->params.find(key);
+  if (it == h->params.end()) return fail(h, DPDLP_ERR_INVALID, std::string("unknown parameter: ") + key);
+  Param& p = it->second;
+  if (!(v >= p.lo && v <= p.hi) || (p.integer && v != std::floor(v)))
+    return fail(h, DPDLP_ERR_INVALID, std::string("value out of range for ") + key);
+  if (std::string(key) == "check_every" && v != p.value) free_graph(h);
+  if (std::string(key) == "eta_safety" || std::string(key) == "power_iters" ||
+      std::string(key) == "power_tol")
+    h->eta_valid = false;
+  p.value = v;
+  return 0;
+}
+
+int dpdlp_get_param(const dpdlp_t* h, const char* key, double* v) {
+  if (!h || !key || !v) return DPDLP_ERR_INVALID;
+  auto it = h->params.find(key);
+  if (it == h->params.end()) return DPDLP_ERR_INVALID;
+  *v = it->second.value;
+  return 0;
+}
+
+int dpdlp_load_lp(dpdlp_t* h, int32_t n, int32_t m, const double* c, const int64_t* row_ptr,
+                  const int32_t* col_idx, const double* val, const double* b, const double* lv,
+                  const double* uv, const int8_t* ctype) {
+  if (!h) return DPDLP_ERR_INVALID;
+  CK(cudaSetDevice(h->device));
+  const auto t0 = std::chrono::steady_clock::now();
+  if (n < 0 || m < 0) return fail(h, DPDLP_ERR_INVALID, "negative dimension");
+  if ((n > 0 && (!c || !lv || !uv)) || !row_ptr)
+    return fail(h, DPDLP_ERR_INVALID, "NULL input array");
+  if ((b == nullptr) != (ctype == nullptr))
+    return fail(h, DPDLP_ERR_INVALID, "b and ctype must both be given or both be NULL");
+  std::string e = validate_csr(m, n, row_ptr, col_idx, val);
+  if (!e.empty()) return fail(h, DPDLP_ERR_INVALID, e);
+  for (int j = 0; j < n; ++j) {
+    if (!std::isfinite(c[j])) return fail(h, DPDLP_ERR_INVALID, "non-finite objective coefficient");
+    if (std::isnan(lv[j]) || std::isnan(uv[j]) || lv[j] > uv[j] || lv[j] == INFINITY ||
+        uv[j] == -INFINITY)
+      return fail(h, DPDLP_ERR_INVALID, "invalid variable bounds at " + std::to_string(j));
+  }
+  std::vector<double> lc(m, -INFINITY), uc(m, INFINITY);
+  if (ctype) {
+    for (int i = 0; i < m; ++i) {
+      if (!std::isfinite(b[i])) return fail(h, DPDLP_ERR_INVALID, "non-finite right-hand side");
+      switch (ctype[i]) {
+        case 0: lc[i] = b[i]; uc[i] = b[i]; break;
+        case 1: uc[i] = b[i]; break;
+        case 2: lc[i] = b[i]; break;
+        default: return fail(h, DPDLP_ERR_INVALID, "constraint type must be 0, 1 or 2");
+      }
+    }
+  }
+  free_problem(h);
+  h->n = n;
+  h->m = m;
+  h->nnz = row_ptr[m];
+  h->h_lc = lc;
+  h->h_uc = uc;
+  const bool perm = h->P("block_permute") != 0.0;
+  const int pb = (int)h->P("perm_block");
+  const uint64_t seed = (uint64_t)h->P("perm_seed");
+  h->prow = block_permutation(m, pb, seed, perm);
+  h->pcol = block_permutation(n, pb, seed + 1, perm);
+  std::vector<int64_t> pptr, tptr;
+  std::vector<int32_t> pidx, tidx;
+  std::vector<double> pval, tval;
+  permute_csr(m, n, row_ptr, col_idx, val, h->prow, h->pcol, pptr, pidx, pval);
+  transpose_csr(m, n, pptr, pidx, pval, tptr, tidx, tval);
+  HostTiled Hr, Hc;
+  build_tiled(m, n, pptr, pidx, pval, Hr);
+  build_tiled(n, m, tptr, tidx, tval, Hc);
+  std::vector<int64_t>().swap(pptr);
+  std::vector<int32_t>().swap(pidx);
+  std::vector<double>().swap(pval);
+  std::vector<int64_t>().swap(tptr);
+  std::vector<int32_t>().swap(tidx);
+  std::vector<double>().swap(tval);
+
+  int rc;
+  if ((rc = upload_tiled(h, Hr, h->csr))) return rc;
+  if ((rc = upload_tiled(h, Hc, h->csc))) return rc;
+  DevVecs& v = h->v;
+  v.n = n;
+  v.m = m;
+  double** nvecs[] = {&v.c, &v.lv, &v.uv, &v.x, &v.x0, &v.xbar, &v.xh, &v.dx, &v.aty,
+                      &v.tmp_n, &v.tmp_n2, &h->xs};
+  for (double** p : nvecs)
+    if ((rc = dalloc(h, p, n))) return rc;
+  double** mvecs[] = {&v.lo, &v.hi, &v.y, &v.y0, &v.yh, &v.axh, &v.adx, &v.tmp_m, &h->ys};
+  for (double** p : mvecs)
+    if ((rc = dalloc(h, p, m))) return rc;
+  v.g_rows = reduction_grid(m);
+  v.g_cols = reduction_grid(n);
+  if ((rc = dalloc(h, &v.red_rows, 1024 * NRED))) return rc;
+  if ((rc = dalloc(h, &v.red_cols, 1024 * NRED))) return rc;
+  if ((rc = dalloc(h, &v.perm_col, n))) return rc;
+  if ((rc = dalloc(h, &v.perm_row, m))) return rc;
+  if ((rc = dalloc(h, &v.pw, 4))) return rc;
+  if ((rc = dalloc(h, &v.sched, 1))) return rc;
+  h->trace_cap = (int)h->P("trace_capacity");
+  if ((rc = dalloc(h, (dpdlp_trace_t**)&v.trace, h->trace_cap > 0 ? h->trace_cap : 1))) return rc;
+  if ((rc = dalloc(h, &h->d_sc, 1))) return rc;
+  if (n) {
+    std::vector<double> tmp = permuted(c, h->pcol);
+    CK(cudaMemcpy(v.c, tmp.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    tmp = permuted(lv, h->pcol);
+    CK(cudaMemcpy(v.lv, tmp.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    tmp = permuted(uv, h->pcol);
+    CK(cudaMemcpy(v.uv, tmp.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(v.perm_col, h->pcol.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+  }
+  if (m) CK(cudaMemcpy(v.perm_row, h->prow.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice));
+  if ((rc = upload_row_bounds(h))) return rc;
+  double cs = 0.0;
+  for (int j = 0; j < n; ++j) cs += c[j] * c[j];
+  h->cnorm = std::sqrt(cs);
+  h->loaded = true;
+  const auto t1 = std::chrono::steady_clock::now();
+  dpdlp_info_t& I = h->info;
+  I.n = n;
+  I.m = m;
+  I.nnz = h->nnz;
+  I.nnz_padded_csr = Hr.nnz_padded;
+  I.nnz_padded_csc = Hc.nnz_padded;
+  I.tiles_csr = (int)Hr.tiles.size();
+  I.tiles_csc = (int)Hc.tiles.size();
+  I.long_rows = Hr.long_rows;
+  I.long_cols = Hc.long_rows;
+  I.device_bytes = h->dev_bytes;
+  I.preprocess_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  return 0;
+}
+
+int dpdlp_set_row_bounds(dpdlp_t* h, const double* lc, const double* uc) {
+  if (!h || !lc || !uc) return DPDLP_ERR_INVALID;
+  if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
+  CK(cudaSetDevice(h->device));
+  for (int i = 0; i < h->m; ++i)
+    if (std::isnan(lc[i]) || std::isnan(uc[i]) || lc[i] > uc[i] || lc[i] == INFINITY ||
+        uc[i] == -INFINITY)
+      return fail(h, DPDLP_ERR_INVALID, "invalid row bounds at " + std::to_string(i));
+  CK(cudaStreamSynchronize(h->stream));
+  h->h_lc.assign(lc, lc + h->m);
+  h->h_uc.assign(uc, uc + h->m);
+  h->has_state = false;
+  h->pending_state = false;
+  return upload_row_bounds(h);
+}
+
+int dpdlp_set_start(dpdlp_t* h, const double* x0, const double* y0) {
+  if (!h) return DPDLP_ERR_INVALID;
+  if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
+  CK(cudaSetDevice(h->device));
+  int rc;
+  h->have_start_x = x0 != nullptr;
+  h->have_start_y = y0 != nullptr;
+  if (x0 && (rc = import_vec(h, x0, h->xs, h->v.perm_col, h->n, h->v.tmp_n))) return rc;
+  if (y0 && (rc = import_vec(h, y0, h->ys, h->v.perm_row, h->m, h->v.tmp_m))) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  return 0;
+}
+
+int dpdlp_solve(dpdlp_t* h, double tol, int64_t max_iter) {
+  if (!h) return DPDLP_ERR_INVALID;
+  if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
+  if (!(tol >= 0.0) || max_iter < 0) return fail(h, DPDLP_ERR_INVALID, "tol must be >= 0, max_iter >= 0");
+  CK(cudaSetDevice(h->device));
+  int rc;
+  const bool resume = (h->P("resume") != 0.0 && h->has_state) || h->pending_state;
+  if (!resume && (rc = init_fresh(h))) return rc;
+  DevScalars& s = h->h_sc;
+  copy_params(h, s);
+  s.eps = tol;
+  s.max_iter = max_iter;
+  h->pending_state = false;
+  if (s.T_base >= max_iter) {
+    s.status = 1;
+    CK(cudaMemcpyAsync(h->d_sc, &s, sizeof(DevScalars), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return 1;
+  }
+  s.status = -1;
+  s.T_check = s.T_base + s.K < max_iter ? s.T_base + s.K : max_iter;
+  fill_weights(s);
+  CK(cudaMemcpyAsync(h->d_sc, &s, sizeof(DevScalars), cudaMemcpyHostToDevice, h->stream));
+  if (h->P("use_graph") != 0.0) {
+    if (h->graph_K != s.K || !h->exec) {
+      CK(cudaStreamSynchronize(h->stream));
+      if ((rc = build_graph(h, s.K))) return rc;
+    }
+    CK(cudaGraphLaunch(h->exec, h->stream));
+  } else {
+    if ((rc = run_host_loop(h))) return rc;
+  }
+  CK(cudaMemcpyAsync(&s, h->d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  return s.status;
+}
+
+int dpdlp_get_solution(dpdlp_t* h, double* x, double* y) {
+  if (!h) return DPDLP_ERR_INVALID;
+  if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
+  CK(cudaSetDevice(h->device));
+  int rc;
+  if ((rc = export_vec(h, h->v.xh, x, h->v.perm_col, h->n, h->v.tmp_n))) return rc;
+  if ((rc = export_vec(h, h->v.yh, y, h->v.perm_row, h->m, h->v.tmp_m))) return rc;
+  return 0;
+}
+
+int dpdlp_get_kkt(dpdlp_t* h, dpdlp_kkt_t* o) {
+  if (!h || !o) return DPDLP_ERR_INVALID;
+  if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
+  const DevScalars& s = h->h_sc;
+  o->r_primal = s.r_p;
+  o->r_dual = s.r_d;
+  o->r_gap = s.r_g;
+  o->obj_p = s.obj_p;
+  o->obj_d = s.obj_d;
+  o->r_fp = s.r_fp;
+  o->omega = s.omega;
+  o->eta = s.eta;
+  o->tau = s.tau;
+  o->sigma = s.sigma;
+  o->iterations = s.T_base;
+  o->restarts = s.restarts;
+  o->checks = s.checks;
+  o->status = h->has_state ? s.status : -1;
+  o->spmv_mode = 0;
+  return 0;
+}
+
+int dpdlp_get_trace(dpdlp_t* h, dpdlp_trace_t* out, int32_t cap, int32_t* count) {
+  if (!h || !count || cap < 0 || (cap > 0 && !out)) return DPDLP_ERR_INVALID;
+  if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
+  CK(cudaSetDevice(h->device));
+  const long long total = h->h_sc.trace_count;
+  const long long avail = total < h->trace_cap ? total : h->trace_cap;
+  const long long take = avail < cap ? avail : cap;
+  std::vector<dpdlp_trace_t> ring(h->trace_cap > 0 ? h->trace_cap : 1);
+  if (h->trace_cap > 0) {
+    CK(cudaMemcpyAsync(ring.data(), h->v.trace, h->trace_cap * sizeof(dpdlp_trace_t),
+                       cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  const long long first = total - avail;  // oldest record kept
+  for (long long r = 0; r < take; ++r) out[r] = ring[(first + r) % h->trace_cap];
+  *count = (int32_t)take;
+  return 0;
+}
+
+int dpdlp_get_state(dpdlp_t* h, double* x, double* y, double* x0, double* y0,
+                    dpdlp_scalar_state_t* st) {
+  if (!h) return DPDLP_ERR_INVALID;
+  if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
+  if (!h->has_state) return fail(h, DPDLP_ERR_INVALID, "no solver state yet");
+  CK(cudaSetDevice(h->device));
+  int rc;
+  if ((rc = export_vec(h, h->v.x, x, h->v.perm_col, h->n, h->v.tmp_n))) return rc;
+  if ((rc = export_vec(h, h->v.y, y, h->v.perm_row, h->m, h->v.tmp_m))) return rc;
+  if ((rc = export_vec(h, h->v.x0, x0, h->v.perm_col, h->n, h->v.tmp_n))) return rc;
+  if ((rc = export_vec(h, h->v.y0, y0, h->v.perm_row, h->m, h->v.tmp_m))) return rc;
+  if (st) {
+    const DevScalars& s = h->h_sc;
+    st->T = s.T_base;
+    st->k = s.k_base;
+    st->restarts = s.restarts;
+    st->checks = s.checks;
+    st->eta = s.eta;
+    st->omega = s.omega;
+    st->r_anchor = s.r_anchor;
+    st->r_prev = s.r_prev;
+    st->e_sum = s.e_sum;
+    st->e_prev = s.e_prev;
+    st->has_anchor = s.has_anchor;
+    st->has_e_prev = s.has_e_prev;
+  }
+  return 0;
+}
+
+int dpdlp_set_state(dpdlp_t* h, const double* x, const double* y, const double* x0,
+                    const double* y0, const dpdlp_scalar_state_t* st) {
+  if (!h || !st || (h->n && (!x || !x0)) || (h->m && (!y || !y0))) return DPDLP_ERR_INVALID;
+  if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
+  if (!(st->eta > 0.0) || !(st->omega > 0.0) || st->T < 0 || st->k < 0)
+    return fail(h, DPDLP_ERR_INVALID, "invalid scalar state");
+  CK(cudaSetDevice(h->device));
+  int rc;
+  if ((rc = import_vec(h, x, h->v.x, h->v.perm_col, h->n, h->v.tmp_n))) return rc;
+  if ((rc = import_vec(h, y, h->v.y, h->v.perm_row, h->m, h->v.tmp_m))) return rc;
+  if ((rc = import_vec(h, x0, h->v.x0, h->v.perm_col, h->n, h->v.tmp_n))) return rc;
+  if ((rc = import_vec(h, y0, h->v.y0, h->v.perm_row, h->m, h->v.tmp_m))) return rc;
+  if (h->n) CK(cudaMemcpyAsync(h->v.xh, h->v.x, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  if (h->m) CK(cudaMemcpyAsync(h->v.yh, h->v.y, h->m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  DevScalars& s = h->h_sc;
+  const int sched = s.sched_len;
+  std::memset(&s, 0, sizeof(s));
+  s.sched_len = sched;
+  s.T_base = st->T;
+  s.k_base = st->k;
+  s.restarts = st->restarts;
+  s.checks = st->checks;
+  s.eta = st->eta;
+  s.omega = st->omega;
+  s.tau = s.eta / s.omega;
+  s.sigma = s.eta * s.omega;
+  s.inv_sigma = 1.0 / s.sigma;
+  s.r_anchor = st->r_anchor;
+  s.r_prev = st->r_prev;
+  s.e_sum = st->e_sum;
+  s.e_prev = st->e_prev;
+  s.has_anchor = st->has_anchor;
+  s.has_e_prev = st->has_e_prev;
+  s.status = -1;
+  s.apply_mode = 2;
+  h->has_state = true;
+  h->pending_state = true;
+  return 0;
+}
+
+int dpdlp_set_schedule(dpdlp_t* h, const int8_t* kinds, int32_t count) {
+  if (!h || count < 0 || (count > 0 && !kinds)) return DPDLP_ERR_INVALID;
+  if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
+  CK(cudaSetDevice(h->device));
+  for (int i = 0; i < count; ++i)
+    if (kinds[i] < 0 || kinds[i] > 3) return fail(h, DPDLP_ERR_INVALID, "restart kind must be 0..3");
+  CK(cudaStreamSynchronize(h->stream));
+  // reallocate the schedule buffer (it is not part of the captured graph's pointers
+  // except through DevVecs, so the graph is rebuilt)
+  free_graph(h);
+  int rc;
+  if ((rc = dalloc(h, &h->v.sched, count > 0 ? count : 1))) return rc;
+  if (count > 0) CK(cudaMemcpy(h->v.sched, kinds, count, cudaMemcpyHostToDevice));
+  h->h_sc.sched_len = count;
+  return 0;
+}
+
+int dpdlp_apply_A(dpdlp_t* h, const double* x, double* out) {
+  if (!h || (h->n && !x) || (h->m && !out)) return DPDLP_ERR_INVALID;
+  if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
+  CK(cudaSetDevice(h->device));
+  int rc;
+  if ((rc = import_vec(h, x, h->v.tmp_n2, h->v.perm_col, h->n, h->v.tmp_n))) return rc;
+  CK(launch_spmv(h->csr, h->v.tmp_n2, nullptr, h->v.axh, nullptr, h->stream));
+  if (h->csr.ntiles == 0 && h->m) CK(launch_fill(h->v.axh, 0.0, h->m, h->stream));
+  return export_vec(h, h->v.axh, out, h->v.perm_row, h->m, h->v.tmp_m);
+}
+
+int dpdlp_apply_AT(dpdlp_t* h, const double* y, double* out) {
+  if (!h || (h->m && !y) || (h->n && !out)) return DPDLP_ERR_INVALID;
+  if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
+  CK(cudaSetDevice(h->device));
+  int rc;
+  if ((rc = import_vec(h, y, h->v.axh, h->v.perm_row, h->m, h->v.tmp_m))) return rc;
+  CK(launch_spmv(h->csc, h->v.axh, nullptr, h->v.tmp_n2, nullptr, h->stream));
+  if (h->csc.ntiles == 0 && h->n) CK(launch_fill(h->v.tmp_n2, 0.0, h->n, h->stream));
+  return export_vec(h, h->v.tmp_n2, out, h->v.perm_col, h->n, h->v.tmp_n);
+}
+
+int dpdlp_time_kernel(dpdlp_t* h, const char* which, int32_t reps, double* avg_ms) {
+  if (!h || !which || reps <= 0 || !avg_ms) return DPDLP_ERR_INVALID;
+  if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
+  const std::string w(which);
+  if (w != "primal" && w != "dual") return fail(h, DPDLP_ERR_INVALID, "kernel must be primal or dual");
+  if (!h->has_state) return fail(h, DPDLP_ERR_INVALID, "solve or set a start first");
+  CK(cudaSetDevice(h->device));
+  // keep the state: snapshot the vectors the kernels update in place
+  if (h->n) CK(cudaMemcpyAsync(h->v.tmp_n, h->v.x, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  if (h->m) CK(cudaMemcpyAsync(h->v.tmp_m, h->v.y, h->m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  if (h->n) CK(cudaMemcpyAsync(h->v.tmp_n2, h->v.xbar, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const IterPlan p{0, 1};
+  CK(cudaEventRecord(e0, h->stream));
+  for (int r = 0; r < reps; ++r) {
+    if (w == "primal") CK(launch_primal(h->csc, h->v, h->d_sc, p, h->stream));
+    else CK(launch_dual(h->csr, h->v, h->d_sc, p, h->stream));
+  }
+  CK(cudaEventRecord(e1, h->stream));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *avg_ms = (double)ms / reps;
+  if (h->n) CK(cudaMemcpyAsync(h->v.x, h->v.tmp_n, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  if (h->m) CK(cudaMemcpyAsync(h->v.y, h->v.tmp_m, h->m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  if (h->n) CK(cudaMemcpyAsync(h->v.xbar, h->v.tmp_n2, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return 0;
+}
+
+int dpdlp_get_info(dpdlp_t* h, dpdlp_info_t* out) {
+  if (!h || !out) return DPDLP_ERR_INVALID;
+  if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
+  *out = h->info;
+  out->device_bytes = h->dev_bytes;
+  return 0;
+}
+
+}  // extern "C"
