@@ -53,6 +53,7 @@ extern "C" {
 #define DPDLP_ERR_CUDA (-3)       /* a CUDA runtime call failed */
 #define DPDLP_ERR_NOT_LOADED (-4) /* no LP loaded on this handle */
 #define DPDLP_ERR_TIMEOUT (-5)    /* a bounded device wait gave up */
+#define DPDLP_ERR_TOO_LARGE (-6)  /* size beyond dpdlp_csr_spmv_noalloc's fixed scratch */
 
 typedef struct dpdlp dpdlp_t; /* opaque solver handle, one LP per handle */
 
@@ -202,6 +203,30 @@ int dpdlp_time_kernel(dpdlp_t* h, const char* which, int32_t reps, double* avg_m
 
 /* Sizes and layout of the loaded LP. */
 int dpdlp_get_info(dpdlp_t* h, dpdlp_info_t* out);
+
+/* y[m] = A x[n] for a plain CSR matrix already in DEVICE memory, allocating nothing.
+ * The paper has no counterpart: this is a service for callers that cannot allocate device
+ * memory where they need the product -- code recording a CUDA graph by stream capture
+ * (cudaMalloc is not a stream operation and may synchronize the device), frameworks
+ * whose pool owns all device memory, allocation-free latency-critical loops.
+ *   row_ptr[m+1] (int32, row_ptr[0] = 0, non-decreasing, row_ptr[m] = nnz), col_idx[nnz]
+ *   (int32 in [0, n)), val[nnz], x[n], y[m]: device pointers on the current device; the
+ *   caller guarantees a valid CSR (it is not checked on the device).
+ *   cuda_stream: a cudaStream_t or NULL; the call only enqueues work, y is ready when the
+ *   stream reaches this point.
+ * Scratch: one fixed array of 192 KB per device (static device storage, reserved when the
+ * library is loaded and held until the process exits) for the partial sums of rows that
+ * cross thread-block boundaries.  Every call on a device shares it, so calls that may run
+ * concurrently on the GPU (different streams without ordering) race and must not overlap;
+ * each call rewrites every slot it reads, so nothing needs clearing between calls.  The
+ * first call on a device looks up the array's device address (once per device, with that
+ * device current); make that first call before any stream capture.
+ * Limits: nnz <= 2^30 (DPDLP_ERR_TOO_LARGE beyond it); negative sizes or NULL pointers:
+ * DPDLP_ERR_INVALID; a failed launch or lookup: DPDLP_ERR_CUDA.  Results are deterministic
+ * (fixed summation order) and agree with dpdlp_apply_A to rounding. */
+int dpdlp_csr_spmv_noalloc(int32_t m, int32_t n, int64_t nnz, const int32_t* row_ptr,
+                           const int32_t* col_idx, const double* val, const double* x, double* y,
+                           void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libdpdlp.so")
 
 CONVERGED, MAX_ITER, NUMERICAL = 0, 1, 2
 ERRORS = {-1: "invalid argument", -2: "out of memory", -3: "CUDA error", -4: "not loaded",
-          -5: "device timeout"}
+          -5: "device timeout", -6: "size beyond the fixed scratch of the no-allocation SpMV"}
 
 
 class DpdlpError(RuntimeError):
@@ -81,6 +81,8 @@ EXPORTS = {
     "dpdlp_apply_AT": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dpdlp_time_kernel": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int32, C.POINTER(C.c_double)]),
     "dpdlp_get_info": (C.c_int, [C.c_void_p, C.POINTER(Info)]),
+    "dpdlp_csr_spmv_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -296,3 +298,19 @@ class Solver:
         i = Info()
         self._check(self.lib.dpdlp_get_info(self.h, C.byref(i)))
         return {f: getattr(i, f) for f, _ in Info._fields_}
+
+
+def csr_spmv_noalloc(row_ptr, col_idx, val, x, y, n, stream=None) -> int:
+    """y = A x through ``dpdlp_csr_spmv_noalloc`` (no device allocation).  All arrays are
+    CUDA tensors (int32 row_ptr/col_idx, float64 val/x/y) on the current device; ``stream``
+    is a raw cudaStream_t handle (default: torch's current stream).  Returns the ABI code."""
+    lib = load_library()
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream().cuda_stream
+    m = int(row_ptr.numel()) - 1
+    return lib.dpdlp_csr_spmv_noalloc(m, int(n), int(col_idx.numel()), C.c_void_p(row_ptr.data_ptr()),
+                                      C.c_void_p(col_idx.data_ptr()), C.c_void_p(val.data_ptr()),
+                                      C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                      C.c_void_p(stream) if stream else None)
