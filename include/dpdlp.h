@@ -148,10 +148,11 @@ int dpdlp_set_row_bounds(dpdlp_t* h, const double* lc, const double* uc);
  *   power_tol (1e-8), omega0 (0 = ||c|| / ||b_finite||), gamma (1.0), halpern (1),
  *   check_every (64, 1..1024), restart (1), beta_sufficient (0.2), beta_necessary (0.8),
  *   beta_artificial (0.36), pid (1), pid_kp (0.99), pid_ki (0.01), pid_kd (0.0),
- *   block_permute (1), perm_block (256), perm_seed (1), use_graph (1),
+ *   block_permute (1), perm_block (256), perm_seed (1), tile_nnz (0 = automatic: 8192, less
+ *   for small matrices; largest nonzeros per thread-block tile, 8..8192), use_graph (1),
  *   ptr_mode_device (0), resume (0: each solve starts from the start point; 1: continue
  *   from the current state), trace_capacity (4096).
- * Load-time keys (block_permute, perm_block, perm_seed) take effect at the next
+ * Load-time keys (block_permute, perm_block, perm_seed, tile_nnz) take effect at the next
  * dpdlp_load_lp.  Unknown key or out-of-range value: DPDLP_ERR_INVALID. */
 int dpdlp_set_param(dpdlp_t* h, const char* key, double v);
 

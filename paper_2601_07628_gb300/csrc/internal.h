@@ -9,18 +9,22 @@
 
 namespace pdhg {
 
-// Thread-block shape of every tiled SpMV kernel: 256 threads, each summing 8 consecutive
-// nonzeros, so one tile holds at most 2048 nonzeros (nonzero-aware partitioning of
-// Section 4.3, applied to thread blocks instead of devices).
+// Thread-block shape of every tiled SpMV kernel: 256 threads, each summing 32 consecutive
+// nonzeros (four batches of 8 loaded with 16-byte vector loads), so one tile holds at most
+// 8192 nonzeros and 768 rows (nonzero-aware partitioning of Section 4.3, applied to thread
+// blocks instead of devices).  Small matrices get smaller tiles so that every SM has work.
 constexpr int TPB = 256;
-constexpr int IPT = 8;
+constexpr int BATCH = 8;
+constexpr int NBATCH = 4;
+constexpr int IPT = BATCH * NBATCH;
 constexpr int TILE_NNZ = TPB * IPT;
+constexpr int MAX_TILE_ROWS = 768;
 constexpr int KMAX = 1024;  // largest check period (iterations per graph body)
 constexpr int NRED = 5;     // quantities per check reduction (rows and columns)
 
 // One tile of a row-major sparse matrix (CSR of A, or CSR of A^T for the column pass).
-// Short tile: whole rows [r0, r1) whose nonzeros [e0, e1) fit in TILE_NNZ; e0 is a
-// multiple of IPT.  Long tile: chunk `chunk` of `nchunks` of the single row r0 (r1 = r0+1)
+// Short tile: whole rows [r0, r1) (at most MAX_TILE_ROWS) whose nonzeros [e0, e1) fit in
+// TILE_NNZ; e0 is a multiple of BATCH.  Long tile: chunk `chunk` of `nchunks` of the single row r0 (r1 = r0+1)
 // that is longer than a tile; `slot` indexes the chunk-partial array (slot + chunk) and
 // `lrow` the per-row arrival counter.  slot < 0 marks a short tile.
 struct Tile {
@@ -28,7 +32,7 @@ struct Tile {
   int slot, lrow, chunk, nchunks;
 };
 
-// Host copy of one tiled orientation.  Every tile starts at an IPT-aligned offset: the
+// Host copy of one tiled orientation.  Every tile starts at a BATCH-aligned offset: the
 // padding between tiles is stored as explicit zero entries appended to the tile's last row
 // (value 0, column = that row's last column, or 0), so row pointers stay a plain CSR.
 struct HostTiled {
@@ -118,8 +122,10 @@ void transpose_csr(int rows, int cols, const std::vector<int64_t>& ptr,
                    std::vector<int64_t>& tptr, std::vector<int32_t>& tidx,
                    std::vector<double>& tval);
 // Tiles and padded arrays of one orientation.
+// tile_cap: largest tile in nonzeros (0 = automatic: TILE_NNZ, smaller for small matrices).
 void build_tiled(int rows, int cols, const std::vector<int64_t>& ptr,
-                 const std::vector<int32_t>& idx, const std::vector<double>& val, HostTiled& out);
+                 const std::vector<int32_t>& idx, const std::vector<double>& val, HostTiled& out,
+                 int tile_cap = 0);
 
 // ---------------------------------------------------------------- kernel launchers
 struct IterPlan {

@@ -1,7 +1,7 @@
 // sm_103a kernels of the PDHG hot path.
 //
 //  tiled_spmv_kernel  one thread block per tile of a row-major sparse matrix (CSR of A for
-//                     A x, CSR of A^T -- the CSC copy -- for A^T y).  Each thread sums 8
+//                     A x, CSR of A^T -- the CSC copy -- for A^T y).  Each thread sums 32
 //                     consecutive nonzeros in stored order with one FMA per nonzero (FP64
 //                     issue slots are scarce on GB300, so no shuffle trees on the common
 //                     path); rows that cross thread boundaries are finished by their owner
@@ -57,6 +57,11 @@ __device__ __forceinline__ int4 ld_stream(const int4* p, unsigned long long pol)
   return r;
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (address 16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Deterministic block sum (fixed xor-butterfly inside warps, fixed order across warps).
 // The result is valid in thread 0.  `buf` holds TPB/32 doubles.
 __device__ __forceinline__ double block_sum(double v, double* buf) {
@@ -76,15 +81,36 @@ __device__ __forceinline__ double block_sum(double v, double* buf) {
 }
 
 // ---------------------------------------------------------------- epilogues
+// An epilogue turns the row sums of one tile into outputs.  `Stage` is the shared-memory
+// copy of the per-row input vectors, fetched with cp.async at kernel start so that their
+// DRAM latency overlaps the SpMV; `apply` works from it, `apply_direct` (rows longer than a
+// tile, finished by one thread) reads global memory.
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 struct StoreEpi1 {
   double* out0;
+  struct Stage {};
   __device__ bool begin() { return true; }
-  __device__ void apply(int r, const double* s) { out0[r] = s[0]; }
+  __device__ void prefetch(int, int, Stage&) {}
+  __device__ void apply(int, int r, const double* s, const Stage&) { out0[r] = s[0]; }
+  __device__ void apply_direct(int r, const double* s) { out0[r] = s[0]; }
 };
 struct StoreEpi2 {
   double *out0, *out1;
+  struct Stage {};
   __device__ bool begin() { return true; }
-  __device__ void apply(int r, const double* s) {
+  __device__ void prefetch(int, int, Stage&) {}
+  __device__ void apply(int, int r, const double* s, const Stage&) {
+    out0[r] = s[0];
+    out1[r] = s[1];
+  }
+  __device__ void apply_direct(int r, const double* s) {
     out0[r] = s[0];
     out1[r] = s[1];
   }
@@ -92,7 +118,7 @@ struct StoreEpi2 {
 
 // Per-iteration scalars read from device memory by the fused epilogues.
 struct IterScalars {
-  double step, inv_step, w1, w0, gamma;
+  double step, inv_step, two_step, w1, w0, gamma;
   int check, halpern, gamma_one;
 };
 
@@ -107,6 +133,7 @@ __device__ __forceinline__ bool load_iter(const DevScalars* sc, IterPlan p, bool
   }
   o.step = primal ? sc->tau : sc->sigma;
   o.inv_step = sc->inv_sigma;
+  o.two_step = 2.0 * o.step;
   o.w1 = sc->w1[p.i];
   o.w0 = sc->w0[p.i];
   o.gamma = sc->gamma;
@@ -117,7 +144,8 @@ __device__ __forceinline__ bool load_iter(const DevScalars* sc, IterPlan p, bool
 
 // Primal step per column j, given s = (A^T y)_j:
 //   x^ = proj_X(x - tau (c - s)),  x_bar = 2 x^ - x,
-//   Halpern: x <- w1 ((1+gamma) x^ - gamma x) + w0 x0   (regular iteration),
+//   Halpern: x <- w1 ((1+gamma) x^ - gamma x) + w0 x0   (with gamma = 1 the reflected point
+//   is x_bar itself), regular iterations;
 //   check iteration: keep x = x^k, store x^ and dx = x^k - x^.
 struct PrimalEpi {
   const DevScalars* sc;
@@ -125,11 +153,24 @@ struct PrimalEpi {
   const double *c, *lv, *uv, *x0;
   double *x, *xbar, *xh, *dx;
   IterScalars q;
+  struct Stage {
+    double c[MAX_TILE_ROWS], lv[MAX_TILE_ROWS], uv[MAX_TILE_ROWS], x[MAX_TILE_ROWS],
+        x0[MAX_TILE_ROWS];
+  };
   __device__ bool begin() { return load_iter(sc, plan, true, q); }
-  __device__ void apply(int j, const double* s) {
-    const double g = c[j] - s[0];
-    const double xj = x[j];
-    const double xhj = clampd(fma(-q.step, g, xj), lv[j], uv[j]);
+  __device__ void prefetch(int r0, int nrows, Stage& st) {
+    for (int r = threadIdx.x; r < nrows; r += TPB) {
+      cp_async8(&st.c[r], c + r0 + r);
+      cp_async8(&st.lv[r], lv + r0 + r);
+      cp_async8(&st.uv[r], uv + r0 + r);
+      cp_async8(&st.x[r], x + r0 + r);
+      if (!q.check && q.halpern) cp_async8(&st.x0[r], x0 + r0 + r);
+    }
+    cp_async_commit();
+  }
+  __device__ void step(int j, double s, double cj, double lvj, double uvj, double xj,
+                       const double* x0p) {
+    const double xhj = clampd(fma(-q.step, cj - s, xj), lvj, uvj);
     const double xb = fma(2.0, xhj, -xj);
     xbar[j] = xb;
     if (q.check) {
@@ -137,36 +178,61 @@ struct PrimalEpi {
       dx[j] = xj - xhj;
     } else if (q.halpern) {
       const double r = q.gamma_one ? xb : fma(1.0 + q.gamma, xhj, -q.gamma * xj);
-      x[j] = fma(q.w1, r, q.w0 * x0[j]);
+      x[j] = fma(q.w1, r, q.w0 * *x0p);
     } else {
       x[j] = xhj;
     }
   }
+  __device__ void apply(int lr, int j, const double* s, const Stage& st) {
+    step(j, s[0], st.c[lr], st.lv[lr], st.uv[lr], st.x[lr], &st.x0[lr]);
+  }
+  __device__ void apply_direct(int j, const double* s) { step(j, s[0], c[j], lv[j], uv[j], x[j], x0 + j); }
 };
 
 // Dual step per row i, given z = (A x_bar)_i:
-//   w = y / sigma - z,  y^ = sigma (w - proj_{-S}(w)),  -S_i = [lo_i, hi_i] = [-uc_i, -lc_i],
-//   Halpern on y as for x; check iteration: keep y = y^k, store y^.
+//   w = y / sigma - z,  d = w - proj_{-S}(w),  y^ = sigma d,  -S_i = [lo_i, hi_i] = [-uc_i, -lc_i];
+//   Halpern: y <- w1 ((1+gamma) y^ - gamma y) + w0 y0, with gamma = 1 evaluated as
+//   w1 (2 sigma d - y) + w0 y0; check iteration: keep y = y^k, store y^.
 struct DualEpi {
   const DevScalars* sc;
   IterPlan plan;
   const double *lo, *hi, *y0;
   double *y, *yh;
   IterScalars q;
+  struct Stage {
+    double lo[MAX_TILE_ROWS], hi[MAX_TILE_ROWS], y[MAX_TILE_ROWS], y0[MAX_TILE_ROWS];
+  };
   __device__ bool begin() { return load_iter(sc, plan, false, q); }
-  __device__ void apply(int i, const double* s) {
-    const double yi = y[i];
-    const double w = fma(yi, q.inv_step, -s[0]);
-    const double yhi = q.step * (w - clampd(w, lo[i], hi[i]));
+  __device__ void prefetch(int r0, int nrows, Stage& st) {
+    for (int r = threadIdx.x; r < nrows; r += TPB) {
+      cp_async8(&st.lo[r], lo + r0 + r);
+      cp_async8(&st.hi[r], hi + r0 + r);
+      cp_async8(&st.y[r], y + r0 + r);
+      if (!q.check && q.halpern) cp_async8(&st.y0[r], y0 + r0 + r);
+    }
+    cp_async_commit();
+  }
+  __device__ void step(int i, double s, double loi, double hii, double yi, const double* y0p) {
+    const double w = fma(yi, q.inv_step, -s);
+    const double d = w - clampd(w, loi, hii);
     if (q.check) {
-      yh[i] = yhi;
+      yh[i] = q.step * d;
     } else if (q.halpern) {
-      const double r = q.gamma_one ? fma(2.0, yhi, -yi) : fma(1.0 + q.gamma, yhi, -q.gamma * yi);
-      y[i] = fma(q.w1, r, q.w0 * y0[i]);
+      double r;
+      if (q.gamma_one) {
+        r = fma(q.two_step, d, -yi);
+      } else {
+        r = fma(1.0 + q.gamma, q.step * d, -q.gamma * yi);
+      }
+      y[i] = fma(q.w1, r, q.w0 * *y0p);
     } else {
-      y[i] = yhi;
+      y[i] = q.step * d;
     }
   }
+  __device__ void apply(int lr, int i, const double* s, const Stage& st) {
+    step(i, s[0], st.lo[lr], st.hi[lr], st.y[lr], &st.y0[lr]);
+  }
+  __device__ void apply_direct(int i, const double* s) { step(i, s[0], lo[i], hi[i], y[i], y0 + i); }
 };
 
 // ---------------------------------------------------------------- tiled SpMV
@@ -175,59 +241,74 @@ struct GatherVecs {
   const double* x[NV];
 };
 
+__device__ __forceinline__ void load_batch(const DevTiled& M, int at, double (&v)[BATCH],
+                                           int (&c)[BATCH], unsigned long long pol) {
+  const double2* vp = reinterpret_cast<const double2*>(M.val + at);
+  const int4* ip = reinterpret_cast<const int4*>(M.idx + at);
+#pragma unroll
+  for (int q = 0; q < BATCH / 2; ++q) {
+    const double2 d = ld_stream(vp + q, pol);
+    v[2 * q] = d.x;
+    v[2 * q + 1] = d.y;
+  }
+#pragma unroll
+  for (int q = 0; q < BATCH / 4; ++q) {
+    const int4 d = ld_stream(ip + q, pol);
+    c[4 * q] = d.x;
+    c[4 * q + 1] = d.y;
+    c[4 * q + 2] = d.z;
+    c[4 * q + 3] = d.w;
+  }
+}
+
+// One thread block per tile.  Each thread owns the 32 consecutive nonzeros
+// [e0 + 32 tid, e0 + 32 tid + 32) of its tile, loaded in four batches of 8 (the next batch's
+// loads are issued before the current batch's gathers), and sums them in stored order with
+// one FMA per nonzero.  A row that starts in a thread's range is owned by that thread; a row
+// that continues into the next threads is finished by its owner from their head partials,
+// in thread order, after a barrier.
 template <int NV, class Epi>
-__global__ void __launch_bounds__(TPB) tiled_spmv_kernel(DevTiled M, GatherVecs<NV> g, Epi epi_in) {
-  __shared__ int srp[TPB + 1];
-  __shared__ double rsum[NV][TPB];
+__global__ void __launch_bounds__(TPB, 3) tiled_spmv_kernel(DevTiled M, GatherVecs<NV> g, Epi epi_in) {
+  __shared__ int srp[MAX_TILE_ROWS + 1];
+  __shared__ double rsum[NV][MAX_TILE_ROWS];
   __shared__ double head[NV][TPB];
   __shared__ double red[TPB / 32];
+  __shared__ typename Epi::Stage stage;
 
   Epi epi = epi_in;
   if (!epi.begin()) return;  // uniform over the launch
 
   const Tile t = M.tiles[blockIdx.x];
   const int tid = threadIdx.x;
-  const int base = t.e0 + tid * IPT;  // IPT-aligned: 16-byte vector loads below
+  const int base = t.e0 + tid * IPT;  // BATCH-aligned: 16-byte vector loads
   const int nvalid = min(IPT, max(0, t.e1 - base));
+  const bool shared_tile = (t.slot == -1);
+  const int nrows = t.r1 - t.r0;
+  if (shared_tile) epi.prefetch(t.r0, nrows, stage);
 
+  // Ask for the whole tile at once (values and indices, one bulk L2 prefetch each) so its
+  // DRAM traffic is in flight before the threads' own loads reach it.
+  if (tid == 0 && t.e1 > t.e0) {
+    prefetch_l2(M.val + t.e0, (unsigned)(t.e1 - t.e0) * 8u);
+    prefetch_l2(M.idx + t.e0, (unsigned)(t.e1 - t.e0) * 4u);
+  }
   const unsigned long long pol = l2_evict_first_policy();
-  double v[IPT];
-  int ci[IPT];
-  {
-    const double2* vp = reinterpret_cast<const double2*>(M.val + base);
-    const int4* ip = reinterpret_cast<const int4*>(M.idx + base);
-#pragma unroll
-    for (int q = 0; q < IPT / 2; ++q) {
-      const double2 d = ld_stream(vp + q, pol);
-      v[2 * q] = d.x;
-      v[2 * q + 1] = d.y;
-    }
-#pragma unroll
-    for (int q = 0; q < IPT / 4; ++q) {
-      const int4 d = ld_stream(ip + q, pol);
-      ci[4 * q] = d.x;
-      ci[4 * q + 1] = d.y;
-      ci[4 * q + 2] = d.z;
-      ci[4 * q + 3] = d.w;
-    }
-  }
-  double xv[NV][IPT];
-#pragma unroll
-  for (int j = 0; j < IPT; ++j) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) xv[k][j] = (j < nvalid) ? __ldg(g.x[k] + ci[j]) : 0.0;
-  }
+  double va[BATCH];
+  int ca[BATCH];
+  if (nvalid > 0) load_batch(M, base, va, ca, pol);
 
-  if (t.slot == -1) {
-    // ---- shared tile: whole rows [r0, r1)
-    const int nrows = t.r1 - t.r0;
-    for (int r = tid; r <= nrows; r += TPB) srp[r] = M.ptr[t.r0 + r];
-    if (tid < nrows) {
+  double acc[NV];
 #pragma unroll
-      for (int k = 0; k < NV; ++k) rsum[k][tid] = 0.0;
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+
+  if (shared_tile) {
+    for (int r = tid; r <= nrows; r += TPB) srp[r] = M.ptr[t.r0 + r];
+    for (int r = tid; r < nrows; r += TPB) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) rsum[k][r] = 0.0;
     }
     __syncthreads();
-    int open_row = -1;  // a row this thread started that continues past its items
+    int open_row = -1;  // a row this thread owns that continues past its items
     if (nvalid > 0) {
       int lo = 0, hi = nrows - 1;  // the row holding item `base`: last r with srp[r] <= base
       while (lo < hi) {
@@ -237,25 +318,42 @@ __global__ void __launch_bounds__(TPB) tiled_spmv_kernel(DevTiled M, GatherVecs<
       int r = lo;
       bool owner = srp[r] >= base;
       int rend = srp[r + 1];
-      double acc[NV];
 #pragma unroll
-      for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+      for (int b = 0; b < NBATCH; ++b) {
+        double vb[BATCH];
+        int cb[BATCH];
+        const bool more = (b + 1 < NBATCH) && ((b + 1) * BATCH < nvalid);
+        if (more) load_batch(M, base + (b + 1) * BATCH, vb, cb, pol);
+        double xv[NV][BATCH];
 #pragma unroll
-      for (int j = 0; j < IPT; ++j) {
-        if (j < nvalid) {
-          const int e = base + j;
-          while (e >= rend) {  // row r ends before item e
+        for (int j = 0; j < BATCH; ++j) {
 #pragma unroll
-            for (int k = 0; k < NV; ++k) {
-              if (owner) rsum[k][r] = acc[k]; else head[k][tid] = acc[k];
-              acc[k] = 0.0;
+          for (int k = 0; k < NV; ++k) xv[k][j] = (b * BATCH + j < nvalid) ? __ldg(g.x[k] + ca[j]) : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < BATCH; ++j) {
+          if (b * BATCH + j < nvalid) {
+            const int e = base + b * BATCH + j;
+            while (e >= rend) {  // row r ends before item e
+#pragma unroll
+              for (int k = 0; k < NV; ++k) {
+                if (owner) rsum[k][r] = acc[k]; else head[k][tid] = acc[k];
+                acc[k] = 0.0;
+              }
+              ++r;
+              rend = srp[r + 1];
+              owner = true;
             }
-            ++r;
-            rend = srp[r + 1];
-            owner = true;
-          }
 #pragma unroll
-          for (int k = 0; k < NV; ++k) acc[k] = fma(v[j], xv[k][j], acc[k]);
+            for (int k = 0; k < NV; ++k) acc[k] = fma(va[j], xv[k][j], acc[k]);
+          }
+        }
+        if (more) {
+#pragma unroll
+          for (int j = 0; j < BATCH; ++j) {
+            va[j] = vb[j];
+            ca[j] = cb[j];
+          }
         }
       }
 #pragma unroll
@@ -274,29 +372,46 @@ __global__ void __launch_bounds__(TPB) tiled_spmv_kernel(DevTiled M, GatherVecs<
         rsum[k][open_row] = s;
       }
     }
+    cp_async_wait_all();
     __syncthreads();
-    if (tid < nrows) {
+    for (int r = tid; r < nrows; r += TPB) {
       double s[NV];
 #pragma unroll
-      for (int k = 0; k < NV; ++k) s[k] = rsum[k][tid];
-      epi.apply(t.r0 + tid, s);
+      for (int k = 0; k < NV; ++k) s[k] = rsum[k][r];
+      epi.apply(r, t.r0 + r, s, stage);
     }
     return;
   }
 
   // ---- a tile of one long row: block sum, then either finish the row (single chunk) or
   // publish the chunk sum; the last chunk to arrive adds all chunks in chunk order.
+#pragma unroll
+  for (int b = 0; b < NBATCH; ++b) {
+    double vb[BATCH];
+    int cb[BATCH];
+    const bool more = (b + 1 < NBATCH) && ((b + 1) * BATCH < nvalid);
+    if (more) load_batch(M, base + (b + 1) * BATCH, vb, cb, pol);
+#pragma unroll
+    for (int j = 0; j < BATCH; ++j) {
+      if (b * BATCH + j < nvalid) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = fma(va[j], __ldg(g.x[k] + ca[j]), acc[k]);
+      }
+    }
+    if (more) {
+#pragma unroll
+      for (int j = 0; j < BATCH; ++j) {
+        va[j] = vb[j];
+        ca[j] = cb[j];
+      }
+    }
+  }
   double tot[NV];
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double a = 0.0;
-#pragma unroll
-    for (int j = 0; j < IPT; ++j) a = fma(v[j], xv[k][j], a);  // zeros beyond nvalid
-    tot[k] = block_sum(a, red);
-  }
+  for (int k = 0; k < NV; ++k) tot[k] = block_sum(acc[k], red);
   if (tid != 0) return;
   if (t.slot == -2) {
-    epi.apply(t.r0, tot);
+    epi.apply_direct(t.r0, tot);
     return;
   }
 #pragma unroll
@@ -313,7 +428,7 @@ __global__ void __launch_bounds__(TPB) tiled_spmv_kernel(DevTiled M, GatherVecs<
       s[k] = a;
     }
     M.lr_count[t.lrow] = 0;  // ready for the next launch
-    epi.apply(t.r0, s);
+    epi.apply_direct(t.r0, s);
   }
 }
 
@@ -327,7 +442,6 @@ static cudaError_t launch_tiled(const DevTiled& M, GatherVecs<NV> g, Epi epi, cu
 cudaError_t launch_primal(const DevTiled& csc, const DevVecs& v, const DevScalars* sc,
                           IterPlan p, cudaStream_t s) {
   PrimalEpi e{sc, p, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, {}};
-  if (csc.ntiles == 0) return cudaSuccess;
   GatherVecs<1> g{{v.y}};
   return launch_tiled<1>(csc, g, e, s);
 }

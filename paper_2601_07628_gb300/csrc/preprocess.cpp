@@ -19,7 +19,7 @@ namespace pdhg {
 
 // Rows longer than this get their own tile(s) and a block-wide reduction instead of the
 // per-thread walk, which bounds the serial fix-up chain of a shared tile to SOLO_NNZ/IPT.
-constexpr int SOLO_NNZ = 512;
+constexpr int SOLO_NNZ = 1024;
 
 std::string validate_csr(int rows, int cols, const int64_t* ptr, const int32_t* idx,
                          const double* val) {
@@ -118,27 +118,34 @@ static inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * 
 
 void build_tiled(int rows, int cols, const std::vector<int64_t>& ptr,
                  const std::vector<int32_t>& idx, const std::vector<double>& val,
-                 HostTiled& out) {
+                 HostTiled& out, int tile_cap) {
   out.rows = rows;
   out.cols = cols;
   out.tiles.clear();
   out.long_rows = 0;
   out.long_chunks = 0;
+  // Tile capacity: TILE_NNZ, or less when the matrix is small, so that there are about
+  // eight tiles per SM (152 SMs) before tiles shrink below 512 nonzeros.
+  const int64_t nnz = ptr[rows];
+  const int64_t cap = tile_cap > 0
+      ? std::min<int64_t>(TILE_NNZ, round_up(tile_cap, BATCH))
+      : std::min<int64_t>(TILE_NNZ, std::max<int64_t>(512, round_up((nnz + 1215) / 1216, BATCH)));
+  const int64_t solo = std::min<int64_t>(SOLO_NNZ, cap);
   // Pass 1: tile plan over the original offsets.
   struct Plan { int r0, r1; bool solo; };
   std::vector<Plan> plan;
   for (int r = 0; r < rows;) {
     const int64_t L = ptr[r + 1] - ptr[r];
-    if (L > SOLO_NNZ) {
+    if (L > solo) {
       plan.push_back({r, r + 1, true});
       ++r;
       continue;
     }
     int r1 = r;
     int64_t nz = 0;
-    while (r1 < rows && r1 - r < TPB) {
+    while (r1 < rows && r1 - r < MAX_TILE_ROWS) {
       const int64_t Lr = ptr[r1 + 1] - ptr[r1];
-      if (Lr > SOLO_NNZ || nz + Lr > TILE_NNZ) break;
+      if (Lr > solo || nz + Lr > cap) break;
       nz += Lr;
       ++r1;
     }
@@ -147,7 +154,7 @@ void build_tiled(int rows, int cols, const std::vector<int64_t>& ptr,
   }
   // Pass 2: padded arrays and tile descriptors.
   int64_t padded = 0;
-  for (const Plan& p : plan) padded += round_up(ptr[p.r1] - ptr[p.r0], IPT);
+  for (const Plan& p : plan) padded += round_up(ptr[p.r1] - ptr[p.r0], BATCH);
   out.nnz_padded = padded;
   out.ptr.assign(rows + 1, 0);
   out.idx.assign(padded + TILE_NNZ, 0);
@@ -164,8 +171,8 @@ void build_tiled(int rows, int cols, const std::vector<int64_t>& ptr,
       }
       pos += L;
     }
-    // explicit zeros appended to the tile's last row keep the next tile IPT-aligned
-    const int64_t end = e0 + round_up(pos - e0, IPT);
+    // explicit zeros appended to the tile's last row keep the next tile BATCH-aligned
+    const int64_t end = e0 + round_up(pos - e0, BATCH);
     const int32_t pad_col = pos > e0 ? out.idx[pos - 1] : 0;
     for (; pos < end; ++pos) {
       out.idx[pos] = pad_col;

@@ -48,6 +48,7 @@ std::map<std::string, Param> default_params() {
       {"block_permute", {1, 0, 1, true}},
       {"perm_block", {256, 1, 1 << 30, true}},
       {"perm_seed", {1, 0, 9007199254740992.0, true}},
+      {"tile_nnz", {0, 0, TILE_NNZ, true}},
       {"use_graph", {1, 0, 1, true}},
       {"ptr_mode_device", {0, 0, 1, true}},
       {"resume", {0, 0, 1, true}},
@@ -491,8 +492,9 @@ int dpdlp_load_lp(dpdlp_t* h, int32_t n, int32_t m, const double* c, const int64
   permute_csr(m, n, row_ptr, col_idx, val, h->prow, h->pcol, pptr, pidx, pval);
   transpose_csr(m, n, pptr, pidx, pval, tptr, tidx, tval);
   HostTiled Hr, Hc;
-  build_tiled(m, n, pptr, pidx, pval, Hr);
-  build_tiled(n, m, tptr, tidx, tval, Hc);
+  const int tile_cap = (int)h->P("tile_nnz");
+  build_tiled(m, n, pptr, pidx, pval, Hr, tile_cap);
+  build_tiled(n, m, tptr, tidx, tval, Hc, tile_cap);
   std::vector<int64_t>().swap(pptr);
   std::vector<int32_t>().swap(pidx);
   std::vector<double>().swap(pval);
