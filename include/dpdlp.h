@@ -99,9 +99,9 @@ typedef struct dpdlp_scalar_state {
 typedef struct dpdlp_info {
   int32_t n, m;
   int64_t nnz;
-  int64_t nnz_padded_csr, nnz_padded_csc;
-  int32_t tiles_csr, tiles_csc;
-  int32_t long_rows, long_cols;
+  int64_t nnz_padded_csr, nnz_padded_csc; /* stored entries of each packed copy, padding included */
+  int32_t tiles_csr, tiles_csc;           /* warp slots (32 lanes x 32 stored entries) of each copy */
+  int32_t long_rows, long_cols;           /* rows / columns longer than one lane (32 nonzeros) */
   int64_t device_bytes;
   double preprocess_ms;
 } dpdlp_info_t;
@@ -131,9 +131,10 @@ int dpdlp_set_stream(dpdlp_t* h, void* cuda_stream);
  *                       2: lc = b, uc = +inf ('>=').  Both may be NULL (rows free until
  *                       dpdlp_set_row_bounds).
  *   lv[n], uv[n]        variable bounds, -INFINITY / +INFINITY allowed, lv <= uv
- * Validates the input (DPDLP_ERR_INVALID on failure), then on the host builds the CSC copy
- * of A, the optional block-wise random permutation (Section 4.2) and the nonzero-balanced
- * tiles (Section 4.3), and copies everything to the device.  Replaces any LP loaded before
+ * Validates the input (DPDLP_ERR_INVALID on failure; n and m must be below 2^30), then on
+ * the host applies the optional block-wise random permutation (Section 4.2), builds the CSC
+ * copy of A, packs the rows of both copies into warp lanes (nonzero-aware partitioning,
+ * Section 4.3, at lane granularity), and copies everything to the device.  Replaces any LP loaded before
  * and resets the solver state. */
 int dpdlp_load_lp(dpdlp_t* h, int32_t n, int32_t m, const double* c, const int64_t* row_ptr,
                   const int32_t* col_idx, const double* val, const double* b,
@@ -148,11 +149,10 @@ int dpdlp_set_row_bounds(dpdlp_t* h, const double* lc, const double* uc);
  *   power_tol (1e-8), omega0 (0 = ||c|| / ||b_finite||), gamma (1.0), halpern (1),
  *   check_every (64, 1..1024), restart (1), beta_sufficient (0.2), beta_necessary (0.8),
  *   beta_artificial (0.36), pid (1), pid_kp (0.99), pid_ki (0.01), pid_kd (0.0),
- *   block_permute (1), perm_block (256), perm_seed (1), tile_nnz (0 = automatic: 8192, less
- *   for small matrices; largest nonzeros per thread-block tile, 8..8192), use_graph (1),
+ *   block_permute (1), perm_block (256), perm_seed (1), use_graph (1),
  *   ptr_mode_device (0), resume (0: each solve starts from the start point; 1: continue
  *   from the current state), trace_capacity (4096).
- * Load-time keys (block_permute, perm_block, perm_seed, tile_nnz) take effect at the next
+ * Load-time keys (block_permute, perm_block, perm_seed) take effect at the next
  * dpdlp_load_lp.  Unknown key or out-of-range value: DPDLP_ERR_INVALID. */
 int dpdlp_set_param(dpdlp_t* h, const char* key, double v);
 

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdpdlp.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "solver.cu", "preprocess.cpp", "noalloc.cu"]
+SOURCES = ["kernels.cu", "solver.cu", "preprocess.cpp", "packing.cpp", "noalloc.cu"]
 
 
 def _nvcc() -> str:

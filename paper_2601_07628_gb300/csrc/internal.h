@@ -9,54 +9,91 @@
 
 namespace pdhg {
 
-// Thread-block shape of every tiled SpMV kernel: 256 threads, each summing 32 consecutive
-// nonzeros (four batches of 8 loaded with 16-byte vector loads), so one tile holds at most
-// 8192 nonzeros and 768 rows (nonzero-aware partitioning of Section 4.3, applied to thread
-// blocks instead of devices).  Small matrices get smaller tiles so that every SM has work.
+// ---------------------------------------------------------------- packed sparse layout
+// Both products (A x_bar over rows of A, A^T y over rows of A^T = columns of A) use one
+// layout.  The rows of the matrix are packed, on the host, into warp lanes: a lane holds
+// at most LANE_ITEMS nonzeros, made of whole short rows (at most LANE_ITEMS nonzeros) and
+// pieces of long rows; 32 lanes form a slot that one warp processes.  Every lane sums its
+// own rows sequentially, one FMA per stored nonzero, so rows never cross lanes, warps or
+// blocks (the nonzero-aware partitioning of Section 4.3 taken down to the lane).  Pieces
+// of long rows are finished by a second, lane-per-row pass that adds them in piece order.
+constexpr int LANES = 32;
+constexpr int LANE_ITEMS = 32;
+constexpr int SLOT_ITEMS = LANES * LANE_ITEMS;
+constexpr int MAX_SLOT_ROWS = 128;  // short rows per slot (shared-memory row sums)
+#ifndef DPDLP_PK_WARPS
+#define DPDLP_PK_WARPS 4
+#endif
+constexpr int PK_WARPS = DPDLP_PK_WARPS;  // slots per thread block of the packed kernels
+constexpr int PK_TPB = PK_WARPS * LANES;
+constexpr uint32_t END_BIT = 0x80000000u;    // last stored nonzero of a row or piece
+constexpr uint32_t PIECE_BIT = 0x40000000u;  // ... and that segment is a long-row piece
+constexpr uint32_t IDX_MASK = 0x3FFFFFFFu;   // column index (< 2^30)
+
+// Long rows with more pieces than these get a thread block / a warp of the long-row pass.
+constexpr int LONG_BLOCK_PIECES = 256;
+constexpr int LONG_WARP_PIECES = 32;
+
+// Thread-block size of the element-wise and reduction kernels.
 constexpr int TPB = 256;
-constexpr int BATCH = 8;
-constexpr int NBATCH = 4;
-constexpr int IPT = BATCH * NBATCH;
-constexpr int TILE_NNZ = TPB * IPT;
-constexpr int MAX_TILE_ROWS = 768;
 constexpr int KMAX = 1024;  // largest check period (iterations per graph body)
 constexpr int NRED = 5;     // quantities per check reduction (rows and columns)
 
-// One tile of a row-major sparse matrix (CSR of A, or CSR of A^T for the column pass).
-// Short tile: whole rows [r0, r1) (at most MAX_TILE_ROWS) whose nonzeros [e0, e1) fit in
-// TILE_NNZ; e0 is a multiple of BATCH.  Long tile: chunk `chunk` of `nchunks` of the single row r0 (r1 = r0+1)
-// that is longer than a tile; `slot` indexes the chunk-partial array (slot + chunk) and
-// `lrow` the per-row arrival counter.  slot < 0 marks a short tile.
-struct Tile {
-  int r0, r1, e0, e1;
-  int slot, lrow, chunk, nchunks;
+// Slot s: its short rows have the new indices [row_base, row_base + nrows).
+struct SlotDesc {
+  int row_base, nrows;
+};
+// Lane l of a slot: slot-local index of its first short row, global id of its first piece.
+struct LaneMeta {
+  int row_local, piece_base;
 };
 
-// Host copy of one tiled orientation.  Every tile starts at a BATCH-aligned offset: the
-// padding between tiles is stored as explicit zero entries appended to the tile's last row
-// (value 0, column = that row's last column, or 0), so row pointers stay a plain CSR.
-struct HostTiled {
+// Host copy of one packed orientation.  Item (lane l, position p) of slot s is stored at
+// val[s*SLOT_ITEMS + ((p/2)*LANES + l)*2 + p%2] and idx[s*SLOT_ITEMS + ((p/4)*LANES + l)*4 + p%4],
+// so a warp reads a slot with 16-byte loads that cover 512 contiguous bytes.
+struct HostPacked {
   int rows = 0, cols = 0;
-  std::vector<int32_t> ptr;  // rows + 1, offsets into the padded arrays
-  std::vector<int32_t> idx;  // padded length + TILE_NNZ tail
+  int nslots = 0, nshort = 0, nlong = 0, npieces = 0;
+  int nlong_block = 0, nlong_warp = 0;  // leading long rows finished by a block / a warp
   std::vector<double> val;
-  std::vector<Tile> tiles;
-  int long_rows = 0;     // rows split over several tiles
-  int long_chunks = 0;   // total chunks of those rows
-  int64_t nnz_padded = 0;
+  std::vector<uint32_t> idx;
+  std::vector<SlotDesc> slots;
+  std::vector<LaneMeta> lanes;
+  std::vector<int32_t> long_row;    // new index of each long row
+  std::vector<int32_t> long_ptr;    // nlong + 1
+  std::vector<int32_t> long_piece;  // piece ids of each long row, in row order
+  int64_t stored = 0;               // nslots * SLOT_ITEMS
 };
 
-// Device copy of one tiled orientation plus the scratch of its long-row combine.
-struct DevTiled {
-  int rows = 0, cols = 0;
-  int32_t* ptr = nullptr;
-  int32_t* idx = nullptr;
-  double* val = nullptr;
-  Tile* tiles = nullptr;
-  int ntiles = 0;
-  double* lr_partial = nullptr;  // 2 * long_chunks (room for two vectors)
-  unsigned* lr_count = nullptr;  // long_rows arrival counters, zero between launches
-  int long_rows = 0, long_chunks = 0;
+// Device copy of one packed orientation plus the per-piece partial sums.
+struct DevPacked {
+  int rows = 0, cols = 0, nslots = 0, nlong = 0, npieces = 0;
+  int nlong_block = 0, nlong_warp = 0;
+  const double* val = nullptr;
+  const uint32_t* idx = nullptr;
+  const SlotDesc* slots = nullptr;
+  const LaneMeta* lanes = nullptr;
+  const int32_t* long_row = nullptr;
+  const int32_t* long_ptr = nullptr;
+  const int32_t* long_piece = nullptr;
+  double* piece_sum = nullptr;  // 2 * npieces (room for two vectors)
+};
+
+// Row order chosen by the packing of one orientation (pre-order = after the block
+// permutation): new_of_old[r] and old_of_new[r'].
+struct PackPlan {
+  std::vector<int32_t> new_of_old, old_of_new;
+  // lane contents: segments (pre-order row, first item, count, piece id or -1)
+  struct Seg {
+    int32_t row, first, count, piece;
+  };
+  std::vector<int32_t> lane_ptr;  // per lane, into segs
+  std::vector<Seg> segs;
+  std::vector<SlotDesc> slots;
+  std::vector<int32_t> slot_lanes;  // LANES entries per slot: lane index or -1 (empty lane)
+  int nshort = 0, nlong = 0, npieces = 0;
+  std::vector<int32_t> long_rows;   // pre-order index of each long row, longest first
+  std::vector<int32_t> long_ptr, long_piece;
 };
 
 // Solver scalars resident in device memory.  The control kernel updates them at every
@@ -86,7 +123,7 @@ struct DevScalars {
   double w1[KMAX], w0[KMAX];  // Halpern weights (k+1)/(k+2), 1/(k+2) of each body iteration
 };
 
-// Device vectors of one LP (internal, permuted index order).
+// Device vectors of one LP (internal, packed index order).
 struct DevVecs {
   int n = 0, m = 0;
   double *c = nullptr, *lv = nullptr, *uv = nullptr;  // [n]
@@ -121,11 +158,15 @@ void transpose_csr(int rows, int cols, const std::vector<int64_t>& ptr,
                    const std::vector<int32_t>& idx, const std::vector<double>& val,
                    std::vector<int64_t>& tptr, std::vector<int32_t>& tidx,
                    std::vector<double>& tval);
-// Tiles and padded arrays of one orientation.
-// tile_cap: largest tile in nonzeros (0 = automatic: TILE_NNZ, smaller for small matrices).
-void build_tiled(int rows, int cols, const std::vector<int64_t>& ptr,
-                 const std::vector<int32_t>& idx, const std::vector<double>& val, HostTiled& out,
-                 int tile_cap = 0);
+// Pack the rows of one orientation into lanes and slots (best-fit decreasing on row
+// lengths); decides the new row order.
+void plan_packing(int rows, const std::vector<int64_t>& ptr, PackPlan& plan);
+// Stored arrays of one orientation from its plan; column indices are mapped through the
+// other orientation's new_of_old.
+void build_packed(int rows, int cols, const std::vector<int64_t>& ptr,
+                  const std::vector<int32_t>& idx, const std::vector<double>& val,
+                  const PackPlan& plan, const std::vector<int32_t>& col_new_of_old,
+                  HostPacked& out);
 
 // ---------------------------------------------------------------- kernel launchers
 struct IterPlan {
@@ -133,14 +174,14 @@ struct IterPlan {
   int force_regular;  // 1: run as a regular iteration regardless of the scalars (timing)
 };
 
-cudaError_t launch_primal(const DevTiled& csc, const DevVecs& v, const DevScalars* sc,
+cudaError_t launch_primal(const DevPacked& csc, const DevVecs& v, const DevScalars* sc,
                           IterPlan p, cudaStream_t s);
-cudaError_t launch_dual(const DevTiled& csr, const DevVecs& v, const DevScalars* sc,
+cudaError_t launch_dual(const DevPacked& csr, const DevVecs& v, const DevScalars* sc,
                         IterPlan p, cudaStream_t s);
-// out0 = M x0 (and out1 = M x1 when x1 != nullptr) for one tiled orientation M.
-cudaError_t launch_spmv(const DevTiled& M, const double* x0, const double* x1, double* out0,
+// out0 = M x0 (and out1 = M x1 when x1 != nullptr) for one packed orientation M.
+cudaError_t launch_spmv(const DevPacked& M, const double* x0, const double* x1, double* out0,
                         double* out1, cudaStream_t s);
-cudaError_t launch_check(const DevTiled& csr, const DevTiled& csc, const DevVecs& v,
+cudaError_t launch_check(const DevPacked& csr, const DevPacked& csc, const DevVecs& v,
                          DevScalars* sc, unsigned long long cond_handle, int use_cond,
                          cudaStream_t s);
 cudaError_t launch_fill_start(const DevVecs& v, int fresh_x, int fresh_y, cudaStream_t s);
@@ -151,7 +192,7 @@ cudaError_t launch_scatter(const double* in, const int32_t* perm, double* out, i
 cudaError_t launch_fill(double* p, double v, int len, cudaStream_t s);
 // One power-iteration round: w = A v, lam = w.w, u = A^T w, v = u / ||u||; pw[0] = lam,
 // pw[1] = ||u||.
-cudaError_t launch_power_round(const DevTiled& csr, const DevTiled& csc, const DevVecs& v,
+cudaError_t launch_power_round(const DevPacked& csr, const DevPacked& csc, const DevVecs& v,
                                double* vec_v, double* vec_w, double* vec_u, cudaStream_t s);
 int reduction_grid(int len);
 

@@ -1,17 +1,18 @@
 // sm_103a kernels of the PDHG hot path.
 //
-//  tiled_spmv_kernel  one thread block per tile of a row-major sparse matrix (CSR of A for
-//                     A x, CSR of A^T -- the CSC copy -- for A^T y).  Each thread sums 32
-//                     consecutive nonzeros in stored order with one FMA per nonzero (FP64
-//                     issue slots are scarce on GB300, so no shuffle trees on the common
-//                     path); rows that cross thread boundaries are finished by their owner
-//                     thread from per-thread head partials in shared memory.  The row
-//                     results feed an epilogue:
+//  packed_spmv_kernel one warp per slot of a lane-packed sparse matrix (rows of A for
+//                     A x, rows of A^T -- the CSC copy -- for A^T y; layout in internal.h).
+//                     Each lane sums its own rows in stored order with one FMA per stored
+//                     nonzero: a GB300 SM issues 2 FP64 FMA lanes per clock and a warp FP64
+//                     instruction holds its sub-partition's unit for 64 cycles whatever its
+//                     active lanes, so no FP64 work runs lane-divergent.  The row results
+//                     feed an epilogue:
 //                       PrimalEpi  the primal step of Section 2.2 / Algorithm 1 step 1 and the
 //                                  Halpern step of Appendix B.1 (K-A);
 //                       DualEpi    the dual step of Section 2.2 / Algorithm 1 step 2 and the
 //                                  Halpern step (K-B);
 //                       StoreEpi   plain output (KKT products, power iteration, A x / A^T y).
+//  finish_long_kernel rows longer than a lane: their pieces added in piece order, epilogue.
 //  reduce_*_kernel    per-row / per-column terms of the relative KKT error (Appendix B.4)
 //                     and of the fixed-point residual (Appendix D.2.1), block partials in a
 //                     fixed order (deterministic, no floating-point atomics).
@@ -42,10 +43,25 @@ __device__ __forceinline__ unsigned long long l2_evict_first_policy() {
 
 // Matrix values and indices are read once per pass and are larger than L2: stream them
 // with an evict-first L2 policy so the gathered vectors (x_bar, y) stay L2-resident.
+#ifndef DPDLP_STREAM_NOALLOC
+#define DPDLP_STREAM_NOALLOC 0
+#endif
+#if DPDLP_STREAM_NOALLOC
+#define DPDLP_LDS_L1 ".L1::no_allocate"
+#else
+#define DPDLP_LDS_L1 ""
+#endif
 __device__ __forceinline__ double2 ld_stream(const double2* p, unsigned long long pol) {
   double2 r;
-  asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+  asm("ld.global.nc" DPDLP_LDS_L1 ".L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
       : "=d"(r.x), "=d"(r.y)
+      : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ uint4 ld_stream(const uint4* p, unsigned long long pol) {
+  uint4 r;
+  asm("ld.global.nc" DPDLP_LDS_L1 ".L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
       : "l"(p), "l"(pol));
   return r;
 }
@@ -55,11 +71,6 @@ __device__ __forceinline__ int4 ld_stream(const int4* p, unsigned long long pol)
       : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
       : "l"(p), "l"(pol));
   return r;
-}
-
-// Bulk prefetch of [p, p + bytes) into L2 (address 16-byte aligned, size a multiple of 16).
-__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // Deterministic block sum (fixed xor-butterfly inside warps, fixed order across warps).
@@ -81,10 +92,10 @@ __device__ __forceinline__ double block_sum(double v, double* buf) {
 }
 
 // ---------------------------------------------------------------- epilogues
-// An epilogue turns the row sums of one tile into outputs.  `Stage` is the shared-memory
-// copy of the per-row input vectors, fetched with cp.async at kernel start so that their
-// DRAM latency overlaps the SpMV; `apply` works from it, `apply_direct` (rows longer than a
-// tile, finished by one thread) reads global memory.
+// An epilogue turns the row sums of one slot into outputs.  `Stage` is the shared-memory
+// copy of the slot's row vectors, fetched with cp.async when the warp starts its slot so
+// that their latency overlaps the products; `apply` works from it, `apply_direct` (long
+// rows, finished by the lane-per-row pass) reads global memory.
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
@@ -97,7 +108,7 @@ struct StoreEpi1 {
   double* out0;
   struct Stage {};
   __device__ bool begin() { return true; }
-  __device__ void prefetch(int, int, Stage&) {}
+  __device__ void prefetch(int, int, Stage&, int) {}
   __device__ void apply(int, int r, const double* s, const Stage&) { out0[r] = s[0]; }
   __device__ void apply_direct(int r, const double* s) { out0[r] = s[0]; }
 };
@@ -105,7 +116,7 @@ struct StoreEpi2 {
   double *out0, *out1;
   struct Stage {};
   __device__ bool begin() { return true; }
-  __device__ void prefetch(int, int, Stage&) {}
+  __device__ void prefetch(int, int, Stage&, int) {}
   __device__ void apply(int, int r, const double* s, const Stage&) {
     out0[r] = s[0];
     out1[r] = s[1];
@@ -154,17 +165,18 @@ struct PrimalEpi {
   double *x, *xbar, *xh, *dx;
   IterScalars q;
   struct Stage {
-    double c[MAX_TILE_ROWS], lv[MAX_TILE_ROWS], uv[MAX_TILE_ROWS], x[MAX_TILE_ROWS],
-        x0[MAX_TILE_ROWS];
+    double c[MAX_SLOT_ROWS], lv[MAX_SLOT_ROWS], uv[MAX_SLOT_ROWS], x[MAX_SLOT_ROWS],
+        x0[MAX_SLOT_ROWS];
   };
   __device__ bool begin() { return load_iter(sc, plan, true, q); }
-  __device__ void prefetch(int r0, int nrows, Stage& st) {
-    for (int r = threadIdx.x; r < nrows; r += TPB) {
+  __device__ void prefetch(int r0, int nrows, Stage& st, int lane) {
+    const bool hal = !q.check && q.halpern;
+    for (int r = lane; r < nrows; r += LANES) {
       cp_async8(&st.c[r], c + r0 + r);
       cp_async8(&st.lv[r], lv + r0 + r);
       cp_async8(&st.uv[r], uv + r0 + r);
       cp_async8(&st.x[r], x + r0 + r);
-      if (!q.check && q.halpern) cp_async8(&st.x0[r], x0 + r0 + r);
+      if (hal) cp_async8(&st.x0[r], x0 + r0 + r);
     }
     cp_async_commit();
   }
@@ -200,15 +212,16 @@ struct DualEpi {
   double *y, *yh;
   IterScalars q;
   struct Stage {
-    double lo[MAX_TILE_ROWS], hi[MAX_TILE_ROWS], y[MAX_TILE_ROWS], y0[MAX_TILE_ROWS];
+    double lo[MAX_SLOT_ROWS], hi[MAX_SLOT_ROWS], y[MAX_SLOT_ROWS], y0[MAX_SLOT_ROWS];
   };
   __device__ bool begin() { return load_iter(sc, plan, false, q); }
-  __device__ void prefetch(int r0, int nrows, Stage& st) {
-    for (int r = threadIdx.x; r < nrows; r += TPB) {
+  __device__ void prefetch(int r0, int nrows, Stage& st, int lane) {
+    const bool hal = !q.check && q.halpern;
+    for (int r = lane; r < nrows; r += LANES) {
       cp_async8(&st.lo[r], lo + r0 + r);
       cp_async8(&st.hi[r], hi + r0 + r);
       cp_async8(&st.y[r], y + r0 + r);
-      if (!q.check && q.halpern) cp_async8(&st.y0[r], y0 + r0 + r);
+      if (hal) cp_async8(&st.y0[r], y0 + r0 + r);
     }
     cp_async_commit();
   }
@@ -235,25 +248,64 @@ struct DualEpi {
   __device__ void apply_direct(int i, const double* s) { step(i, s[0], lo[i], hi[i], y[i], y0 + i); }
 };
 
-// ---------------------------------------------------------------- tiled SpMV
+// ---------------------------------------------------------------- packed SpMV
+// Build-time tuning knobs (defaults are the measured best; see the profiles):
+//   DPDLP_PK_MIN_BLOCKS  resident blocks per SM the register allocation targets
+//   DPDLP_GATHER_NOALLOC gather x[col] without allocating in L1 (random, no reuse there)
+//   DPDLP_PK_BATCH       stored entries per pipeline stage of a lane (4 or 8)
+//   DPDLP_PK_STAGE       copy the slot's row vectors to shared memory with cp.async (1) or
+//                        read them from global memory in the epilogue (0); staging takes
+//                        shared memory from L1, which the gathers' in-flight lines need
+//   DPDLP_STREAM_NOALLOC stream matrix values and indices without allocating in L1
+#ifndef DPDLP_PK_MIN_BLOCKS
+#define DPDLP_PK_MIN_BLOCKS 8
+#endif
+#ifndef DPDLP_GATHER_NOALLOC
+#define DPDLP_GATHER_NOALLOC 0
+#endif
+#ifndef DPDLP_PK_BATCH
+#define DPDLP_PK_BATCH 4
+#endif
+#ifndef DPDLP_PK_STAGE
+#define DPDLP_PK_STAGE 0
+#endif
+#ifndef DPDLP_STREAM_NOALLOC
+#define DPDLP_STREAM_NOALLOC 0
+#endif
+
 template <int NV>
 struct GatherVecs {
   const double* x[NV];
 };
 
-__device__ __forceinline__ void load_batch(const DevTiled& M, int at, double (&v)[BATCH],
-                                           int (&c)[BATCH], unsigned long long pol) {
-  const double2* vp = reinterpret_cast<const double2*>(M.val + at);
-  const int4* ip = reinterpret_cast<const int4*>(M.idx + at);
+__device__ __forceinline__ double gather(const double* p) {
+#if DPDLP_GATHER_NOALLOC
+  double r;
+  asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(r) : "l"(p));
+  return r;
+#else
+  return __ldg(p);
+#endif
+}
+
+// Values and indices of batch b (positions B*b .. B*b+B-1) of this lane: 16-byte loads,
+// each covering 512 contiguous bytes across the warp.
+template <int B>
+__device__ __forceinline__ void load_vals(const double2* vp, int b, double (&v)[B],
+                                          unsigned long long pol) {
 #pragma unroll
-  for (int q = 0; q < BATCH / 2; ++q) {
-    const double2 d = ld_stream(vp + q, pol);
+  for (int q = 0; q < B / 2; ++q) {
+    const double2 d = ld_stream(vp + ((B / 2) * b + q) * LANES, pol);
     v[2 * q] = d.x;
     v[2 * q + 1] = d.y;
   }
+}
+template <int B>
+__device__ __forceinline__ void load_idx(const uint4* ip, int b, uint32_t (&c)[B],
+                                         unsigned long long pol) {
 #pragma unroll
-  for (int q = 0; q < BATCH / 4; ++q) {
-    const int4 d = ld_stream(ip + q, pol);
+  for (int q = 0; q < B / 4; ++q) {
+    const uint4 d = ld_stream(ip + ((B / 4) * b + q) * LANES, pol);
     c[4 * q] = d.x;
     c[4 * q + 1] = d.y;
     c[4 * q + 2] = d.z;
@@ -261,206 +313,196 @@ __device__ __forceinline__ void load_batch(const DevTiled& M, int at, double (&v
   }
 }
 
-// One thread block per tile.  Each thread owns the 32 consecutive nonzeros
-// [e0 + 32 tid, e0 + 32 tid + 32) of its tile, loaded in four batches of 8 (the next batch's
-// loads are issued before the current batch's gathers), and sums them in stored order with
-// one FMA per nonzero.  A row that starts in a thread's range is owned by that thread; a row
-// that continues into the next threads is finished by its owner from their head partials,
-// in thread order, after a barrier.
+// One warp per slot, four slots per block, no block-level barrier.  Each lane sums the
+// 32 stored nonzeros of its lane in order, one FMA each, and at every end flag writes the
+// finished sum: short rows to shared memory, long-row pieces to the piece array.  Then the
+// lanes apply the epilogue to the slot's short rows, one row per lane.  The lane's items
+// go through a three-stage pipeline of batches: indices two batches ahead, values and the
+// x[col] gathers one batch ahead, so gathers are in flight while the FMA chain runs.
 template <int NV, class Epi>
-__global__ void __launch_bounds__(TPB, 3) tiled_spmv_kernel(DevTiled M, GatherVecs<NV> g, Epi epi_in) {
-  __shared__ int srp[MAX_TILE_ROWS + 1];
-  __shared__ double rsum[NV][MAX_TILE_ROWS];
-  __shared__ double head[NV][TPB];
-  __shared__ double red[TPB / 32];
-  __shared__ typename Epi::Stage stage;
+__global__ void __launch_bounds__(PK_TPB, DPDLP_PK_MIN_BLOCKS) packed_spmv_kernel(DevPacked M, GatherVecs<NV> g, Epi epi_in) {
+  constexpr int B = DPDLP_PK_BATCH;
+  constexpr int NB = LANE_ITEMS / B;
+  __shared__ double srow[PK_WARPS][NV][MAX_SLOT_ROWS];
+#if DPDLP_PK_STAGE
+  __shared__ typename Epi::Stage stage[PK_WARPS];
+#endif
 
   Epi epi = epi_in;
   if (!epi.begin()) return;  // uniform over the launch
-
-  const Tile t = M.tiles[blockIdx.x];
-  const int tid = threadIdx.x;
-  const int base = t.e0 + tid * IPT;  // BATCH-aligned: 16-byte vector loads
-  const int nvalid = min(IPT, max(0, t.e1 - base));
-  const bool shared_tile = (t.slot == -1);
-  const int nrows = t.r1 - t.r0;
-  if (shared_tile) epi.prefetch(t.r0, nrows, stage);
-
-  // Ask for the whole tile at once (values and indices, one bulk L2 prefetch each) so its
-  // DRAM traffic is in flight before the threads' own loads reach it.
-  if (tid == 0 && t.e1 > t.e0) {
-    prefetch_l2(M.val + t.e0, (unsigned)(t.e1 - t.e0) * 8u);
-    prefetch_l2(M.idx + t.e0, (unsigned)(t.e1 - t.e0) * 4u);
-  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.x * PK_WARPS + w;
+  if (s >= M.nslots) return;  // uniform over the warp
+  const SlotDesc sd = M.slots[s];
+#if DPDLP_PK_STAGE
+  epi.prefetch(sd.row_base, sd.nrows, stage[w], lane);
+#endif
+  const LaneMeta lm = M.lanes[(size_t)s * LANES + lane];
+  int rl = lm.row_local, pid = lm.piece_base;
+  const size_t off = (size_t)s * SLOT_ITEMS;
+  const double2* vp = reinterpret_cast<const double2*>(M.val + off) + lane;
+  const uint4* ip = reinterpret_cast<const uint4*>(M.idx + off) + lane;
   const unsigned long long pol = l2_evict_first_policy();
-  double va[BATCH];
-  int ca[BATCH];
-  if (nvalid > 0) load_batch(M, base, va, ca, pol);
 
   double acc[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  uint32_t c0[B], c1[B];
+  double v0[B], x0v[NV][B];
+  load_idx<B>(ip, 0, c0, pol);
+  if (NB > 1) load_idx<B>(ip, 1, c1, pol);
+  load_vals<B>(vp, 0, v0, pol);
+#pragma unroll
+  for (int j = 0; j < B; ++j) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) x0v[k][j] = gather(g.x[k] + (c0[j] & IDX_MASK));
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    uint32_t c2[B];
+    double v1[B], x1v[NV][B];
+    if (b + 2 < NB) load_idx<B>(ip, b + 2, c2, pol);
+    if (b + 1 < NB) {
+      load_vals<B>(vp, b + 1, v1, pol);
+#pragma unroll
+      for (int j = 0; j < B; ++j) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) x1v[k][j] = gather(g.x[k] + (c1[j] & IDX_MASK));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) acc[k] = fma(v0[j], x0v[k][j], acc[k]);
+      if (c0[j] & END_BIT) {
+        if (c0[j] & PIECE_BIT) {
+#pragma unroll
+          for (int k = 0; k < NV; ++k) M.piece_sum[(size_t)k * M.npieces + pid] = acc[k];
+          ++pid;
+        } else {
+#pragma unroll
+          for (int k = 0; k < NV; ++k) srow[w][k][rl] = acc[k];
+          ++rl;
+        }
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+      }
+    }
+    if (b + 1 < NB) {  // rotate the pipeline
+#pragma unroll
+      for (int j = 0; j < B; ++j) {
+        c0[j] = c1[j];
+        v0[j] = v1[j];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) x0v[k][j] = x1v[k][j];
+        if (b + 2 < NB) c1[j] = c2[j];
+      }
+    }
+  }
+#if DPDLP_PK_STAGE
+  cp_async_wait_all();
+#endif
+  __syncwarp();
+  for (int r = lane; r < sd.nrows; r += LANES) {
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = srow[w][k][r];
+#if DPDLP_PK_STAGE
+    epi.apply(r, sd.row_base + r, v, stage[w]);
+#else
+    epi.apply_direct(sd.row_base + r, v);
+#endif
+  }
+}
 
-  if (shared_tile) {
-    for (int r = tid; r <= nrows; r += TPB) srp[r] = M.ptr[t.r0 + r];
-    for (int r = tid; r < nrows; r += TPB) {
-#pragma unroll
-      for (int k = 0; k < NV; ++k) rsum[k][r] = 0.0;
-    }
-    __syncthreads();
-    int open_row = -1;  // a row this thread owns that continues past its items
-    if (nvalid > 0) {
-      int lo = 0, hi = nrows - 1;  // the row holding item `base`: last r with srp[r] <= base
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (srp[mid] <= base) lo = mid; else hi = mid - 1;
-      }
-      int r = lo;
-      bool owner = srp[r] >= base;
-      int rend = srp[r + 1];
-#pragma unroll
-      for (int b = 0; b < NBATCH; ++b) {
-        double vb[BATCH];
-        int cb[BATCH];
-        const bool more = (b + 1 < NBATCH) && ((b + 1) * BATCH < nvalid);
-        if (more) load_batch(M, base + (b + 1) * BATCH, vb, cb, pol);
-        double xv[NV][BATCH];
-#pragma unroll
-        for (int j = 0; j < BATCH; ++j) {
-#pragma unroll
-          for (int k = 0; k < NV; ++k) xv[k][j] = (b * BATCH + j < nvalid) ? __ldg(g.x[k] + ca[j]) : 0.0;
-        }
-#pragma unroll
-        for (int j = 0; j < BATCH; ++j) {
-          if (b * BATCH + j < nvalid) {
-            const int e = base + b * BATCH + j;
-            while (e >= rend) {  // row r ends before item e
-#pragma unroll
-              for (int k = 0; k < NV; ++k) {
-                if (owner) rsum[k][r] = acc[k]; else head[k][tid] = acc[k];
-                acc[k] = 0.0;
-              }
-              ++r;
-              rend = srp[r + 1];
-              owner = true;
-            }
-#pragma unroll
-            for (int k = 0; k < NV; ++k) acc[k] = fma(va[j], xv[k][j], acc[k]);
-          }
-        }
-        if (more) {
-#pragma unroll
-          for (int j = 0; j < BATCH; ++j) {
-            va[j] = vb[j];
-            ca[j] = cb[j];
-          }
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < NV; ++k) {
-        if (owner) rsum[k][r] = acc[k]; else head[k][tid] = acc[k];
-      }
-      if (owner && rend > base + nvalid) open_row = r;
-    }
-    __syncthreads();
-    if (open_row >= 0) {  // add the head partials of the following threads, in order
-      const int t_end = (srp[open_row + 1] - 1 - t.e0) / IPT;
-#pragma unroll
-      for (int k = 0; k < NV; ++k) {
-        double s = rsum[k][open_row];
-        for (int tt = tid + 1; tt <= t_end; ++tt) s += head[k][tt];
-        rsum[k][open_row] = s;
-      }
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    for (int r = tid; r < nrows; r += TPB) {
-      double s[NV];
-#pragma unroll
-      for (int k = 0; k < NV; ++k) s[k] = rsum[k][r];
-      epi.apply(r, t.r0 + r, s, stage);
-    }
-    return;
-  }
-
-  // ---- a tile of one long row: block sum, then either finish the row (single chunk) or
-  // publish the chunk sum; the last chunk to arrive adds all chunks in chunk order.
-#pragma unroll
-  for (int b = 0; b < NBATCH; ++b) {
-    double vb[BATCH];
-    int cb[BATCH];
-    const bool more = (b + 1 < NBATCH) && ((b + 1) * BATCH < nvalid);
-    if (more) load_batch(M, base + (b + 1) * BATCH, vb, cb, pol);
-#pragma unroll
-    for (int j = 0; j < BATCH; ++j) {
-      if (b * BATCH + j < nvalid) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) acc[k] = fma(va[j], __ldg(g.x[k] + ca[j]), acc[k]);
-      }
-    }
-    if (more) {
-#pragma unroll
-      for (int j = 0; j < BATCH; ++j) {
-        va[j] = vb[j];
-        ca[j] = cb[j];
-      }
-    }
-  }
-  double tot[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) tot[k] = block_sum(acc[k], red);
-  if (tid != 0) return;
-  if (t.slot == -2) {
-    epi.apply_direct(t.r0, tot);
-    return;
-  }
-#pragma unroll
-  for (int k = 0; k < NV; ++k) M.lr_partial[k * M.long_chunks + t.slot + t.chunk] = tot[k];
-  __threadfence();
-  const unsigned prev = atomicAdd(&M.lr_count[t.lrow], 1u);
-  if (prev == (unsigned)(t.nchunks - 1)) {
-    __threadfence();
-    double s[NV];
+// Long rows: add each row's pieces, then its epilogue.  Rows come longest first: the first
+// nlong_block rows get a thread block each, the next nlong_warp rows a warp each (fixed
+// strided sums and fixed reduction trees), the rest a thread each (pieces in order).
+template <int NV, class Epi>
+__global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_in) {
+  __shared__ double red[TPB / 32];
+  Epi epi = epi_in;
+  if (!epi.begin()) return;
+  const int nb = M.nlong_block, nw = M.nlong_warp;
+  const int wblocks = (nw + TPB / 32 - 1) / (TPB / 32);
+  int b = blockIdx.x;
+  double v[NV];
+  if (b < nb) {
+    const int i = b;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       double a = 0.0;
-      for (int c = 0; c < t.nchunks; ++c) a += __ldcg(&M.lr_partial[k * M.long_chunks + t.slot + c]);
-      s[k] = a;
+      for (int q = M.long_ptr[i] + threadIdx.x; q < M.long_ptr[i + 1]; q += TPB)
+        a += M.piece_sum[(size_t)k * M.npieces + M.long_piece[q]];
+      v[k] = block_sum(a, red);
     }
-    M.lr_count[t.lrow] = 0;  // ready for the next launch
-    epi.apply_direct(t.r0, s);
+    if (threadIdx.x == 0) epi.apply_direct(M.long_row[i], v);
+    return;
   }
+  b -= nb;
+  if (b < wblocks) {
+    const int i = nb + b * (TPB / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= nb + nw) return;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double a = 0.0;
+      for (int q = M.long_ptr[i] + lane; q < M.long_ptr[i + 1]; q += LANES)
+        a += M.piece_sum[(size_t)k * M.npieces + M.long_piece[q]];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      v[k] = a;
+    }
+    if (lane == 0) epi.apply_direct(M.long_row[i], v);
+    return;
+  }
+  b -= wblocks;
+  const int i = nb + nw + b * TPB + threadIdx.x;
+  if (i >= M.nlong) return;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double a = 0.0;
+    for (int q = M.long_ptr[i]; q < M.long_ptr[i + 1]; ++q)
+      a += M.piece_sum[(size_t)k * M.npieces + M.long_piece[q]];
+    v[k] = a;
+  }
+  epi.apply_direct(M.long_row[i], v);
 }
 
 template <int NV, class Epi>
-static cudaError_t launch_tiled(const DevTiled& M, GatherVecs<NV> g, Epi epi, cudaStream_t s) {
-  if (M.ntiles == 0) return cudaSuccess;
-  tiled_spmv_kernel<NV, Epi><<<M.ntiles, TPB, 0, s>>>(M, g, epi);
+static cudaError_t launch_packed(const DevPacked& M, GatherVecs<NV> g, Epi epi, cudaStream_t s) {
+  if (M.nslots > 0)
+    packed_spmv_kernel<NV, Epi><<<(M.nslots + PK_WARPS - 1) / PK_WARPS, PK_TPB, 0, s>>>(M, g, epi);
+  if (M.nlong > 0) {
+    const int rest = M.nlong - M.nlong_block - M.nlong_warp;
+    const int grid = M.nlong_block + (M.nlong_warp + TPB / 32 - 1) / (TPB / 32) + (rest + TPB - 1) / TPB;
+    finish_long_kernel<NV, Epi><<<grid, TPB, 0, s>>>(M, epi);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_primal(const DevTiled& csc, const DevVecs& v, const DevScalars* sc,
+cudaError_t launch_primal(const DevPacked& csc, const DevVecs& v, const DevScalars* sc,
                           IterPlan p, cudaStream_t s) {
   PrimalEpi e{sc, p, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, {}};
   GatherVecs<1> g{{v.y}};
-  return launch_tiled<1>(csc, g, e, s);
+  return launch_packed<1>(csc, g, e, s);
 }
 
-cudaError_t launch_dual(const DevTiled& csr, const DevVecs& v, const DevScalars* sc,
+cudaError_t launch_dual(const DevPacked& csr, const DevVecs& v, const DevScalars* sc,
                         IterPlan p, cudaStream_t s) {
   DualEpi e{sc, p, v.lo, v.hi, v.y0, v.y, v.yh, {}};
   GatherVecs<1> g{{v.xbar}};
-  return launch_tiled<1>(csr, g, e, s);
+  return launch_packed<1>(csr, g, e, s);
 }
 
-cudaError_t launch_spmv(const DevTiled& M, const double* x0, const double* x1, double* out0,
+cudaError_t launch_spmv(const DevPacked& M, const double* x0, const double* x1, double* out0,
                         double* out1, cudaStream_t s) {
   if (x1) {
     GatherVecs<2> g{{x0, x1}};
-    return launch_tiled<2>(M, g, StoreEpi2{out0, out1}, s);
+    return launch_packed<2>(M, g, StoreEpi2{out0, out1}, s);
   }
   GatherVecs<1> g{{x0}};
-  return launch_tiled<1>(M, g, StoreEpi1{out0}, s);
+  return launch_packed<1>(M, g, StoreEpi1{out0}, s);
 }
 
 // ---------------------------------------------------------------- check reductions
@@ -690,7 +732,7 @@ __global__ void __launch_bounds__(TPB) apply_kernel(DevVecs v, const DevScalars*
   }
 }
 
-cudaError_t launch_check(const DevTiled& csr, const DevTiled& csc, const DevVecs& v,
+cudaError_t launch_check(const DevPacked& csr, const DevPacked& csc, const DevVecs& v,
                          DevScalars* sc, unsigned long long cond_handle, int use_cond,
                          cudaStream_t s) {
   cudaError_t e;
@@ -798,7 +840,7 @@ __global__ void scale_kernel(double* v, const double* u, const double* pw, int l
   if (i < len) v[i] = u[i] * pw[2];
 }
 
-cudaError_t launch_power_round(const DevTiled& csr, const DevTiled& csc, const DevVecs& v,
+cudaError_t launch_power_round(const DevPacked& csr, const DevPacked& csc, const DevVecs& v,
                                double* vec_v, double* vec_w, double* vec_u, cudaStream_t s) {
   cudaError_t e;
   if ((e = launch_spmv(csr, vec_v, nullptr, vec_w, nullptr, s)) != cudaSuccess) return e;

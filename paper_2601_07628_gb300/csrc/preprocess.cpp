@@ -5,9 +5,7 @@
 //    B indices (B = 256 by default) are shuffled, the order inside a block is kept.
 //  * The CSC copy of A (the paper keeps both CSR and CSC in device memory so that A^T y
 //    needs no atomics, Appendix E.2), built as the CSR of A^T by a stable counting sort.
-//  * Nonzero-aware partitioning (Section 4.3) at thread-block granularity: consecutive
-//    rows are grouped into tiles of at most TILE_NNZ nonzeros; a row longer than
-//    SOLO_NNZ gets tiles of its own (one per TILE_NNZ chunk).
+//  * (packing.cpp) nonzero-aware partitioning (Section 4.3) down to warp lanes.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -17,10 +15,6 @@
 
 namespace pdhg {
 
-// Rows longer than this get their own tile(s) and a block-wide reduction instead of the
-// per-thread walk, which bounds the serial fix-up chain of a shared tile to SOLO_NNZ/IPT.
-constexpr int SOLO_NNZ = 1024;
-
 std::string validate_csr(int rows, int cols, const int64_t* ptr, const int32_t* idx,
                          const double* val) {
   if (rows < 0 || cols < 0) return "negative dimension";
@@ -29,8 +23,8 @@ std::string validate_csr(int rows, int cols, const int64_t* ptr, const int32_t* 
   for (int r = 0; r < rows; ++r)
     if (ptr[r + 1] < ptr[r]) return "row_ptr not non-decreasing at row " + std::to_string(r);
   const int64_t nnz = ptr[rows];
-  if (nnz > (int64_t)INT32_MAX - 16LL * TILE_NNZ - 8LL * rows)
-    return "too many nonzeros for 32-bit indices";
+  if (nnz > (int64_t)INT32_MAX / 2) return "too many nonzeros for 32-bit offsets";
+  if (cols > (int)IDX_MASK) return "too many columns for the packed index format";
   if (nnz > 0 && (!idx || !val)) return "col_idx or val is NULL";
   for (int64_t e = 0; e < nnz; ++e) {
     if (idx[e] < 0 || idx[e] >= cols)
@@ -112,90 +106,6 @@ void transpose_csr(int rows, int cols, const std::vector<int64_t>& ptr,
       tidx[p] = r;
       tval[p] = val[e];
     }
-}
-
-static inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
-
-void build_tiled(int rows, int cols, const std::vector<int64_t>& ptr,
-                 const std::vector<int32_t>& idx, const std::vector<double>& val,
-                 HostTiled& out, int tile_cap) {
-  out.rows = rows;
-  out.cols = cols;
-  out.tiles.clear();
-  out.long_rows = 0;
-  out.long_chunks = 0;
-  // Tile capacity: TILE_NNZ, or less when the matrix is small, so that there are about
-  // eight tiles per SM (152 SMs) before tiles shrink below 512 nonzeros.
-  const int64_t nnz = ptr[rows];
-  const int64_t cap = tile_cap > 0
-      ? std::min<int64_t>(TILE_NNZ, round_up(tile_cap, BATCH))
-      : std::min<int64_t>(TILE_NNZ, std::max<int64_t>(512, round_up((nnz + 1215) / 1216, BATCH)));
-  const int64_t solo = std::min<int64_t>(SOLO_NNZ, cap);
-  // Pass 1: tile plan over the original offsets.
-  struct Plan { int r0, r1; bool solo; };
-  std::vector<Plan> plan;
-  for (int r = 0; r < rows;) {
-    const int64_t L = ptr[r + 1] - ptr[r];
-    if (L > solo) {
-      plan.push_back({r, r + 1, true});
-      ++r;
-      continue;
-    }
-    int r1 = r;
-    int64_t nz = 0;
-    while (r1 < rows && r1 - r < MAX_TILE_ROWS) {
-      const int64_t Lr = ptr[r1 + 1] - ptr[r1];
-      if (Lr > solo || nz + Lr > cap) break;
-      nz += Lr;
-      ++r1;
-    }
-    plan.push_back({r, r1, false});
-    r = r1;
-  }
-  // Pass 2: padded arrays and tile descriptors.
-  int64_t padded = 0;
-  for (const Plan& p : plan) padded += round_up(ptr[p.r1] - ptr[p.r0], BATCH);
-  out.nnz_padded = padded;
-  out.ptr.assign(rows + 1, 0);
-  out.idx.assign(padded + TILE_NNZ, 0);
-  out.val.assign(padded + TILE_NNZ, 0.0);
-  int64_t pos = 0;
-  for (const Plan& p : plan) {
-    const int64_t e0 = pos;
-    for (int r = p.r0; r < p.r1; ++r) {
-      out.ptr[r] = (int32_t)pos;
-      const int64_t L = ptr[r + 1] - ptr[r];
-      if (L > 0) {
-        std::memcpy(&out.idx[pos], &idx[ptr[r]], L * sizeof(int32_t));
-        std::memcpy(&out.val[pos], &val[ptr[r]], L * sizeof(double));
-      }
-      pos += L;
-    }
-    // explicit zeros appended to the tile's last row keep the next tile BATCH-aligned
-    const int64_t end = e0 + round_up(pos - e0, BATCH);
-    const int32_t pad_col = pos > e0 ? out.idx[pos - 1] : 0;
-    for (; pos < end; ++pos) {
-      out.idx[pos] = pad_col;
-      out.val[pos] = 0.0;
-    }
-    if (!p.solo) {
-      out.tiles.push_back({p.r0, p.r1, (int)e0, (int)pos, -1, -1, 0, 1});
-    } else {
-      const int nch = (int)((pos - e0 + TILE_NNZ - 1) / TILE_NNZ);
-      if (nch <= 1) {
-        out.tiles.push_back({p.r0, p.r1, (int)e0, (int)pos, -2, -1, 0, 1});
-      } else {
-        for (int c = 0; c < nch; ++c) {
-          const int64_t a = e0 + (int64_t)c * TILE_NNZ;
-          const int64_t b = std::min<int64_t>(a + TILE_NNZ, pos);
-          out.tiles.push_back({p.r0, p.r1, (int)a, (int)b, out.long_chunks, out.long_rows, c, nch});
-        }
-        out.long_chunks += nch;
-        out.long_rows += 1;
-      }
-    }
-  }
-  out.ptr[rows] = (int32_t)pos;
 }
 
 }  // namespace pdhg

@@ -48,7 +48,6 @@ std::map<std::string, Param> default_params() {
       {"block_permute", {1, 0, 1, true}},
       {"perm_block", {256, 1, 1 << 30, true}},
       {"perm_seed", {1, 0, 9007199254740992.0, true}},
-      {"tile_nnz", {0, 0, TILE_NNZ, true}},
       {"use_graph", {1, 0, 1, true}},
       {"ptr_mode_device", {0, 0, 1, true}},
       {"resume", {0, 0, 1, true}},
@@ -71,7 +70,7 @@ struct dpdlp {
   int64_t nnz = 0;
   std::vector<int32_t> prow, pcol;  // internal index -> caller index
   std::vector<double> h_lc, h_uc;   // caller order
-  DevTiled csr, csc;
+  DevPacked csr, csc;
   DevVecs v;
   double *xs = nullptr, *ys = nullptr;  // warm start (internal order)
   bool have_start_x = false, have_start_y = false;
@@ -138,8 +137,8 @@ void free_problem(dpdlp* h) {
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
   h->dev_bytes = 0;
-  h->csr = DevTiled{};
-  h->csc = DevTiled{};
+  h->csr = DevPacked{};
+  h->csc = DevPacked{};
   h->v = DevVecs{};
   h->xs = h->ys = nullptr;
   h->d_sc = nullptr;
@@ -150,25 +149,46 @@ void free_problem(dpdlp* h) {
   h->have_start_x = h->have_start_y = false;
 }
 
-int upload_tiled(dpdlp* h, const HostTiled& H, DevTiled& D) {
+int upload_packed(dpdlp* h, const HostPacked& H, DevPacked& D) {
   D.rows = H.rows;
   D.cols = H.cols;
-  D.ntiles = (int)H.tiles.size();
-  D.long_rows = H.long_rows;
-  D.long_chunks = H.long_chunks;
+  D.nslots = H.nslots;
+  D.nlong = H.nlong;
+  D.npieces = H.npieces;
+  D.nlong_block = H.nlong_block;
+  D.nlong_warp = H.nlong_warp;
   int rc;
-  if ((rc = dalloc(h, &D.ptr, H.ptr.size()))) return rc;
-  if ((rc = dalloc(h, &D.idx, H.idx.size()))) return rc;
-  if ((rc = dalloc(h, &D.val, H.val.size()))) return rc;
-  if ((rc = dalloc(h, &D.tiles, H.tiles.size()))) return rc;
-  if ((rc = dalloc(h, &D.lr_partial, 2 * (size_t)H.long_chunks + 2))) return rc;
-  if ((rc = dalloc(h, &D.lr_count, (size_t)H.long_rows + 1))) return rc;
-  CK(cudaMemcpy(D.ptr, H.ptr.data(), H.ptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(D.idx, H.idx.data(), H.idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(D.val, H.val.data(), H.val.size() * sizeof(double), cudaMemcpyHostToDevice));
-  if (!H.tiles.empty())
-    CK(cudaMemcpy(D.tiles, H.tiles.data(), H.tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
-  CK(cudaMemset(D.lr_count, 0, ((size_t)H.long_rows + 1) * sizeof(unsigned)));
+  double *val, *psum;
+  uint32_t* idx;
+  SlotDesc* slots;
+  LaneMeta* lanes;
+  int32_t *lrow, *lptr, *lpiece;
+  if ((rc = dalloc(h, &val, H.val.size()))) return rc;
+  if ((rc = dalloc(h, &idx, H.idx.size()))) return rc;
+  if ((rc = dalloc(h, &slots, H.slots.size()))) return rc;
+  if ((rc = dalloc(h, &lanes, H.lanes.size()))) return rc;
+  if ((rc = dalloc(h, &lrow, H.long_row.size()))) return rc;
+  if ((rc = dalloc(h, &lptr, H.long_ptr.size()))) return rc;
+  if ((rc = dalloc(h, &lpiece, H.long_piece.size()))) return rc;
+  if ((rc = dalloc(h, &psum, 2 * (size_t)H.npieces))) return rc;
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    return bytes ? cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+  };
+  CK(up(val, H.val.data(), H.val.size() * sizeof(double)));
+  CK(up(idx, H.idx.data(), H.idx.size() * sizeof(uint32_t)));
+  CK(up(slots, H.slots.data(), H.slots.size() * sizeof(SlotDesc)));
+  CK(up(lanes, H.lanes.data(), H.lanes.size() * sizeof(LaneMeta)));
+  CK(up(lrow, H.long_row.data(), H.long_row.size() * sizeof(int32_t)));
+  CK(up(lptr, H.long_ptr.data(), H.long_ptr.size() * sizeof(int32_t)));
+  CK(up(lpiece, H.long_piece.data(), H.long_piece.size() * sizeof(int32_t)));
+  D.val = val;
+  D.idx = idx;
+  D.slots = slots;
+  D.lanes = lanes;
+  D.long_row = lrow;
+  D.long_ptr = lptr;
+  D.long_piece = lpiece;
+  D.piece_sum = psum;
   return 0;
 }
 
@@ -455,6 +475,7 @@ int dpdlp_load_lp(dpdlp_t* h, int32_t n, int32_t m, const double* c, const int64
     return fail(h, DPDLP_ERR_INVALID, "NULL input array");
   if ((b == nullptr) != (ctype == nullptr))
     return fail(h, DPDLP_ERR_INVALID, "b and ctype must both be given or both be NULL");
+  if (m > (int32_t)IDX_MASK) return fail(h, DPDLP_ERR_INVALID, "too many rows for the packed index format");
   std::string e = validate_csr(m, n, row_ptr, col_idx, val);
   if (!e.empty()) return fail(h, DPDLP_ERR_INVALID, e);
   for (int j = 0; j < n; ++j) {
@@ -491,30 +512,44 @@ int dpdlp_load_lp(dpdlp_t* h, int32_t n, int32_t m, const double* c, const int64
   std::vector<double> pval, tval;
   permute_csr(m, n, row_ptr, col_idx, val, h->prow, h->pcol, pptr, pidx, pval);
   transpose_csr(m, n, pptr, pidx, pval, tptr, tidx, tval);
-  HostTiled Hr, Hc;
-  const int tile_cap = (int)h->P("tile_nnz");
-  build_tiled(m, n, pptr, pidx, pval, Hr, tile_cap);
-  build_tiled(n, m, tptr, tidx, tval, Hc, tile_cap);
+  // pack rows of A and rows of A^T into warp lanes; each packing fixes one index order
+  PackPlan rplan, cplan;
+  plan_packing(m, pptr, rplan);
+  plan_packing(n, tptr, cplan);
+  HostPacked Hr, Hc;
+  build_packed(m, n, pptr, pidx, pval, rplan, cplan.new_of_old, Hr);
+  build_packed(n, m, tptr, tidx, tval, cplan, rplan.new_of_old, Hc);
   std::vector<int64_t>().swap(pptr);
   std::vector<int32_t>().swap(pidx);
   std::vector<double>().swap(pval);
   std::vector<int64_t>().swap(tptr);
   std::vector<int32_t>().swap(tidx);
   std::vector<double>().swap(tval);
+  {  // internal index -> caller index: packing order after the block permutation
+    std::vector<int32_t> pr(m), pc(n);
+    for (int i = 0; i < m; ++i) pr[i] = h->prow[rplan.old_of_new[i]];
+    for (int j = 0; j < n; ++j) pc[j] = h->pcol[cplan.old_of_new[j]];
+    h->prow.swap(pr);
+    h->pcol.swap(pc);
+  }
 
   int rc;
-  if ((rc = upload_tiled(h, Hr, h->csr))) return rc;
-  if ((rc = upload_tiled(h, Hc, h->csc))) return rc;
+  if ((rc = upload_packed(h, Hr, h->csr))) return rc;
+  if ((rc = upload_packed(h, Hc, h->csc))) return rc;
   DevVecs& v = h->v;
   v.n = n;
   v.m = m;
   double** nvecs[] = {&v.c, &v.lv, &v.uv, &v.x, &v.x0, &v.xbar, &v.xh, &v.dx, &v.aty,
                       &v.tmp_n, &v.tmp_n2, &h->xs};
-  for (double** p : nvecs)
+  for (double** p : nvecs) {
     if ((rc = dalloc(h, p, n))) return rc;
+    CK(cudaMemset(*p, 0, (n > 0 ? n : 2) * sizeof(double)));  // padding gathers read finite zeros
+  }
   double** mvecs[] = {&v.lo, &v.hi, &v.y, &v.y0, &v.yh, &v.axh, &v.adx, &v.tmp_m, &h->ys};
-  for (double** p : mvecs)
+  for (double** p : mvecs) {
     if ((rc = dalloc(h, p, m))) return rc;
+    CK(cudaMemset(*p, 0, (m > 0 ? m : 2) * sizeof(double)));
+  }
   v.g_rows = reduction_grid(m);
   v.g_cols = reduction_grid(n);
   if ((rc = dalloc(h, &v.red_rows, 1024 * NRED))) return rc;
@@ -546,12 +581,12 @@ int dpdlp_load_lp(dpdlp_t* h, int32_t n, int32_t m, const double* c, const int64
   I.n = n;
   I.m = m;
   I.nnz = h->nnz;
-  I.nnz_padded_csr = Hr.nnz_padded;
-  I.nnz_padded_csc = Hc.nnz_padded;
-  I.tiles_csr = (int)Hr.tiles.size();
-  I.tiles_csc = (int)Hc.tiles.size();
-  I.long_rows = Hr.long_rows;
-  I.long_cols = Hc.long_rows;
+  I.nnz_padded_csr = Hr.stored;
+  I.nnz_padded_csc = Hc.stored;
+  I.tiles_csr = Hr.nslots;
+  I.tiles_csc = Hc.nslots;
+  I.long_rows = Hr.nlong;
+  I.long_cols = Hc.nlong;
   I.device_bytes = h->dev_bytes;
   I.preprocess_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
   return 0;
@@ -769,7 +804,6 @@ int dpdlp_apply_A(dpdlp_t* h, const double* x, double* out) {
   int rc;
   if ((rc = import_vec(h, x, h->v.tmp_n2, h->v.perm_col, h->n, h->v.tmp_n))) return rc;
   CK(launch_spmv(h->csr, h->v.tmp_n2, nullptr, h->v.axh, nullptr, h->stream));
-  if (h->csr.ntiles == 0 && h->m) CK(launch_fill(h->v.axh, 0.0, h->m, h->stream));
   return export_vec(h, h->v.axh, out, h->v.perm_row, h->m, h->v.tmp_m);
 }
 
@@ -780,7 +814,6 @@ int dpdlp_apply_AT(dpdlp_t* h, const double* y, double* out) {
   int rc;
   if ((rc = import_vec(h, y, h->v.axh, h->v.perm_row, h->m, h->v.tmp_m))) return rc;
   CK(launch_spmv(h->csc, h->v.axh, nullptr, h->v.tmp_n2, nullptr, h->stream));
-  if (h->csc.ntiles == 0 && h->n) CK(launch_fill(h->v.tmp_n2, 0.0, h->n, h->stream));
   return export_vec(h, h->v.tmp_n2, out, h->v.perm_col, h->n, h->v.tmp_n);
 }
 

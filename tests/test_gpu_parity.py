@@ -118,11 +118,9 @@ def test_converges_to_1e4_and_1e8(Solver):
 
 
 # --------------------------------------------------------------------------- tile shapes
-# Row lengths around every boundary of the tiling: thread ranges (multiples of 8 and 32),
-# the single-tile limit for shared tiles (1024), the tile size (8192) and multi-chunk rows,
-# plus empty rows and runs of short rows that fill tiles to the 768-row limit.  Each case
-# runs with the automatic tile size (512 nonzeros at this size) and with full 8192-nonzero
-# tiles.
+# Row lengths around every boundary of the lane packing: rows that fill a lane exactly (32),
+# rows one longer (a full piece plus a one-nonzero tail), multiples of 32, long rows of many
+# pieces, empty rows, and runs of one-nonzero rows that hit the per-slot row budget.
 STRESS_LENGTHS = ([0, 1, 7, 8, 9, 31, 32, 33, 0, 0, 255, 256, 257, 511, 512, 513, 1000, 1023,
                    1024, 1025, 2047, 2048, 2049, 4095, 4096, 4097, 8191, 8192, 8193, 9000, 0]
                   + [5] * 600 + [0, 3000, 16385, 30000] + [17] * 200 + [1] * 900 + [0, 0])
@@ -133,14 +131,12 @@ def stress_lp():
     return lpgen.row_length_stress_lp(11, STRESS_LENGTHS, n=40000)
 
 
-@pytest.mark.parametrize("tile_nnz", [0, 8192])
-def test_spmv_tiles_against_oracle(Solver, stress_lp, tile_nnz):
+def test_spmv_tiles_against_oracle(Solver, stress_lp):
     """A x and A^T y on rows/columns of every tile kind (empty rows, rows straddling
     thread and tile boundaries, single-chunk and multi-chunk long rows)."""
     lp = stress_lp
     o = O.OracleLP.from_lpgen(lp)
     s = Solver()
-    s.set_param("tile_nnz", tile_nnz)
     s.load(lp)
     rng = np.random.default_rng(0)
     for _ in range(3):
@@ -153,22 +149,19 @@ def test_spmv_tiles_against_oracle(Solver, stress_lp, tile_nnz):
     assert info["long_rows"] >= 3 and info["nnz"] == lp.nnz
 
 
-@pytest.mark.parametrize("tile_nnz", [0, 8192])
-def test_stress_lp_iterations(Solver, stress_lp, tile_nnz):
-    s = Solver()
-    s.set_param("tile_nnz", tile_nnz)
-    ores, s, status, x, y = run_pair(Solver, stress_lp, 130, solver=s)
+def test_stress_lp_iterations(Solver, stress_lp):
+    ores, s, status, x, y = run_pair(Solver, stress_lp, 130)
     assert_parity(ores, x, y)
 
 
 @pytest.mark.parametrize("per_col", [3000, 10000])
 def test_long_columns(Solver, per_col):
-    """Few columns with thousands of nonzeros: the CSC pass takes the solo-tile path (one
-    chunk) or the multi-chunk path (combined by the last chunk to arrive)."""
+    """Few columns with thousands of nonzeros: the CSC pass splits them into lane pieces
+    that the long-row pass adds in order."""
     lp = lpgen.small_random_lp(4, n=40, m=12000, nnz_per_col=per_col)
     ores, s, status, x, y = run_pair(Solver, lp, 100)
     assert_parity(ores, x, y)
-    assert (s.info()["long_cols"] > 0) == (per_col > 8192)
+    assert s.info()["long_cols"] == lp.n
 
 
 def test_general_bounds(Solver):

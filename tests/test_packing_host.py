@@ -1,0 +1,85 @@
+"""Host logic of the lane packing, checked on the CPU (no GPU).
+
+``packing_check.cpp`` is compiled against the library's packing code; it packs a matrix,
+replays on the host what the warp lanes and the long-row pass compute from the stored
+arrays, and compares with a plain CSR product (plus the layout's invariants: a row
+permutation, consecutive slot rows within the per-slot budget, every nonzero stored once,
+one end flag per row or piece).
+"""
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import lpgen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2601_07628_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def checker(tmp_path_factory):
+    d = tmp_path_factory.mktemp("pack")
+    exe = str(d / "packing_check")
+    cuda_inc = "/usr/local/cuda/include"
+    cmd = ["g++", "-O2", "-std=c++17", "-I", CSRC, "-I", os.path.join(ROOT, "include"), "-I",
+           cuda_inc, os.path.join(os.path.dirname(__file__), "packing_check.cpp"),
+           os.path.join(CSRC, "packing.cpp"), "-o", exe]
+    subprocess.run(cmd, check=True)
+    return exe, d
+
+
+def run(checker, row_ptr, col, val, ncols, seed=0):
+    exe, d = checker
+    rows = len(row_ptr) - 1
+    x = np.random.default_rng(seed).standard_normal(ncols)
+    path = str(d / f"m{seed}_{rows}_{ncols}.bin")
+    with open(path, "wb") as f:
+        np.array([rows, ncols, row_ptr[-1]], dtype=np.int64).tofile(f)
+        np.asarray(row_ptr, dtype=np.int64).tofile(f)
+        np.asarray(col, dtype=np.int32).tofile(f)
+        np.asarray(val, dtype=np.float64).tofile(f)
+        x.tofile(f)
+    out = subprocess.run([exe, path], capture_output=True, text=True).stdout.strip()
+    assert out.startswith("ok"), out
+    return dict(kv.split("=") for kv in out.split()[1:])
+
+
+LENGTHS = ([0, 1, 7, 8, 9, 31, 32, 33, 0, 0, 63, 64, 65, 255, 256, 257, 1000, 1023, 1024, 1025,
+            4097, 9000, 0] + [5] * 600 + [0, 3000] + [17] * 200 + [1] * 900 + [0, 0])
+
+
+def test_stress_rows(checker):
+    lp = lpgen.row_length_stress_lp(11, LENGTHS, n=12000)
+    st = run(checker, lp.row_ptr, lp.col, lp.val, lp.n)
+    assert int(st["nlong"]) == sum(1 for L in LENGTHS if L > 32)
+
+
+def test_transpose_of_stress(checker):
+    """The CSC orientation of the same matrix (long columns of the transposed view)."""
+    import scipy.sparse as sp
+
+    lp = lpgen.row_length_stress_lp(12, LENGTHS, n=3000)
+    A = sp.csr_matrix((lp.val, lp.col, lp.row_ptr), shape=(lp.m, lp.n)).T.tocsr()
+    A.sort_indices()
+    run(checker, A.indptr, A.indices, A.data, A.shape[1], seed=1)
+
+
+def test_only_tiny_rows_and_empty(checker):
+    """Many one-nonzero and empty rows: the per-slot row budget, not the lanes, limits."""
+    rng = np.random.default_rng(3)
+    lengths = rng.integers(0, 2, size=5000)
+    lp = lpgen.row_length_stress_lp(13, lengths, n=50)
+    run(checker, lp.row_ptr, lp.col, lp.val, lp.n, seed=2)
+
+
+def test_empty_matrix_and_all_empty_rows(checker):
+    run(checker, np.zeros(6, np.int64), np.zeros(0, np.int32), np.zeros(0), 4, seed=3)
+    run(checker, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0), 4, seed=4)
+
+
+def test_powerlaw_fill(checker):
+    lp = lpgen.scaled_powerlaw_lp(1, 0.01)
+    st = run(checker, lp.row_ptr, lp.col, lp.val, lp.n, seed=5)
+    assert float(st["fill"]) > 0.85, st
