@@ -73,6 +73,42 @@ __device__ __forceinline__ int4 ld_stream(const int4* p, unsigned long long pol)
   return r;
 }
 
+// L2 priority hints for the per-row vectors (DPDLP_L2_HINTS, off: measured 3 % slower on the
+// power-law LP): vectors that the next kernel
+// gathers at random (x_bar, y) are written and gathered evict-last so they stay in L2;
+// vectors only streamed once per launch are read and written evict-first.
+#ifndef DPDLP_L2_HINTS
+#define DPDLP_L2_HINTS 0
+#endif
+__device__ __forceinline__ unsigned long long l2_evict_last_policy() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ double ld_once(const double* p) {
+#if DPDLP_L2_HINTS
+  double r;
+  asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(p), "l"(l2_evict_first_policy()));
+  return r;
+#else
+  return *p;
+#endif
+}
+__device__ __forceinline__ void st_once(double* p, double v) {
+#if DPDLP_L2_HINTS
+  asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(l2_evict_first_policy()) : "memory");
+#else
+  *p = v;
+#endif
+}
+__device__ __forceinline__ void st_keep(double* p, double v) {
+#if DPDLP_L2_HINTS
+  asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(l2_evict_last_policy()) : "memory");
+#else
+  *p = v;
+#endif
+}
+
 // Deterministic block sum (fixed xor-butterfly inside warps, fixed order across warps).
 // The result is valid in thread 0.  `buf` holds TPB/32 doubles.
 __device__ __forceinline__ double block_sum(double v, double* buf) {
@@ -92,35 +128,16 @@ __device__ __forceinline__ double block_sum(double v, double* buf) {
 }
 
 // ---------------------------------------------------------------- epilogues
-// An epilogue turns the row sums of one slot into outputs.  `Stage` is the shared-memory
-// copy of the slot's row vectors, fetched with cp.async when the warp starts its slot so
-// that their latency overlaps the products; `apply` works from it, `apply_direct` (long
-// rows, finished by the lane-per-row pass) reads global memory.
-
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// An epilogue turns finished row sums into outputs: `apply_direct(row, sums)`.
 
 struct StoreEpi1 {
   double* out0;
-  struct Stage {};
   __device__ bool begin() { return true; }
-  __device__ void prefetch(int, int, Stage&, int) {}
-  __device__ void apply(int, int r, const double* s, const Stage&) { out0[r] = s[0]; }
   __device__ void apply_direct(int r, const double* s) { out0[r] = s[0]; }
 };
 struct StoreEpi2 {
   double *out0, *out1;
-  struct Stage {};
   __device__ bool begin() { return true; }
-  __device__ void prefetch(int, int, Stage&, int) {}
-  __device__ void apply(int, int r, const double* s, const Stage&) {
-    out0[r] = s[0];
-    out1[r] = s[1];
-  }
   __device__ void apply_direct(int r, const double* s) {
     out0[r] = s[0];
     out1[r] = s[1];
@@ -164,41 +181,25 @@ struct PrimalEpi {
   const double *c, *lv, *uv, *x0;
   double *x, *xbar, *xh, *dx;
   IterScalars q;
-  struct Stage {
-    double c[MAX_SLOT_ROWS], lv[MAX_SLOT_ROWS], uv[MAX_SLOT_ROWS], x[MAX_SLOT_ROWS],
-        x0[MAX_SLOT_ROWS];
-  };
   __device__ bool begin() { return load_iter(sc, plan, true, q); }
-  __device__ void prefetch(int r0, int nrows, Stage& st, int lane) {
-    const bool hal = !q.check && q.halpern;
-    for (int r = lane; r < nrows; r += LANES) {
-      cp_async8(&st.c[r], c + r0 + r);
-      cp_async8(&st.lv[r], lv + r0 + r);
-      cp_async8(&st.uv[r], uv + r0 + r);
-      cp_async8(&st.x[r], x + r0 + r);
-      if (hal) cp_async8(&st.x0[r], x0 + r0 + r);
-    }
-    cp_async_commit();
-  }
   __device__ void step(int j, double s, double cj, double lvj, double uvj, double xj,
                        const double* x0p) {
     const double xhj = clampd(fma(-q.step, cj - s, xj), lvj, uvj);
     const double xb = fma(2.0, xhj, -xj);
-    xbar[j] = xb;
+    st_keep(xbar + j, xb);
     if (q.check) {
       xh[j] = xhj;
       dx[j] = xj - xhj;
     } else if (q.halpern) {
       const double r = q.gamma_one ? xb : fma(1.0 + q.gamma, xhj, -q.gamma * xj);
-      x[j] = fma(q.w1, r, q.w0 * *x0p);
+      st_once(x + j, fma(q.w1, r, q.w0 * ld_once(x0p)));
     } else {
       x[j] = xhj;
     }
   }
-  __device__ void apply(int lr, int j, const double* s, const Stage& st) {
-    step(j, s[0], st.c[lr], st.lv[lr], st.uv[lr], st.x[lr], &st.x0[lr]);
+  __device__ void apply_direct(int j, const double* s) {
+    step(j, s[0], ld_once(c + j), ld_once(lv + j), ld_once(uv + j), ld_once(x + j), x0 + j);
   }
-  __device__ void apply_direct(int j, const double* s) { step(j, s[0], c[j], lv[j], uv[j], x[j], x0 + j); }
 };
 
 // Dual step per row i, given z = (A x_bar)_i:
@@ -211,20 +212,7 @@ struct DualEpi {
   const double *lo, *hi, *y0;
   double *y, *yh;
   IterScalars q;
-  struct Stage {
-    double lo[MAX_SLOT_ROWS], hi[MAX_SLOT_ROWS], y[MAX_SLOT_ROWS], y0[MAX_SLOT_ROWS];
-  };
   __device__ bool begin() { return load_iter(sc, plan, false, q); }
-  __device__ void prefetch(int r0, int nrows, Stage& st, int lane) {
-    const bool hal = !q.check && q.halpern;
-    for (int r = lane; r < nrows; r += LANES) {
-      cp_async8(&st.lo[r], lo + r0 + r);
-      cp_async8(&st.hi[r], hi + r0 + r);
-      cp_async8(&st.y[r], y + r0 + r);
-      if (hal) cp_async8(&st.y0[r], y0 + r0 + r);
-    }
-    cp_async_commit();
-  }
   __device__ void step(int i, double s, double loi, double hii, double yi, const double* y0p) {
     const double w = fma(yi, q.inv_step, -s);
     const double d = w - clampd(w, loi, hii);
@@ -237,15 +225,14 @@ struct DualEpi {
       } else {
         r = fma(1.0 + q.gamma, q.step * d, -q.gamma * yi);
       }
-      y[i] = fma(q.w1, r, q.w0 * *y0p);
+      st_keep(y + i, fma(q.w1, r, q.w0 * ld_once(y0p)));
     } else {
-      y[i] = q.step * d;
+      st_keep(y + i, q.step * d);
     }
   }
-  __device__ void apply(int lr, int i, const double* s, const Stage& st) {
-    step(i, s[0], st.lo[lr], st.hi[lr], st.y[lr], &st.y0[lr]);
+  __device__ void apply_direct(int i, const double* s) {
+    step(i, s[0], ld_once(lo + i), ld_once(hi + i), ld_once(y + i), y0 + i);
   }
-  __device__ void apply_direct(int i, const double* s) { step(i, s[0], lo[i], hi[i], y[i], y0 + i); }
 };
 
 // ---------------------------------------------------------------- packed SpMV
@@ -253,9 +240,6 @@ struct DualEpi {
 //   DPDLP_PK_MIN_BLOCKS  resident blocks per SM the register allocation targets
 //   DPDLP_GATHER_NOALLOC gather x[col] without allocating in L1 (random, no reuse there)
 //   DPDLP_PK_BATCH       stored entries per pipeline stage of a lane (4 or 8)
-//   DPDLP_PK_STAGE       copy the slot's row vectors to shared memory with cp.async (1) or
-//                        read them from global memory in the epilogue (0); staging takes
-//                        shared memory from L1, which the gathers' in-flight lines need
 //   DPDLP_STREAM_NOALLOC stream matrix values and indices without allocating in L1
 #ifndef DPDLP_PK_MIN_BLOCKS
 #define DPDLP_PK_MIN_BLOCKS 8
@@ -265,9 +249,6 @@ struct DualEpi {
 #endif
 #ifndef DPDLP_PK_BATCH
 #define DPDLP_PK_BATCH 4
-#endif
-#ifndef DPDLP_PK_STAGE
-#define DPDLP_PK_STAGE 0
 #endif
 #ifndef DPDLP_STREAM_NOALLOC
 #define DPDLP_STREAM_NOALLOC 0
@@ -279,7 +260,11 @@ struct GatherVecs {
 };
 
 __device__ __forceinline__ double gather(const double* p) {
-#if DPDLP_GATHER_NOALLOC
+#if DPDLP_L2_HINTS && !DPDLP_GATHER_NOALLOC
+  double r;
+  asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(p), "l"(l2_evict_last_policy()));
+  return r;
+#elif DPDLP_GATHER_NOALLOC
   double r;
   asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(r) : "l"(p));
   return r;
@@ -324,9 +309,6 @@ __global__ void __launch_bounds__(PK_TPB, DPDLP_PK_MIN_BLOCKS) packed_spmv_kerne
   constexpr int B = DPDLP_PK_BATCH;
   constexpr int NB = LANE_ITEMS / B;
   __shared__ double srow[PK_WARPS][NV][MAX_SLOT_ROWS];
-#if DPDLP_PK_STAGE
-  __shared__ typename Epi::Stage stage[PK_WARPS];
-#endif
 
   Epi epi = epi_in;
   if (!epi.begin()) return;  // uniform over the launch
@@ -334,9 +316,6 @@ __global__ void __launch_bounds__(PK_TPB, DPDLP_PK_MIN_BLOCKS) packed_spmv_kerne
   const int s = blockIdx.x * PK_WARPS + w;
   if (s >= M.nslots) return;  // uniform over the warp
   const SlotDesc sd = M.slots[s];
-#if DPDLP_PK_STAGE
-  epi.prefetch(sd.row_base, sd.nrows, stage[w], lane);
-#endif
   const LaneMeta lm = M.lanes[(size_t)s * LANES + lane];
   int rl = lm.row_local, pid = lm.piece_base;
   const size_t off = (size_t)s * SLOT_ITEMS;
@@ -399,19 +378,12 @@ __global__ void __launch_bounds__(PK_TPB, DPDLP_PK_MIN_BLOCKS) packed_spmv_kerne
       }
     }
   }
-#if DPDLP_PK_STAGE
-  cp_async_wait_all();
-#endif
   __syncwarp();
   for (int r = lane; r < sd.nrows; r += LANES) {
     double v[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) v[k] = srow[w][k][r];
-#if DPDLP_PK_STAGE
-    epi.apply(r, sd.row_base + r, v, stage[w]);
-#else
     epi.apply_direct(sd.row_base + r, v);
-#endif
   }
 }
 
