@@ -42,8 +42,10 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="powerlaw", choices=["powerlaw", "powerlaw_quarter", "small"])
     p.add_argument("--e2e-steps", type=int, default=20)
-    p.add_argument("--tol-runs", default="small", choices=["none", "small", "all"],
-                   help="time-to-tolerance runs: small LP only (default), both LPs, or none")
+    p.add_argument("--tol-runs", default="default", choices=["none", "default", "all"],
+                   help="time-to-tolerance runs: default = small LP to 1e-4 and 1e-8 and the "
+                        "benchmark LP to 1e-4 (FP64 and mixed precision); all adds the "
+                        "benchmark LP to 1e-8; none")
     p.add_argument("--cpu-sample-iters", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--host-loop", action="store_true",
@@ -216,20 +218,22 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def time_to_tol(Solver, lp, tol, max_iter, stream):
-    import torch
-
-    s = Solver(torch.cuda.current_device())
-    s.set_stream(stream)
-    s.load(lp)
-    s.solve(tol, 64)  # power iteration and graph build outside the timed solve
+def time_to_tol(s, tol, max_iter, fp32_mode=0):
+    """Fresh solve to ``tol`` on a loaded handle (power iteration and graph build done by a
+    64-iteration solve before the timed one)."""
+    s.set_param("resume", 0)
+    s.set_param("spmv_fp32", fp32_mode)
+    s.solve(tol, 64)
     t0 = time.perf_counter()
     st = s.solve(tol, max_iter)
     dt = time.perf_counter() - t0
     k = s.kkt()
-    s.close()
-    return {"tol": tol, "status": st, "seconds": dt, "iterations": k["iterations"],
-            "restarts": k["restarts"], "rel_kkt": max(k["r_primal"], k["r_dual"], k["r_gap"])}
+    tr = s.trace(1 << 16)
+    switch = next((r["T"] for r in tr if r["spmv_mode"] == 0), None) if fp32_mode else None
+    return {"tol": tol, "form": ["fp64", "mixed_fp32", "fp32_values"][fp32_mode], "status": st,
+            "seconds": dt, "iterations": k["iterations"], "restarts": k["restarts"],
+            "rel_kkt": max(k["r_primal"], k["r_dual"], k["r_gap"]),
+            "fp64_from_iteration": switch}
 
 
 def main():
@@ -309,6 +313,34 @@ def main():
                    "fp64_frac": fp64_ops[k] / (kt[k] * 1e-3) / 1e9 / fp64_peak}
                for k in kt}
 
+    # ---- mixed-precision form: FP32 matrix values (FP64 products), same steps
+    s.set_param("spmv_fp32", 2)
+    s.set_param("resume", 0)
+    T32 = K_CHECK
+    s.solve(0.0, T32)
+    s.set_param("resume", 1)
+    for _ in range(2):
+        T32 += K_CHECK
+        s.solve(0.0, T32)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n32 = max(args.steps // 2, 3)
+    f0.record()
+    for _ in range(n32):
+        T32 += K_CHECK
+        s.solve(0.0, T32)
+    f1.record()
+    torch.cuda.synchronize()
+    value32 = n32 * K_CHECK * world / (f0.elapsed_time(f1) / 1e3)
+    kb32 = kernel_bytes(lp.n, lp.m, lp.nnz, val_bytes=4)
+    kt32 = {k: s.time_kernel(k, 50) for k in ("primal", "dual")}
+    forms = {"fp64": {"value": value, "unit": "iter/s"},
+             "fp32_values": {"value": value32, "unit": "iter/s",
+                             "kernels": {k: {"ms": kt32[k], "GB/s": kb32[k] / (kt32[k] * 1e-3) / 1e9,
+                                             "hbm_frac": kb32[k] / (kt32[k] * 1e-3) / 1e9 / peak}
+                                         for k in kt32}}}
+    s.set_param("spmv_fp32", 0)
+
     # ---- end to end through the C ABI with pinned host buffers
     xh = torch.empty(lp.n, dtype=torch.float64, pin_memory=True).numpy()
     yh = torch.empty(lp.m, dtype=torch.float64, pin_memory=True).numpy()
@@ -330,19 +362,26 @@ def main():
     e2e = {"value": args.e2e_steps * K_CHECK * world / (e2e_ms / 1e3), "unit": "iter/s",
            "h2d_bytes_per_step": 8 * (lp.n + lp.m), "d2h_bytes_per_step": 8 * (lp.n + lp.m),
            "step": "set_start(host x,y) + 64 iterations from it + get_solution(host)"}
-    s.close()
 
-    # ---- time to tolerance
+    # ---- time to tolerance (plain FP64 and mixed precision)
     ttt = {}
     if args.tol_runs != "none" and rank == 0:
+        if args.workload == "powerlaw":
+            for mode in (0, 1):
+                key = f"powerlaw_1e-4_{['fp64', 'mixed_fp32'][mode]}"
+                ttt[key] = time_to_tol(s, 1e-4, 400_000, mode)
+            if args.tol_runs == "all":
+                ttt["powerlaw_1e-8_fp64"] = time_to_tol(s, 1e-8, 2_000_000, 0)
         import lpgen
 
-        small = lpgen.small_random_lp(0)
-        ttt["small_lp_1e-4"] = time_to_tol(Solver, small, 1e-4, 1_000_000, stream)
-        ttt["small_lp_1e-8"] = time_to_tol(Solver, small, 1e-8, 1_000_000, stream)
-        if args.tol_runs == "all":
-            ttt["powerlaw_1e-4"] = time_to_tol(Solver, lp, 1e-4, 400_000, stream)
-            ttt["powerlaw_1e-8"] = time_to_tol(Solver, lp, 1e-8, 400_000, stream)
+        sm = Solver(dev)
+        sm.set_stream(stream)
+        sm.load(lpgen.small_random_lp(0))
+        for tol in (1e-4, 1e-8):
+            for mode in (0, 1):
+                ttt[f"small_lp_{tol:.0e}_{['fp64', 'mixed_fp32'][mode]}"] = time_to_tol(sm, tol, 1_000_000, mode)
+        sm.close()
+    s.close()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -361,7 +400,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "block_permute": 1, "tiles_csr": info["tiles_csr"], "tiles_csc": info["tiles_csc"]},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-        "roofline": roofline, "kernels": kernels,
+        "roofline": roofline, "kernels": kernels, "forms": forms,
         "fp64_peak_Gops": fp64_peak, "time_to_tol": ttt, "preprocess_ms": info["preprocess_ms"],
         "cpu_baseline": cpu,
     }

@@ -72,7 +72,7 @@ typedef struct dpdlp_kkt {
   int64_t restarts;
   int64_t checks;
   int32_t status;    /* DPDLP_CONVERGED / DPDLP_MAX_ITER / DPDLP_NUMERICAL, -1 before a solve */
-  int32_t spmv_mode; /* 0: FP64 matrix values */
+  int32_t spmv_mode; /* iteration products at the end: 0 FP64 values, 1 FP32 values */
 } dpdlp_kkt_t;
 
 /* One record per check, kept in a device ring of the last trace_capacity checks. */
@@ -83,7 +83,7 @@ typedef struct dpdlp_trace {
   double r_fp;      /* fixed-point residual */
   double omega;     /* primal weight used by this check's iteration */
   int32_t restart;  /* 0 none, 1 sufficient decay, 2 necessary decay, 3 artificial */
-  int32_t pad;
+  int32_t spmv_mode;/* values used by this check's iteration: 0 FP64, 1 FP32 */
 } dpdlp_trace_t;
 
 /* Scalar part of a checkpoint (the vector part is x, y, x0, y0). */
@@ -93,6 +93,9 @@ typedef struct dpdlp_scalar_state {
   double r_anchor, r_prev; /* restart references; has_anchor = 0 means "unset" */
   double e_sum, e_prev;    /* PID integral and last error; has_e_prev = 0 means "unset" */
   int32_t has_anchor, has_e_prev;
+  int32_t spmv_mode;       /* 1: iterations use the FP32 values (mixed precision) */
+  int32_t stall_checks;    /* FP32 mode: checks since the KKT error last halved */
+  double best_kkt;         /* FP32 mode: best KKT error so far */
 } dpdlp_scalar_state_t;
 
 /* Sizes and layout facts of the loaded LP. */
@@ -151,7 +154,13 @@ int dpdlp_set_row_bounds(dpdlp_t* h, const double* lc, const double* uc);
  *   beta_artificial (0.36), pid (1), pid_kp (0.99), pid_ki (0.01), pid_kd (0.0),
  *   block_permute (1), perm_block (256), perm_seed (1), use_graph (1),
  *   ptr_mode_device (0), resume (0: each solve starts from the start point; 1: continue
- *   from the current state), trace_capacity (4096).
+ *   from the current state), trace_capacity (4096), spmv_fp32 (0: FP64 matrix values;
+ *   1: mixed precision -- the iteration products use an FP32 copy of A's values, formed
+ *   and accumulated in FP64, until the KKT error reaches fp32_switch_tol (1e-6), or is below
+ *   100 x fp32_switch_tol and fails to halve over fp32_stall_checks (64) consecutive checks,
+ *   then FP64 values; 2: FP32 values
+ *   throughout).  KKT, restart and step-size products always use FP64 values.  Needs every
+ *   value of A to round to a normal float or zero, else the FP64 values are used.
  * Load-time keys (block_permute, perm_block, perm_seed) take effect at the next
  * dpdlp_load_lp.  Unknown key or out-of-range value: DPDLP_ERR_INVALID. */
 int dpdlp_set_param(dpdlp_t* h, const char* key, double v);

@@ -49,13 +49,15 @@ struct LaneMeta {
 };
 
 // Host copy of one packed orientation.  Item (lane l, position p) of slot s is stored at
-// val[s*SLOT_ITEMS + ((p/2)*LANES + l)*2 + p%2] and idx[s*SLOT_ITEMS + ((p/4)*LANES + l)*4 + p%4],
-// so a warp reads a slot with 16-byte loads that cover 512 contiguous bytes.
+// val[s*SLOT_ITEMS + ((p/2)*LANES + l)*2 + p%2] and idx[s*SLOT_ITEMS + ((p/4)*LANES + l)*4 + p%4]
+// (val32 like idx), so a warp reads a slot with 16-byte loads that cover 512 contiguous bytes.
 struct HostPacked {
   int rows = 0, cols = 0;
   int nslots = 0, nshort = 0, nlong = 0, npieces = 0;
   int nlong_block = 0, nlong_warp = 0;  // leading long rows finished by a block / a warp
   std::vector<double> val;
+  std::vector<float> val32;         // FP32 copy, stored like idx (groups of 4 per lane)
+  bool fp32_exact_range = true;     // every value rounds to a normal float (or is zero)
   std::vector<uint32_t> idx;
   std::vector<SlotDesc> slots;
   std::vector<LaneMeta> lanes;
@@ -70,6 +72,7 @@ struct DevPacked {
   int rows = 0, cols = 0, nslots = 0, nlong = 0, npieces = 0;
   int nlong_block = 0, nlong_warp = 0;
   const double* val = nullptr;
+  const float* val32 = nullptr;  // FP32 copy of the values (nullptr: not representable)
   const uint32_t* idx = nullptr;
   const SlotDesc* slots = nullptr;
   const LaneMeta* lanes = nullptr;
@@ -118,6 +121,12 @@ struct DevScalars {
   int apply_mode;   // what the apply kernel does: 0 Halpern step, 1 restart, 2 nothing
   double w1_check, w0_check;  // Halpern weights of the check iteration
   int sched_len;    // forced restart schedule length (0: off)
+  int spmv_fp32;    // iteration products use the FP32 values (mixed precision)
+  int fp32_switch;  // switch to FP64 values when the KKT error stalls
+  int stall_checks; // consecutive checks without halving the best KKT error (FP32 mode)
+  int fp32_stall_limit;    // ... after this many such checks: FP64 values
+  double best_kkt;  // best max(r_primal, r_dual, r_gap) seen in FP32 mode
+  double fp32_switch_tol;  // FP64 values once the KKT error is at or below this
   int trace_cap;
   long long trace_count;
   double w1[KMAX], w0[KMAX];  // Halpern weights (k+1)/(k+2), 1/(k+2) of each body iteration

@@ -58,6 +58,13 @@ __device__ __forceinline__ double2 ld_stream(const double2* p, unsigned long lon
       : "l"(p), "l"(pol));
   return r;
 }
+__device__ __forceinline__ float4 ld_stream(const float4* p, unsigned long long pol) {
+  float4 r;
+  asm("ld.global.nc" DPDLP_LDS_L1 ".L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+      : "l"(p), "l"(pol));
+  return r;
+}
 __device__ __forceinline__ uint4 ld_stream(const uint4* p, unsigned long long pol) {
   uint4 r;
   asm("ld.global.nc" DPDLP_LDS_L1 ".L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
@@ -133,11 +140,13 @@ __device__ __forceinline__ double block_sum(double v, double* buf) {
 struct StoreEpi1 {
   double* out0;
   __device__ bool begin() { return true; }
+  __device__ bool fp32() const { return false; }  // KKT and step-size products: FP64 values
   __device__ void apply_direct(int r, const double* s) { out0[r] = s[0]; }
 };
 struct StoreEpi2 {
   double *out0, *out1;
   __device__ bool begin() { return true; }
+  __device__ bool fp32() const { return false; }
   __device__ void apply_direct(int r, const double* s) {
     out0[r] = s[0];
     out1[r] = s[1];
@@ -147,7 +156,7 @@ struct StoreEpi2 {
 // Per-iteration scalars read from device memory by the fused epilogues.
 struct IterScalars {
   double step, inv_step, two_step, w1, w0, gamma;
-  int check, halpern, gamma_one;
+  int check, halpern, gamma_one, fp32;
 };
 
 __device__ __forceinline__ bool load_iter(const DevScalars* sc, IterPlan p, bool primal,
@@ -167,6 +176,7 @@ __device__ __forceinline__ bool load_iter(const DevScalars* sc, IterPlan p, bool
   o.gamma = sc->gamma;
   o.halpern = sc->halpern;
   o.gamma_one = (sc->gamma == 1.0);
+  o.fp32 = sc->spmv_fp32;
   return true;
 }
 
@@ -182,6 +192,7 @@ struct PrimalEpi {
   double *x, *xbar, *xh, *dx;
   IterScalars q;
   __device__ bool begin() { return load_iter(sc, plan, true, q); }
+  __device__ bool fp32() const { return q.fp32 != 0; }
   __device__ void step(int j, double s, double cj, double lvj, double uvj, double xj,
                        const double* x0p) {
     const double xhj = clampd(fma(-q.step, cj - s, xj), lvj, uvj);
@@ -213,6 +224,7 @@ struct DualEpi {
   double *y, *yh;
   IterScalars q;
   __device__ bool begin() { return load_iter(sc, plan, false, q); }
+  __device__ bool fp32() const { return q.fp32 != 0; }
   __device__ void step(int i, double s, double loi, double hii, double yi, const double* y0p) {
     const double w = fma(yi, q.inv_step, -s);
     const double d = w - clampd(w, loi, hii);
@@ -274,17 +286,57 @@ __device__ __forceinline__ double gather(const double* p) {
 }
 
 // Values and indices of batch b (positions B*b .. B*b+B-1) of this lane: 16-byte loads,
-// each covering 512 contiguous bytes across the warp.
-template <int B>
-__device__ __forceinline__ void load_vals(const double2* vp, int b, double (&v)[B],
-                                          unsigned long long pol) {
-#pragma unroll
-  for (int q = 0; q < B / 2; ++q) {
-    const double2 d = ld_stream(vp + ((B / 2) * b + q) * LANES, pol);
-    v[2 * q] = d.x;
-    v[2 * q + 1] = d.y;
+// each covering 512 contiguous bytes across the warp.  FP64 values are stored in pairs per
+// lane, FP32 values and indices in fours.
+template <typename V>
+struct Vals;
+template <>
+struct Vals<double> {
+  using vec = double2;
+  static __device__ __forceinline__ const double2* base(const DevPacked& M, size_t off, int lane) {
+    return reinterpret_cast<const double2*>(M.val + off) + lane;
   }
-}
+  template <int B>
+  static __device__ __forceinline__ void load(const double2* vp, int b, double (&v)[B],
+                                              unsigned long long pol) {
+#pragma unroll
+    for (int q = 0; q < B / 2; ++q) {
+      const double2 d = ld_stream(vp + ((B / 2) * b + q) * LANES, pol);
+      v[2 * q] = d.x;
+      v[2 * q + 1] = d.y;
+    }
+  }
+  static __device__ __forceinline__ double widen(double v) { return v; }
+};
+template <>
+struct Vals<float> {
+  using vec = float4;
+  static __device__ __forceinline__ const float4* base(const DevPacked& M, size_t off, int lane) {
+    return reinterpret_cast<const float4*>(M.val32 + off) + lane;
+  }
+  template <int B>
+  static __device__ __forceinline__ void load(const float4* vp, int b, float (&v)[B],
+                                              unsigned long long pol) {
+#pragma unroll
+    for (int q = 0; q < B / 4; ++q) {
+      const float4 d = ld_stream(vp + ((B / 4) * b + q) * LANES, pol);
+      v[4 * q] = d.x;
+      v[4 * q + 1] = d.y;
+      v[4 * q + 2] = d.z;
+      v[4 * q + 3] = d.w;
+    }
+  }
+  // Exact float -> double for normal floats and zero (the only values the packing stores
+  // in FP32 mode), with integer operations: rebias the exponent (+896) and shift the
+  // fraction into place.  Keeps the conversion off the FP64 unit.
+  static __device__ __forceinline__ double widen(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned long long mag = b & 0x7fffffffu;
+    const unsigned long long d = mag ? ((mag + (896ull << 23)) << 29) : 0ull;
+    return __longlong_as_double((long long)(d | ((unsigned long long)(b & 0x80000000u) << 32)));
+  }
+};
+
 template <int B>
 __device__ __forceinline__ void load_idx(const uint4* ip, int b, uint32_t (&c)[B],
                                          unsigned long long pol) {
@@ -298,39 +350,29 @@ __device__ __forceinline__ void load_idx(const uint4* ip, int b, uint32_t (&c)[B
   }
 }
 
-// One warp per slot, four slots per block, no block-level barrier.  Each lane sums the
-// 32 stored nonzeros of its lane in order, one FMA each, and at every end flag writes the
-// finished sum: short rows to shared memory, long-row pieces to the piece array.  Then the
-// lanes apply the epilogue to the slot's short rows, one row per lane.  The lane's items
-// go through a three-stage pipeline of batches: indices two batches ahead, values and the
-// x[col] gathers one batch ahead, so gathers are in flight while the FMA chain runs.
-template <int NV, class Epi>
-__global__ void __launch_bounds__(PK_TPB, DPDLP_PK_MIN_BLOCKS) packed_spmv_kernel(DevPacked M, GatherVecs<NV> g, Epi epi_in) {
+// The 32 stored nonzeros of one lane, summed in order with one FMA each (products formed
+// in FP64 from values of type V); at every end flag the finished sum goes to the slot's row
+// sums (short rows) or to the piece array (long-row pieces).  Three-stage pipeline of
+// batches: indices two batches ahead, values and the x[col] gathers one batch ahead, so
+// gathers are in flight while the FMA chain runs.
+template <typename V, int NV>
+__device__ __forceinline__ void lane_sums(const DevPacked& M, const GatherVecs<NV>& g, size_t off,
+                                          int lane, int rl, int pid,
+                                          double (*srow)[MAX_SLOT_ROWS]) {
   constexpr int B = DPDLP_PK_BATCH;
   constexpr int NB = LANE_ITEMS / B;
-  __shared__ double srow[PK_WARPS][NV][MAX_SLOT_ROWS];
-
-  Epi epi = epi_in;
-  if (!epi.begin()) return;  // uniform over the launch
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = blockIdx.x * PK_WARPS + w;
-  if (s >= M.nslots) return;  // uniform over the warp
-  const SlotDesc sd = M.slots[s];
-  const LaneMeta lm = M.lanes[(size_t)s * LANES + lane];
-  int rl = lm.row_local, pid = lm.piece_base;
-  const size_t off = (size_t)s * SLOT_ITEMS;
-  const double2* vp = reinterpret_cast<const double2*>(M.val + off) + lane;
+  const auto* vp = Vals<V>::base(M, off, lane);
   const uint4* ip = reinterpret_cast<const uint4*>(M.idx + off) + lane;
   const unsigned long long pol = l2_evict_first_policy();
-
   double acc[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = 0.0;
   uint32_t c0[B], c1[B];
-  double v0[B], x0v[NV][B];
+  V v0[B];
+  double x0v[NV][B];
   load_idx<B>(ip, 0, c0, pol);
   if (NB > 1) load_idx<B>(ip, 1, c1, pol);
-  load_vals<B>(vp, 0, v0, pol);
+  Vals<V>::template load<B>(vp, 0, v0, pol);
 #pragma unroll
   for (int j = 0; j < B; ++j) {
 #pragma unroll
@@ -339,10 +381,11 @@ __global__ void __launch_bounds__(PK_TPB, DPDLP_PK_MIN_BLOCKS) packed_spmv_kerne
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     uint32_t c2[B];
-    double v1[B], x1v[NV][B];
+    V v1[B];
+    double x1v[NV][B];
     if (b + 2 < NB) load_idx<B>(ip, b + 2, c2, pol);
     if (b + 1 < NB) {
-      load_vals<B>(vp, b + 1, v1, pol);
+      Vals<V>::template load<B>(vp, b + 1, v1, pol);
 #pragma unroll
       for (int j = 0; j < B; ++j) {
 #pragma unroll
@@ -351,8 +394,9 @@ __global__ void __launch_bounds__(PK_TPB, DPDLP_PK_MIN_BLOCKS) packed_spmv_kerne
     }
 #pragma unroll
     for (int j = 0; j < B; ++j) {
+      const double a = Vals<V>::widen(v0[j]);
 #pragma unroll
-      for (int k = 0; k < NV; ++k) acc[k] = fma(v0[j], x0v[k][j], acc[k]);
+      for (int k = 0; k < NV; ++k) acc[k] = fma(a, x0v[k][j], acc[k]);
       if (c0[j] & END_BIT) {
         if (c0[j] & PIECE_BIT) {
 #pragma unroll
@@ -360,7 +404,7 @@ __global__ void __launch_bounds__(PK_TPB, DPDLP_PK_MIN_BLOCKS) packed_spmv_kerne
           ++pid;
         } else {
 #pragma unroll
-          for (int k = 0; k < NV; ++k) srow[w][k][rl] = acc[k];
+          for (int k = 0; k < NV; ++k) srow[k][rl] = acc[k];
           ++rl;
         }
 #pragma unroll
@@ -378,6 +422,25 @@ __global__ void __launch_bounds__(PK_TPB, DPDLP_PK_MIN_BLOCKS) packed_spmv_kerne
       }
     }
   }
+}
+
+// One warp per slot, PK_WARPS slots per block, no block-level barrier: the lanes sum their
+// rows (lane_sums), then apply the epilogue to the slot's short rows, one row per lane.
+template <int NV, class Epi>
+__global__ void __launch_bounds__(PK_TPB, DPDLP_PK_MIN_BLOCKS) packed_spmv_kernel(DevPacked M, GatherVecs<NV> g, Epi epi_in) {
+  __shared__ double srow[PK_WARPS][NV][MAX_SLOT_ROWS];
+  Epi epi = epi_in;
+  if (!epi.begin()) return;  // uniform over the launch
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.x * PK_WARPS + w;
+  if (s >= M.nslots) return;  // uniform over the warp
+  const SlotDesc sd = M.slots[s];
+  const LaneMeta lm = M.lanes[(size_t)s * LANES + lane];
+  const size_t off = (size_t)s * SLOT_ITEMS;
+  if (epi.fp32() && M.val32)  // uniform over the launch
+    lane_sums<float, NV>(M, g, off, lane, lm.row_local, lm.piece_base, srow[w]);
+  else
+    lane_sums<double, NV>(M, g, off, lane, lm.row_local, lm.piece_base, srow[w]);
   __syncwarp();
   for (int r = lane; r < sd.nrows; r += LANES) {
     double v[NV];
@@ -582,6 +645,18 @@ __global__ void __launch_bounds__(TPB) control_kernel(DevVecs v, DevScalars* sc,
     const long long check_idx = s.checks;
     s.checks += 1;
     s.r_p = r_p; s.r_d = r_d; s.r_g = r_g; s.obj_p = obj_p; s.obj_d = obj_d; s.r_fp = r;
+    const int mode_used = s.spmv_fp32;
+    if (s.spmv_fp32 && s.fp32_switch) {  // mixed precision: FP64 values once the error is
+      const double kk = fmax(r_p, fmax(r_d, r_g));  // small enough or stops halving
+      if (kk <= s.fp32_switch_tol) {
+        s.spmv_fp32 = 0;
+      } else if (kk <= 0.5 * s.best_kkt) {
+        s.best_kkt = kk;
+        s.stall_checks = 0;
+      } else if (kk <= 100.0 * s.fp32_switch_tol && ++s.stall_checks >= s.fp32_stall_limit) {
+        s.spmv_fp32 = 0;  // stalled near the floor the FP32 values set
+      }
+    }
     bool finite = isfinite(r) && isfinite(r_p) && isfinite(r_d) && isfinite(r_g);
     for (int k = 0; k < NRED; ++k) finite = finite && isfinite(R[k]) && isfinite(C[k]);
     int kind = 0;
@@ -657,7 +732,7 @@ __global__ void __launch_bounds__(TPB) control_kernel(DevVecs v, DevScalars* sc,
       tr->r_fp = r;
       tr->omega = omega;
       tr->restart = kind;
-      tr->pad = 0;
+      tr->spmv_mode = mode_used;
       s.trace_count += 1;
     }
     if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, go);

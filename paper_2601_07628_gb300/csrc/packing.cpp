@@ -8,6 +8,8 @@
 // renumbered in slot / lane / position order, so each slot's rows are consecutive and its
 // row vectors are read with coalesced loads; long rows come after all short rows.
 #include <algorithm>
+#include <cfloat>
+#include <cmath>
 #include <numeric>
 
 #include "internal.h"
@@ -169,6 +171,7 @@ void build_packed(int rows, int cols, const std::vector<int64_t>& ptr,
   out.npieces = P.npieces;
   out.stored = (int64_t)out.nslots * SLOT_ITEMS;
   out.val.assign(out.stored, 0.0);  // padding: value 0, column 0, no flag
+  out.val32.assign(out.stored, 0.0f);
   out.idx.assign(out.stored, 0u);
   out.slots = P.slots;
   out.lanes.assign((size_t)out.nslots * LANES, LaneMeta{0, 0});
@@ -184,9 +187,13 @@ void build_packed(int rows, int cols, const std::vector<int64_t>& ptr,
       const int32_t lane = P.slot_lanes[(size_t)s * LANES + l];
       if (lane < 0) continue;
       int p = 0;
+      float* sf = out.val32.data() + (size_t)s * SLOT_ITEMS;
       auto put = [&](double v, uint32_t c) {
         sv[((p >> 1) * LANES + l) * 2 + (p & 1)] = v;
         si[((p >> 2) * LANES + l) * 4 + (p & 3)] = c;
+        const float f = (float)v;
+        if (v != 0.0 && !(std::isfinite(f) && std::fabs(f) >= FLT_MIN)) out.fp32_exact_range = false;
+        sf[((p >> 2) * LANES + l) * 4 + (p & 3)] = f;
         ++p;
       };
       for (int k = P.lane_ptr[lane]; k < P.lane_ptr[lane + 1]; ++k) {

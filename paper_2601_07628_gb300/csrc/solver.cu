@@ -52,6 +52,9 @@ std::map<std::string, Param> default_params() {
       {"ptr_mode_device", {0, 0, 1, true}},
       {"resume", {0, 0, 1, true}},
       {"trace_capacity", {4096, 0, 1 << 20, true}},
+      {"spmv_fp32", {0, 0, 2, true}},
+      {"fp32_switch_tol", {1e-6, 0.0, 1.0, false}},
+      {"fp32_stall_checks", {64, 1, 1 << 30, true}},
   };
 }
 
@@ -159,12 +162,14 @@ int upload_packed(dpdlp* h, const HostPacked& H, DevPacked& D) {
   D.nlong_warp = H.nlong_warp;
   int rc;
   double *val, *psum;
+  float* val32 = nullptr;
   uint32_t* idx;
   SlotDesc* slots;
   LaneMeta* lanes;
   int32_t *lrow, *lptr, *lpiece;
   if ((rc = dalloc(h, &val, H.val.size()))) return rc;
   if ((rc = dalloc(h, &idx, H.idx.size()))) return rc;
+  if (H.fp32_exact_range && (rc = dalloc(h, &val32, H.val32.size()))) return rc;
   if ((rc = dalloc(h, &slots, H.slots.size()))) return rc;
   if ((rc = dalloc(h, &lanes, H.lanes.size()))) return rc;
   if ((rc = dalloc(h, &lrow, H.long_row.size()))) return rc;
@@ -176,12 +181,14 @@ int upload_packed(dpdlp* h, const HostPacked& H, DevPacked& D) {
   };
   CK(up(val, H.val.data(), H.val.size() * sizeof(double)));
   CK(up(idx, H.idx.data(), H.idx.size() * sizeof(uint32_t)));
+  if (val32) CK(up(val32, H.val32.data(), H.val32.size() * sizeof(float)));
   CK(up(slots, H.slots.data(), H.slots.size() * sizeof(SlotDesc)));
   CK(up(lanes, H.lanes.data(), H.lanes.size() * sizeof(LaneMeta)));
   CK(up(lrow, H.long_row.data(), H.long_row.size() * sizeof(int32_t)));
   CK(up(lptr, H.long_ptr.data(), H.long_ptr.size() * sizeof(int32_t)));
   CK(up(lpiece, H.long_piece.data(), H.long_piece.size() * sizeof(int32_t)));
   D.val = val;
+  D.val32 = val32;
   D.idx = idx;
   D.slots = slots;
   D.lanes = lanes;
@@ -316,6 +323,9 @@ void copy_params(dpdlp* h, DevScalars& s) {
   s.bnorm = h->bnorm;
   s.cnorm = h->cnorm;
   s.trace_cap = h->trace_cap;
+  s.fp32_switch = h->P("spmv_fp32") == 1.0;
+  s.fp32_switch_tol = h->P("fp32_switch_tol");
+  s.fp32_stall_limit = (int)h->P("fp32_stall_checks");
 }
 
 // Fresh start: x = proj_X(0) (or the warm start), y = 0 (or the warm start), anchor = start.
@@ -347,6 +357,8 @@ int init_fresh(dpdlp* h) {
   s.inv_sigma = 1.0 / s.sigma;
   s.status = -1;
   s.apply_mode = 2;
+  s.spmv_fp32 = (h->P("spmv_fp32") >= 1.0 && h->csr.val32 && h->csc.val32) ? 1 : 0;
+  s.best_kkt = INFINITY;
   h->has_state = true;
   return 0;
 }
@@ -687,7 +699,7 @@ int dpdlp_get_kkt(dpdlp_t* h, dpdlp_kkt_t* o) {
   o->restarts = s.restarts;
   o->checks = s.checks;
   o->status = h->has_state ? s.status : -1;
-  o->spmv_mode = 0;
+  o->spmv_mode = s.spmv_fp32;
   return 0;
 }
 
@@ -735,6 +747,9 @@ int dpdlp_get_state(dpdlp_t* h, double* x, double* y, double* x0, double* y0,
     st->e_prev = s.e_prev;
     st->has_anchor = s.has_anchor;
     st->has_e_prev = s.has_e_prev;
+    st->spmv_mode = s.spmv_fp32;
+    st->stall_checks = s.stall_checks;
+    st->best_kkt = s.best_kkt;
   }
   return 0;
 }
@@ -773,6 +788,9 @@ int dpdlp_set_state(dpdlp_t* h, const double* x, const double* y, const double* 
   s.e_prev = st->e_prev;
   s.has_anchor = st->has_anchor;
   s.has_e_prev = st->has_e_prev;
+  s.spmv_fp32 = (st->spmv_mode && h->csr.val32 && h->csc.val32) ? 1 : 0;
+  s.stall_checks = st->stall_checks;
+  s.best_kkt = st->best_kkt;
   s.status = -1;
   s.apply_mode = 2;
   h->has_state = true;

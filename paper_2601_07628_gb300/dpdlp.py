@@ -40,13 +40,14 @@ class Trace(C.Structure):
     _fields_ = [("T", C.c_int64), ("k", C.c_int64)] + \
                [(k, C.c_double) for k in ("r_primal", "r_dual", "r_gap", "obj_p", "obj_d", "r_fp",
                                           "omega")] + \
-               [("restart", C.c_int32), ("pad", C.c_int32)]
+               [("restart", C.c_int32), ("spmv_mode", C.c_int32)]
 
 
 class ScalarState(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("T", "k", "restarts", "checks")] + \
                [(k, C.c_double) for k in ("eta", "omega", "r_anchor", "r_prev", "e_sum", "e_prev")] + \
-               [("has_anchor", C.c_int32), ("has_e_prev", C.c_int32)]
+               [("has_anchor", C.c_int32), ("has_e_prev", C.c_int32),
+                ("spmv_mode", C.c_int32), ("stall_checks", C.c_int32), ("best_kkt", C.c_double)]
 
 
 class Info(C.Structure):
@@ -250,7 +251,7 @@ class Solver:
         buf = (Trace * cap)()
         cnt = C.c_int32()
         self._check(self.lib.dpdlp_get_trace(self.h, buf, cap, C.byref(cnt)))
-        return [{f: getattr(buf[i], f) for f, _ in Trace._fields_ if f != "pad"} for i in range(cnt.value)]
+        return [{f: getattr(buf[i], f) for f, _ in Trace._fields_} for i in range(cnt.value)]
 
     def get_state(self) -> dict:
         self._mode()
