@@ -8,6 +8,9 @@ fixed-point residual, restart, PID).  ``value`` is PDHG iterations per second wi
 resident in HBM; ``e2e`` is the same metric through the C ABI with host buffers (pinned):
 each step uploads the start point, runs 64 iterations from it and reads the solution back.
 
+``batch`` (default run): 256 uneven LPs solved together in one handle against the same LPs
+solved one after another (time to 1e-4), plus the batch's iteration throughput.
+
 ``--impl reference`` times the CPU oracle on the same workload and metric (one PDHG
 iteration per step, on the host cores).  With torchrun (N > 1) every rank solves its own
 copy (replicas, no collective on the data path); rank 0 prints.
@@ -48,6 +51,10 @@ def parse():
                         "benchmark LP to 1e-8; none")
     p.add_argument("--cpu-sample-iters", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batch", action="store_true",
+                   help="skip the batched form (256 uneven LPs solved together vs one by one)")
+    p.add_argument("--batch-count", type=int, default=256)
+    p.add_argument("--batch-tol", type=float, default=1e-4)
     p.add_argument("--host-loop", action="store_true",
                    help="launch the iteration kernels from a host loop instead of the CUDA graph "
                         "(same kernels; for profilers that do not descend into graph loops)")
@@ -236,6 +243,122 @@ def time_to_tol(s, tol, max_iter, fp32_mode=0):
             "fp64_from_iteration": switch}
 
 
+def _uneven(args):
+    import lpgen
+
+    return lpgen.uneven_lp(*args)
+
+
+def make_batch(count, seed=3):
+    """The batched workload (``lpgen.batch_lps``), instances generated in a process pool
+    started with spawn."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    import lpgen
+
+    ms = lpgen.batch_sizes(seed, count)
+    jobs = [(1000 * seed + i, int(mi)) for i, mi in enumerate(ms)]
+    workers = max(1, min(16, os.cpu_count() or 1))
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_uneven, jobs, chunksize=4))
+
+
+def launches_per_body(info, ninst):
+    """Kernel launches of one graph body (K iterations and one check)."""
+    lr, lc = int(info["long_rows"] > 0), int(info["long_cols"] > 0)
+    it = (1 + lc) + (1 + lr)
+    check = (1 + lr) + (1 + lc) + int(info["m"] > 0) + int(info["n"] > 0) + 2 + 1
+    return K_CHECK * it + check
+
+
+def run_batch(args, dev, stream, peak):
+    """Batched form: the LPs in one handle (per-instance step sizes, weights, restarts and
+    statuses; converged instances are skipped), against the same LPs solved one after
+    another with the plain single-LP path.  Power iteration and graph capture happen in an
+    untimed 64-iteration solve before each timed solve, on both sides."""
+    import numpy as np
+    import torch
+
+    from paper_2601_07628_gb300 import autotune
+    from paper_2601_07628_gb300.costmodel import kernel_bytes
+    from paper_2601_07628_gb300.dpdlp import Solver
+
+    t0 = time.perf_counter()
+    lps = make_batch(args.batch_count)
+    gen_s = time.perf_counter() - t0
+    n = sum(lp.n for lp in lps)
+    m = sum(lp.m for lp in lps)
+    nnz = sum(lp.nnz for lp in lps)
+    s = Solver(dev)
+    s.set_stream(stream)
+    t0 = time.perf_counter()
+    s.load_batch(lps)
+    load_s = time.perf_counter() - t0
+    info = s.info()
+    tune = autotune.tune(s, cache=os.path.join(tempfile.gettempdir(), "dpdlp_autotune.json"),
+                         reps=10, rounds=2, force=True)
+    # throughput with every instance running (fixed iteration counts, no convergence)
+    s.set_param("resume", 1)
+    T = 0
+    for _ in range(3):
+        T += K_CHECK
+        s.solve(0.0, T)
+    torch.cuda.synchronize()
+    steps = max(3, args.steps // 10)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        T += K_CHECK
+        s.solve(0.0, T)
+    e1.record()
+    torch.cuda.synchronize()
+    it_s = steps * K_CHECK / (e0.elapsed_time(e1) / 1e3)
+    kb = kernel_bytes(n, m, nnz)
+    kt = {k: s.time_kernel(k, 20) for k in ("primal", "dual")}
+    kern = {k: {"ms": kt[k], "GB/s": kb[k] / (kt[k] * 1e-3) / 1e9,
+                "hbm_frac": kb[k] / (kt[k] * 1e-3) / 1e9 / peak} for k in kt}
+    # batched solve to tolerance
+    tol = args.batch_tol
+    s.set_param("resume", 0)
+    s.solve(tol, K_CHECK)
+    t0 = time.perf_counter()
+    st = s.solve(tol, 500_000)
+    batched_s = time.perf_counter() - t0
+    bk = s.batch_kkt()
+    iters = np.array([k["iterations"] for k in bk], dtype=np.float64)
+    s.close()
+    # the same LPs one by one
+    seq_s, seq_iters, seq_status, seq_load = 0.0, [], [], 0.0
+    one = Solver(dev)
+    one.set_stream(stream)
+    for lp in lps:
+        t0 = time.perf_counter()
+        one.load(lp)
+        seq_load += time.perf_counter() - t0
+        r = time_to_tol(one, tol, 500_000, 0)
+        seq_s += r["seconds"]
+        seq_iters.append(r["iterations"])
+        seq_status.append(r["status"])
+    one.close()
+    sgm10 = float(np.exp(np.mean(np.log(iters + 10.0))) - 10.0)
+    return {
+        "workload": f"{len(lps)} uneven LPs (m_i ~ U{{500..50000}}, n_i = 2 m_i, 5-15 nnz/col, seed 3): "
+                    f"n={n:,} m={m:,} nnz={nnz:,}",
+        "generate_s": gen_s, "load_s": load_s, "preprocess_ms": info["preprocess_ms"],
+        "autotune": {k: tune[k] for k in ("cta_slots_primal", "cta_slots_dual", "ms")},
+        "iter_per_s_all_running": it_s, "kernels": kern,
+        "gpu_launches_per_body": launches_per_body(info, len(lps)),
+        "tol": tol, "batched": {"seconds": batched_s, "status": st,
+                                "converged": int(sum(k["status"] == 0 for k in bk)),
+                                "max_iterations": int(iters.max()), "sgm10_iterations": sgm10},
+        "sequential": {"seconds": seq_s, "load_s": seq_load,
+                       "converged": int(sum(x == 0 for x in seq_status)),
+                       "max_iterations": int(max(seq_iters))},
+        "speedup_vs_sequential": seq_s / batched_s if batched_s > 0 else None,
+    }
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
@@ -382,6 +505,9 @@ def main():
                 ttt[f"small_lp_{tol:.0e}_{['fp64', 'mixed_fp32'][mode]}"] = time_to_tol(sm, tol, 1_000_000, mode)
         sm.close()
     s.close()
+    batch = None
+    if rank == 0 and args.workload == "powerlaw" and not args.no_batch:
+        batch = run_batch(args, dev, stream, peak)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -389,7 +515,7 @@ def main():
 
     if rank != 0:
         return
-    launches_per_step = 2 * K_CHECK + 6
+    launches_per_step = launches_per_body(info, 1)
     line = {
         "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -402,7 +528,7 @@ def main():
         "clocks": clk, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
         "roofline": roofline, "kernels": kernels, "forms": forms,
         "fp64_peak_Gops": fp64_peak, "time_to_tol": ttt, "preprocess_ms": info["preprocess_ms"],
-        "cpu_baseline": cpu,
+        "cpu_baseline": cpu, "batch": batch,
     }
     print(json.dumps(line), flush=True)
 

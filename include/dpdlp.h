@@ -23,7 +23,8 @@
  *   - Arrays are plain C arrays in the caller's index order (the library permutes
  *     internally and undoes it on output).  Sizes: n = number of variables (columns of A),
  *     m = number of rows.
- *   - Pointer location: dpdlp_load_lp and dpdlp_set_row_bounds take HOST pointers.  Vector
+ *   - Pointer location: dpdlp_load_lp, dpdlp_load_batch and dpdlp_set_row_bounds take
+ *     HOST pointers.  Vector
  *     arguments of dpdlp_set_start, dpdlp_get_solution, dpdlp_get_state, dpdlp_set_state,
  *     dpdlp_apply_A and dpdlp_apply_AT are HOST pointers by default and DEVICE pointers
  *     (on the handle's device) after dpdlp_set_param(h, "ptr_mode_device", 1).
@@ -75,7 +76,9 @@ typedef struct dpdlp_kkt {
   int32_t spmv_mode; /* iteration products at the end: 0 FP64 values, 1 FP32 values */
 } dpdlp_kkt_t;
 
-/* One record per check, kept in a device ring of the last trace_capacity checks. */
+/* One record per check and instance (a batch of N instances writes N records per check,
+ * instance order, every instance every check), kept in a device ring of the last
+ * trace_capacity records. */
 typedef struct dpdlp_trace {
   int64_t T;        /* total iterations at the check */
   int64_t k;        /* iterations since the last restart, after this check's iteration */
@@ -84,6 +87,8 @@ typedef struct dpdlp_trace {
   double omega;     /* primal weight used by this check's iteration */
   int32_t restart;  /* 0 none, 1 sufficient decay, 2 necessary decay, 3 artificial */
   int32_t spmv_mode;/* values used by this check's iteration: 0 FP64, 1 FP32 */
+  int32_t inst;     /* instance of a batch (0 for a single LP) */
+  int32_t status;   /* the instance's status after the check (-1 still running) */
 } dpdlp_trace_t;
 
 /* Scalar part of a checkpoint (the vector part is x, y, x0, y0). */
@@ -143,6 +148,30 @@ int dpdlp_load_lp(dpdlp_t* h, int32_t n, int32_t m, const double* c, const int64
                   const int32_t* col_idx, const double* val, const double* b,
                   const double* lv, const double* uv, const int8_t* ctype);
 
+/* Load a batch of `count` independent LPs into one handle (the batched solve of many
+ * small and medium LPs; the instances iterate together in the same kernels).  The
+ * arguments are those of dpdlp_load_lp for the block-diagonal LP that stacks the
+ * instances, plus HOST ranges row_off[count+1] and col_off[count+1]: instance i owns rows
+ * [row_off[i], row_off[i+1]) and columns [col_off[i], col_off[i+1]) (row_off[0] =
+ * col_off[0] = 0, non-decreasing, row_off[count] = m, col_off[count] = n), and every
+ * nonzero of its rows must lie in its columns (else DPDLP_ERR_INVALID).  Each instance
+ * gets its own step size (power iteration on its own block), primal weight, restart
+ * epoch, PID state, mixed-precision switch and status; the iteration counter, the check
+ * period and the parameters are shared.  An instance that converges stops iterating (its
+ * rows are skipped) while the others continue; dpdlp_solve returns when none is running,
+ * with the worst status (2 > 1 > 0).  The block permutation acts inside every instance
+ * (instance i draws seeds perm_seed + 2i and perm_seed + 2i + 1), so count = 1 is
+ * dpdlp_load_lp.  Checkpoints (dpdlp_get_state / dpdlp_set_state) hold a single LP. */
+int dpdlp_load_batch(dpdlp_t* h, int32_t count, const int32_t* row_off, const int32_t* col_off,
+                     int32_t n, int32_t m, const double* c, const int64_t* row_ptr,
+                     const int32_t* col_idx, const double* val, const double* b,
+                     const double* lv, const double* uv, const int8_t* ctype);
+
+/* Per-instance step sizes eta[count] (HOST, count = the number of loaded instances) used
+ * by the next fresh solve instead of the power iteration; count = 0 clears them.  The
+ * "eta" parameter, when > 0, still takes precedence. */
+int dpdlp_set_batch_eta(dpdlp_t* h, const double* eta, int32_t count);
+
 /* Replace the row bounds with general ranges lc[m] <= A x <= uc[m] (HOST arrays, +-inf
  * allowed, lc <= uc, no NaN).  Resets the solver state. */
 int dpdlp_set_row_bounds(dpdlp_t* h, const double* lc, const double* uc);
@@ -161,6 +190,9 @@ int dpdlp_set_row_bounds(dpdlp_t* h, const double* lc, const double* uc);
  *   then FP64 values; 2: FP32 values
  *   throughout).  KKT, restart and step-size products always use FP64 values.  Needs every
  *   value of A to round to a normal float or zero, else the FP64 values are used.
+ *   cta_slots_primal, cta_slots_dual (4): warp slots per thread block of the primal (A^T y)
+ *   and dual (A x_bar) iteration kernels, 2, 4 or 8 (64, 128 or 256 threads); a launch
+ *   shape only, results do not depend on it (set by the autotuner).
  * Load-time keys (block_permute, perm_block, perm_seed) take effect at the next
  * dpdlp_load_lp.  Unknown key or out-of-range value: DPDLP_ERR_INVALID. */
 int dpdlp_set_param(dpdlp_t* h, const char* key, double v);
@@ -182,8 +214,15 @@ int dpdlp_solve(dpdlp_t* h, double tol, int64_t max_iter);
  * (either may be NULL). */
 int dpdlp_get_solution(dpdlp_t* h, double* x, double* y);
 
-/* Residuals and counters of the last solve (HOST struct). */
+/* Residuals and counters of the last solve (HOST struct).  For a batch: the largest
+ * residuals, the summed objectives and restarts, instance 0's step sizes and weight, and
+ * the batch status. */
 int dpdlp_get_kkt(dpdlp_t* h, dpdlp_kkt_t* out);
+
+/* Per-instance residuals and counters of the last solve into HOST out[count]; count must
+ * equal the number of loaded instances.  `iterations` is the iteration count at the
+ * instance's last check (where it converged, for a converged instance). */
+int dpdlp_get_batch_kkt(dpdlp_t* h, dpdlp_kkt_t* out, int32_t count);
 
 /* Copy up to `cap` trace records, oldest first, into HOST `out`; *count receives the number
  * copied. */
@@ -198,7 +237,9 @@ int dpdlp_set_state(dpdlp_t* h, const double* x, const double* y, const double* 
                     const double* y0, const dpdlp_scalar_state_t* s);
 
 /* Parity mode: restart decisions of checks 0..count-1 (0 none, 1..3 restart kinds) are
- * taken from `kinds` (HOST) instead of the restart test; count = 0 switches it off. */
+ * taken from `kinds` (HOST) instead of the restart test; count = 0 switches it off.  For a
+ * batch of N instances count = N * L and kinds[i * L + c] is instance i's decision at
+ * check c (count not a multiple of N: DPDLP_ERR_INVALID). */
 int dpdlp_set_schedule(dpdlp_t* h, const int8_t* kinds, int32_t count);
 
 /* Operator application with the solver's SpMV kernels: out[m] = A x[n], out[n] = A^T y[m]. */

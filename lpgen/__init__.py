@@ -113,7 +113,7 @@ def _planted_optimum(rng, n, m, row_ptr, col, val, ctype):
     z_star[cat == 0] = rng.uniform(0.1, 1.0, size=int((cat == 0).sum()))
     z_star[cat == 1] = -rng.uniform(0.1, 1.0, size=int((cat == 1).sum()))
     ax = _csr_matvec(row_ptr, col, val, x_star)
-    b = ax.copy()
+    b = np.array(ax, dtype=np.float64)
     le = ctype == LE
     b[le] += rng.uniform(0.0, 1.0, size=int(le.sum()))
     y_star = np.zeros(m)
@@ -284,3 +284,61 @@ def scaled_powerlaw_lp(seed: int, scale: float) -> LP:
     z = max(m, int(round(40_000_000 * scale)))
     cap = max(1, min(n, int(round(100_000 * math.sqrt(scale)))))
     return powerlaw_lp(seed=seed, n=n, m=m, target_nnz=z, cap=cap)
+
+
+def _distinct_rows_per_column(rng, m: int, k: np.ndarray, draws: int = 24) -> np.ndarray:
+    """For column j, k[j] distinct rows uniformly at random (rows in draw order; a
+    sequential draw without replacement).  Returns the rows, column-major."""
+    n = k.shape[0]
+    kmax = int(k.max()) if n else 0
+    if n == 0 or m == 0:
+        return np.zeros(0, dtype=np.int64)
+    cand = rng.integers(0, m, size=(n, max(draws, kmax)))
+    order = np.argsort(cand, axis=1, kind="stable")
+    srt = np.take_along_axis(cand, order, 1)
+    first = np.ones(srt.shape, dtype=bool)
+    first[:, 1:] = srt[:, 1:] != srt[:, :-1]
+    keep = np.zeros(srt.shape, dtype=bool)
+    np.put_along_axis(keep, order, first, 1)  # first occurrence of each row, draw order
+    rank = np.cumsum(keep, axis=1) - 1
+    sel = keep & (rank < k[:, None])
+    short = np.nonzero(sel.sum(axis=1) < k)[0]
+    rows = [cand[j][sel[j]] for j in range(n)] if short.size else None
+    if rows is None:
+        return cand[sel]
+    for j in short:  # rare: too few distinct draws, take a fresh subset
+        rows[j] = rng.choice(m, size=int(k[j]), replace=False)
+    return np.concatenate(rows)
+
+
+def uneven_lp(seed: int, m: int, n: int | None = None, nnz_lo: int = 5, nnz_hi: int = 15) -> LP:
+    """One instance of the batched workload: ``n = 2 m`` columns by default, each holding
+    U{nnz_lo..nnz_hi} distinct rows drawn uniformly, values N(0, 1); the first 60 % of rows
+    are equalities and the rest ``<=`` rows; bounds and planted optimum as
+    ``small_random_lp``."""
+    rng = np.random.default_rng(seed)
+    n = 2 * m if n is None else n
+    k = np.minimum(rng.integers(nnz_lo, nnz_hi + 1, size=n), m)
+    rows = _distinct_rows_per_column(rng, m, k)
+    cols = np.repeat(np.arange(n, dtype=np.int64), k)
+    vals = rng.standard_normal(rows.shape[0])
+    row_ptr, col, val = _csr_from_coo(m, n, rows.astype(np.int64), cols, vals)
+    ctype = np.where(np.arange(m) < (m * 6) // 10, EQ, LE).astype(np.int8)
+    lv, uv, xs, ys, zs, b, c = _planted_optimum(rng, n, m, row_ptr, col, val, ctype)
+    lc, uc = bounds_from_types(ctype, b)
+    return LP(n, m, c, row_ptr, col, val, lc, uc, lv, uv, ctype, b, xs, ys, zs,
+              name=f"uneven_lp(seed={seed},m={m},n={n})")
+
+
+def batch_sizes(seed: int = 3, count: int = 256, m_lo: int = 500, m_hi: int = 50_000) -> np.ndarray:
+    """Row counts m_i ~ U{m_lo..m_hi} of the batched workload."""
+    return np.random.default_rng(seed).integers(m_lo, m_hi + 1, size=count)
+
+
+def batch_lps(seed: int = 3, count: int = 256, m_lo: int = 500, m_hi: int = 50_000) -> list:
+    """The batched workload: ``count`` independent LPs of uneven sizes (m_i ~ U{m_lo..m_hi},
+    n_i = 2 m_i, 5-15 nonzeros per column).  Instance i is ``uneven_lp`` with seed
+    1000 * seed + i.  With the defaults: 256 LPs, about 6.5M rows, 12.9M columns and 129M
+    nonzeros in total."""
+    ms = batch_sizes(seed, count, m_lo, m_hi)
+    return [uneven_lp(1000 * seed + i, int(mi)) for i, mi in enumerate(ms)]

@@ -39,9 +39,10 @@ constexpr int TPB = 256;
 constexpr int KMAX = 1024;  // largest check period (iterations per graph body)
 constexpr int NRED = 5;     // quantities per check reduction (rows and columns)
 
-// Slot s: its short rows have the new indices [row_base, row_base + nrows).
+// Slot s: its short rows have the new indices [row_base, row_base + nrows); all belong to
+// LP instance `inst` (a slot never mixes instances of a batch).
 struct SlotDesc {
-  int row_base, nrows;
+  int row_base, nrows, inst, pad;
 };
 // Lane l of a slot: slot-local index of its first short row, global id of its first piece.
 struct LaneMeta {
@@ -62,6 +63,7 @@ struct HostPacked {
   std::vector<SlotDesc> slots;
   std::vector<LaneMeta> lanes;
   std::vector<int32_t> long_row;    // new index of each long row
+  std::vector<int32_t> long_inst;   // instance of each long row
   std::vector<int32_t> long_ptr;    // nlong + 1
   std::vector<int32_t> long_piece;  // piece ids of each long row, in row order
   int64_t stored = 0;               // nslots * SLOT_ITEMS
@@ -71,12 +73,14 @@ struct HostPacked {
 struct DevPacked {
   int rows = 0, cols = 0, nslots = 0, nlong = 0, npieces = 0;
   int nlong_block = 0, nlong_warp = 0;
+  int cta_slots = PK_WARPS;  // slots per block of this orientation's iteration kernel (2, 4, 8)
   const double* val = nullptr;
   const float* val32 = nullptr;  // FP32 copy of the values (nullptr: not representable)
   const uint32_t* idx = nullptr;
   const SlotDesc* slots = nullptr;
   const LaneMeta* lanes = nullptr;
   const int32_t* long_row = nullptr;
+  const int32_t* long_inst = nullptr;
   const int32_t* long_ptr = nullptr;
   const int32_t* long_piece = nullptr;
   double* piece_sum = nullptr;  // 2 * npieces (room for two vectors)
@@ -96,40 +100,49 @@ struct PackPlan {
   std::vector<int32_t> slot_lanes;  // LANES entries per slot: lane index or -1 (empty lane)
   int nshort = 0, nlong = 0, npieces = 0;
   std::vector<int32_t> long_rows;   // pre-order index of each long row, longest first
+  std::vector<int32_t> long_inst;   // instance of each long row
   std::vector<int32_t> long_ptr, long_piece;
 };
 
-// Solver scalars resident in device memory.  The control kernel updates them at every
-// check; the iteration kernels only read them.  The host writes them at the start of a
-// solve and reads them at the end.
+// Solver scalars resident in device memory, in two parts.  All instances of a batch take
+// their iterations together (one iteration counter); each has its own step sizes, primal
+// weight, restart epoch and status.  The control kernel updates both at every check; the
+// iteration kernels only read them.  The host writes them at the start of a solve and
+// reads them at the end.
 struct DevScalars {
   long long T_base;    // total iterations before the current graph body
-  long long k_base;    // iterations since the last restart, before the current body
   long long T_check;   // total iteration count at the end of the current body's check
   long long max_iter;
-  double tau, sigma, inv_sigma, omega, eta, gamma, eps;
+  double gamma, eps;
   double beta_s, beta_n, beta_a, kp, ki, kd;
-  double bnorm, cnorm;
   int K, halpern, restart_enabled, pid_enabled;
-  // epoch and PID state
-  double r_anchor, r_prev, e_sum, e_prev;
-  int has_anchor, has_e_prev;
-  long long restarts, checks;
-  // results of the last check
-  double r_p, r_d, r_g, obj_p, obj_d, r_fp;
-  int status;       // -1 running, 0 converged, 1 iteration limit, 2 non-finite
-  int apply_mode;   // what the apply kernel does: 0 Halpern step, 1 restart, 2 nothing
-  double w1_check, w0_check;  // Halpern weights of the check iteration
-  int sched_len;    // forced restart schedule length (0: off)
-  int spmv_fp32;    // iteration products use the FP32 values (mixed precision)
-  int fp32_switch;  // switch to FP64 values when the KKT error stalls
-  int stall_checks; // consecutive checks without halving the best KKT error (FP32 mode)
-  int fp32_stall_limit;    // ... after this many such checks: FP64 values
-  double best_kkt;  // best max(r_primal, r_dual, r_gap) seen in FP32 mode
-  double fp32_switch_tol;  // FP64 values once the KKT error is at or below this
+  int ninst;
+  int running;         // instances still iterating
+  long long checks;
+  int status;          // -1 running, else the worst instance status (2 > 1 > 0)
+  int sched_len;       // forced restart schedule length per instance (0: off)
   int trace_cap;
   long long trace_count;
-  double w1[KMAX], w0[KMAX];  // Halpern weights (k+1)/(k+2), 1/(k+2) of each body iteration
+  int fp32_switch;     // mixed precision: switch to FP64 values when the KKT error stalls
+  int fp32_stall_limit;
+  double fp32_switch_tol;
+};
+
+struct InstScalars {
+  double tau, sigma, inv_sigma, omega, eta;
+  double bnorm, cnorm;
+  long long k_base;    // iterations since the instance's last restart, before the body
+  long long iterations;  // total iterations the instance has taken
+  double r_anchor, r_prev, e_sum, e_prev;
+  int has_anchor, has_e_prev;
+  long long restarts;
+  double r_p, r_d, r_g, obj_p, obj_d, r_fp;
+  int status;          // -1 running, 0 converged, 1 iteration limit, 2 non-finite
+  int apply_mode;      // what the apply kernel does: 0 Halpern step, 1 restart, 2 nothing
+  double w1_check, w0_check;  // Halpern weights of the check iteration
+  int spmv_fp32;       // this instance's products use FP32 values
+  int stall_checks;
+  double best_kkt;
 };
 
 // Device vectors of one LP (internal, packed index order).
@@ -141,11 +154,20 @@ struct DevVecs {
   double *aty = nullptr;                               // [n]
   double *y = nullptr, *y0 = nullptr, *yh = nullptr;   // [m]
   double *axh = nullptr, *adx = nullptr;               // [m]
-  double *red_rows = nullptr, *red_cols = nullptr;     // reduction partials [G][NRED]
-  int g_rows = 1, g_cols = 1;
+  double *red_rows = nullptr, *red_cols = nullptr;     // reduction partials [chunks][NRED]
+  const int4* chunk_rows = nullptr;                   // reduction chunks {inst, start, len, -}
+  const int4* chunk_cols = nullptr;
+  const int32_t* inst_chunk_rows = nullptr;           // ninst + 1: chunks of each instance
+  const int32_t* inst_chunk_cols = nullptr;
+  int g_rows = 1, g_cols = 1;                         // number of chunks
+  const int32_t* inst_of_row = nullptr;               // [m]
+  const int32_t* inst_of_col = nullptr;               // [n]
+  InstScalars* inst = nullptr;                        // [ninst]
+  double* wtab = nullptr;                             // [ninst][2][KMAX] Halpern weights
+  int ninst = 1;
   int32_t *perm_col = nullptr, *perm_row = nullptr;    // internal index -> caller index
   double *tmp_n = nullptr, *tmp_m = nullptr, *tmp_n2 = nullptr;  // scratch vectors
-  double *pw = nullptr;                                // power-iteration scalars [4]
+  double *pw = nullptr;                                // power-iteration scalars [ninst][4]
   int8_t* sched = nullptr;                             // forced schedule
   void* trace = nullptr;                               // dpdlp_trace_t ring
 };
@@ -170,6 +192,10 @@ void transpose_csr(int rows, int cols, const std::vector<int64_t>& ptr,
 // Pack the rows of one orientation into lanes and slots (best-fit decreasing on row
 // lengths); decides the new row order.
 void plan_packing(int rows, const std::vector<int64_t>& ptr, PackPlan& plan);
+// The same for a batch: rows [offsets[i], offsets[i+1]) are instance i; each instance is
+// packed into slots of its own and keeps its row range in the new order.
+void plan_packing_batch(int rows, const std::vector<int64_t>& ptr,
+                        const std::vector<int32_t>& offsets, PackPlan& plan);
 // Stored arrays of one orientation from its plan; column indices are mapped through the
 // other orientation's new_of_old.
 void build_packed(int rows, int cols, const std::vector<int64_t>& ptr,
@@ -199,10 +225,14 @@ cudaError_t launch_gather(const double* in, const int32_t* perm, double* out, in
 cudaError_t launch_scatter(const double* in, const int32_t* perm, double* out, int len,
                            cudaStream_t s);  // out[perm[i]] = in[i]
 cudaError_t launch_fill(double* p, double v, int len, cudaStream_t s);
-// One power-iteration round: w = A v, lam = w.w, u = A^T w, v = u / ||u||; pw[0] = lam,
-// pw[1] = ||u||.
+// One power-iteration round for every instance: w = A v, lam_i = w_i.w_i, u = A^T w,
+// v_i = u_i / ||u_i||; pw[4 i] = lam_i, pw[4 i + 1] = ||u_i||.
 cudaError_t launch_power_round(const DevPacked& csr, const DevPacked& csc, const DevVecs& v,
                                double* vec_v, double* vec_w, double* vec_u, cudaStream_t s);
-int reduction_grid(int len);
+// Reduction chunks of at most `chunk` consecutive elements inside one instance, as
+// {inst, start, len, 0} quadruples; inst_chunk[i] .. inst_chunk[i+1] are instance i's.
+void build_chunks(const std::vector<int32_t>& offsets, int chunk, std::vector<int32_t>& chunks,
+                  std::vector<int32_t>& inst_chunk);
+constexpr int RED_CHUNK = 4096;
 
 }  // namespace pdhg

@@ -138,14 +138,20 @@ __device__ __forceinline__ double block_sum(double v, double* buf) {
 // An epilogue turns finished row sums into outputs: `apply_direct(row, sums)`.
 
 struct StoreEpi1 {
+  static constexpr bool kTunable = false;
   double* out0;
   __device__ bool begin() { return true; }
+  __device__ bool inst(int) { return true; }
+  __device__ void prepare(int) {}
   __device__ bool fp32() const { return false; }  // KKT and step-size products: FP64 values
   __device__ void apply_direct(int r, const double* s) { out0[r] = s[0]; }
 };
 struct StoreEpi2 {
+  static constexpr bool kTunable = false;
   double *out0, *out1;
   __device__ bool begin() { return true; }
+  __device__ bool inst(int) { return true; }
+  __device__ void prepare(int) {}
   __device__ bool fp32() const { return false; }
   __device__ void apply_direct(int r, const double* s) {
     out0[r] = s[0];
@@ -153,14 +159,14 @@ struct StoreEpi2 {
   }
 };
 
-// Per-iteration scalars read from device memory by the fused epilogues.
+// Per-iteration scalars read from device memory by the fused epilogues: the global part
+// (iteration limit, check iteration) once per launch, the instance part once per slot.
 struct IterScalars {
   double step, inv_step, two_step, w1, w0, gamma;
   int check, halpern, gamma_one, fp32;
 };
 
-__device__ __forceinline__ bool load_iter(const DevScalars* sc, IterPlan p, bool primal,
-                                          IterScalars& o) {
+__device__ __forceinline__ bool load_global(const DevScalars* sc, IterPlan p, IterScalars& o) {
   if (p.force_regular) {
     o.check = 0;
   } else {
@@ -168,16 +174,32 @@ __device__ __forceinline__ bool load_iter(const DevScalars* sc, IterPlan p, bool
     if (T >= sc->max_iter) return false;  // past the iteration limit inside this body
     o.check = (T + 1 == sc->T_check);
   }
-  o.step = primal ? sc->tau : sc->sigma;
-  o.inv_step = sc->inv_sigma;
-  o.two_step = 2.0 * o.step;
-  o.w1 = sc->w1[p.i];
-  o.w0 = sc->w0[p.i];
   o.gamma = sc->gamma;
   o.halpern = sc->halpern;
   o.gamma_one = (sc->gamma == 1.0);
-  o.fp32 = sc->spmv_fp32;
   return true;
+}
+
+// Instance part, in two steps for a batch: whether the instance still runs and which
+// values its products use (before the lane sums), then its step sizes and Halpern weights
+// (after them, so they are not held in registers across the sums).
+__device__ __forceinline__ bool load_inst_mode(const InstScalars* tab, int inst, IterPlan p,
+                                               IterScalars& o) {
+  const InstScalars& I = tab[inst];
+  if (I.status != -1 && !p.force_regular) return false;  // converged instance: skip its rows
+  o.fp32 = I.spmv_fp32;
+  return true;
+}
+
+__device__ __forceinline__ void load_inst_steps(const InstScalars* tab, const double* wtab,
+                                                int inst, IterPlan p, bool primal,
+                                                IterScalars& o) {
+  const InstScalars& I = tab[inst];
+  o.step = primal ? I.tau : I.sigma;
+  o.inv_step = I.inv_sigma;
+  o.two_step = 2.0 * o.step;
+  o.w1 = wtab[(size_t)inst * 2 * KMAX + p.i];
+  o.w0 = wtab[(size_t)inst * 2 * KMAX + KMAX + p.i];
 }
 
 // Primal step per column j, given s = (A^T y)_j:
@@ -185,13 +207,30 @@ __device__ __forceinline__ bool load_iter(const DevScalars* sc, IterPlan p, bool
 //   Halpern: x <- w1 ((1+gamma) x^ - gamma x) + w0 x0   (with gamma = 1 the reflected point
 //   is x_bar itself), regular iterations;
 //   check iteration: keep x = x^k, store x^ and dx = x^k - x^.
+template <bool Single>
 struct PrimalEpi {
+  static constexpr bool kTunable = true;
   const DevScalars* sc;
+  const InstScalars* itab;
+  const double* wtab;
   IterPlan plan;
   const double *c, *lv, *uv, *x0;
   double *x, *xbar, *xh, *dx;
   IterScalars q;
-  __device__ bool begin() { return load_iter(sc, plan, true, q); }
+  // Single: one instance, whose scalars are loaded once per launch in begin()
+  __device__ bool begin() {
+    if (!Single) return load_global(sc, plan, q);
+    // all loads issued before the first branch, so they overlap
+    const int st = itab[0].status;
+    q.fp32 = itab[0].spmv_fp32;
+    load_inst_steps(itab, wtab, 0, plan, true, q);
+    const bool go = load_global(sc, plan, q);
+    return go && (st == -1 || plan.force_regular);
+  }
+  __device__ bool inst(int i) { return Single || load_inst_mode(itab, i, plan, q); }
+  __device__ void prepare(int i) {
+    if (!Single) load_inst_steps(itab, wtab, i, plan, true, q);
+  }
   __device__ bool fp32() const { return q.fp32 != 0; }
   __device__ void step(int j, double s, double cj, double lvj, double uvj, double xj,
                        const double* x0p) {
@@ -217,13 +256,30 @@ struct PrimalEpi {
 //   w = y / sigma - z,  d = w - proj_{-S}(w),  y^ = sigma d,  -S_i = [lo_i, hi_i] = [-uc_i, -lc_i];
 //   Halpern: y <- w1 ((1+gamma) y^ - gamma y) + w0 y0, with gamma = 1 evaluated as
 //   w1 (2 sigma d - y) + w0 y0; check iteration: keep y = y^k, store y^.
+template <bool Single>
 struct DualEpi {
+  static constexpr bool kTunable = true;
   const DevScalars* sc;
+  const InstScalars* itab;
+  const double* wtab;
   IterPlan plan;
   const double *lo, *hi, *y0;
   double *y, *yh;
   IterScalars q;
-  __device__ bool begin() { return load_iter(sc, plan, false, q); }
+  // Single: one instance, whose scalars are loaded once per launch in begin()
+  __device__ bool begin() {
+    if (!Single) return load_global(sc, plan, q);
+    // all loads issued before the first branch, so they overlap
+    const int st = itab[0].status;
+    q.fp32 = itab[0].spmv_fp32;
+    load_inst_steps(itab, wtab, 0, plan, false, q);
+    const bool go = load_global(sc, plan, q);
+    return go && (st == -1 || plan.force_regular);
+  }
+  __device__ bool inst(int i) { return Single || load_inst_mode(itab, i, plan, q); }
+  __device__ void prepare(int i) {
+    if (!Single) load_inst_steps(itab, wtab, i, plan, false, q);
+  }
   __device__ bool fp32() const { return q.fp32 != 0; }
   __device__ void step(int i, double s, double loi, double hii, double yi, const double* y0p) {
     const double w = fma(yi, q.inv_step, -s);
@@ -426,22 +482,27 @@ __device__ __forceinline__ void lane_sums(const DevPacked& M, const GatherVecs<N
 
 // One warp per slot, PK_WARPS slots per block, no block-level barrier: the lanes sum their
 // rows (lane_sums), then apply the epilogue to the slot's short rows, one row per lane.
-template <int NV, class Epi>
-__global__ void __launch_bounds__(PK_TPB, DPDLP_PK_MIN_BLOCKS) packed_spmv_kernel(DevPacked M, GatherVecs<NV> g, Epi epi_in) {
-  __shared__ double srow[PK_WARPS][NV][MAX_SLOT_ROWS];
+// W slots (warps) per block; the register cap keeps the same number of resident warps per
+// SM for every W (W * min-blocks = PK_WARPS * DPDLP_PK_MIN_BLOCKS).
+template <int NV, int W, class Epi>
+__global__ void __launch_bounds__(W * LANES, (DPDLP_PK_MIN_BLOCKS * PK_WARPS) / W)
+    packed_spmv_kernel(DevPacked M, GatherVecs<NV> g, Epi epi_in) {
+  __shared__ double srow[W][NV][MAX_SLOT_ROWS];
   Epi epi = epi_in;
   if (!epi.begin()) return;  // uniform over the launch
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = blockIdx.x * PK_WARPS + w;
+  const int s = blockIdx.x * W + w;
   if (s >= M.nslots) return;  // uniform over the warp
   const SlotDesc sd = M.slots[s];
+  if (!epi.inst(sd.inst)) return;  // uniform over the warp: instance scalars, or converged
   const LaneMeta lm = M.lanes[(size_t)s * LANES + lane];
   const size_t off = (size_t)s * SLOT_ITEMS;
-  if (epi.fp32() && M.val32)  // uniform over the launch
+  if (epi.fp32() && M.val32)  // uniform over the warp
     lane_sums<float, NV>(M, g, off, lane, lm.row_local, lm.piece_base, srow[w]);
   else
     lane_sums<double, NV>(M, g, off, lane, lm.row_local, lm.piece_base, srow[w]);
   __syncwarp();
+  epi.prepare(sd.inst);
   for (int r = lane; r < sd.nrows; r += LANES) {
     double v[NV];
 #pragma unroll
@@ -464,6 +525,7 @@ __global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_i
   double v[NV];
   if (b < nb) {
     const int i = b;
+    if (!epi.inst(M.long_inst[i])) return;  // uniform over the block
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       double a = 0.0;
@@ -471,7 +533,10 @@ __global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_i
         a += M.piece_sum[(size_t)k * M.npieces + M.long_piece[q]];
       v[k] = block_sum(a, red);
     }
-    if (threadIdx.x == 0) epi.apply_direct(M.long_row[i], v);
+    if (threadIdx.x == 0) {
+      epi.prepare(M.long_inst[i]);
+      epi.apply_direct(M.long_row[i], v);
+    }
     return;
   }
   b -= nb;
@@ -479,6 +544,7 @@ __global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_i
     const int i = nb + b * (TPB / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= nb + nw) return;
+    if (!epi.inst(M.long_inst[i])) return;  // uniform over the warp
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       double a = 0.0;
@@ -488,12 +554,16 @@ __global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_i
       for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
       v[k] = a;
     }
-    if (lane == 0) epi.apply_direct(M.long_row[i], v);
+    if (lane == 0) {
+      epi.prepare(M.long_inst[i]);
+      epi.apply_direct(M.long_row[i], v);
+    }
     return;
   }
   b -= wblocks;
   const int i = nb + nw + b * TPB + threadIdx.x;
   if (i >= M.nlong) return;
+  if (!epi.inst(M.long_inst[i])) return;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
     double a = 0.0;
@@ -501,13 +571,30 @@ __global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_i
       a += M.piece_sum[(size_t)k * M.npieces + M.long_piece[q]];
     v[k] = a;
   }
+  epi.prepare(M.long_inst[i]);
   epi.apply_direct(M.long_row[i], v);
 }
 
+template <int NV, int W, class Epi>
+static void launch_slots(const DevPacked& M, GatherVecs<NV> g, Epi epi, cudaStream_t s) {
+  packed_spmv_kernel<NV, W, Epi><<<(M.nslots + W - 1) / W, W * LANES, 0, s>>>(M, g, epi);
+}
+
+// Iteration kernels (Epi::kTunable) run with the orientation's chosen slots per block;
+// the plain products of the checks and the power iteration use PK_WARPS.
 template <int NV, class Epi>
 static cudaError_t launch_packed(const DevPacked& M, GatherVecs<NV> g, Epi epi, cudaStream_t s) {
-  if (M.nslots > 0)
-    packed_spmv_kernel<NV, Epi><<<(M.nslots + PK_WARPS - 1) / PK_WARPS, PK_TPB, 0, s>>>(M, g, epi);
+  if (M.nslots > 0) {
+    if constexpr (Epi::kTunable) {
+      switch (M.cta_slots) {
+        case 2: launch_slots<NV, 2>(M, g, epi, s); break;
+        case 8: launch_slots<NV, 8>(M, g, epi, s); break;
+        default: launch_slots<NV, 4>(M, g, epi, s); break;
+      }
+    } else {
+      launch_slots<NV, PK_WARPS>(M, g, epi, s);
+    }
+  }
   if (M.nlong > 0) {
     const int rest = M.nlong - M.nlong_block - M.nlong_warp;
     const int grid = M.nlong_block + (M.nlong_warp + TPB / 32 - 1) / (TPB / 32) + (rest + TPB - 1) / TPB;
@@ -518,16 +605,18 @@ static cudaError_t launch_packed(const DevPacked& M, GatherVecs<NV> g, Epi epi, 
 
 cudaError_t launch_primal(const DevPacked& csc, const DevVecs& v, const DevScalars* sc,
                           IterPlan p, cudaStream_t s) {
-  PrimalEpi e{sc, p, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, {}};
   GatherVecs<1> g{{v.y}};
-  return launch_packed<1>(csc, g, e, s);
+  if (v.ninst == 1)
+    return launch_packed<1>(csc, g, PrimalEpi<true>{sc, v.inst, v.wtab, p, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, {}}, s);
+  return launch_packed<1>(csc, g, PrimalEpi<false>{sc, v.inst, v.wtab, p, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, {}}, s);
 }
 
 cudaError_t launch_dual(const DevPacked& csr, const DevVecs& v, const DevScalars* sc,
                         IterPlan p, cudaStream_t s) {
-  DualEpi e{sc, p, v.lo, v.hi, v.y0, v.y, v.yh, {}};
   GatherVecs<1> g{{v.xbar}};
-  return launch_packed<1>(csr, g, e, s);
+  if (v.ninst == 1)
+    return launch_packed<1>(csr, g, DualEpi<true>{sc, v.inst, v.wtab, p, v.lo, v.hi, v.y0, v.y, v.yh, {}}, s);
+  return launch_packed<1>(csr, g, DualEpi<false>{sc, v.inst, v.wtab, p, v.lo, v.hi, v.y0, v.y, v.yh, {}}, s);
 }
 
 cudaError_t launch_spmv(const DevPacked& M, const double* x0, const double* x1, double* out0,
@@ -541,31 +630,32 @@ cudaError_t launch_spmv(const DevPacked& M, const double* x0, const double* x1, 
 }
 
 // ---------------------------------------------------------------- check reductions
-int reduction_grid(int len) {
-  const int g = (len + 4095) / 4096;
-  return g < 1 ? 1 : (g > 1024 ? 1024 : g);
-}
+// One thread block per reduction chunk (at most RED_CHUNK consecutive rows or columns of
+// one instance); instances that are no longer running contribute zeros.
 
 // Row terms at (x^, y^): [0] (Ax^ - proj_S(Ax^))^2, [1] the p(-y^; lc, uc) term,
 // [2] (y^k - y^)^2, [3] (A dx)_i (y^k - y^)_i, [4] (y^ - y0)^2.
-__global__ void __launch_bounds__(TPB) reduce_rows_kernel(DevVecs v, int m) {
+__global__ void __launch_bounds__(TPB) reduce_rows_kernel(DevVecs v) {
   __shared__ double buf[TPB / 32];
+  const int4 ch = v.chunk_rows[blockIdx.x];  // {instance, start, length, -}
   double q[NRED] = {0, 0, 0, 0, 0};
-  for (int i = blockIdx.x * TPB + threadIdx.x; i < m; i += gridDim.x * TPB) {
-    const double lc = -v.hi[i], uc = -v.lo[i];
-    const double ax = v.axh[i];
-    const double d = ax - clampd(ax, lc, uc);
-    q[0] = fma(d, d, q[0]);
-    const double yh = v.yh[i];
-    double p = 0.0;  // u (-y)^+ - l (-y)^-, a term vanishing when its multiplier is 0
-    if (yh < 0.0) p = uc * (-yh);
-    if (yh > 0.0) p = -(lc * yh);
-    q[1] += p;
-    const double dy = v.y[i] - yh;
-    q[2] = fma(dy, dy, q[2]);
-    q[3] = fma(v.adx[i], dy, q[3]);
-    const double ya = yh - v.y0[i];
-    q[4] = fma(ya, ya, q[4]);
+  if (v.inst[ch.x].status == -1) {
+    for (int i = ch.y + threadIdx.x; i < ch.y + ch.z; i += TPB) {
+      const double lc = -v.hi[i], uc = -v.lo[i];
+      const double ax = v.axh[i];
+      const double d = ax - clampd(ax, lc, uc);
+      q[0] = fma(d, d, q[0]);
+      const double yh = v.yh[i];
+      double p = 0.0;  // u (-y)^+ - l (-y)^-, a term vanishing when its multiplier is 0
+      if (yh < 0.0) p = uc * (-yh);
+      if (yh > 0.0) p = -(lc * yh);
+      q[1] += p;
+      const double dy = v.y[i] - yh;
+      q[2] = fma(dy, dy, q[2]);
+      q[3] = fma(v.adx[i], dy, q[3]);
+      const double ya = yh - v.y0[i];
+      q[4] = fma(ya, ya, q[4]);
+    }
   }
 #pragma unroll
   for (int k = 0; k < NRED; ++k) {
@@ -574,26 +664,30 @@ __global__ void __launch_bounds__(TPB) reduce_rows_kernel(DevVecs v, int m) {
   }
 }
 
-// Column terms at (x^, y^) with the current tau: g = c - A^T y^, xt = x^ - tau g,
-// px = proj_X(xt): [0] (px - x^)^2, [1] (px - xt) x^ (= tau s_j x^_j), [2] c x^,
-// [3] dx^2, [4] (x^ - x0)^2.
-__global__ void __launch_bounds__(TPB) reduce_cols_kernel(DevVecs v, int n, const DevScalars* sc) {
+// Column terms at (x^, y^) with the instance's current tau: g = c - A^T y^,
+// xt = x^ - tau g, px = proj_X(xt): [0] (px - x^)^2, [1] (px - xt) x^ (= tau s_j x^_j),
+// [2] c x^, [3] dx^2, [4] (x^ - x0)^2.
+__global__ void __launch_bounds__(TPB) reduce_cols_kernel(DevVecs v) {
   __shared__ double buf[TPB / 32];
-  const double tau = sc->tau;
+  const int4 ch = v.chunk_cols[blockIdx.x];
   double q[NRED] = {0, 0, 0, 0, 0};
-  for (int j = blockIdx.x * TPB + threadIdx.x; j < n; j += gridDim.x * TPB) {
-    const double xhj = v.xh[j];
-    const double g = v.c[j] - v.aty[j];
-    const double xt = fma(-tau, g, xhj);
-    const double px = clampd(xt, v.lv[j], v.uv[j]);
-    const double d = px - xhj;
-    q[0] = fma(d, d, q[0]);
-    q[1] = fma(px - xt, xhj, q[1]);
-    q[2] = fma(v.c[j], xhj, q[2]);
-    const double dx = v.dx[j];
-    q[3] = fma(dx, dx, q[3]);
-    const double xa = xhj - v.x0[j];
-    q[4] = fma(xa, xa, q[4]);
+  const InstScalars& I = v.inst[ch.x];
+  if (I.status == -1) {
+    const double tau = I.tau;
+    for (int j = ch.y + threadIdx.x; j < ch.y + ch.z; j += TPB) {
+      const double xhj = v.xh[j];
+      const double g = v.c[j] - v.aty[j];
+      const double xt = fma(-tau, g, xhj);
+      const double px = clampd(xt, v.lv[j], v.uv[j]);
+      const double d = px - xhj;
+      q[0] = fma(d, d, q[0]);
+      q[1] = fma(px - xt, xhj, q[1]);
+      q[2] = fma(v.c[j], xhj, q[2]);
+      const double dx = v.dx[j];
+      q[3] = fma(dx, dx, q[3]);
+      const double xa = xhj - v.x0[j];
+      q[4] = fma(xa, xa, q[4]);
+    }
   }
 #pragma unroll
   for (int k = 0; k < NRED; ++k) {
@@ -611,168 +705,217 @@ __device__ int restart_kind(double r, double r_anchor, double r_prev, bool first
   return 0;
 }
 
-__global__ void __launch_bounds__(TPB) control_kernel(DevVecs v, DevScalars* sc,
-                                                      unsigned long long cond, int use_cond) {
+// Sum of one instance's chunk partials of quantity k, in a fixed order.
+__device__ double inst_sum(const double* part, const int32_t* inst_chunk, int inst, int k,
+                           double* buf) {
+  double a = 0.0;
+  for (int c = inst_chunk[inst] + threadIdx.x; c < inst_chunk[inst + 1]; c += TPB)
+    a += part[c * NRED + k];
+  return block_sum(a, buf);
+}
+
+// Control step of one instance (one thread block per instance): KKT errors (Section 2.2),
+// the fixed-point residual of the restart test, the restart decision (Appendix B.2), the
+// PID primal weight (Appendix B.3), the mixed-precision switch, the trace entry and the
+// Halpern weights of the next graph body.  Global bookkeeping follows in finalize_kernel.
+__global__ void __launch_bounds__(TPB) control_kernel(DevVecs v, const DevScalars* sc) {
   __shared__ double buf[TPB / 32];
   __shared__ double S[2][NRED];
   __shared__ long long kb_next;
-  for (int k = 0; k < NRED; ++k) {
-    double a = 0.0;
-    for (int gi = threadIdx.x; gi < v.g_rows; gi += TPB) a += v.red_rows[gi * NRED + k];
-    a = block_sum(a, buf);
-    double b = 0.0;
-    for (int gi = threadIdx.x; gi < v.g_cols; gi += TPB) b += v.red_cols[gi * NRED + k];
-    b = block_sum(b, buf);
-    if (threadIdx.x == 0) {
-      S[0][k] = a;
-      S[1][k] = b;
+  const int inst = blockIdx.x;
+  InstScalars& I = v.inst[inst];
+  const DevScalars& s = *sc;
+  const bool running = I.status == -1;  // uniform over the block
+  if (running) {
+    for (int k = 0; k < NRED; ++k) {
+      const double a = inst_sum(v.red_rows, v.inst_chunk_rows, inst, k, buf);
+      const double b = inst_sum(v.red_cols, v.inst_chunk_cols, inst, k, buf);
+      if (threadIdx.x == 0) {
+        S[0][k] = a;
+        S[1][k] = b;
+      }
     }
   }
+  const long long T = s.T_check;
   if (threadIdx.x == 0) {
-    DevScalars& s = *sc;
-    const double tau = s.tau, omega = s.omega, eta = s.eta;
-    const double* R = S[0];
-    const double* C = S[1];
-    const double r_p = sqrt(R[0]) / (1.0 + s.bnorm);
-    const double r_d = sqrt(C[0]) / tau / (1.0 + s.cnorm);
-    const double obj_p = C[2];
-    const double obj_d = -R[1] + C[1] / tau;
-    const double r_g = fabs(obj_p - obj_d) / (1.0 + fmax(fabs(obj_p), fabs(obj_d)));
-    const double rsq = (omega / eta) * C[3] + (1.0 / (eta * omega)) * R[2] + 2.0 * R[3];
-    const double r = sqrt(fmax(0.0, rsq));
-    const long long T = s.T_check;
-    const long long k_after = s.k_base + (T - s.T_base);
-    const long long check_idx = s.checks;
-    s.checks += 1;
-    s.r_p = r_p; s.r_d = r_d; s.r_g = r_g; s.obj_p = obj_p; s.obj_d = obj_d; s.r_fp = r;
-    const int mode_used = s.spmv_fp32;
-    if (s.spmv_fp32 && s.fp32_switch) {  // mixed precision: FP64 values once the error is
-      const double kk = fmax(r_p, fmax(r_d, r_g));  // small enough or stops halving
-      if (kk <= s.fp32_switch_tol) {
-        s.spmv_fp32 = 0;
-      } else if (kk <= 0.5 * s.best_kkt) {
-        s.best_kkt = kk;
-        s.stall_checks = 0;
-      } else if (kk <= 100.0 * s.fp32_switch_tol && ++s.stall_checks >= s.fp32_stall_limit) {
-        s.spmv_fp32 = 0;  // stalled near the floor the FP32 values set
-      }
-    }
-    bool finite = isfinite(r) && isfinite(r_p) && isfinite(r_d) && isfinite(r_g);
-    for (int k = 0; k < NRED; ++k) finite = finite && isfinite(R[k]) && isfinite(C[k]);
+    const long long k_after = I.k_base + (T - s.T_base);
     int kind = 0;
-    unsigned go = 0;
+    const int mode_used = I.spmv_fp32;
+    const double omega = I.omega;
     long long k_next = k_after;
-    s.T_base = T;
-    if (!finite) {
-      s.status = 2;
-      s.apply_mode = 2;
-    } else if (fmax(r_p, fmax(r_d, r_g)) <= s.eps) {
-      s.status = 0;
-      s.apply_mode = 2;
-    } else {
-      const bool first = !s.has_anchor;
-      if (first) {
-        s.r_anchor = r;
-        s.r_prev = r;
-        s.has_anchor = 1;
-      }
-      const int8_t* sched = v.sched;
-      if (s.sched_len > 0) {
-        kind = check_idx < s.sched_len ? (int)sched[check_idx] : 0;
-      } else if (s.restart_enabled) {
-        kind = restart_kind(r, s.r_anchor, s.r_prev, first, k_after, T, s);
-      }
-      s.r_prev = r;
-      if (kind) {
-        s.restarts += 1;
-        if (s.pid_enabled) {
-          const double d_x = sqrt(C[4]), d_y = sqrt(R[4]);
-          if (d_x > 0.0 && d_y > 0.0 && isfinite(d_x) && isfinite(d_y)) {
-            const double so = sqrt(omega);
-            const double e = log((so * d_x) / (d_y / so));
-            s.e_sum += e;
-            const double de = s.has_e_prev ? (e - s.e_prev) : 0.0;
-            const double lw = log(omega) - (s.kp * e + s.ki * s.e_sum + s.kd * de);
-            s.omega = exp(lw);
-            s.e_prev = e;
-            s.has_e_prev = 1;
-          }
+    if (running) {
+      const double tau = I.tau, eta = I.eta;
+      const double* R = S[0];
+      const double* C = S[1];
+      const double r_p = sqrt(R[0]) / (1.0 + I.bnorm);
+      const double r_d = sqrt(C[0]) / tau / (1.0 + I.cnorm);
+      const double obj_p = C[2];
+      const double obj_d = -R[1] + C[1] / tau;
+      const double r_g = fabs(obj_p - obj_d) / (1.0 + fmax(fabs(obj_p), fabs(obj_d)));
+      const double rsq = (omega / eta) * C[3] + (1.0 / (eta * omega)) * R[2] + 2.0 * R[3];
+      const double r = sqrt(fmax(0.0, rsq));
+      I.r_p = r_p; I.r_d = r_d; I.r_g = r_g; I.obj_p = obj_p; I.obj_d = obj_d; I.r_fp = r;
+      I.iterations = T;
+      if (I.spmv_fp32 && s.fp32_switch) {  // mixed precision: FP64 values once the error is
+        const double kk = fmax(r_p, fmax(r_d, r_g));  // small enough or stops halving
+        if (kk <= s.fp32_switch_tol) {
+          I.spmv_fp32 = 0;
+        } else if (kk <= 0.5 * I.best_kkt) {
+          I.best_kkt = kk;
+          I.stall_checks = 0;
+        } else if (kk <= 100.0 * s.fp32_switch_tol && ++I.stall_checks >= s.fp32_stall_limit) {
+          I.spmv_fp32 = 0;  // stalled near the floor the FP32 values set
         }
-        s.tau = s.eta / s.omega;
-        s.sigma = s.eta * s.omega;
-        s.inv_sigma = 1.0 / s.sigma;
-        s.has_anchor = 0;
-        k_next = 0;
-        s.apply_mode = 1;
-      } else {
-        const double kc = (double)(k_after - 1);
-        s.w1_check = (kc + 1.0) / (kc + 2.0);
-        s.w0_check = 1.0 / (kc + 2.0);
-        s.apply_mode = 0;
       }
-      if (T >= s.max_iter) {
-        s.status = 1;
+      bool finite = isfinite(r) && isfinite(r_p) && isfinite(r_d) && isfinite(r_g);
+      for (int k = 0; k < NRED; ++k) finite = finite && isfinite(R[k]) && isfinite(C[k]);
+      if (!finite) {
+        I.status = 2;
+        I.apply_mode = 2;
+      } else if (fmax(r_p, fmax(r_d, r_g)) <= s.eps) {
+        I.status = 0;
+        I.apply_mode = 2;
       } else {
-        s.status = -1;
-        go = 1;
-        s.T_check = T + s.K < s.max_iter ? T + s.K : s.max_iter;
+        const bool first = !I.has_anchor;
+        if (first) {
+          I.r_anchor = r;
+          I.r_prev = r;
+          I.has_anchor = 1;
+        }
+        if (s.sched_len > 0) {
+          kind = s.checks < s.sched_len ? (int)v.sched[(size_t)inst * s.sched_len + s.checks] : 0;
+        } else if (s.restart_enabled) {
+          kind = restart_kind(r, I.r_anchor, I.r_prev, first, k_after, T, s);
+        }
+        I.r_prev = r;
+        if (kind) {
+          I.restarts += 1;
+          if (s.pid_enabled) {
+            const double d_x = sqrt(C[4]), d_y = sqrt(R[4]);
+            if (d_x > 0.0 && d_y > 0.0 && isfinite(d_x) && isfinite(d_y)) {
+              const double so = sqrt(omega);
+              const double e = log((so * d_x) / (d_y / so));
+              I.e_sum += e;
+              const double de = I.has_e_prev ? (e - I.e_prev) : 0.0;
+              const double lw = log(omega) - (s.kp * e + s.ki * I.e_sum + s.kd * de);
+              I.omega = exp(lw);
+              I.e_prev = e;
+              I.has_e_prev = 1;
+            }
+          }
+          I.tau = I.eta / I.omega;
+          I.sigma = I.eta * I.omega;
+          I.inv_sigma = 1.0 / I.sigma;
+          I.has_anchor = 0;
+          k_next = 0;
+          I.apply_mode = 1;
+        } else {
+          const double kc = (double)(k_after - 1);
+          I.w1_check = (kc + 1.0) / (kc + 2.0);
+          I.w0_check = 1.0 / (kc + 2.0);
+          I.apply_mode = 0;
+        }
+        I.status = T >= s.max_iter ? 1 : -1;
       }
+      I.k_base = k_next;
+    } else {
+      I.apply_mode = 2;
     }
-    s.k_base = k_next;
     kb_next = k_next;
     if (s.trace_cap > 0) {
-      dpdlp_trace_t* tr = static_cast<dpdlp_trace_t*>(v.trace) + (s.trace_count % s.trace_cap);
+      dpdlp_trace_t* tr =
+          static_cast<dpdlp_trace_t*>(v.trace) + ((s.trace_count + inst) % s.trace_cap);
       tr->T = T;
       tr->k = k_after;
-      tr->r_primal = r_p;
-      tr->r_dual = r_d;
-      tr->r_gap = r_g;
-      tr->obj_p = obj_p;
-      tr->obj_d = obj_d;
-      tr->r_fp = r;
+      tr->r_primal = I.r_p;
+      tr->r_dual = I.r_d;
+      tr->r_gap = I.r_g;
+      tr->obj_p = I.obj_p;
+      tr->obj_d = I.obj_d;
+      tr->r_fp = I.r_fp;
       tr->omega = omega;
       tr->restart = kind;
       tr->spmv_mode = mode_used;
-      s.trace_count += 1;
+      tr->inst = inst;
+      tr->status = I.status;
     }
-    if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, go);
   }
   __syncthreads();
+  if (!running) return;
   const double kb = (double)kb_next;
-  for (int i = threadIdx.x; i < sc->K; i += TPB) {
-    sc->w1[i] = (kb + i + 1.0) / (kb + i + 2.0);
-    sc->w0[i] = 1.0 / (kb + i + 2.0);
+  double* w = v.wtab + (size_t)inst * 2 * KMAX;
+  for (int i = threadIdx.x; i < s.K; i += TPB) {
+    w[i] = (kb + i + 1.0) / (kb + i + 2.0);
+    w[KMAX + i] = 1.0 / (kb + i + 2.0);
   }
 }
 
+// Global bookkeeping after the instances' control steps: the iteration counter, the check
+// and trace counters, the batch status and the conditional of the device-side loop (it
+// continues while any instance is running).
+__global__ void __launch_bounds__(TPB) finalize_kernel(DevVecs v, DevScalars* sc,
+                                                       unsigned long long cond, int use_cond) {
+  __shared__ int nrun, worst;
+  if (threadIdx.x == 0) {
+    nrun = 0;
+    worst = 0;
+  }
+  __syncthreads();
+  int cnt = 0, wst = 0;
+  for (int i = threadIdx.x; i < v.ninst; i += TPB) {
+    const int st = v.inst[i].status;
+    if (st == -1) ++cnt;
+    else wst = st > wst ? st : wst;
+  }
+  atomicAdd(&nrun, cnt);  // integer sum and max: the result does not depend on the order
+  atomicMax(&worst, wst);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    DevScalars& s = *sc;
+    const long long T = s.T_check;
+    s.T_base = T;
+    s.checks += 1;
+    if (s.trace_cap > 0) s.trace_count += v.ninst;
+    s.running = nrun;
+    s.status = nrun > 0 ? -1 : worst;
+    if (nrun > 0) s.T_check = T + s.K < s.max_iter ? T + s.K : s.max_iter;
+    if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, nrun > 0 ? 1u : 0u);
+  }
+}
+
+// Halpern step (or restart) at the check iteration, per element with its instance's mode.
 __global__ void __launch_bounds__(TPB) apply_kernel(DevVecs v, const DevScalars* sc) {
-  const int mode = sc->apply_mode;
-  if (mode == 2) return;
   const int id = blockIdx.x * TPB + threadIdx.x;
-  const double w1 = sc->w1_check, w0 = sc->w0_check, gamma = sc->gamma;
+  const double gamma = sc->gamma;
   const bool g1 = (gamma == 1.0), hal = sc->halpern != 0;
   if (id < v.n) {
+    const InstScalars& I = v.inst[v.ninst == 1 ? 0 : v.inst_of_col[id]];
+    const int mode = I.apply_mode;
     const double xh = v.xh[id];
     if (mode == 1) {
       v.x[id] = xh;
       v.x0[id] = xh;
+    } else if (mode == 2) {
     } else if (hal) {
       const double xj = v.x[id];
       const double r = g1 ? fma(2.0, xh, -xj) : fma(1.0 + gamma, xh, -gamma * xj);
-      v.x[id] = fma(w1, r, w0 * v.x0[id]);
+      v.x[id] = fma(I.w1_check, r, I.w0_check * v.x0[id]);
     } else {
       v.x[id] = xh;
     }
   }
   if (id < v.m) {
+    const InstScalars& I = v.inst[v.ninst == 1 ? 0 : v.inst_of_row[id]];
+    const int mode = I.apply_mode;
     const double yh = v.yh[id];
     if (mode == 1) {
       v.y[id] = yh;
       v.y0[id] = yh;
+    } else if (mode == 2) {
     } else if (hal) {
       const double yi = v.y[id];
       const double r = g1 ? fma(2.0, yh, -yi) : fma(1.0 + gamma, yh, -gamma * yi);
-      v.y[id] = fma(w1, r, w0 * v.y0[id]);
+      v.y[id] = fma(I.w1_check, r, I.w0_check * v.y0[id]);
     } else {
       v.y[id] = yh;
     }
@@ -785,17 +928,10 @@ cudaError_t launch_check(const DevPacked& csr, const DevPacked& csc, const DevVe
   cudaError_t e;
   if ((e = launch_spmv(csr, v.xh, v.dx, v.axh, v.adx, s)) != cudaSuccess) return e;
   if ((e = launch_spmv(csc, v.yh, nullptr, v.aty, nullptr, s)) != cudaSuccess) return e;
-  if (v.m > 0) {
-    reduce_rows_kernel<<<v.g_rows, TPB, 0, s>>>(v, v.m);
-  } else {
-    cudaMemsetAsync(v.red_rows, 0, sizeof(double) * NRED * v.g_rows, s);
-  }
-  if (v.n > 0) {
-    reduce_cols_kernel<<<v.g_cols, TPB, 0, s>>>(v, v.n, sc);
-  } else {
-    cudaMemsetAsync(v.red_cols, 0, sizeof(double) * NRED * v.g_cols, s);
-  }
-  control_kernel<<<1, TPB, 0, s>>>(v, sc, cond_handle, use_cond);
+  if (v.g_rows > 0) reduce_rows_kernel<<<v.g_rows, TPB, 0, s>>>(v);
+  if (v.g_cols > 0) reduce_cols_kernel<<<v.g_cols, TPB, 0, s>>>(v);
+  control_kernel<<<v.ninst, TPB, 0, s>>>(v, sc);
+  finalize_kernel<<<1, TPB, 0, s>>>(v, sc, cond_handle, use_cond);
   const int len = v.n > v.m ? v.n : v.m;
   if (len > 0) apply_kernel<<<(len + TPB - 1) / TPB, TPB, 0, s>>>(v, sc);
   return cudaGetLastError();
@@ -857,34 +993,40 @@ cudaError_t launch_fill(double* p, double val, int len, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- power iteration
-__global__ void __launch_bounds__(TPB) sumsq_kernel(const double* a, int len, double* part) {
+// Per-instance sums of squares: one block per reduction chunk, then one block per instance.
+__global__ void __launch_bounds__(TPB) sumsq_kernel(const double* a, const int4* chunks,
+                                                    double* part) {
   __shared__ double buf[TPB / 32];
+  const int4 ch = chunks[blockIdx.x];
   double q = 0.0;
-  for (int i = blockIdx.x * TPB + threadIdx.x; i < len; i += gridDim.x * TPB) q = fma(a[i], a[i], q);
+  for (int i = ch.y + threadIdx.x; i < ch.y + ch.z; i += TPB) q = fma(a[i], a[i], q);
   q = block_sum(q, buf);
   if (threadIdx.x == 0) part[blockIdx.x] = q;
 }
 
-__global__ void __launch_bounds__(TPB) power_finish_kernel(const double* pw_part, int gw,
-                                                           const double* pu_part, int gu,
-                                                           double* pw) {
+__global__ void __launch_bounds__(TPB) power_finish_kernel(DevVecs v) {
   __shared__ double buf[TPB / 32];
+  const int inst = blockIdx.x;
   double a = 0.0;
-  for (int i = threadIdx.x; i < gw; i += TPB) a += pw_part[i];
+  for (int c = v.inst_chunk_rows[inst] + threadIdx.x; c < v.inst_chunk_rows[inst + 1]; c += TPB)
+    a += v.red_rows[c];
   a = block_sum(a, buf);
   double b = 0.0;
-  for (int i = threadIdx.x; i < gu; i += TPB) b += pu_part[i];
+  for (int c = v.inst_chunk_cols[inst] + threadIdx.x; c < v.inst_chunk_cols[inst + 1]; c += TPB)
+    b += v.red_cols[c];
   b = block_sum(b, buf);
   if (threadIdx.x == 0) {
+    double* pw = v.pw + 4 * inst;
     pw[0] = a;
     pw[1] = sqrt(b);
     pw[2] = pw[1] > 0.0 ? 1.0 / pw[1] : 0.0;
   }
 }
 
-__global__ void scale_kernel(double* v, const double* u, const double* pw, int len) {
+__global__ void scale_kernel(double* vv, const double* u, const double* pw, const int32_t* inst_of,
+                             int single, int len) {
   const int i = blockIdx.x * TPB + threadIdx.x;
-  if (i < len) v[i] = u[i] * pw[2];
+  if (i < len) vv[i] = u[i] * pw[4 * (single ? 0 : inst_of[i]) + 2];
 }
 
 cudaError_t launch_power_round(const DevPacked& csr, const DevPacked& csc, const DevVecs& v,
@@ -892,12 +1034,13 @@ cudaError_t launch_power_round(const DevPacked& csr, const DevPacked& csc, const
   cudaError_t e;
   if ((e = launch_spmv(csr, vec_v, nullptr, vec_w, nullptr, s)) != cudaSuccess) return e;
   if ((e = launch_spmv(csc, vec_w, nullptr, vec_u, nullptr, s)) != cudaSuccess) return e;
-  const int gw = reduction_grid(v.m), gu = reduction_grid(v.n);
-  // partials live in the check-reduction buffers (at least 1024 * NRED doubles each)
-  sumsq_kernel<<<gw, TPB, 0, s>>>(vec_w, v.m, v.red_rows);
-  sumsq_kernel<<<gu, TPB, 0, s>>>(vec_u, v.n, v.red_cols);
-  power_finish_kernel<<<1, TPB, 0, s>>>(v.red_rows, gw, v.red_cols, gu, v.pw);
-  if (v.n > 0) scale_kernel<<<(v.n + TPB - 1) / TPB, TPB, 0, s>>>(vec_v, vec_u, v.pw, v.n);
+  // partials live in the check-reduction buffers (NRED doubles per chunk)
+  if (v.g_rows > 0) sumsq_kernel<<<v.g_rows, TPB, 0, s>>>(vec_w, v.chunk_rows, v.red_rows);
+  if (v.g_cols > 0) sumsq_kernel<<<v.g_cols, TPB, 0, s>>>(vec_u, v.chunk_cols, v.red_cols);
+  power_finish_kernel<<<v.ninst, TPB, 0, s>>>(v);
+  if (v.n > 0)
+    scale_kernel<<<(v.n + TPB - 1) / TPB, TPB, 0, s>>>(vec_v, vec_u, v.pw, v.inst_of_col,
+                                                       v.ninst == 1, v.n);
   return cudaGetLastError();
 }
 

@@ -115,6 +115,8 @@ void plan_packing(int rows, const std::vector<int64_t>& ptr, PackPlan& P) {
   int32_t nshort = 0, npieces = 0;
   std::vector<int32_t> piece_of_seg(segs.size(), -1);
   for (int s = 0; s < nslots; ++s) {
+    P.slots[s].inst = 0;
+    P.slots[s].pad = 0;
     P.slots[s].row_base = nshort;
     for (int l = 0; l < LANES; ++l) {
       const int32_t lane = slot_lanes[(size_t)s * LANES + l];
@@ -145,6 +147,7 @@ void plan_packing(int rows, const std::vector<int64_t>& ptr, PackPlan& P) {
       P.segs[k++] = {segs[g].row, segs[g].first, segs[g].count, piece_of_seg[g]};
   }
   // pieces of each long row in row order
+  P.long_inst.assign(P.nlong, 0);
   P.long_ptr.assign(P.nlong + 1, 0);
   for (int i = 0; i < P.nlong; ++i) {
     const int64_t L = ptr[P.long_rows[i] + 1] - ptr[P.long_rows[i]];
@@ -155,6 +158,63 @@ void plan_packing(int rows, const std::vector<int64_t>& ptr, PackPlan& P) {
     if (!segs[g].piece) continue;
     const int32_t i = long_of_row[segs[g].row];
     P.long_piece[P.long_ptr[i] + segs[g].first / LANE_ITEMS] = piece_of_seg[g];
+  }
+}
+
+void plan_packing_batch(int rows, const std::vector<int64_t>& ptr,
+                        const std::vector<int32_t>& offsets, PackPlan& P) {
+  P = PackPlan{};
+  P.new_of_old.assign(rows, 0);
+  P.old_of_new.assign(rows, 0);
+  P.lane_ptr.assign(1, 0);
+  std::vector<int32_t> lrow, linst, lcount;
+  std::vector<std::vector<int32_t>> lpieces;
+  const int ninst = (int)offsets.size() - 1;
+  for (int i = 0; i < ninst; ++i) {
+    const int off = offsets[i], len = offsets[i + 1] - offsets[i];
+    std::vector<int64_t> sub(len + 1);
+    for (int r = 0; r <= len; ++r) sub[r] = ptr[off + r] - ptr[off];
+    PackPlan Q;
+    plan_packing(len, sub, Q);
+    const int32_t lane_off = (int32_t)P.lane_ptr.size() - 1;
+    const int32_t seg_off = (int32_t)P.segs.size();
+    const int32_t piece_off = P.npieces;
+    for (int r = 0; r < len; ++r) {
+      P.new_of_old[off + r] = off + Q.new_of_old[r];
+      P.old_of_new[off + r] = off + Q.old_of_new[r];
+    }
+    for (size_t k = 1; k < Q.lane_ptr.size(); ++k) P.lane_ptr.push_back(seg_off + Q.lane_ptr[k]);
+    for (const PackPlan::Seg& g : Q.segs)
+      P.segs.push_back({g.row + off, g.first, g.count, g.piece >= 0 ? g.piece + piece_off : -1});
+    for (int32_t l : Q.slot_lanes) P.slot_lanes.push_back(l >= 0 ? l + lane_off : -1);
+    for (SlotDesc d : Q.slots) {
+      d.row_base += off;
+      d.inst = i;
+      P.slots.push_back(d);
+    }
+    for (int k = 0; k < Q.nlong; ++k) {
+      lrow.push_back(Q.long_rows[k] + off);
+      linst.push_back(i);
+      std::vector<int32_t> pcs;
+      for (int q = Q.long_ptr[k]; q < Q.long_ptr[k + 1]; ++q) pcs.push_back(Q.long_piece[q] + piece_off);
+      lpieces.push_back(pcs);
+    }
+    P.nshort += Q.nshort;
+    P.npieces += Q.npieces;
+  }
+  // long rows of all instances, longest first (their new indices are already fixed)
+  std::vector<int32_t> order(lrow.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return lpieces[a].size() > lpieces[b].size();
+  });
+  P.nlong = (int)lrow.size();
+  P.long_ptr.assign(1, 0);
+  for (int32_t k : order) {
+    P.long_rows.push_back(lrow[k]);
+    P.long_inst.push_back(linst[k]);
+    for (int32_t q : lpieces[k]) P.long_piece.push_back(q);
+    P.long_ptr.push_back((int32_t)P.long_piece.size());
   }
 }
 
@@ -214,13 +274,28 @@ void build_packed(int rows, int cols, const std::vector<int64_t>& ptr,
   }
   out.long_row.resize(P.nlong);
   for (int i = 0; i < P.nlong; ++i) out.long_row[i] = P.new_of_old[P.long_rows[i]];
+  out.long_inst = P.long_inst;
   out.long_ptr = P.long_ptr;
   out.long_piece = P.long_piece;
-  out.nlong_block = out.nlong_warp = 0;  // rows sorted by length: block rows, then warp rows
+  out.nlong_block = out.nlong_warp = 0;  // rows sorted by pieces: block rows, then warp rows
   for (int i = 0; i < P.nlong; ++i) {
     const int pieces = P.long_ptr[i + 1] - P.long_ptr[i];
     if (pieces > LONG_BLOCK_PIECES) ++out.nlong_block;
     else if (pieces > LONG_WARP_PIECES) ++out.nlong_warp;
+  }
+}
+
+void build_chunks(const std::vector<int32_t>& offsets, int chunk, std::vector<int32_t>& chunks,
+                  std::vector<int32_t>& inst_chunk) {
+  chunks.clear();
+  inst_chunk.assign(1, 0);
+  const int ninst = (int)offsets.size() - 1;
+  for (int i = 0; i < ninst; ++i) {
+    for (int a = offsets[i]; a < offsets[i + 1]; a += chunk) {
+      const int len = std::min(chunk, offsets[i + 1] - a);
+      chunks.insert(chunks.end(), {i, a, len, 0});
+    }
+    inst_chunk.push_back((int32_t)(chunks.size() / 4));
   }
 }
 

@@ -5,6 +5,12 @@
 // control kernel of the check sets the loop condition on the device, so the host waits
 // once per solve.  With use_graph = 0 the same kernels are launched from a host loop that
 // reads the status after every check.
+//
+// A handle holds a batch of independent LPs (a single LP is a batch of one): the matrix is
+// block diagonal, every instance keeps its rows and columns in its own index range, has
+// its own step sizes, primal weight, restart epoch and status, and all instances take
+// their iterations in the same kernels.  Converged instances are skipped; the loop ends
+// when no instance is running.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -55,6 +61,8 @@ std::map<std::string, Param> default_params() {
       {"spmv_fp32", {0, 0, 2, true}},
       {"fp32_switch_tol", {1e-6, 0.0, 1.0, false}},
       {"fp32_stall_checks", {64, 1, 1 << 30, true}},
+      {"cta_slots_primal", {4, 2, 8, true}},
+      {"cta_slots_dual", {4, 2, 8, true}},
   };
 }
 
@@ -79,9 +87,13 @@ struct dpdlp {
   bool have_start_x = false, have_start_y = false;
   DevScalars* d_sc = nullptr;
   DevScalars h_sc{};
-  double bnorm = 0.0, cnorm = 0.0;
-  double eta_cached = 0.0;
+  int ninst = 1;
+  std::vector<int32_t> row_off, col_off;    // instance ranges (caller = internal ranges)
+  std::vector<InstScalars> h_inst;          // host mirror of the instance scalars
+  std::vector<double> inst_bnorm, inst_cnorm;
+  std::vector<double> eta_inst;             // power-iteration step size per instance
   bool eta_valid = false;
+  std::vector<double> eta_user;             // per-instance step sizes set by the caller
   bool pending_state = false;
   bool has_state = false;
   int trace_cap = 0;
@@ -166,13 +178,14 @@ int upload_packed(dpdlp* h, const HostPacked& H, DevPacked& D) {
   uint32_t* idx;
   SlotDesc* slots;
   LaneMeta* lanes;
-  int32_t *lrow, *lptr, *lpiece;
+  int32_t *lrow, *linst, *lptr, *lpiece;
   if ((rc = dalloc(h, &val, H.val.size()))) return rc;
   if ((rc = dalloc(h, &idx, H.idx.size()))) return rc;
   if (H.fp32_exact_range && (rc = dalloc(h, &val32, H.val32.size()))) return rc;
   if ((rc = dalloc(h, &slots, H.slots.size()))) return rc;
   if ((rc = dalloc(h, &lanes, H.lanes.size()))) return rc;
   if ((rc = dalloc(h, &lrow, H.long_row.size()))) return rc;
+  if ((rc = dalloc(h, &linst, H.long_inst.size()))) return rc;
   if ((rc = dalloc(h, &lptr, H.long_ptr.size()))) return rc;
   if ((rc = dalloc(h, &lpiece, H.long_piece.size()))) return rc;
   if ((rc = dalloc(h, &psum, 2 * (size_t)H.npieces))) return rc;
@@ -185,6 +198,7 @@ int upload_packed(dpdlp* h, const HostPacked& H, DevPacked& D) {
   CK(up(slots, H.slots.data(), H.slots.size() * sizeof(SlotDesc)));
   CK(up(lanes, H.lanes.data(), H.lanes.size() * sizeof(LaneMeta)));
   CK(up(lrow, H.long_row.data(), H.long_row.size() * sizeof(int32_t)));
+  CK(up(linst, H.long_inst.data(), H.long_inst.size() * sizeof(int32_t)));
   CK(up(lptr, H.long_ptr.data(), H.long_ptr.size() * sizeof(int32_t)));
   CK(up(lpiece, H.long_piece.data(), H.long_piece.size() * sizeof(int32_t)));
   D.val = val;
@@ -193,6 +207,7 @@ int upload_packed(dpdlp* h, const HostPacked& H, DevPacked& D) {
   D.slots = slots;
   D.lanes = lanes;
   D.long_row = lrow;
+  D.long_inst = linst;
   D.long_ptr = lptr;
   D.long_piece = lpiece;
   D.piece_sum = psum;
@@ -206,11 +221,11 @@ std::vector<T> permuted(const T* src, const std::vector<int32_t>& p) {
   return out;
 }
 
-// ||[lc, uc]|| over finite entries, an equality row counted once (reading of the
-// r_primal denominator of Appendix B.4 and of the initial primal weight).
-double bound_norm(const std::vector<double>& lc, const std::vector<double>& uc) {
+// ||[lc, uc]|| over finite entries of rows [r0, r1), an equality row counted once (reading
+// of the r_primal denominator of Appendix B.4 and of the initial primal weight).
+double bound_norm(const std::vector<double>& lc, const std::vector<double>& uc, int r0, int r1) {
   double s = 0.0;
-  for (size_t i = 0; i < lc.size(); ++i) {
+  for (int i = r0; i < r1; ++i) {
     const bool lf = std::isfinite(lc[i]), uf = std::isfinite(uc[i]);
     if (lf && uf && lc[i] == uc[i]) {
       s += lc[i] * lc[i];
@@ -233,7 +248,9 @@ int upload_row_bounds(dpdlp* h) {
     CK(cudaMemcpy(h->v.lo, lo.data(), h->m * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->v.hi, hi.data(), h->m * sizeof(double), cudaMemcpyHostToDevice));
   }
-  h->bnorm = bound_norm(h->h_lc, h->h_uc);
+  h->inst_bnorm.assign(h->ninst, 0.0);
+  for (int i = 0; i < h->ninst; ++i)
+    h->inst_bnorm[i] = bound_norm(h->h_lc, h->h_uc, h->row_off[i], h->row_off[i + 1]);
   return 0;
 }
 
@@ -266,46 +283,73 @@ int export_vec(dpdlp* h, const double* src, double* dst, const int32_t* perm, in
   return 0;
 }
 
-// eta = eta_safety / sigma_max(A) by power iteration on A^T A (start 1/sqrt(n), stop when
-// the Rayleigh quotient changes by <= power_tol relatively, at most power_iters rounds);
-// eta = 1 when A has no nonzeros.
+// eta_i = eta_safety / sigma_max(A_i) for every instance i by power iteration on A_i^T A_i
+// (start 1/sqrt(n_i), stop when the Rayleigh quotient changes by <= power_tol relatively,
+// at most power_iters rounds); eta_i = 1 when A_i has no nonzeros.  The instances iterate
+// together; each keeps the quotient of the round at which it stopped.
 int compute_eta(dpdlp* h) {
   if (h->eta_valid) return 0;
-  const int n = h->n;
-  if (n == 0 || h->nnz == 0) {
-    h->eta_cached = 1.0;
-    h->eta_valid = true;
-    return 0;
+  const int n = h->n, N = h->ninst;
+  std::vector<double> lam(N, 0.0), lam_prev(N, 0.0);
+  std::vector<char> done(N, 0);
+  if (n > 0 && h->nnz > 0) {
+    double* vv = h->v.tmp_n;
+    double* ww = h->v.tmp_m;
+    double* uu = h->v.tmp_n2;
+    std::vector<double> start(n);
+    for (int i = 0; i < N; ++i) {
+      const int a = h->col_off[i], b = h->col_off[i + 1];
+      for (int j = a; j < b; ++j) start[j] = 1.0 / std::sqrt((double)(b - a));
+      if (a == b) done[i] = 1;
+    }
+    CK(cudaMemcpyAsync(vv, start.data(), n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    const int iters = (int)h->P("power_iters");
+    const double tol = h->P("power_tol");
+    std::vector<double> pw(4 * (size_t)N);
+    int left = 0;
+    for (int i = 0; i < N; ++i) left += !done[i];
+    for (int it = 0; it < iters && left > 0; ++it) {
+      CK(launch_power_round(h->csr, h->csc, h->v, vv, ww, uu, h->stream));
+      CK(cudaMemcpyAsync(pw.data(), h->v.pw, pw.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                         h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      for (int i = 0; i < N; ++i) {
+        if (done[i]) continue;
+        lam[i] = pw[4 * i];
+        if (pw[4 * i + 1] == 0.0 || lam[i] == 0.0 || std::fabs(lam[i] - lam_prev[i]) <= tol * lam[i]) {
+          done[i] = 1;
+          --left;
+        } else {
+          lam_prev[i] = lam[i];
+        }
+      }
+    }
   }
-  double* vv = h->v.tmp_n;
-  double* ww = h->v.tmp_m;
-  double* uu = h->v.tmp_n2;
-  CK(launch_fill(vv, 1.0 / std::sqrt((double)n), n, h->stream));
-  const int iters = (int)h->P("power_iters");
-  const double tol = h->P("power_tol");
-  double lam = 0.0, lam_prev = 0.0;
-  for (int it = 0; it < iters; ++it) {
-    CK(launch_power_round(h->csr, h->csc, h->v, vv, ww, uu, h->stream));
-    double pw[3];
-    CK(cudaMemcpyAsync(pw, h->v.pw, sizeof(pw), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    lam = pw[0];
-    if (pw[1] == 0.0 || lam == 0.0) break;
-    if (std::fabs(lam - lam_prev) <= tol * lam) break;
-    lam_prev = lam;
+  h->eta_inst.assign(N, 1.0);
+  for (int i = 0; i < N; ++i) {
+    const double s = std::sqrt(lam[i]);
+    h->eta_inst[i] = s > 0.0 ? h->P("eta_safety") / s : 1.0;
   }
-  const double s = std::sqrt(lam);
-  h->eta_cached = s > 0.0 ? h->P("eta_safety") / s : 1.0;
   h->eta_valid = true;
   return 0;
 }
 
-void fill_weights(DevScalars& s) {
-  const double kb = (double)s.k_base;
-  for (int i = 0; i < s.K; ++i) {
-    s.w1[i] = (kb + i + 1.0) / (kb + i + 2.0);
-    s.w0[i] = 1.0 / (kb + i + 2.0);
+// Halpern weights of the next graph body for every instance, from its k_base.
+int upload_weights(dpdlp* h) {
+  const int K = h->h_sc.K;
+  std::vector<double> w((size_t)h->ninst * 2 * KMAX, 0.0);
+  for (int i = 0; i < h->ninst; ++i) {
+    const double kb = (double)h->h_inst[i].k_base;
+    double* wi = w.data() + (size_t)i * 2 * KMAX;
+    for (int k = 0; k < K; ++k) {
+      wi[k] = (kb + k + 1.0) / (kb + k + 2.0);
+      wi[KMAX + k] = 1.0 / (kb + k + 2.0);
+    }
   }
+  CK(cudaMemcpyAsync(h->v.wtab, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return 0;
 }
 
 void copy_params(dpdlp* h, DevScalars& s) {
@@ -320,27 +364,37 @@ void copy_params(dpdlp* h, DevScalars& s) {
   s.kp = h->P("pid_kp");
   s.ki = h->P("pid_ki");
   s.kd = h->P("pid_kd");
-  s.bnorm = h->bnorm;
-  s.cnorm = h->cnorm;
+  s.ninst = h->ninst;
   s.trace_cap = h->trace_cap;
   s.fp32_switch = h->P("spmv_fp32") == 1.0;
   s.fp32_switch_tol = h->P("fp32_switch_tol");
   s.fp32_stall_limit = (int)h->P("fp32_stall_checks");
 }
 
+// Instance scalars at iteration 0 with step size eta and primal weight omega.
+InstScalars fresh_inst(const dpdlp* h, int i, double eta, double omega, int fp32) {
+  InstScalars I;
+  std::memset(&I, 0, sizeof(I));
+  I.eta = eta;
+  I.omega = omega;
+  I.tau = eta / omega;
+  I.sigma = eta * omega;
+  I.inv_sigma = 1.0 / I.sigma;
+  I.bnorm = h->inst_bnorm[i];
+  I.cnorm = h->inst_cnorm[i];
+  I.status = -1;
+  I.apply_mode = 2;
+  I.spmv_fp32 = fp32;
+  I.best_kkt = INFINITY;
+  return I;
+}
+
 // Fresh start: x = proj_X(0) (or the warm start), y = 0 (or the warm start), anchor = start.
 int init_fresh(dpdlp* h) {
   int rc;
   const double pe = h->P("eta");
-  double eta;
-  if (pe > 0.0) {
-    eta = pe;
-  } else {
-    if ((rc = compute_eta(h))) return rc;
-    eta = h->eta_cached;
-  }
+  if (pe <= 0.0 && h->eta_user.empty() && (rc = compute_eta(h))) return rc;
   const double po = h->P("omega0");
-  const double omega = po > 0.0 ? po : ((h->cnorm > 0.0 && h->bnorm > 0.0) ? h->cnorm / h->bnorm : 1.0);
   if (h->have_start_x && h->n)
     CK(cudaMemcpyAsync(h->v.x, h->xs, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   if (h->have_start_y && h->m)
@@ -350,15 +404,15 @@ int init_fresh(dpdlp* h) {
   const int sched = s.sched_len;  // the forced schedule outlives a fresh start
   std::memset(&s, 0, sizeof(s));
   s.sched_len = sched;
-  s.eta = eta;
-  s.omega = omega;
-  s.tau = eta / omega;
-  s.sigma = eta * omega;
-  s.inv_sigma = 1.0 / s.sigma;
   s.status = -1;
-  s.apply_mode = 2;
-  s.spmv_fp32 = (h->P("spmv_fp32") >= 1.0 && h->csr.val32 && h->csc.val32) ? 1 : 0;
-  s.best_kkt = INFINITY;
+  const int fp32 = (h->P("spmv_fp32") >= 1.0 && h->csr.val32 && h->csc.val32) ? 1 : 0;
+  h->h_inst.resize(h->ninst);
+  for (int i = 0; i < h->ninst; ++i) {
+    const double eta = pe > 0.0 ? pe : (!h->eta_user.empty() ? h->eta_user[i] : h->eta_inst[i]);
+    const double cn = h->inst_cnorm[i], bn = h->inst_bnorm[i];
+    const double omega = po > 0.0 ? po : ((cn > 0.0 && bn > 0.0) ? cn / bn : 1.0);
+    h->h_inst[i] = fresh_inst(h, i, eta, omega, fp32);
+  }
   h->has_state = true;
   return 0;
 }
@@ -460,11 +514,17 @@ int dpdlp_set_param(dpdlp_t* h, const char* key, double v) {
   Param& p = it->second;
   if (!(v >= p.lo && v <= p.hi) || (p.integer && v != std::floor(v)))
     return fail(h, DPDLP_ERR_INVALID, std::string("value out of range for ") + key);
-  if (std::string(key) == "check_every" && v != p.value) free_graph(h);
+  const std::string k(key);
+  if ((k == "cta_slots_primal" || k == "cta_slots_dual") && v != 2 && v != 4 && v != 8)
+    return fail(h, DPDLP_ERR_INVALID, k + " must be 2, 4 or 8");
+  if ((k == "check_every" || k == "cta_slots_primal" || k == "cta_slots_dual") && v != p.value)
+    free_graph(h);  // the captured graph holds the launch shapes
   if (std::string(key) == "eta_safety" || std::string(key) == "power_iters" ||
       std::string(key) == "power_tol")
     h->eta_valid = false;
   p.value = v;
+  h->csc.cta_slots = (int)h->P("cta_slots_primal");
+  h->csr.cta_slots = (int)h->P("cta_slots_dual");
   return 0;
 }
 
@@ -476,10 +536,16 @@ int dpdlp_get_param(const dpdlp_t* h, const char* key, double* v) {
   return 0;
 }
 
-int dpdlp_load_lp(dpdlp_t* h, int32_t n, int32_t m, const double* c, const int64_t* row_ptr,
-                  const int32_t* col_idx, const double* val, const double* b, const double* lv,
-                  const double* uv, const int8_t* ctype) {
-  if (!h) return DPDLP_ERR_INVALID;
+}  // extern "C"
+
+namespace {
+
+// Loads `count` instances: instance i owns rows [row_off[i], row_off[i+1]) and columns
+// [col_off[i], col_off[i+1]) of one block-diagonal matrix.
+int load_impl(dpdlp* h, int32_t count, const int32_t* row_off, const int32_t* col_off,
+              int32_t n, int32_t m, const double* c, const int64_t* row_ptr,
+              const int32_t* col_idx, const double* val, const double* b, const double* lv,
+              const double* uv, const int8_t* ctype) {
   CK(cudaSetDevice(h->device));
   const auto t0 = std::chrono::steady_clock::now();
   if (n < 0 || m < 0) return fail(h, DPDLP_ERR_INVALID, "negative dimension");
@@ -488,8 +554,20 @@ int dpdlp_load_lp(dpdlp_t* h, int32_t n, int32_t m, const double* c, const int64
   if ((b == nullptr) != (ctype == nullptr))
     return fail(h, DPDLP_ERR_INVALID, "b and ctype must both be given or both be NULL");
   if (m > (int32_t)IDX_MASK) return fail(h, DPDLP_ERR_INVALID, "too many rows for the packed index format");
+  if (count < 1 || !row_off || !col_off) return fail(h, DPDLP_ERR_INVALID, "invalid instance count or ranges");
+  if (row_off[0] != 0 || col_off[0] != 0 || row_off[count] != m || col_off[count] != n)
+    return fail(h, DPDLP_ERR_INVALID, "instance ranges must start at 0 and end at m and n");
+  for (int i = 0; i < count; ++i)
+    if (row_off[i + 1] < row_off[i] || col_off[i + 1] < col_off[i])
+      return fail(h, DPDLP_ERR_INVALID, "instance ranges must be non-decreasing");
   std::string e = validate_csr(m, n, row_ptr, col_idx, val);
   if (!e.empty()) return fail(h, DPDLP_ERR_INVALID, e);
+  for (int i = 0; i < count; ++i)
+    for (int r = row_off[i]; r < row_off[i + 1]; ++r)
+      for (int64_t q = row_ptr[r]; q < row_ptr[r + 1]; ++q)
+        if (col_idx[q] < col_off[i] || col_idx[q] >= col_off[i + 1])
+          return fail(h, DPDLP_ERR_INVALID, "nonzero outside its instance's columns in row " +
+                                                std::to_string(r));
   for (int j = 0; j < n; ++j) {
     if (!std::isfinite(c[j])) return fail(h, DPDLP_ERR_INVALID, "non-finite objective coefficient");
     if (std::isnan(lv[j]) || std::isnan(uv[j]) || lv[j] > uv[j] || lv[j] == INFINITY ||
@@ -514,11 +592,22 @@ int dpdlp_load_lp(dpdlp_t* h, int32_t n, int32_t m, const double* c, const int64
   h->nnz = row_ptr[m];
   h->h_lc = lc;
   h->h_uc = uc;
+  h->ninst = count;
+  h->row_off.assign(row_off, row_off + count + 1);
+  h->col_off.assign(col_off, col_off + count + 1);
+  h->eta_user.clear();
+  // block permutation inside every instance (instance i draws seeds seed + 2i, seed + 2i + 1)
   const bool perm = h->P("block_permute") != 0.0;
   const int pb = (int)h->P("perm_block");
   const uint64_t seed = (uint64_t)h->P("perm_seed");
-  h->prow = block_permutation(m, pb, seed, perm);
-  h->pcol = block_permutation(n, pb, seed + 1, perm);
+  h->prow.assign(m, 0);
+  h->pcol.assign(n, 0);
+  for (int i = 0; i < count; ++i) {
+    const std::vector<int32_t> pr = block_permutation(row_off[i + 1] - row_off[i], pb, seed + 2 * (uint64_t)i, perm);
+    const std::vector<int32_t> pc = block_permutation(col_off[i + 1] - col_off[i], pb, seed + 2 * (uint64_t)i + 1, perm);
+    for (size_t k = 0; k < pr.size(); ++k) h->prow[row_off[i] + k] = row_off[i] + pr[k];
+    for (size_t k = 0; k < pc.size(); ++k) h->pcol[col_off[i] + k] = col_off[i] + pc[k];
+  }
   std::vector<int64_t> pptr, tptr;
   std::vector<int32_t> pidx, tidx;
   std::vector<double> pval, tval;
@@ -526,8 +615,13 @@ int dpdlp_load_lp(dpdlp_t* h, int32_t n, int32_t m, const double* c, const int64
   transpose_csr(m, n, pptr, pidx, pval, tptr, tidx, tval);
   // pack rows of A and rows of A^T into warp lanes; each packing fixes one index order
   PackPlan rplan, cplan;
-  plan_packing(m, pptr, rplan);
-  plan_packing(n, tptr, cplan);
+  if (count == 1) {
+    plan_packing(m, pptr, rplan);
+    plan_packing(n, tptr, cplan);
+  } else {
+    plan_packing_batch(m, pptr, h->row_off, rplan);
+    plan_packing_batch(n, tptr, h->col_off, cplan);
+  }
   HostPacked Hr, Hc;
   build_packed(m, n, pptr, pidx, pval, rplan, cplan.new_of_old, Hr);
   build_packed(n, m, tptr, tidx, tval, cplan, rplan.new_of_old, Hc);
@@ -548,9 +642,12 @@ int dpdlp_load_lp(dpdlp_t* h, int32_t n, int32_t m, const double* c, const int64
   int rc;
   if ((rc = upload_packed(h, Hr, h->csr))) return rc;
   if ((rc = upload_packed(h, Hc, h->csc))) return rc;
+  h->csc.cta_slots = (int)h->P("cta_slots_primal");
+  h->csr.cta_slots = (int)h->P("cta_slots_dual");
   DevVecs& v = h->v;
   v.n = n;
   v.m = m;
+  v.ninst = count;
   double** nvecs[] = {&v.c, &v.lv, &v.uv, &v.x, &v.x0, &v.xbar, &v.xh, &v.dx, &v.aty,
                       &v.tmp_n, &v.tmp_n2, &h->xs};
   for (double** p : nvecs) {
@@ -562,13 +659,47 @@ int dpdlp_load_lp(dpdlp_t* h, int32_t n, int32_t m, const double* c, const int64
     if ((rc = dalloc(h, p, m))) return rc;
     CK(cudaMemset(*p, 0, (m > 0 ? m : 2) * sizeof(double)));
   }
-  v.g_rows = reduction_grid(m);
-  v.g_cols = reduction_grid(n);
-  if ((rc = dalloc(h, &v.red_rows, 1024 * NRED))) return rc;
-  if ((rc = dalloc(h, &v.red_cols, 1024 * NRED))) return rc;
+  // reduction chunks and the instance of every row and column
+  std::vector<int32_t> chr, chc, icr, icc;
+  build_chunks(h->row_off, RED_CHUNK, chr, icr);
+  build_chunks(h->col_off, RED_CHUNK, chc, icc);
+  v.g_rows = (int)chr.size() / 4;
+  v.g_cols = (int)chc.size() / 4;
+  std::vector<int32_t> ior(m), ioc(n);
+  for (int i = 0; i < count; ++i) {
+    for (int r = row_off[i]; r < row_off[i + 1]; ++r) ior[r] = i;
+    for (int j = col_off[i]; j < col_off[i + 1]; ++j) ioc[j] = i;
+  }
+  int32_t *d_chr, *d_chc, *d_icr, *d_icc, *d_ior, *d_ioc;
+  if ((rc = dalloc(h, &d_chr, chr.size()))) return rc;
+  if ((rc = dalloc(h, &d_chc, chc.size()))) return rc;
+  if ((rc = dalloc(h, &d_icr, icr.size()))) return rc;
+  if ((rc = dalloc(h, &d_icc, icc.size()))) return rc;
+  if ((rc = dalloc(h, &d_ior, m))) return rc;
+  if ((rc = dalloc(h, &d_ioc, n))) return rc;
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    return bytes ? cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+  };
+  CK(up(d_chr, chr.data(), chr.size() * sizeof(int32_t)));
+  CK(up(d_chc, chc.data(), chc.size() * sizeof(int32_t)));
+  CK(up(d_icr, icr.data(), icr.size() * sizeof(int32_t)));
+  CK(up(d_icc, icc.data(), icc.size() * sizeof(int32_t)));
+  CK(up(d_ior, ior.data(), ior.size() * sizeof(int32_t)));
+  CK(up(d_ioc, ioc.data(), ioc.size() * sizeof(int32_t)));
+  v.chunk_rows = reinterpret_cast<const int4*>(d_chr);
+  v.chunk_cols = reinterpret_cast<const int4*>(d_chc);
+  v.inst_chunk_rows = d_icr;
+  v.inst_chunk_cols = d_icc;
+  v.inst_of_row = d_ior;
+  v.inst_of_col = d_ioc;
+  const size_t gr = v.g_rows > 0 ? v.g_rows : 1, gc = v.g_cols > 0 ? v.g_cols : 1;
+  if ((rc = dalloc(h, &v.red_rows, gr * NRED))) return rc;
+  if ((rc = dalloc(h, &v.red_cols, gc * NRED))) return rc;
   if ((rc = dalloc(h, &v.perm_col, n))) return rc;
   if ((rc = dalloc(h, &v.perm_row, m))) return rc;
-  if ((rc = dalloc(h, &v.pw, 4))) return rc;
+  if ((rc = dalloc(h, &v.pw, 4 * (size_t)count))) return rc;
+  if ((rc = dalloc(h, &v.inst, count))) return rc;
+  if ((rc = dalloc(h, &v.wtab, (size_t)count * 2 * KMAX))) return rc;
   if ((rc = dalloc(h, &v.sched, 1))) return rc;
   h->trace_cap = (int)h->P("trace_capacity");
   if ((rc = dalloc(h, (dpdlp_trace_t**)&v.trace, h->trace_cap > 0 ? h->trace_cap : 1))) return rc;
@@ -584,9 +715,12 @@ int dpdlp_load_lp(dpdlp_t* h, int32_t n, int32_t m, const double* c, const int64
   }
   if (m) CK(cudaMemcpy(v.perm_row, h->prow.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice));
   if ((rc = upload_row_bounds(h))) return rc;
-  double cs = 0.0;
-  for (int j = 0; j < n; ++j) cs += c[j] * c[j];
-  h->cnorm = std::sqrt(cs);
+  h->inst_cnorm.assign(count, 0.0);
+  for (int i = 0; i < count; ++i) {
+    double cs = 0.0;
+    for (int j = col_off[i]; j < col_off[i + 1]; ++j) cs += c[j] * c[j];
+    h->inst_cnorm[i] = std::sqrt(cs);
+  }
   h->loaded = true;
   const auto t1 = std::chrono::steady_clock::now();
   dpdlp_info_t& I = h->info;
@@ -602,6 +736,26 @@ int dpdlp_load_lp(dpdlp_t* h, int32_t n, int32_t m, const double* c, const int64
   I.device_bytes = h->dev_bytes;
   I.preprocess_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
   return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dpdlp_load_lp(dpdlp_t* h, int32_t n, int32_t m, const double* c, const int64_t* row_ptr,
+                  const int32_t* col_idx, const double* val, const double* b, const double* lv,
+                  const double* uv, const int8_t* ctype) {
+  if (!h) return DPDLP_ERR_INVALID;
+  const int32_t ro[2] = {0, m < 0 ? 0 : m}, co[2] = {0, n < 0 ? 0 : n};
+  return load_impl(h, 1, ro, co, n, m, c, row_ptr, col_idx, val, b, lv, uv, ctype);
+}
+
+int dpdlp_load_batch(dpdlp_t* h, int32_t count, const int32_t* row_off, const int32_t* col_off,
+                     int32_t n, int32_t m, const double* c, const int64_t* row_ptr,
+                     const int32_t* col_idx, const double* val, const double* b,
+                     const double* lv, const double* uv, const int8_t* ctype) {
+  if (!h) return DPDLP_ERR_INVALID;
+  return load_impl(h, count, row_off, col_off, n, m, c, row_ptr, col_idx, val, b, lv, uv, ctype);
 }
 
 int dpdlp_set_row_bounds(dpdlp_t* h, const double* lc, const double* uc) {
@@ -646,16 +800,24 @@ int dpdlp_solve(dpdlp_t* h, double tol, int64_t max_iter) {
   s.eps = tol;
   s.max_iter = max_iter;
   h->pending_state = false;
+  for (InstScalars& I : h->h_inst) I.status = -1;  // a solve continues every instance
   if (s.T_base >= max_iter) {
     s.status = 1;
+    for (InstScalars& I : h->h_inst) I.status = 1;
+    s.running = 0;
     CK(cudaMemcpyAsync(h->d_sc, &s, sizeof(DevScalars), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->v.inst, h->h_inst.data(), h->ninst * sizeof(InstScalars),
+                       cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return 1;
   }
   s.status = -1;
+  s.running = h->ninst;
   s.T_check = s.T_base + s.K < max_iter ? s.T_base + s.K : max_iter;
-  fill_weights(s);
+  if ((rc = upload_weights(h))) return rc;
   CK(cudaMemcpyAsync(h->d_sc, &s, sizeof(DevScalars), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->v.inst, h->h_inst.data(), h->ninst * sizeof(InstScalars),
+                     cudaMemcpyHostToDevice, h->stream));
   if (h->P("use_graph") != 0.0) {
     if (h->graph_K != s.K || !h->exec) {
       CK(cudaStreamSynchronize(h->stream));
@@ -666,6 +828,8 @@ int dpdlp_solve(dpdlp_t* h, double tol, int64_t max_iter) {
     if ((rc = run_host_loop(h))) return rc;
   }
   CK(cudaMemcpyAsync(&s, h->d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->h_inst.data(), h->v.inst, h->ninst * sizeof(InstScalars),
+                     cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaGetLastError());
   return s.status;
@@ -681,25 +845,83 @@ int dpdlp_get_solution(dpdlp_t* h, double* x, double* y) {
   return 0;
 }
 
+}  // extern "C"
+
+namespace {
+
+void inst_kkt(const dpdlp* h, int i, dpdlp_kkt_t* o) {
+  const DevScalars& s = h->h_sc;
+  const InstScalars& I = h->h_inst[i];
+  o->r_primal = I.r_p;
+  o->r_dual = I.r_d;
+  o->r_gap = I.r_g;
+  o->obj_p = I.obj_p;
+  o->obj_d = I.obj_d;
+  o->r_fp = I.r_fp;
+  o->omega = I.omega;
+  o->eta = I.eta;
+  o->tau = I.tau;
+  o->sigma = I.sigma;
+  o->iterations = h->ninst == 1 ? s.T_base : I.iterations;
+  o->restarts = I.restarts;
+  o->checks = s.checks;
+  o->status = I.status;
+  o->spmv_mode = I.spmv_fp32;
+}
+
+}  // namespace
+
+extern "C" {
+
 int dpdlp_get_kkt(dpdlp_t* h, dpdlp_kkt_t* o) {
   if (!h || !o) return DPDLP_ERR_INVALID;
   if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
-  const DevScalars& s = h->h_sc;
-  o->r_primal = s.r_p;
-  o->r_dual = s.r_d;
-  o->r_gap = s.r_g;
-  o->obj_p = s.obj_p;
-  o->obj_d = s.obj_d;
-  o->r_fp = s.r_fp;
-  o->omega = s.omega;
-  o->eta = s.eta;
-  o->tau = s.tau;
-  o->sigma = s.sigma;
-  o->iterations = s.T_base;
-  o->restarts = s.restarts;
-  o->checks = s.checks;
-  o->status = h->has_state ? s.status : -1;
-  o->spmv_mode = s.spmv_fp32;
+  std::memset(o, 0, sizeof(*o));
+  o->status = -1;
+  if (!h->has_state) return 0;
+  inst_kkt(h, 0, o);
+  if (h->ninst > 1) {  // batch: worst residuals, summed objectives and restarts
+    for (int i = 1; i < h->ninst; ++i) {
+      dpdlp_kkt_t k;
+      inst_kkt(h, i, &k);
+      o->r_primal = std::fmax(o->r_primal, k.r_primal);
+      o->r_dual = std::fmax(o->r_dual, k.r_dual);
+      o->r_gap = std::fmax(o->r_gap, k.r_gap);
+      o->r_fp = std::fmax(o->r_fp, k.r_fp);
+      o->obj_p += k.obj_p;
+      o->obj_d += k.obj_d;
+      o->restarts += k.restarts;
+      o->spmv_mode = o->spmv_mode > k.spmv_mode ? o->spmv_mode : k.spmv_mode;
+    }
+    o->iterations = h->h_sc.T_base;
+  }
+  o->status = h->h_sc.status;
+  return 0;
+}
+
+int dpdlp_get_batch_kkt(dpdlp_t* h, dpdlp_kkt_t* out, int32_t count) {
+  if (!h || !out) return DPDLP_ERR_INVALID;
+  if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
+  if (count != h->ninst) return fail(h, DPDLP_ERR_INVALID, "count must equal the number of instances");
+  for (int i = 0; i < count; ++i) {
+    std::memset(&out[i], 0, sizeof(out[i]));
+    out[i].status = -1;
+    if (h->has_state) inst_kkt(h, i, &out[i]);
+  }
+  return 0;
+}
+
+int dpdlp_set_batch_eta(dpdlp_t* h, const double* eta, int32_t count) {
+  if (!h || (count > 0 && !eta)) return DPDLP_ERR_INVALID;
+  if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
+  if (count == 0) {
+    h->eta_user.clear();
+    return 0;
+  }
+  if (count != h->ninst) return fail(h, DPDLP_ERR_INVALID, "count must equal the number of instances");
+  for (int i = 0; i < count; ++i)
+    if (!(eta[i] > 0.0) || !std::isfinite(eta[i])) return fail(h, DPDLP_ERR_INVALID, "eta must be positive and finite");
+  h->eta_user.assign(eta, eta + count);
   return 0;
 }
 
@@ -727,6 +949,7 @@ int dpdlp_get_state(dpdlp_t* h, double* x, double* y, double* x0, double* y0,
   if (!h) return DPDLP_ERR_INVALID;
   if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
   if (!h->has_state) return fail(h, DPDLP_ERR_INVALID, "no solver state yet");
+  if (h->ninst != 1) return fail(h, DPDLP_ERR_INVALID, "checkpoints hold a single LP, not a batch");
   CK(cudaSetDevice(h->device));
   int rc;
   if ((rc = export_vec(h, h->v.x, x, h->v.perm_col, h->n, h->v.tmp_n))) return rc;
@@ -734,11 +957,11 @@ int dpdlp_get_state(dpdlp_t* h, double* x, double* y, double* x0, double* y0,
   if ((rc = export_vec(h, h->v.x0, x0, h->v.perm_col, h->n, h->v.tmp_n))) return rc;
   if ((rc = export_vec(h, h->v.y0, y0, h->v.perm_row, h->m, h->v.tmp_m))) return rc;
   if (st) {
-    const DevScalars& s = h->h_sc;
-    st->T = s.T_base;
+    const InstScalars& s = h->h_inst[0];
+    st->T = h->h_sc.T_base;
     st->k = s.k_base;
     st->restarts = s.restarts;
-    st->checks = s.checks;
+    st->checks = h->h_sc.checks;
     st->eta = s.eta;
     st->omega = s.omega;
     st->r_anchor = s.r_anchor;
@@ -760,6 +983,7 @@ int dpdlp_set_state(dpdlp_t* h, const double* x, const double* y, const double* 
   if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
   if (!(st->eta > 0.0) || !(st->omega > 0.0) || st->T < 0 || st->k < 0)
     return fail(h, DPDLP_ERR_INVALID, "invalid scalar state");
+  if (h->ninst != 1) return fail(h, DPDLP_ERR_INVALID, "checkpoints hold a single LP, not a batch");
   CK(cudaSetDevice(h->device));
   int rc;
   if ((rc = import_vec(h, x, h->v.x, h->v.perm_col, h->n, h->v.tmp_n))) return rc;
@@ -769,30 +993,28 @@ int dpdlp_set_state(dpdlp_t* h, const double* x, const double* y, const double* 
   if (h->n) CK(cudaMemcpyAsync(h->v.xh, h->v.x, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   if (h->m) CK(cudaMemcpyAsync(h->v.yh, h->v.y, h->m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  DevScalars& s = h->h_sc;
-  const int sched = s.sched_len;
-  std::memset(&s, 0, sizeof(s));
-  s.sched_len = sched;
-  s.T_base = st->T;
+  DevScalars& g = h->h_sc;
+  const int sched = g.sched_len;
+  std::memset(&g, 0, sizeof(g));
+  g.sched_len = sched;
+  g.T_base = st->T;
+  g.checks = st->checks;
+  g.status = -1;
+  h->h_inst.resize(1);
+  InstScalars& s = h->h_inst[0];
+  s = fresh_inst(h, 0, st->eta, st->omega,
+                 (st->spmv_mode && h->csr.val32 && h->csc.val32) ? 1 : 0);
   s.k_base = st->k;
   s.restarts = st->restarts;
-  s.checks = st->checks;
-  s.eta = st->eta;
-  s.omega = st->omega;
-  s.tau = s.eta / s.omega;
-  s.sigma = s.eta * s.omega;
-  s.inv_sigma = 1.0 / s.sigma;
   s.r_anchor = st->r_anchor;
   s.r_prev = st->r_prev;
   s.e_sum = st->e_sum;
   s.e_prev = st->e_prev;
   s.has_anchor = st->has_anchor;
   s.has_e_prev = st->has_e_prev;
-  s.spmv_fp32 = (st->spmv_mode && h->csr.val32 && h->csc.val32) ? 1 : 0;
   s.stall_checks = st->stall_checks;
   s.best_kkt = st->best_kkt;
-  s.status = -1;
-  s.apply_mode = 2;
+  s.iterations = st->T;
   h->has_state = true;
   h->pending_state = true;
   return 0;
@@ -802,6 +1024,8 @@ int dpdlp_set_schedule(dpdlp_t* h, const int8_t* kinds, int32_t count) {
   if (!h || count < 0 || (count > 0 && !kinds)) return DPDLP_ERR_INVALID;
   if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
   CK(cudaSetDevice(h->device));
+  if (count % h->ninst != 0)
+    return fail(h, DPDLP_ERR_INVALID, "schedule length must be a multiple of the instance count");
   for (int i = 0; i < count; ++i)
     if (kinds[i] < 0 || kinds[i] > 3) return fail(h, DPDLP_ERR_INVALID, "restart kind must be 0..3");
   CK(cudaStreamSynchronize(h->stream));
@@ -811,7 +1035,7 @@ int dpdlp_set_schedule(dpdlp_t* h, const int8_t* kinds, int32_t count) {
   int rc;
   if ((rc = dalloc(h, &h->v.sched, count > 0 ? count : 1))) return rc;
   if (count > 0) CK(cudaMemcpy(h->v.sched, kinds, count, cudaMemcpyHostToDevice));
-  h->h_sc.sched_len = count;
+  h->h_sc.sched_len = count / h->ninst;  // per instance: kinds[i * len + check]
   return 0;
 }
 

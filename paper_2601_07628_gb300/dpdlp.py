@@ -40,7 +40,8 @@ class Trace(C.Structure):
     _fields_ = [("T", C.c_int64), ("k", C.c_int64)] + \
                [(k, C.c_double) for k in ("r_primal", "r_dual", "r_gap", "obj_p", "obj_d", "r_fp",
                                           "omega")] + \
-               [("restart", C.c_int32), ("spmv_mode", C.c_int32)]
+               [("restart", C.c_int32), ("spmv_mode", C.c_int32), ("inst", C.c_int32),
+                ("status", C.c_int32)]
 
 
 class ScalarState(C.Structure):
@@ -65,6 +66,11 @@ EXPORTS = {
     "dpdlp_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "dpdlp_load_lp": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dpdlp_load_batch": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dpdlp_set_batch_eta": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "dpdlp_get_batch_kkt": (C.c_int, [C.c_void_p, C.POINTER(KKT), C.c_int32]),
     "dpdlp_set_row_bounds": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dpdlp_set_param": (C.c_int, [C.c_void_p, C.c_char_p, C.c_double]),
     "dpdlp_get_param": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_double)]),
@@ -195,9 +201,63 @@ class Solver:
                                            _ptr(b) if ctype is not None else None, _ptr(lv), _ptr(uv),
                                            _ptr(ctype) if ctype is not None else None))
         self.n, self.m = n, m
+        self.row_off = np.array([0, m], np.int32)
+        self.col_off = np.array([0, n], np.int32)
         if ctype is None:
             self.set_row_bounds(lc, uc)
         return self
+
+    def load_batch(self, lps):
+        """Load a batch of LPs (a list of ``lpgen.LP``) into one handle: the block-diagonal
+        stack of the instances, solved together with per-instance step sizes, weights,
+        restarts and statuses.  Row bounds come from (b, ctype) when every instance has
+        them, else from the instances' (lc, uc)."""
+        lps = list(lps)
+        if not lps:
+            raise ValueError("empty batch")
+        row_off = np.zeros(len(lps) + 1, np.int32)
+        col_off = np.zeros(len(lps) + 1, np.int32)
+        row_off[1:] = np.cumsum([lp.m for lp in lps])
+        col_off[1:] = np.cumsum([lp.n for lp in lps])
+        n, m = int(col_off[-1]), int(row_off[-1])
+        c = np.ascontiguousarray(np.concatenate([lp.c for lp in lps]), dtype=np.float64)
+        lv = np.ascontiguousarray(np.concatenate([lp.lv for lp in lps]), dtype=np.float64)
+        uv = np.ascontiguousarray(np.concatenate([lp.uv for lp in lps]), dtype=np.float64)
+        nnz_off = np.concatenate([[0], np.cumsum([int(lp.row_ptr[-1]) for lp in lps])])
+        row_ptr = np.ascontiguousarray(np.concatenate(
+            [[0]] + [np.asarray(lp.row_ptr[1:], np.int64) + nnz_off[i] for i, lp in enumerate(lps)]),
+            dtype=np.int64)
+        col = np.ascontiguousarray(np.concatenate(
+            [np.asarray(lp.col, np.int64) + col_off[i] for i, lp in enumerate(lps)]), dtype=np.int32)
+        val = np.ascontiguousarray(np.concatenate([lp.val for lp in lps]), dtype=np.float64)
+        typed = all(lp.ctype is not None for lp in lps)
+        b = ctype = None
+        if typed:
+            b = np.ascontiguousarray(np.concatenate([lp.b for lp in lps]), dtype=np.float64)
+            ctype = np.ascontiguousarray(np.concatenate([lp.ctype for lp in lps]), dtype=np.int8)
+        self._check(self.lib.dpdlp_load_batch(
+            self.h, len(lps), _ptr(row_off), _ptr(col_off), n, m, _ptr(c), _ptr(row_ptr), _ptr(col),
+            _ptr(val), _ptr(b) if typed else None, _ptr(lv), _ptr(uv), _ptr(ctype) if typed else None))
+        self.n, self.m = n, m
+        self.row_off, self.col_off = row_off, col_off
+        if not typed:
+            self.set_row_bounds(np.concatenate([lp.lc for lp in lps]), np.concatenate([lp.uc for lp in lps]))
+        return self
+
+    def split(self, x, y):
+        """Per-instance pieces [(x_i, y_i)] of stacked batch vectors."""
+        ro, co = self.row_off, self.col_off
+        return [(x[co[i]:co[i + 1]], y[ro[i]:ro[i + 1]]) for i in range(len(ro) - 1)]
+
+    def set_batch_eta(self, eta):
+        e = np.ascontiguousarray(eta, dtype=np.float64)
+        self._check(self.lib.dpdlp_set_batch_eta(self.h, _ptr(e) if e.size else None, int(e.size)))
+
+    def batch_kkt(self) -> list:
+        cnt = len(self.row_off) - 1
+        buf = (KKT * cnt)()
+        self._check(self.lib.dpdlp_get_batch_kkt(self.h, buf, cnt))
+        return [{f: getattr(buf[i], f) for f, _ in KKT._fields_} for i in range(cnt)]
 
     def set_row_bounds(self, lc, uc):
         lc, uc = _host_f64(lc, self.m), _host_f64(uc, self.m)
@@ -268,6 +328,11 @@ class Solver:
         self._check(self.lib.dpdlp_set_state(self.h, _ptr(x), _ptr(y), _ptr(x0), _ptr(y0), C.byref(s)))
 
     def set_schedule(self, kinds):
+        """Forced restart decisions per check.  For a batch: a list with one sequence per
+        instance (shorter ones are padded with 0, no restart)."""
+        if len(kinds) and not np.isscalar(kinds[0]):
+            L = max(len(k) for k in kinds)
+            kinds = np.concatenate([np.pad(np.asarray(k, np.int8), (0, L - len(k))) for k in kinds])
         k = np.ascontiguousarray(kinds, dtype=np.int8)
         self._check(self.lib.dpdlp_set_schedule(self.h, _ptr(k) if k.size else None, int(k.size)))
 
