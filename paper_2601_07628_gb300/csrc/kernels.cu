@@ -137,14 +137,42 @@ __device__ __forceinline__ double block_sum(double v, double* buf) {
 // ---------------------------------------------------------------- epilogues
 // An epilogue turns finished row sums into outputs: `apply_direct(row, sums)`.
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// L2 prefetch of the 128-byte lines that hold elements [r0, r0 + nr) of NA double arrays
+// (256-byte aligned allocations), spread over the lanes of a warp.
+template <int NA>
+__device__ __forceinline__ void prefetch_rows(const double* const (&arr)[NA], int r0, int nr,
+                                              int lane) {
+  if (nr <= 0) return;
+  const long long l0 = ((long long)r0 * 8) >> 7, l1 = ((long long)(r0 + nr) * 8 - 1) >> 7;
+  const int nl = (int)(l1 - l0 + 1);
+  for (int t = lane; t < NA * nl; t += LANES) {
+    const int a = t / nl;
+    const double* base = arr[0];
+#pragma unroll
+    for (int k = 1; k < NA; ++k)
+      if (a == k) base = arr[k];
+    prefetch_l2(reinterpret_cast<const char*>(base) + ((l0 + t - a * nl) << 7));
+  }
+}
+
 struct StoreEpi1 {
   static constexpr bool kTunable = false;
   double* out0;
   __device__ bool begin() { return true; }
   __device__ bool inst(int) { return true; }
   __device__ void prepare(int) {}
+  __device__ void prefetch(int, int, int) {}
   __device__ bool fp32() const { return false; }  // KKT and step-size products: FP64 values
   __device__ void apply_direct(int r, const double* s) { out0[r] = s[0]; }
+  __device__ void apply_rows(int r0, int nr, int lane, const double (*sr)[MAX_SLOT_ROWS]) {
+    for (int r = lane; r < nr; r += LANES) {
+      out0[r0 + r] = sr[0][r];
+    }
+  }
 };
 struct StoreEpi2 {
   static constexpr bool kTunable = false;
@@ -152,10 +180,17 @@ struct StoreEpi2 {
   __device__ bool begin() { return true; }
   __device__ bool inst(int) { return true; }
   __device__ void prepare(int) {}
+  __device__ void prefetch(int, int, int) {}
   __device__ bool fp32() const { return false; }
   __device__ void apply_direct(int r, const double* s) {
     out0[r] = s[0];
     out1[r] = s[1];
+  }
+  __device__ void apply_rows(int r0, int nr, int lane, const double (*sr)[MAX_SLOT_ROWS]) {
+    for (int r = lane; r < nr; r += LANES) {
+      out0[r0 + r] = sr[0][r];
+      out1[r0 + r] = sr[1][r];
+    }
   }
 };
 
@@ -231,9 +266,15 @@ struct PrimalEpi {
   __device__ void prepare(int i) {
     if (!Single) load_inst_steps(itab, wtab, i, plan, true, q);
   }
+  __device__ void prefetch(int r0, int nr, int lane) {
+    const double* const a[5] = {c, lv, uv, x, x0};
+    prefetch_rows<5>(a, r0, nr, lane);
+  }
   __device__ bool fp32() const { return q.fp32 != 0; }
+  // anchor value x0_j is read only when used (Halpern, not a check iteration)
+  __device__ bool need_anchor() const { return q.halpern && !q.check; }
   __device__ void step(int j, double s, double cj, double lvj, double uvj, double xj,
-                       const double* x0p) {
+                       double x0j) {
     const double xhj = clampd(fma(-q.step, cj - s, xj), lvj, uvj);
     const double xb = fma(2.0, xhj, -xj);
     st_keep(xbar + j, xb);
@@ -242,13 +283,38 @@ struct PrimalEpi {
       dx[j] = xj - xhj;
     } else if (q.halpern) {
       const double r = q.gamma_one ? xb : fma(1.0 + q.gamma, xhj, -q.gamma * xj);
-      st_once(x + j, fma(q.w1, r, q.w0 * ld_once(x0p)));
+      st_once(x + j, fma(q.w1, r, q.w0 * x0j));
     } else {
       x[j] = xhj;
     }
   }
   __device__ void apply_direct(int j, const double* s) {
-    step(j, s[0], ld_once(c + j), ld_once(lv + j), ld_once(uv + j), ld_once(x + j), x0 + j);
+    step(j, s[0], ld_once(c + j), ld_once(lv + j), ld_once(uv + j), ld_once(x + j),
+         need_anchor() ? ld_once(x0 + j) : 0.0);
+  }
+  // Epilogue of a slot's rows r0 + r (r = lane + 32 k < nr): every load first, then the
+  // updates, so the loads of all rows are in flight together.
+  __device__ void apply_rows(int r0, int nr, int lane, const double (*sr)[MAX_SLOT_ROWS]) {
+    constexpr int R = MAX_SLOT_ROWS / LANES;
+    double cj[R], lj[R], uj[R], xj[R], aj[R];
+    const bool na = need_anchor();
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int r = lane + k * LANES;
+      if (r < nr) {
+        const int j = r0 + r;
+        cj[k] = ld_once(c + j);
+        lj[k] = ld_once(lv + j);
+        uj[k] = ld_once(uv + j);
+        xj[k] = ld_once(x + j);
+        aj[k] = na ? ld_once(x0 + j) : 0.0;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int r = lane + k * LANES;
+      if (r < nr) step(r0 + r, sr[0][r], cj[k], lj[k], uj[k], xj[k], aj[k]);
+    }
   }
 };
 
@@ -280,8 +346,13 @@ struct DualEpi {
   __device__ void prepare(int i) {
     if (!Single) load_inst_steps(itab, wtab, i, plan, false, q);
   }
+  __device__ void prefetch(int r0, int nr, int lane) {
+    const double* const a[4] = {lo, hi, y, y0};
+    prefetch_rows<4>(a, r0, nr, lane);
+  }
   __device__ bool fp32() const { return q.fp32 != 0; }
-  __device__ void step(int i, double s, double loi, double hii, double yi, const double* y0p) {
+  __device__ bool need_anchor() const { return q.halpern && !q.check; }
+  __device__ void step(int i, double s, double loi, double hii, double yi, double y0i) {
     const double w = fma(yi, q.inv_step, -s);
     const double d = w - clampd(w, loi, hii);
     if (q.check) {
@@ -293,13 +364,35 @@ struct DualEpi {
       } else {
         r = fma(1.0 + q.gamma, q.step * d, -q.gamma * yi);
       }
-      st_keep(y + i, fma(q.w1, r, q.w0 * ld_once(y0p)));
+      st_keep(y + i, fma(q.w1, r, q.w0 * y0i));
     } else {
       st_keep(y + i, q.step * d);
     }
   }
   __device__ void apply_direct(int i, const double* s) {
-    step(i, s[0], ld_once(lo + i), ld_once(hi + i), ld_once(y + i), y0 + i);
+    step(i, s[0], ld_once(lo + i), ld_once(hi + i), ld_once(y + i),
+         need_anchor() ? ld_once(y0 + i) : 0.0);
+  }
+  __device__ void apply_rows(int r0, int nr, int lane, const double (*sr)[MAX_SLOT_ROWS]) {
+    constexpr int R = MAX_SLOT_ROWS / LANES;
+    double lj[R], hj[R], yj[R], aj[R];
+    const bool na = need_anchor();
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int r = lane + k * LANES;
+      if (r < nr) {
+        const int i = r0 + r;
+        lj[k] = ld_once(lo + i);
+        hj[k] = ld_once(hi + i);
+        yj[k] = ld_once(y + i);
+        aj[k] = na ? ld_once(y0 + i) : 0.0;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int r = lane + k * LANES;
+      if (r < nr) step(r0 + r, sr[0][r], lj[k], hj[k], yj[k], aj[k]);
+    }
   }
 };
 
@@ -321,6 +414,25 @@ struct DualEpi {
 #ifndef DPDLP_STREAM_NOALLOC
 #define DPDLP_STREAM_NOALLOC 0
 #endif
+//   DPDLP_HOIST_SLOT     load the slot descriptor before the launch scalars are checked
+//   DPDLP_EPI_PREFETCH   prefetch the slot rows' epilogue vectors into L2 at slot start
+#ifndef DPDLP_HOIST_SLOT
+#define DPDLP_HOIST_SLOT 1
+#endif
+#ifndef DPDLP_EPI_PREFETCH
+#define DPDLP_EPI_PREFETCH 0
+#endif
+//   DPDLP_HOIST_IDX      issue the first two index batches at kernel entry
+//   DPDLP_EPI_BATCH      epilogue loads of all of a lane's rows before any update
+#ifndef DPDLP_HOIST_IDX
+#define DPDLP_HOIST_IDX 0
+#endif
+static_assert(LANE_ITEMS % DPDLP_PK_BATCH == 0 && LANE_ITEMS / DPDLP_PK_BATCH >= 2,
+              "a lane holds at least two pipeline batches (both are loaded before the sums)");
+#ifndef DPDLP_EPI_BATCH
+#define DPDLP_EPI_BATCH 1
+#endif
+
 
 template <int NV>
 struct GatherVecs {
@@ -411,23 +523,19 @@ __device__ __forceinline__ void load_idx(const uint4* ip, int b, uint32_t (&c)[B
 // sums (short rows) or to the piece array (long-row pieces).  Three-stage pipeline of
 // batches: indices two batches ahead, values and the x[col] gathers one batch ahead, so
 // gathers are in flight while the FMA chain runs.
-template <typename V, int NV>
+template <typename V, int NV, int B>
 __device__ __forceinline__ void lane_sums(const DevPacked& M, const GatherVecs<NV>& g, size_t off,
                                           int lane, int rl, int pid,
-                                          double (*srow)[MAX_SLOT_ROWS]) {
-  constexpr int B = DPDLP_PK_BATCH;
+                                          double (*srow)[MAX_SLOT_ROWS], const uint4* ip,
+                                          unsigned long long pol, uint32_t (&c0)[B],
+                                          uint32_t (&c1)[B]) {
   constexpr int NB = LANE_ITEMS / B;
   const auto* vp = Vals<V>::base(M, off, lane);
-  const uint4* ip = reinterpret_cast<const uint4*>(M.idx + off) + lane;
-  const unsigned long long pol = l2_evict_first_policy();
   double acc[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-  uint32_t c0[B], c1[B];
   V v0[B];
   double x0v[NV][B];
-  load_idx<B>(ip, 0, c0, pol);
-  if (NB > 1) load_idx<B>(ip, 1, c1, pol);
   Vals<V>::template load<B>(vp, 0, v0, pol);
 #pragma unroll
   for (int j = 0; j < B; ++j) {
@@ -489,26 +597,59 @@ __global__ void __launch_bounds__(W * LANES, (DPDLP_PK_MIN_BLOCKS * PK_WARPS) / 
     packed_spmv_kernel(DevPacked M, GatherVecs<NV> g, Epi epi_in) {
   __shared__ double srow[W][NV][MAX_SLOT_ROWS];
   Epi epi = epi_in;
-  if (!epi.begin()) return;  // uniform over the launch
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = blockIdx.x * W + w;
-  if (s >= M.nslots) return;  // uniform over the warp
-  const SlotDesc sd = M.slots[s];
-  if (!epi.inst(sd.inst)) return;  // uniform over the warp: instance scalars, or converged
-  const LaneMeta lm = M.lanes[(size_t)s * LANES + lane];
+  constexpr int B = DPDLP_PK_BATCH;
   const size_t off = (size_t)s * SLOT_ITEMS;
+  const uint4* ip = reinterpret_cast<const uint4*>(M.idx + off) + lane;
+  const unsigned long long pol = l2_evict_first_policy();
+  uint32_t c0[B], c1[B];
+#if DPDLP_HOIST_IDX
+  if (s < M.nslots) {  // the first index batches depend on the slot only
+    load_idx<B>(ip, 0, c0, pol);
+    load_idx<B>(ip, 1, c1, pol);
+  }
+#endif
+#if DPDLP_HOIST_SLOT
+  // the slot's descriptors are loaded while the launch scalars are in flight
+  SlotDesc sd{0, 0, 0, 0};
+  LaneMeta lm{0, 0};
+  if (s < M.nslots) {
+    sd = M.slots[s];
+    lm = M.lanes[(size_t)s * LANES + lane];
+  }
+  if (!epi.begin()) return;   // uniform over the launch
+  if (s >= M.nslots) return;  // uniform over the warp
+#else
+  if (!epi.begin()) return;
+  if (s >= M.nslots) return;
+  const SlotDesc sd = M.slots[s];
+  const LaneMeta lm = M.lanes[(size_t)s * LANES + lane];
+#endif
+  if (!epi.inst(sd.inst)) return;  // uniform over the warp: instance scalars, or converged
+#if DPDLP_EPI_PREFETCH
+  epi.prefetch(sd.row_base, sd.nrows, lane);
+#endif
+#if !DPDLP_HOIST_IDX
+  load_idx<B>(ip, 0, c0, pol);
+  load_idx<B>(ip, 1, c1, pol);
+#endif
   if (epi.fp32() && M.val32)  // uniform over the warp
-    lane_sums<float, NV>(M, g, off, lane, lm.row_local, lm.piece_base, srow[w]);
+    lane_sums<float, NV, B>(M, g, off, lane, lm.row_local, lm.piece_base, srow[w], ip, pol, c0, c1);
   else
-    lane_sums<double, NV>(M, g, off, lane, lm.row_local, lm.piece_base, srow[w]);
+    lane_sums<double, NV, B>(M, g, off, lane, lm.row_local, lm.piece_base, srow[w], ip, pol, c0, c1);
   __syncwarp();
   epi.prepare(sd.inst);
+#if DPDLP_EPI_BATCH
+  epi.apply_rows(sd.row_base, sd.nrows, lane, srow[w]);
+#else
   for (int r = lane; r < sd.nrows; r += LANES) {
     double v[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) v[k] = srow[w][k][r];
     epi.apply_direct(sd.row_base + r, v);
   }
+#endif
 }
 
 // Long rows: add each row's pieces, then its epilogue.  Rows come longest first: the first
