@@ -342,3 +342,52 @@ def batch_lps(seed: int = 3, count: int = 256, m_lo: int = 500, m_hi: int = 50_0
     nonzeros in total."""
     ms = batch_sizes(seed, count, m_lo, m_hi)
     return [uneven_lp(1000 * seed + i, int(mi)) for i, mi in enumerate(ms)]
+
+
+# ---------------------------------------------------------------- transportation family
+def transport_family(seed: int = 4, S: int = 300, D: int = 300, side_rows: int = 20_000,
+                     arcs_per_side: int = 10) -> dict:
+    """Shared structure of a family of transportation LPs (one matrix, perturbed b and c).
+
+    Arc (i, j) from source i to sink j is variable i * D + j, x >= 0.  Rows: S supply rows
+    sum_j x_ij <= s_i, D demand rows sum_i x_ij = d_j, and ``side_rows`` capacity rows, each
+    over ``arcs_per_side`` distinct random arcs.  Returns the base costs U(1, 100), the base
+    supplies and demands, and the side rows' arc lists."""
+    rng = np.random.default_rng(seed)
+    n = S * D
+    side = np.stack([rng.choice(n, size=arcs_per_side, replace=False) for _ in range(side_rows)]) \
+        if side_rows else np.zeros((0, arcs_per_side), np.int64)
+    return dict(S=S, D=D, n=n, side=side.astype(np.int64),
+                c_base=rng.uniform(1.0, 100.0, size=n),
+                s_base=rng.uniform(50.0, 150.0, size=S),
+                d_base=rng.uniform(50.0, 150.0, size=D))
+
+
+def transport_lp(fam: dict, seed: int) -> LP:
+    """One instance of a transportation family: costs c_base * U(0.9, 1.1) per arc, supplies
+    and demands s_base, d_base * U(0.8, 1.2), demands scaled so sum d = 0.9 sum s, and side
+    capacities cap_r = (1 + U(0, 0.5)) * sum_{arcs in r} s_i d_j / sum s, so the proportional
+    flow x_ij = s_i d_j / sum s is feasible.  The optimum is not planted (x_star etc. are
+    None)."""
+    rng = np.random.default_rng(seed)
+    S, D, n, side = fam["S"], fam["D"], fam["n"], fam["side"]
+    c = fam["c_base"] * rng.uniform(0.9, 1.1, size=n)
+    s = fam["s_base"] * rng.uniform(0.8, 1.2, size=S)
+    d = fam["d_base"] * rng.uniform(0.8, 1.2, size=D)
+    d *= 0.9 * s.sum() / d.sum()
+    src, snk = side // D, side % D
+    cap = (1.0 + rng.uniform(0.0, 0.5, size=side.shape[0])) * (s[src] * d[snk]).sum(axis=1) / s.sum()
+    R = side.shape[0]
+    m = S + D + R
+    rows = np.concatenate([np.repeat(np.arange(S), D),                       # supply rows
+                           S + np.tile(np.arange(D), S),                     # demand rows
+                           S + D + np.repeat(np.arange(R), side.shape[1])])  # side rows
+    cols = np.concatenate([np.arange(n), np.arange(n), side.reshape(-1)])
+    vals = np.ones(rows.shape[0])
+    row_ptr, col, val = _csr_from_coo(m, n, rows.astype(np.int64), cols.astype(np.int64), vals)
+    ctype = np.concatenate([np.full(S, LE), np.full(D, EQ), np.full(R, LE)]).astype(np.int8)
+    b = np.concatenate([s, d, cap])
+    lv, uv = np.zeros(n), np.full(n, np.inf)
+    lc, uc = bounds_from_types(ctype, b)
+    return LP(n, m, c, row_ptr, col, val, lc, uc, lv, uv, ctype, b, None, None, None,
+              name=f"transport_lp(S={S},D={D},R={R},seed={seed})")
