@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdpdlp.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "solver.cu", "preprocess.cpp", "packing.cpp", "noalloc.cu"]
+SOURCES = ["kernels.cu", "solver.cu", "preprocess.cpp", "packing.cpp", "noalloc.cu", "gnn.cu"]
 
 
 def _nvcc() -> str:
@@ -38,7 +38,7 @@ def _stale(target: str, deps) -> bool:
 
 def _deps():
     out = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp", ".h"))]
-    out.append(os.path.join(INCLUDE, "dpdlp.h"))
+    out += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     out.append(os.path.abspath(__file__))
     return out
 

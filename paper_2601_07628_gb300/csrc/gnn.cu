@@ -1,0 +1,758 @@
+// Warm-start network (include/dpdlp_gnn.h): forward and backward kernels and the C ABI.
+//
+// Four kinds of kernel carry the whole network:
+//   spmm_kernel       sparse aggregation over A's pattern, H = 64 features per node
+//                     (warp per row, two features per lane, sums in stored order);
+//   linear_kernel     relu(X1 W1^T + X2 W2^T + b) for 64-row tiles (BF16 weights widened
+//                     into shared memory, FP32 products and sums);
+//   linear_bwd_kernel the ReLU mask and the products with W1 and W2 for the backward pass;
+//   wgrad_kernel      weight and bias gradients dZ^T X as fixed per-block partial sums,
+//                     added in block order by reduce_partials_kernel.
+// No floating-point atomics anywhere: every result is bitwise reproducible.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/dpdlp.h"
+#include "../../include/dpdlp_gnn.h"
+
+namespace {
+
+constexpr int H = DPDLP_GNN_HIDDEN;
+constexpr int F = DPDLP_GNN_FEATURES;
+constexpr int L = DPDLP_GNN_ROUNDS;
+constexpr int TPB = 256;
+constexpr int TILE = 64;   // rows per block of the dense kernels
+constexpr int WG_BLOCKS = 304;  // blocks of the weight-gradient reductions (2 per SM)
+
+// Offsets of the parameter blocks in the flat vector (order of dpdlp_gnn.h).
+struct Layout {
+  int64_t Ev, ev, Ec, ec;
+  int64_t Uc[L], Vc[L], bc[L], Uv[L], Vv[L], bv[L];
+  int64_t wx, bx, wy, by, total;
+  Layout() {
+    int64_t o = 0;
+    auto take = [&](int64_t k) {
+      const int64_t r = o;
+      o += k;
+      return r;
+    };
+    Ev = take(H * F);
+    ev = take(H);
+    Ec = take(H * F);
+    ec = take(H);
+    for (int l = 0; l < L; ++l) {
+      Uc[l] = take(H * H);
+      Vc[l] = take(H * H);
+      bc[l] = take(H);
+      Uv[l] = take(H * H);
+      Vv[l] = take(H * H);
+      bv[l] = take(H);
+    }
+    wx = take(H);
+    bx = take(1);
+    wy = take(H);
+    by = take(1);
+    total = o;
+  }
+};
+const Layout LAY;
+
+// ---------------------------------------------------------------- kernels
+// out[r][:] (=|+=) sum_k val[k] * in[idx[k]][:] over row r's stored entries, in order.
+__global__ void __launch_bounds__(TPB) spmm_kernel(int rows, const int64_t* __restrict__ ptr,
+                                                   const int* __restrict__ idx,
+                                                   const float* __restrict__ val,
+                                                   const float* __restrict__ in, float* out,
+                                                   int accumulate) {
+  const int r = (int)((blockIdx.x * (size_t)TPB + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int64_t k = ptr[r]; k < ptr[r + 1]; ++k) {
+    const float a = val[k];
+    const float2 h = reinterpret_cast<const float2*>(in + (size_t)idx[k] * H)[lane];
+    acc.x = fmaf(a, h.x, acc.x);
+    acc.y = fmaf(a, h.y, acc.y);
+  }
+  float2* o = reinterpret_cast<float2*>(out + (size_t)r * H) + lane;
+  if (accumulate) {
+    const float2 p = *o;
+    acc.x += p.x;
+    acc.y += p.y;
+  }
+  *o = acc;
+}
+
+// Stage a 64-row tile of an N x K row-major matrix into shared memory (rows past N read 0).
+template <int K>
+__device__ __forceinline__ void stage_rows(float (*S)[K + 1], const float* X, int r0, int N) {
+  for (int e = threadIdx.x; e < TILE * K; e += TPB) {
+    const int rr = e / K, kk = e % K;
+    S[rr][kk] = (r0 + rr < N) ? X[(size_t)(r0 + rr) * K + kk] : 0.f;
+  }
+}
+
+// Stage a BF16 weight matrix W[H][K] widened to FP32.
+template <int K>
+__device__ __forceinline__ void stage_weights(float (*S)[H + 1], const __nv_bfloat16* W) {
+  for (int e = threadIdx.x; e < H * K; e += TPB) S[e / K][e % K] = __bfloat162float(W[e]);
+}
+
+// out = relu(X1 W1^T + X2 W2^T + b) on a 64-row tile; thread (rg, cg) owns rows
+// 4 rg .. 4 rg + 3 and columns 4 cg .. 4 cg + 3.
+template <int K1, bool HAS2>
+__global__ void __launch_bounds__(TPB) linear_kernel(int N, const float* __restrict__ X1,
+                                                     const __nv_bfloat16* __restrict__ W1,
+                                                     const float* __restrict__ X2,
+                                                     const __nv_bfloat16* __restrict__ W2,
+                                                     const float* __restrict__ b, float* out) {
+  __shared__ float Xs[TILE][H + 1];
+  __shared__ float Ws[H][H + 1];
+  const int r0 = blockIdx.x * TILE;
+  const int t = threadIdx.x, rg = t >> 4, cg = t & 15;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  stage_rows<K1>(reinterpret_cast<float(*)[K1 + 1]>(&Xs[0][0]), X1, r0, N);
+  stage_weights<K1>(Ws, W1);
+  __syncthreads();
+  {
+    const float(*S)[K1 + 1] = reinterpret_cast<const float(*)[K1 + 1]>(&Xs[0][0]);
+#pragma unroll 8
+    for (int k = 0; k < K1; ++k) {
+      float a[4], w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = S[rg * 4 + i][k];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[j] = Ws[cg * 4 + j][k];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
+    }
+  }
+  if (HAS2) {
+    __syncthreads();
+    stage_rows<H>(Xs, X2, r0, N);
+    stage_weights<H>(Ws, W2);
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < H; ++k) {
+      float a[4], w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = Xs[rg * 4 + i][k];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[j] = Ws[cg * 4 + j][k];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], w[j], acc[i][j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int row = r0 + rg * 4 + i;
+    if (row >= N) continue;
+    float4 v;
+    v.x = fmaxf(acc[i][0] + b[cg * 4 + 0], 0.f);
+    v.y = fmaxf(acc[i][1] + b[cg * 4 + 1], 0.f);
+    v.z = fmaxf(acc[i][2] + b[cg * 4 + 2], 0.f);
+    v.w = fmaxf(acc[i][3] + b[cg * 4 + 3], 0.f);
+    reinterpret_cast<float4*>(out + (size_t)row * H)[cg] = v;
+  }
+}
+
+// Backward of out = relu(X1 W1^T + X2 W2^T + b): dZ = dOut * [out > 0] (stored), then
+// dX1 = dZ W1 (H x H weights only) and dX2 = dZ W2 when requested.
+__device__ __forceinline__ void tile_times_w(const float (*Z)[H + 1], const float (*Ws)[H + 1],
+                                             float* dst, int r0, int N) {
+  const int t = threadIdx.x, rg = t >> 4, cg = t & 15;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 8
+  for (int o = 0; o < H; ++o) {
+    float z[4], w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) z[i] = Z[rg * 4 + i][o];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[j] = Ws[o][cg * 4 + j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(z[i], w[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int row = r0 + rg * 4 + i;
+    if (row < N)
+      reinterpret_cast<float4*>(dst + (size_t)row * H)[cg] =
+          make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+  }
+}
+
+__global__ void __launch_bounds__(TPB) linear_bwd_kernel(int N, const float* __restrict__ dOut,
+                                                         const float* __restrict__ Hout,
+                                                         const __nv_bfloat16* __restrict__ W1,
+                                                         const __nv_bfloat16* __restrict__ W2,
+                                                         float* dZ, float* dX1, float* dX2) {
+  __shared__ float Zs[TILE][H + 1];
+  __shared__ float Ws[H][H + 1];
+  const int r0 = blockIdx.x * TILE;
+  for (int e = threadIdx.x; e < TILE * H; e += TPB) {
+    const int rr = e / H, o = e % H, row = r0 + rr;
+    float z = 0.f;
+    if (row < N) {
+      const size_t g = (size_t)row * H + o;
+      z = Hout[g] > 0.f ? dOut[g] : 0.f;
+      dZ[g] = z;
+    }
+    Zs[rr][o] = z;
+  }
+  if (dX1) {
+    stage_weights<H>(Ws, W1);
+    __syncthreads();
+    tile_times_w(Zs, Ws, dX1, r0, N);
+  }
+  if (dX2) {
+    __syncthreads();
+    stage_weights<H>(Ws, W2);
+    __syncthreads();
+    tile_times_w(Zs, Ws, dX2, r0, N);
+  }
+}
+
+// partial[block][o * K + k] = sum over the block's rows r of dZ[r][o] X[r][k], and
+// partial[block][H * K + o] = sum of dZ[r][o] (bias); tiles t = block, block + grid, ...
+template <int K>
+__global__ void __launch_bounds__(TPB) wgrad_kernel(int N, const float* __restrict__ dZ,
+                                                    const float* __restrict__ X,
+                                                    float* __restrict__ partial) {
+  __shared__ float Zs[TILE][H + 1];
+  __shared__ float Xs[TILE][K + 1];
+  constexpr int PER = H * K / TPB;  // outputs per thread: 16 (K = 64) or 2 (K = 8)
+  const int t = threadIdx.x;
+  float acc[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) acc[q] = 0.f;
+  float bacc = 0.f;
+  for (int tile = blockIdx.x; tile * TILE < N; tile += gridDim.x) {
+    const int r0 = tile * TILE;
+    __syncthreads();
+    stage_rows<H>(Zs, dZ, r0, N);
+    stage_rows<K>(Xs, X, r0, N);
+    __syncthreads();
+    for (int r = 0; r < TILE; ++r) {
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int e = t * PER + q, o = e / K, k = e % K;
+        acc[q] = fmaf(Zs[r][o], Xs[r][k], acc[q]);
+      }
+      if (t < H) bacc += Zs[r][t];
+    }
+  }
+  float* p = partial + (size_t)blockIdx.x * (H * K + H);
+#pragma unroll
+  for (int q = 0; q < PER; ++q) p[t * PER + q] = acc[q];
+  if (t < H) p[H * K + t] = bacc;
+}
+
+// grad[e] += sum over blocks g (in order) of partial[g * stride + e], e < len.
+__global__ void reduce_partials_kernel(int G, int len, int stride,
+                                       const float* __restrict__ partial, float* grad) {
+  const int e = blockIdx.x * TPB + threadIdx.x;
+  if (e >= len) return;
+  float s = 0.f;
+  for (int g = 0; g < G; ++g) s += partial[(size_t)g * stride + e];
+  grad[e] += s;
+}
+
+// out[r] = Hm[r] . w + b (warp per row, fixed shuffle tree).
+__global__ void __launch_bounds__(TPB) head_kernel(int N, const float* __restrict__ Hm,
+                                                   const __nv_bfloat16* __restrict__ w,
+                                                   const float* __restrict__ b, float* out) {
+  const int r = (int)((blockIdx.x * (size_t)TPB + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= N) return;
+  const float2 h = reinterpret_cast<const float2*>(Hm + (size_t)r * H)[lane];
+  float p = fmaf(h.x, __bfloat162float(w[2 * lane]), h.y * __bfloat162float(w[2 * lane + 1]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+  if (lane == 0) out[r] = p + b[0];
+}
+
+// d[r] = 2 (out[r] - t[r]) / N, dH[r][:] = d[r] w, loss_part[block] = sum (out - t)^2 / N.
+__global__ void __launch_bounds__(TPB) head_bwd_kernel(int N, const float* __restrict__ out,
+                                                       const float* __restrict__ tgt,
+                                                       const __nv_bfloat16* __restrict__ w,
+                                                       float* __restrict__ d, float* dH,
+                                                       float* __restrict__ loss_part) {
+  __shared__ float ls[TPB / 32];
+  const int r = (int)((blockIdx.x * (size_t)TPB + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  float l = 0.f;
+  if (r < N) {
+    const float e = out[r] - tgt[r];
+    const float dr = 2.f * e / (float)N;
+    reinterpret_cast<float2*>(dH + (size_t)r * H)[lane] =
+        make_float2(dr * __bfloat162float(w[2 * lane]), dr * __bfloat162float(w[2 * lane + 1]));
+    if (lane == 0) {
+      d[r] = dr;
+      l = e * e / (float)N;
+    }
+  }
+  if (lane == 0) ls[wi] = l;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int k = 0; k < TPB / 32; ++k) s += ls[k];
+    loss_part[blockIdx.x] = s;
+  }
+}
+
+// partial[block][k] = sum over the block's rows of d[r] Hm[r][k] (k < H), [H] = sum d[r].
+__global__ void __launch_bounds__(TPB) head_wgrad_kernel(int N, const float* __restrict__ d,
+                                                         const float* __restrict__ Hm,
+                                                         float* __restrict__ partial) {
+  const int t = threadIdx.x;
+  float acc = 0.f;
+  for (int tile = blockIdx.x; tile * TILE < N; tile += gridDim.x) {
+    const int r1 = min(N, (tile + 1) * TILE);
+    for (int r = tile * TILE; r < r1; ++r) {
+      if (t < H) acc = fmaf(d[r], Hm[(size_t)r * H + t], acc);
+      else if (t == H) acc += d[r];
+    }
+  }
+  if (t <= H) partial[(size_t)blockIdx.x * (H + 1) + t] = acc;
+}
+
+__global__ void sum_parts_kernel(int G, const float* __restrict__ parts, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int g = 0; g < G; ++g) s += parts[g];
+  *out = s;
+}
+
+__global__ void adam_kernel(int64_t P, float* theta, float* grad, float* m1, float* m2,
+                            float lr, float b1, float b2, float eps, float bc1, float bc2,
+                            __nv_bfloat16* wbf) {
+  const int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
+  if (i >= P) return;
+  const float g = grad[i];
+  const float a = b1 * m1[i] + (1.f - b1) * g;
+  const float v = b2 * m2[i] + (1.f - b2) * g * g;
+  m1[i] = a;
+  m2[i] = v;
+  const float th = theta[i] - lr * (a / bc1) / (sqrtf(v / bc2) + eps);
+  theta[i] = th;
+  wbf[i] = __float2bfloat16_rn(th);
+  grad[i] = 0.f;
+}
+
+__global__ void to_bf16_kernel(int64_t P, const float* theta, __nv_bfloat16* wbf) {
+  const int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
+  if (i < P) wbf[i] = __float2bfloat16_rn(theta[i]);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- handle
+struct dpdlp_gnn {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int ptr_dev = 0;
+  int n = 0, m = 0;
+  bool graph = false, fwd_done = false;
+  std::vector<void*> allocs;  // graph-dependent buffers
+  // A (m rows): R values (row-normalised) and Ct values (A D_c^-1, for C^T in backward);
+  // A^T (n rows): C values (column-normalised) and Rt values (A^T D_r^-1, for R^T)
+  int64_t *a_ptr = nullptr, *t_ptr = nullptr;
+  int *a_idx = nullptr, *t_idx = nullptr;
+  float *a_R = nullptr, *a_Ct = nullptr, *t_C = nullptr, *t_Rt = nullptr;
+  float *Fv = nullptr, *Fc = nullptr, *tx = nullptr, *ty = nullptr;
+  float* hv[L + 1] = {};
+  float* hc[L + 1] = {};
+  float* gv[L] = {};
+  float* gc[L] = {};
+  float *xhat = nullptr, *yhat = nullptr;
+  float *dhv[2] = {}, *dhc[2] = {}, *dzv = nullptr, *dzc = nullptr, *dgv = nullptr, *dgc = nullptr;
+  float *dx = nullptr, *dy = nullptr, *loss_part = nullptr;
+  double* loss_d = nullptr;
+  // parameters (graph-independent)
+  float *theta = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr, *partial = nullptr;
+  __nv_bfloat16* wbf = nullptr;
+};
+
+namespace {
+
+int gfail(dpdlp_gnn* g, int code, const std::string& msg) {
+  if (g) g->err = msg;
+  return code;
+}
+
+#define GCK(call)                                                                    \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return gfail(g, e_ == cudaErrorMemoryAllocation ? DPDLP_ERR_OOM : DPDLP_ERR_CUDA, \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));              \
+  } while (0)
+
+template <class T>
+int galloc(dpdlp_gnn* g, T** p, size_t count) {
+  *p = nullptr;
+  cudaError_t e = cudaMalloc((void**)p, (count > 0 ? count : 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return gfail(g, DPDLP_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  g->allocs.push_back(*p);
+  return 0;
+}
+
+void free_graph_buffers(dpdlp_gnn* g) {
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  for (void* p : g->allocs) cudaFree(p);
+  g->allocs.clear();
+  g->graph = false;
+  g->fwd_done = false;
+}
+
+int blocks_for_rows(int rows) { return (rows + TILE - 1) / TILE; }
+int warp_blocks(int rows) { return (int)(((size_t)rows * 32 + TPB - 1) / TPB); }
+int wg_grid(int rows) {
+  const int b = blocks_for_rows(rows);
+  return b < WG_BLOCKS ? (b > 0 ? b : 1) : WG_BLOCKS;
+}
+
+cudaMemcpyKind in_kind(const dpdlp_gnn* g) {
+  return g->ptr_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+cudaMemcpyKind out_kind(const dpdlp_gnn* g) {
+  return g->ptr_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+// weight gradient of one layer: grad[off .. off + H*K) += dZ^T X and, with_bias, the next
+// H entries (the bias that follows the weight in the parameter order) += column sums of dZ
+template <int K>
+int add_wgrad(dpdlp_gnn* g, int N, const float* dZ, const float* X, int64_t off,
+              bool with_bias) {
+  const int G = wg_grid(N);
+  const int stride = H * K + H;
+  const int len = with_bias ? stride : H * K;
+  wgrad_kernel<K><<<G, TPB, 0, g->stream>>>(N, dZ, X, g->partial);
+  reduce_partials_kernel<<<(len + TPB - 1) / TPB, TPB, 0, g->stream>>>(G, len, stride, g->partial,
+                                                                        g->grad + off);
+  GCK(cudaGetLastError());
+  return 0;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+int64_t dpdlp_gnn_param_count(void) { return LAY.total; }
+
+int dpdlp_gnn_create(dpdlp_gnn_t** out, int device) {
+  if (!out) return DPDLP_ERR_INVALID;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+    return DPDLP_ERR_INVALID;
+  dpdlp_gnn* g = new (std::nothrow) dpdlp_gnn();
+  if (!g) return DPDLP_ERR_OOM;
+  g->device = device;
+  const size_t P = (size_t)LAY.total;
+  const size_t part = (size_t)WG_BLOCKS * (H * H + H);
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&g->theta, P * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&g->grad, P * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&g->m1, P * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&g->m2, P * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&g->wbf, P * sizeof(__nv_bfloat16)) != cudaSuccess ||
+      cudaMalloc(&g->partial, part * sizeof(float)) != cudaSuccess) {
+    dpdlp_gnn_destroy(g);
+    return DPDLP_ERR_CUDA;
+  }
+  cudaMemset(g->theta, 0, P * sizeof(float));
+  cudaMemset(g->grad, 0, P * sizeof(float));
+  cudaMemset(g->m1, 0, P * sizeof(float));
+  cudaMemset(g->m2, 0, P * sizeof(float));
+  cudaMemset(g->wbf, 0, P * sizeof(__nv_bfloat16));
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    dpdlp_gnn_destroy(g);
+    return DPDLP_ERR_CUDA;
+  }
+  *out = g;
+  return 0;
+}
+
+void dpdlp_gnn_destroy(dpdlp_gnn_t* g) {
+  if (!g) return;
+  cudaSetDevice(g->device);
+  free_graph_buffers(g);
+  void* ps[] = {g->theta, g->grad, g->m1, g->m2, g->wbf, g->partial};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  if (g->stream) cudaStreamDestroy(g->stream);
+  delete g;
+}
+
+const char* dpdlp_gnn_last_error(const dpdlp_gnn_t* g) { return g ? g->err.c_str() : "null handle"; }
+
+int dpdlp_gnn_set_ptr_mode(dpdlp_gnn_t* g, int device) {
+  if (!g || (device != 0 && device != 1)) return DPDLP_ERR_INVALID;
+  g->ptr_dev = device;
+  return 0;
+}
+
+int dpdlp_gnn_set_params(dpdlp_gnn_t* g, const float* params, int64_t count) {
+  if (!g || !params || count != LAY.total) return gfail(g, DPDLP_ERR_INVALID, "params: count must be dpdlp_gnn_param_count()");
+  GCK(cudaSetDevice(g->device));
+  const size_t P = (size_t)LAY.total;
+  GCK(cudaMemcpyAsync(g->theta, params, P * sizeof(float), cudaMemcpyHostToDevice, g->stream));
+  GCK(cudaMemsetAsync(g->grad, 0, P * sizeof(float), g->stream));
+  GCK(cudaMemsetAsync(g->m1, 0, P * sizeof(float), g->stream));
+  GCK(cudaMemsetAsync(g->m2, 0, P * sizeof(float), g->stream));
+  to_bf16_kernel<<<(unsigned)((P + TPB - 1) / TPB), TPB, 0, g->stream>>>((int64_t)P, g->theta, g->wbf);
+  GCK(cudaGetLastError());
+  GCK(cudaStreamSynchronize(g->stream));
+  return 0;
+}
+
+int dpdlp_gnn_get_params(dpdlp_gnn_t* g, float* params, int64_t count) {
+  if (!g || !params || count != LAY.total) return gfail(g, DPDLP_ERR_INVALID, "params: count must be dpdlp_gnn_param_count()");
+  GCK(cudaSetDevice(g->device));
+  GCK(cudaMemcpyAsync(params, g->theta, (size_t)count * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+  GCK(cudaStreamSynchronize(g->stream));
+  return 0;
+}
+
+int dpdlp_gnn_get_grads(dpdlp_gnn_t* g, float* grads, int64_t count) {
+  if (!g || !grads || count != LAY.total) return gfail(g, DPDLP_ERR_INVALID, "grads: count must be dpdlp_gnn_param_count()");
+  GCK(cudaSetDevice(g->device));
+  GCK(cudaMemcpyAsync(grads, g->grad, (size_t)count * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+  GCK(cudaStreamSynchronize(g->stream));
+  return 0;
+}
+
+int dpdlp_gnn_zero_grads(dpdlp_gnn_t* g) {
+  if (!g) return DPDLP_ERR_INVALID;
+  GCK(cudaSetDevice(g->device));
+  GCK(cudaMemsetAsync(g->grad, 0, (size_t)LAY.total * sizeof(float), g->stream));
+  GCK(cudaStreamSynchronize(g->stream));
+  return 0;
+}
+
+int dpdlp_gnn_set_graph(dpdlp_gnn_t* g, int32_t n, int32_t m, const int64_t* row_ptr,
+                        const int32_t* col_idx, const double* val) {
+  if (!g || n < 0 || m < 0 || !row_ptr) return gfail(g, DPDLP_ERR_INVALID, "graph: invalid arguments");
+  const int64_t nnz = row_ptr[m];
+  if (row_ptr[0] != 0 || nnz < 0 || (nnz > 0 && (!col_idx || !val)) || nnz > (int64_t)1 << 31)
+    return gfail(g, DPDLP_ERR_INVALID, "graph: invalid row pointers");
+  for (int i = 0; i < m; ++i)
+    if (row_ptr[i + 1] < row_ptr[i]) return gfail(g, DPDLP_ERR_INVALID, "graph: row pointers decrease");
+  for (int64_t k = 0; k < nnz; ++k)
+    if (col_idx[k] < 0 || col_idx[k] >= n || !std::isfinite(val[k]))
+      return gfail(g, DPDLP_ERR_INVALID, "graph: column index out of range or non-finite value");
+  GCK(cudaSetDevice(g->device));
+  free_graph_buffers(g);
+  g->n = n;
+  g->m = m;
+  // row and column sums of |A|, then the four value arrays
+  std::vector<double> rs(m, 0.0), cs(n, 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+      rs[i] += std::fabs(val[k]);
+      cs[col_idx[k]] += std::fabs(val[k]);
+    }
+  for (auto& v : rs) v = v > 1.0 ? v : 1.0;
+  for (auto& v : cs) v = v > 1.0 ? v : 1.0;
+  std::vector<float> aR(nnz), aCt(nnz);
+  for (int i = 0; i < m; ++i)
+    for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+      aR[k] = (float)(val[k] / rs[i]);
+      aCt[k] = (float)(val[k] / cs[col_idx[k]]);
+    }
+  // A^T by a stable counting sort (entries of a column in row order)
+  std::vector<int64_t> tptr(n + 1, 0);
+  for (int64_t k = 0; k < nnz; ++k) ++tptr[col_idx[k] + 1];
+  for (int j = 0; j < n; ++j) tptr[j + 1] += tptr[j];
+  std::vector<int32_t> tidx(nnz);
+  std::vector<float> tC(nnz), tRt(nnz);
+  {
+    std::vector<int64_t> pos(tptr.begin(), tptr.end() - 1);
+    for (int i = 0; i < m; ++i)
+      for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+        const int j = col_idx[k];
+        const int64_t q = pos[j]++;
+        tidx[q] = i;
+        tC[q] = (float)(val[k] / cs[j]);
+        tRt[q] = (float)(val[k] / rs[i]);
+      }
+  }
+  int rc;
+  const size_t nH = (size_t)n * H, mH = (size_t)m * H;
+  if ((rc = galloc(g, &g->a_ptr, m + 1)) || (rc = galloc(g, &g->t_ptr, n + 1)) ||
+      (rc = galloc(g, &g->a_idx, nnz)) || (rc = galloc(g, &g->t_idx, nnz)) ||
+      (rc = galloc(g, &g->a_R, nnz)) || (rc = galloc(g, &g->a_Ct, nnz)) ||
+      (rc = galloc(g, &g->t_C, nnz)) || (rc = galloc(g, &g->t_Rt, nnz)))
+    return rc;
+  for (int l = 0; l <= L; ++l)
+    if ((rc = galloc(g, &g->hv[l], nH)) || (rc = galloc(g, &g->hc[l], mH))) return rc;
+  for (int l = 0; l < L; ++l)
+    if ((rc = galloc(g, &g->gv[l], nH)) || (rc = galloc(g, &g->gc[l], mH))) return rc;
+  if ((rc = galloc(g, &g->dhv[0], nH)) || (rc = galloc(g, &g->dhv[1], nH)) ||
+      (rc = galloc(g, &g->dhc[0], mH)) || (rc = galloc(g, &g->dhc[1], mH)) ||
+      (rc = galloc(g, &g->dzv, nH)) || (rc = galloc(g, &g->dzc, mH)) ||
+      (rc = galloc(g, &g->dgv, nH)) || (rc = galloc(g, &g->dgc, mH)) ||
+      (rc = galloc(g, &g->xhat, n)) || (rc = galloc(g, &g->yhat, m)) ||
+      (rc = galloc(g, &g->dx, n)) || (rc = galloc(g, &g->dy, m)) ||
+      (rc = galloc(g, &g->tx, n)) || (rc = galloc(g, &g->ty, m)) ||
+      (rc = galloc(g, &g->Fv, (size_t)n * F)) || (rc = galloc(g, &g->Fc, (size_t)m * F)) ||
+      (rc = galloc(g, &g->loss_part, warp_blocks(n) + warp_blocks(m) + 1)) ||
+      (rc = galloc(g, &g->loss_d, 1)))
+    return rc;
+  auto up = [&](void* d, const void* h, size_t bytes) {
+    return bytes ? cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+  };
+  GCK(up(g->a_ptr, row_ptr, (m + 1) * sizeof(int64_t)));
+  GCK(up(g->t_ptr, tptr.data(), (n + 1) * sizeof(int64_t)));
+  GCK(up(g->a_idx, col_idx, nnz * sizeof(int32_t)));
+  GCK(up(g->t_idx, tidx.data(), nnz * sizeof(int32_t)));
+  GCK(up(g->a_R, aR.data(), nnz * sizeof(float)));
+  GCK(up(g->a_Ct, aCt.data(), nnz * sizeof(float)));
+  GCK(up(g->t_C, tC.data(), nnz * sizeof(float)));
+  GCK(up(g->t_Rt, tRt.data(), nnz * sizeof(float)));
+  g->graph = true;
+  return 0;
+}
+
+int dpdlp_gnn_set_features(dpdlp_gnn_t* g, const float* fv, const float* fc) {
+  if (!g || (g->n && !fv) || (g->m && !fc)) return gfail(g, DPDLP_ERR_INVALID, "features: NULL array");
+  if (!g->graph) return gfail(g, DPDLP_ERR_NOT_LOADED, "no graph set");
+  GCK(cudaSetDevice(g->device));
+  if (g->n) GCK(cudaMemcpyAsync(g->Fv, fv, (size_t)g->n * F * sizeof(float), in_kind(g), g->stream));
+  if (g->m) GCK(cudaMemcpyAsync(g->Fc, fc, (size_t)g->m * F * sizeof(float), in_kind(g), g->stream));
+  g->fwd_done = false;
+  return 0;
+}
+
+int dpdlp_gnn_forward(dpdlp_gnn_t* g, float* x_hat, float* y_hat) {
+  if (!g) return DPDLP_ERR_INVALID;
+  if (!g->graph) return gfail(g, DPDLP_ERR_NOT_LOADED, "no graph set");
+  GCK(cudaSetDevice(g->device));
+  const int n = g->n, m = g->m;
+  cudaStream_t s = g->stream;
+  const float* th = g->theta;
+  const __nv_bfloat16* w = g->wbf;
+  if (n) linear_kernel<F, false><<<blocks_for_rows(n), TPB, 0, s>>>(n, g->Fv, w + LAY.Ev, nullptr, nullptr, th + LAY.ev, g->hv[0]);
+  if (m) linear_kernel<F, false><<<blocks_for_rows(m), TPB, 0, s>>>(m, g->Fc, w + LAY.Ec, nullptr, nullptr, th + LAY.ec, g->hc[0]);
+  for (int l = 0; l < L; ++l) {
+    if (m) {
+      spmm_kernel<<<warp_blocks(m), TPB, 0, s>>>(m, g->a_ptr, g->a_idx, g->a_R, g->hv[l], g->gc[l], 0);
+      linear_kernel<H, true><<<blocks_for_rows(m), TPB, 0, s>>>(m, g->hc[l], w + LAY.Uc[l], g->gc[l], w + LAY.Vc[l], th + LAY.bc[l], g->hc[l + 1]);
+    }
+    if (n) {
+      spmm_kernel<<<warp_blocks(n), TPB, 0, s>>>(n, g->t_ptr, g->t_idx, g->t_C, g->hc[l + 1], g->gv[l], 0);
+      linear_kernel<H, true><<<blocks_for_rows(n), TPB, 0, s>>>(n, g->hv[l], w + LAY.Uv[l], g->gv[l], w + LAY.Vv[l], th + LAY.bv[l], g->hv[l + 1]);
+    }
+  }
+  if (n) head_kernel<<<warp_blocks(n), TPB, 0, s>>>(n, g->hv[L], w + LAY.wx, th + LAY.bx, g->xhat);
+  if (m) head_kernel<<<warp_blocks(m), TPB, 0, s>>>(m, g->hc[L], w + LAY.wy, th + LAY.by, g->yhat);
+  GCK(cudaGetLastError());
+  if (x_hat && n) GCK(cudaMemcpyAsync(x_hat, g->xhat, n * sizeof(float), out_kind(g), s));
+  if (y_hat && m) GCK(cudaMemcpyAsync(y_hat, g->yhat, m * sizeof(float), out_kind(g), s));
+  GCK(cudaStreamSynchronize(s));
+  g->fwd_done = true;
+  return 0;
+}
+
+int dpdlp_gnn_backward(dpdlp_gnn_t* g, const float* tx, const float* ty, double* loss) {
+  if (!g || (g->n && !tx) || (g->m && !ty)) return gfail(g, DPDLP_ERR_INVALID, "backward: NULL target");
+  if (!g->graph || !g->fwd_done) return gfail(g, DPDLP_ERR_INVALID, "backward needs a forward pass first");
+  GCK(cudaSetDevice(g->device));
+  const int n = g->n, m = g->m;
+  cudaStream_t s = g->stream;
+  const __nv_bfloat16* w = g->wbf;
+  if (n) GCK(cudaMemcpyAsync(g->tx, tx, n * sizeof(float), in_kind(g), s));
+  if (m) GCK(cudaMemcpyAsync(g->ty, ty, m * sizeof(float), in_kind(g), s));
+  int cv = 0, cc = 0;  // dhv[cv], dhc[cc]: gradients of the current hv, hc (the heads write all rows)
+  const int gx = n ? warp_blocks(n) : 0, gy = m ? warp_blocks(m) : 0;
+  if (n) {
+    head_bwd_kernel<<<gx, TPB, 0, s>>>(n, g->xhat, g->tx, w + LAY.wx, g->dx, g->dhv[0], g->loss_part);
+    const int G = wg_grid(n);
+    head_wgrad_kernel<<<G, TPB, 0, s>>>(n, g->dx, g->hv[L], g->partial);
+    reduce_partials_kernel<<<1, TPB, 0, s>>>(G, H + 1, H + 1, g->partial, g->grad + LAY.wx);
+  }
+  if (m) {
+    head_bwd_kernel<<<gy, TPB, 0, s>>>(m, g->yhat, g->ty, w + LAY.wy, g->dy, g->dhc[0], g->loss_part + gx);
+    const int G = wg_grid(m);
+    head_wgrad_kernel<<<G, TPB, 0, s>>>(m, g->dy, g->hc[L], g->partial);
+    reduce_partials_kernel<<<1, TPB, 0, s>>>(G, H + 1, H + 1, g->partial, g->grad + LAY.wy);
+  }
+  sum_parts_kernel<<<1, 32, 0, s>>>(gx + gy, g->loss_part, g->loss_d);
+  int rc;
+  for (int l = L - 1; l >= 0; --l) {
+    // variable update of round l: hv[l+1] = relu(hv[l] Uv^T + gv[l] Vv^T + bv), gv = C hc[l+1]
+    if (n) {
+      linear_bwd_kernel<<<blocks_for_rows(n), TPB, 0, s>>>(n, g->dhv[cv], g->hv[l + 1], w + LAY.Uv[l], w + LAY.Vv[l], g->dzv, g->dhv[1 - cv], g->dgv);
+      if ((rc = add_wgrad<H>(g, n, g->dzv, g->hv[l], LAY.Uv[l], false))) return rc;
+      if ((rc = add_wgrad<H>(g, n, g->dzv, g->gv[l], LAY.Vv[l], true))) return rc;
+      if (m) spmm_kernel<<<warp_blocks(m), TPB, 0, s>>>(m, g->a_ptr, g->a_idx, g->a_Ct, g->dgv, g->dhc[cc], 1);
+      cv = 1 - cv;
+    }
+    // constraint update of round l: hc[l+1] = relu(hc[l] Uc^T + gc[l] Vc^T + bc), gc = R hv[l]
+    if (m) {
+      linear_bwd_kernel<<<blocks_for_rows(m), TPB, 0, s>>>(m, g->dhc[cc], g->hc[l + 1], w + LAY.Uc[l], w + LAY.Vc[l], g->dzc, g->dhc[1 - cc], g->dgc);
+      if ((rc = add_wgrad<H>(g, m, g->dzc, g->hc[l], LAY.Uc[l], false))) return rc;
+      if ((rc = add_wgrad<H>(g, m, g->dzc, g->gc[l], LAY.Vc[l], true))) return rc;
+      if (n) spmm_kernel<<<warp_blocks(n), TPB, 0, s>>>(n, g->t_ptr, g->t_idx, g->t_Rt, g->dgc, g->dhv[cv], 1);
+      cc = 1 - cc;
+    }
+  }
+  if (n) {
+    linear_bwd_kernel<<<blocks_for_rows(n), TPB, 0, s>>>(n, g->dhv[cv], g->hv[0], nullptr, nullptr, g->dzv, nullptr, nullptr);
+    if ((rc = add_wgrad<F>(g, n, g->dzv, g->Fv, LAY.Ev, true))) return rc;
+  }
+  if (m) {
+    linear_bwd_kernel<<<blocks_for_rows(m), TPB, 0, s>>>(m, g->dhc[cc], g->hc[0], nullptr, nullptr, g->dzc, nullptr, nullptr);
+    if ((rc = add_wgrad<F>(g, m, g->dzc, g->Fc, LAY.Ec, true))) return rc;
+  }
+  GCK(cudaGetLastError());
+  double lv = 0.0;
+  GCK(cudaMemcpyAsync(&lv, g->loss_d, sizeof(double), cudaMemcpyDeviceToHost, s));
+  GCK(cudaStreamSynchronize(s));
+  if (loss) *loss = lv;
+  return 0;
+}
+
+int dpdlp_gnn_adam(dpdlp_gnn_t* g, double lr, double beta1, double beta2, double eps,
+                   int64_t step) {
+  if (!g || step < 1 || !(lr >= 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) ||
+      !(eps > 0))
+    return gfail(g, DPDLP_ERR_INVALID, "adam: invalid hyper-parameters");
+  GCK(cudaSetDevice(g->device));
+  const int64_t P = LAY.total;
+  const float bc1 = (float)(1.0 - std::pow(beta1, (double)step));
+  const float bc2 = (float)(1.0 - std::pow(beta2, (double)step));
+  adam_kernel<<<(unsigned)((P + TPB - 1) / TPB), TPB, 0, g->stream>>>(
+      P, g->theta, g->grad, g->m1, g->m2, (float)lr, (float)beta1, (float)beta2, (float)eps, bc1,
+      bc2, g->wbf);
+  GCK(cudaGetLastError());
+  GCK(cudaStreamSynchronize(g->stream));
+  return 0;
+}
+
+}  // extern "C"

@@ -6,13 +6,16 @@ import subprocess
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "dpdlp.h")
+HEADERS = [os.path.join(ROOT, "include", f) for f in ("dpdlp.h", "dpdlp_gnn.h")]
 
 
 def declared_symbols():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(dpdlp_[a-z_A-Z0-9]+)\s*\(", text)))
+    out = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        out |= set(re.findall(r"\b(dpdlp_[a-z_A-Z0-9]+)\s*\(", text))
+    return sorted(out)
 
 
 @pytest.fixture(scope="module")
@@ -37,9 +40,19 @@ def test_library_exports_every_declared_symbol(lib):
     exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
     missing = [s for s in declared_symbols() if s not in exported]
     assert not missing, missing
+    from paper_2601_07628_gb300 import gnn
+
     for s in declared_symbols():
         assert hasattr(lib, s)
-        assert s in dpdlp.EXPORTS, f"binding lacks a signature for {s}"
+        assert s in dpdlp.EXPORTS or s in gnn.EXPORTS, f"binding lacks a signature for {s}"
+
+
+def test_gnn_param_count_matches_reference_layout(lib):
+    from oracle import gnn as G
+    from paper_2601_07628_gb300 import gnn
+
+    assert gnn.param_count() == G.param_count()
+    assert gnn.init_params(0).shape == (G.param_count(),)
 
 
 def test_struct_layouts_match_header(lib):

@@ -1,0 +1,163 @@
+"""Warm-start network on the GPU against the FP64 reference (oracle/gnn.py).
+
+The GPU runs BF16 weights with FP32 activations and sums; the reference gets the same BF16
+values (as float64), so the two differ only by FP32 rounding: forward outputs agree to
+1e-4 and gradients to 1e-3 (relative 2-norm per parameter block).  Then the network is
+trained on solver solutions of a small transportation family, and its warm start must
+save PDHG iterations on held-out instances.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import lpgen
+from oracle import gnn as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="session")
+def mods():
+    from paper_2601_07628_gb300 import build, dpdlp, gnn
+
+    build()
+    return dpdlp, gnn
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def random_case(seed, n=300, m=120):
+    rng = np.random.default_rng(seed)
+    A = sp.random(m, n, density=0.03, random_state=np.random.RandomState(seed),
+                  data_rvs=lambda k: rng.uniform(0.2, 3.0, k) * rng.choice([-1, 1], k)).tocsr()
+    A = A.tolil()
+    A[5, :] = 0      # an empty row
+    A[:, 7] = 0      # an empty column
+    A = A.tocsr()
+    A.eliminate_zeros()
+    A.sort_indices()
+    Fv = rng.standard_normal((n, G.F)).astype(np.float32)
+    Fc = rng.standard_normal((m, G.F)).astype(np.float32)
+    tx = rng.standard_normal(n).astype(np.float32)
+    ty = rng.standard_normal(m).astype(np.float32)
+    return A, Fv, Fc, tx, ty
+
+
+def theta_for(seed, gnn):
+    t = gnn.init_params(seed).astype(np.float64)
+    P = G.unpack(t)
+    rng = np.random.default_rng(seed + 7)
+    for k in P:  # non-trivial biases
+        if not G.is_weight(k):
+            P[k] = np.asarray(P[k]) + 0.05 * rng.standard_normal(np.shape(P[k]))
+    return G.pack(P).astype(np.float32)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_forward_and_gradients_match_reference(mods, seed):
+    dpdlp, gnn = mods
+    A, Fv, Fc, tx, ty = random_case(seed)
+    n, m = A.shape[1], A.shape[0]
+    th = theta_for(seed, gnn)
+    net = gnn.Network()
+    net.set_params(th)
+    net.set_graph(n, m, A.indptr, A.indices, A.data)
+    net.set_features(Fv, Fc)
+    xh, yh = net.forward()
+    loss = net.backward(tx, ty)
+    g = net.grads().astype(np.float64)
+    thr = G.round_weights_bf16(th)
+    R, Cm = G.aggregation(n, m, A.indptr, A.indices, A.data)
+    xr, yr, _ = G.forward(thr, R, Cm, Fv.astype(np.float64), Fc.astype(np.float64))
+    lr, gr = G.backward(thr, R, Cm, Fv.astype(np.float64), Fc.astype(np.float64),
+                        tx.astype(np.float64), ty.astype(np.float64))
+    assert rel(xh, xr) < 1e-4 and rel(yh, yr) < 1e-4
+    assert loss == pytest.approx(lr, rel=1e-4)
+    o = 0
+    for name, shape in G.param_layout():
+        k = int(np.prod(shape))
+        gb, rb = g[o:o + k], gr[o:o + k]
+        if np.linalg.norm(rb) > 1e-8:
+            assert rel(gb, rb) < 1e-3, name
+        o += k
+    net.close()
+
+
+def test_backward_is_deterministic_and_accumulates(mods):
+    dpdlp, gnn = mods
+    A, Fv, Fc, tx, ty = random_case(3)
+    net = gnn.Network()
+    net.set_params(theta_for(3, gnn))
+    net.set_graph(A.shape[1], A.shape[0], A.indptr, A.indices, A.data)
+    net.set_features(Fv, Fc)
+    net.forward()
+    net.backward(tx, ty)
+    g1 = net.grads()
+    net.zero_grads()
+    net.forward()
+    net.backward(tx, ty)
+    g2 = net.grads()
+    assert np.array_equal(g1, g2)
+    net.backward(tx, ty)  # a second backward adds the same gradient
+    assert np.allclose(net.grads(), 2 * g1, rtol=1e-6, atol=0)
+    net.adam(1e-3, 1)
+    assert not np.any(net.grads())  # the step zeroes the gradient
+    net.close()
+
+
+def test_invalid_inputs(mods):
+    dpdlp, gnn = mods
+    net = gnn.Network()
+    with pytest.raises(dpdlp.DpdlpError):
+        net.forward()  # no graph
+    with pytest.raises(dpdlp.DpdlpError):
+        net.set_graph(3, 2, np.array([0, 1, 2]), np.array([0, 5]), np.array([1.0, 1.0]))
+    net.set_graph(3, 2, np.array([0, 1, 2]), np.array([0, 2]), np.array([1.0, 1.0]))
+    with pytest.raises(dpdlp.DpdlpError):
+        net.backward(np.zeros(3), np.zeros(2))  # no forward pass yet
+    with pytest.raises(ValueError):
+        net.set_params(np.zeros(5))
+    net.close()
+
+
+def solve_batch(dpdlp, lps, tol, starts=None):
+    s = dpdlp.Solver()
+    s.load_batch(lps)
+    if starts is not None:
+        s.set_start(np.concatenate([x for x, _ in starts]), np.concatenate([y for _, y in starts]))
+    st = s.solve(tol, 400_000)
+    x, y = s.solution()
+    kk = s.batch_kkt()
+    s.close()
+    return st, s.split(x, y), [k["iterations"] for k in kk]
+
+
+def test_training_and_warm_start_on_small_family(mods):
+    """A 30 x 30 transportation family with 200 side rows: train on 96 solver solutions,
+    then warm-start 16 held-out instances; the warm starts need fewer iterations to 1e-6."""
+    dpdlp, gnn = mods
+    fam = lpgen.transport_family(seed=11, S=30, D=30, side_rows=200, arcs_per_side=10)
+    train_lps = [lpgen.transport_lp(fam, 100 + i) for i in range(96)]
+    test_lps = [lpgen.transport_lp(fam, 5000 + i) for i in range(16)]
+    st, sols, _ = solve_batch(dpdlp, train_lps, 1e-6)
+    assert st == 0
+    xs, ys = [x for x, _ in sols], [y for _, y in sols]
+    sc = gnn.fit_scales(train_lps, xs, ys)
+    net = gnn.Network()
+    net.set_params(gnn.init_params(0))
+    lp0 = train_lps[0]
+    net.set_graph(lp0.n, lp0.m, lp0.row_ptr, lp0.col, lp0.val)
+    data = []
+    for lp, x, y in zip(train_lps, xs, ys):
+        fv, fc = gnn.features(lp, sc)
+        data.append((fv, fc, (x / sc.x_scale).astype(np.float32), (y / sc.y_scale).astype(np.float32)))
+    hist = gnn.train(net, data, epochs=30, lr=2e-3)
+    assert hist[-1] < 0.5 * hist[0]
+    starts = [gnn.predict(net, lp, sc) for lp in test_lps]
+    _, _, cold = solve_batch(dpdlp, test_lps, 1e-6)
+    stw, _, warm = solve_batch(dpdlp, test_lps, 1e-6, starts)
+    assert stw == 0
+    assert np.median(warm) < np.median(cold), (warm, cold)
+    net.close()
