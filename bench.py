@@ -55,6 +55,12 @@ def parse():
                    help="skip the batched form (256 uneven LPs solved together vs one by one)")
     p.add_argument("--batch-count", type=int, default=256)
     p.add_argument("--batch-tol", type=float, default=1e-4)
+    p.add_argument("--no-warm-start", action="store_true",
+                   help="skip the learned warm start (train on solver solutions, warm vs cold)")
+    p.add_argument("--x3-full", action="store_true",
+                   help="learned warm start on the full transportation family (300 x 300 arcs, "
+                        "20,000 side rows; 2,000 training and 200 test instances) instead of "
+                        "the 100 x 100 one; several minutes")
     p.add_argument("--host-loop", action="store_true",
                    help="launch the iteration kernels from a host loop instead of the CUDA graph "
                         "(same kernels; for profilers that do not descend into graph loops)")
@@ -359,6 +365,96 @@ def run_batch(args, dev, stream, peak):
     }
 
 
+def run_warm_start(args, dev, stream):
+    """Learned warm start: solve a family of transportation LPs (shared A, perturbed b and
+    c) with the plain solver, train the network on those solutions with the library's own
+    kernels, then solve held-out instances from zero and from the network's prediction.
+    Solves run batched (every instance with its own restarts and status); the warm time
+    includes the network's inference."""
+    import numpy as np
+    import torch
+
+    import lpgen
+    from paper_2601_07628_gb300 import gnn
+    from paper_2601_07628_gb300.dpdlp import Solver
+
+    if args.x3_full:
+        fam = lpgen.transport_family(seed=4)
+        ntrain, ntest, tol_train, epochs, chunk = 2000, 200, 1e-4, 8, 250
+    else:
+        fam = lpgen.transport_family(seed=12, S=100, D=100, side_rows=2000, arcs_per_side=10)
+        ntrain, ntest, tol_train, epochs, chunk = 256, 32, 1e-6, 30, 256
+
+    def solve(lps, tol, starts=None):
+        s = Solver(dev)
+        s.set_stream(stream)
+        s.load_batch(lps)
+        if starts is not None:
+            s.set_start(np.concatenate([x for x, _ in starts]), np.concatenate([y for _, y in starts]))
+        s.solve(tol, 64)  # power iteration and graph capture, untimed
+        s.set_param("resume", 0)
+        if starts is not None:
+            s.set_start(np.concatenate([x for x, _ in starts]), np.concatenate([y for _, y in starts]))
+        t0 = time.perf_counter()
+        st = s.solve(tol, 2_000_000)
+        dt = time.perf_counter() - t0
+        x, y = s.solution()
+        its = [k["iterations"] for k in s.batch_kkt()]
+        parts = s.split(x, y)
+        s.close()
+        return st, dt, parts, its
+
+    t0 = time.perf_counter()
+    train = [lpgen.transport_lp(fam, 100 + i) for i in range(ntrain)]
+    test = [lpgen.transport_lp(fam, 1_000_000 + i) for i in range(ntest)]
+    xs, ys, data_s = [], [], 0.0
+    for a in range(0, ntrain, chunk):
+        st, dt, parts, _ = solve(train[a:a + chunk], tol_train)
+        data_s += dt
+        xs += [x.copy() for x, _ in parts]
+        ys += [y.copy() for _, y in parts]
+    gen_s = time.perf_counter() - t0
+    sc = gnn.fit_scales(train, xs, ys)
+    net = gnn.Network(dev)
+    net.set_params(gnn.init_params(0))
+    net.set_graph(train[0].n, train[0].m, train[0].row_ptr, train[0].col, train[0].val)
+    net.device_arrays(True)
+    data = []
+    for lp, x, y in zip(train, xs, ys):
+        fv, fc = gnn.features(lp, sc)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(f"cuda:{dev}")
+        data.append((t(fv), t(fc), t(x / sc.x_scale), t(y / sc.y_scale)))
+    del xs, ys
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = gnn.train(net, data, epochs=epochs, lr=2e-3)
+    train_s = time.perf_counter() - t0
+    steps = epochs * ntrain
+    del data
+    t0 = time.perf_counter()
+    starts = [gnn.predict(net, lp, sc) for lp in test]
+    infer_s = time.perf_counter() - t0
+    net.close()
+    out = {"family": f"transportation {fam['S']} x {fam['D']} arcs + {fam['side'].shape[0]} side rows "
+                     f"(n={train[0].n:,}, m={train[0].m:,}, nnz={train[0].nnz:,}), costs and "
+                     f"supplies/demands perturbed per instance",
+           "train_instances": ntrain, "train_tol": tol_train, "solve_train_s": data_s,
+           "generate_and_solve_s": gen_s, "epochs": epochs, "train_s": train_s,
+           "train_ms_per_step": 1e3 * train_s / steps, "loss_first_last": [hist[0], hist[-1]],
+           "test_instances": ntest, "inference_s": infer_s}
+    for tol in (1e-6, 1e-8):
+        stc, tc, _, itc = solve(test, tol)
+        stw, tw, _, itw = solve(test, tol, starts)
+        out[f"{tol:.0e}"] = {
+            "cold": {"status": stc, "seconds": tc, "median_iterations": float(np.median(itc)),
+                     "mean_iterations": float(np.mean(itc))},
+            "warm": {"status": stw, "seconds": tw + infer_s, "median_iterations": float(np.median(itw)),
+                     "mean_iterations": float(np.mean(itw))},
+            "instances_faster_warm": int(sum(w < c for w, c in zip(itw, itc))),
+        }
+    return out
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
@@ -508,6 +604,9 @@ def main():
     batch = None
     if rank == 0 and args.workload == "powerlaw" and not args.no_batch:
         batch = run_batch(args, dev, stream, peak)
+    warm = None
+    if rank == 0 and args.workload == "powerlaw" and not args.no_warm_start:
+        warm = run_warm_start(args, dev, stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -528,7 +627,7 @@ def main():
         "clocks": clk, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
         "roofline": roofline, "kernels": kernels, "forms": forms,
         "fp64_peak_Gops": fp64_peak, "time_to_tol": ttt, "preprocess_ms": info["preprocess_ms"],
-        "cpu_baseline": cpu, "batch": batch,
+        "cpu_baseline": cpu, "batch": batch, "warm_start": warm,
     }
     print(json.dumps(line), flush=True)
 

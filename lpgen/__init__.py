@@ -378,16 +378,18 @@ def transport_lp(fam: dict, seed: int) -> LP:
     src, snk = side // D, side % D
     cap = (1.0 + rng.uniform(0.0, 0.5, size=side.shape[0])) * (s[src] * d[snk]).sum(axis=1) / s.sum()
     R = side.shape[0]
-    m = S + D + R
-    rows = np.concatenate([np.repeat(np.arange(S), D),                       # supply rows
-                           S + np.tile(np.arange(D), S),                     # demand rows
-                           S + D + np.repeat(np.arange(R), side.shape[1])])  # side rows
-    cols = np.concatenate([np.arange(n), np.arange(n), side.reshape(-1)])
-    vals = np.ones(rows.shape[0])
-    row_ptr, col, val = _csr_from_coo(m, n, rows.astype(np.int64), cols.astype(np.int64), vals)
-    ctype = np.concatenate([np.full(S, LE), np.full(D, EQ), np.full(R, LE)]).astype(np.int8)
+    if "_shared" not in fam:  # the matrix, row types and bounds are the family's, built once
+        m = S + D + R
+        rows = np.concatenate([np.repeat(np.arange(S), D),                       # supply rows
+                               S + np.tile(np.arange(D), S),                     # demand rows
+                               S + D + np.repeat(np.arange(R), side.shape[1])])  # side rows
+        cols = np.concatenate([np.arange(n), np.arange(n), side.reshape(-1)])
+        vals = np.ones(rows.shape[0])
+        row_ptr, col, val = _csr_from_coo(m, n, rows.astype(np.int64), cols.astype(np.int64), vals)
+        ctype = np.concatenate([np.full(S, LE), np.full(D, EQ), np.full(R, LE)]).astype(np.int8)
+        fam["_shared"] = (m, row_ptr, col, val, ctype, np.zeros(n), np.full(n, np.inf))
+    m, row_ptr, col, val, ctype, lv, uv = fam["_shared"]
     b = np.concatenate([s, d, cap])
-    lv, uv = np.zeros(n), np.full(n, np.inf)
     lc, uc = bounds_from_types(ctype, b)
     return LP(n, m, c, row_ptr, col, val, lc, uc, lv, uv, ctype, b, None, None, None,
               name=f"transport_lp(S={S},D={D},R={R},seed={seed})")

@@ -3,7 +3,7 @@
 The GPU runs BF16 weights with FP32 activations and sums; the reference gets the same BF16
 values (as float64), so the two differ only by FP32 rounding: forward outputs agree to
 1e-4 and gradients to 1e-3 (relative 2-norm per parameter block).  Then the network is
-trained on solver solutions of a small transportation family, and its warm start must
+trained on solver solutions of a transportation family, and its warm start must
 save PDHG iterations on held-out instances.
 """
 import numpy as np
@@ -134,13 +134,15 @@ def solve_batch(dpdlp, lps, tol, starts=None):
     return st, s.split(x, y), [k["iterations"] for k in kk]
 
 
-def test_training_and_warm_start_on_small_family(mods):
-    """A 30 x 30 transportation family with 200 side rows: train on 96 solver solutions,
-    then warm-start 16 held-out instances; the warm starts need fewer iterations to 1e-6."""
+def test_training_and_warm_start_on_transport_family(mods):
+    """A 100 x 100 transportation family with 2,000 side rows (n = 10,000, m = 2,200): train
+    on 192 solver solutions, then warm-start 24 held-out instances.  The warm starts need
+    fewer iterations to 1e-6 than cold starts (measured on this family: about 20 % fewer;
+    on a 30 x 30 family every start point, even the training mean, is as slow as zero)."""
     dpdlp, gnn = mods
-    fam = lpgen.transport_family(seed=11, S=30, D=30, side_rows=200, arcs_per_side=10)
-    train_lps = [lpgen.transport_lp(fam, 100 + i) for i in range(96)]
-    test_lps = [lpgen.transport_lp(fam, 5000 + i) for i in range(16)]
+    fam = lpgen.transport_family(seed=12, S=100, D=100, side_rows=2000, arcs_per_side=10)
+    train_lps = [lpgen.transport_lp(fam, 100 + i) for i in range(192)]
+    test_lps = [lpgen.transport_lp(fam, 50000 + i) for i in range(24)]
     st, sols, _ = solve_batch(dpdlp, train_lps, 1e-6)
     assert st == 0
     xs, ys = [x for x, _ in sols], [y for _, y in sols]
@@ -154,7 +156,7 @@ def test_training_and_warm_start_on_small_family(mods):
         fv, fc = gnn.features(lp, sc)
         data.append((fv, fc, (x / sc.x_scale).astype(np.float32), (y / sc.y_scale).astype(np.float32)))
     hist = gnn.train(net, data, epochs=30, lr=2e-3)
-    assert hist[-1] < 0.5 * hist[0]
+    assert hist[-1] < 0.3 * hist[0]
     starts = [gnn.predict(net, lp, sc) for lp in test_lps]
     _, _, cold = solve_batch(dpdlp, test_lps, 1e-6)
     stw, _, warm = solve_batch(dpdlp, test_lps, 1e-6, starts)
