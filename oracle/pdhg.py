@@ -206,24 +206,35 @@ def halpern(zh, z, z0, k, gamma):
 
 
 # ----------------------------------------------------------------------------- residuals
-def kkt(lp: OracleLP, x, y, tau, bnorm=None, cnorm=None):
+def kkt(lp: OracleLP, x, y, tau, bnorm=None, cnorm=None, row_w=None, col_w=None):
     """Relative KKT errors of Appendix B.4 at (x, y), with the current primal step tau.
 
     r_primal = ||Ax - proj_S(Ax)|| / (1 + ||[lc, uc]||)
     r_dual   = ||proj_X(x - tau (c - A^T y)) - x|| / tau / (1 + ||c||)
     r_gap    = |c^T x + p(-y) - s^T x| / (1 + max(|c^T x|, |-p(-y) + s^T x|))
     s        = (proj_X(x - tau (c - A^T y)) - (x - tau (c - A^T y))) / tau
+
+    ``row_w`` and ``col_w`` (optional) weight the entries of the primal and dual residual
+    vectors: for an LP scaled as D_r A D_c they are 1 / D_r and 1 / D_c, which turns the
+    residuals of the scaled LP into those of the original one (the objectives are the same
+    in both); ``bnorm`` and ``cnorm`` are then the original LP's.
     """
     if bnorm is None:
         bnorm = finite_bound_norm(lp.lc, lp.uc)
     if cnorm is None:
         cnorm = float(np.linalg.norm(lp.c))
     ax = lp.Ax(x)
-    r_p = float(np.linalg.norm(ax - proj_S(ax, lp.lc, lp.uc))) / (1.0 + bnorm)
+    rp_vec = ax - proj_S(ax, lp.lc, lp.uc)
+    if row_w is not None:
+        rp_vec = rp_vec * row_w
+    r_p = float(np.linalg.norm(rp_vec)) / (1.0 + bnorm)
     g = lp.c - lp.ATy(y)
     xt = x - tau * g
     px = proj_X(xt, lp.lv, lp.uv)
-    r_d = float(np.linalg.norm(px - x)) / tau / (1.0 + cnorm)
+    rd_vec = px - x
+    if col_w is not None:
+        rd_vec = rd_vec * col_w
+    r_d = float(np.linalg.norm(rd_vec)) / tau / (1.0 + cnorm)
     s = (px - xt) / tau
     obj_p = float(np.dot(lp.c, x))
     obj_d = -p_fun(-y, lp.lc, lp.uc) + float(np.dot(s, x))
@@ -298,20 +309,26 @@ class OracleResult:
 
 
 def solve(lp: OracleLP, eps=1e-8, max_iter=100_000, params=None, x_start=None, y_start=None,
-          state=None):
+          state=None, kkt_weights=None):
     """Restarted reflected-Halpern PDHG (Algorithm 1 on one device, with Appendix B).
 
     Every ``check_every`` iterations, and at ``max_iter``, the check runs at the PDHG output
     (x^, y^) of that iteration: relative KKT (stop when all three are <= eps), the
     fixed-point residual, the restart test and, on restart, the PID weight update.
 
-    ``state`` (from a previous result's ``.state``) resumes a stopped solve exactly."""
+    ``state`` (from a previous result's ``.state``) resumes a stopped solve exactly.
+    ``kkt_weights`` = (row_w, col_w, bnorm, cnorm) reports the KKT errors of another LP of
+    which ``lp`` is a diagonal scaling (see ``kkt``)."""
     P = dict(DEFAULTS)
     P.update(params or {})
     n, m = lp.n, lp.m
     K = int(P["check_every"])
-    bnorm = finite_bound_norm(lp.lc, lp.uc)
-    cnorm = float(np.linalg.norm(lp.c))
+    row_w = col_w = None
+    if kkt_weights is not None:
+        row_w, col_w, bnorm, cnorm = kkt_weights
+    else:
+        bnorm = finite_bound_norm(lp.lc, lp.uc)
+        cnorm = float(np.linalg.norm(lp.c))
     if state is not None:
         S = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in state.items()}
     else:
@@ -346,7 +363,7 @@ def solve(lp: OracleLP, eps=1e-8, max_iter=100_000, params=None, x_start=None, y
             continue
         # ---- check at the PDHG output of this iteration
         S["checks"] += 1
-        last_kkt = kkt(lp, xh, yh, tau, bnorm, cnorm)
+        last_kkt = kkt(lp, xh, yh, tau, bnorm, cnorm, row_w, col_w)
         r = fixed_point_residual(lp, x, y, xh, yh, omega, eta)
         rec = dict(T=S["T"], k=S["k"], r=r, omega=omega, restart=0, **last_kkt)
         trace.append(rec)
