@@ -190,11 +190,19 @@ int dpdlp_set_row_bounds(dpdlp_t* h, const double* lc, const double* uc);
  *   then FP64 values; 2: FP32 values
  *   throughout).  KKT, restart and step-size products always use FP64 values.  Needs every
  *   value of A to round to a normal float or zero, else the FP64 values are used.
+ *   precond (0): 1 = solve the diagonally scaled LP D_r A D_c instead of A (the paper
+ *   defines no preconditioning; this is an option): ruiz_passes (10) Ruiz infinity-norm
+ *   passes, then, if pock_chambolle (1), one Pock-Chambolle pass (alpha = 1); every factor
+ *   is a power of two, so scaling is exact.  Vectors at the boundary (start points,
+ *   solutions, checkpoints, dpdlp_apply_A/AT) stay in the original variables; reported
+ *   KKT errors and objectives are those of the original LP (primal and dual residual
+ *   vectors of the scaled LP divided by D_r and D_c); eta, the initial omega and the
+ *   restart metric belong to the scaled LP.  Load-time keys.
  *   cta_slots_primal, cta_slots_dual (4): warp slots per thread block of the primal (A^T y)
  *   and dual (A x_bar) iteration kernels, 2, 4 or 8 (64, 128 or 256 threads); a launch
  *   shape only, results do not depend on it (set by the autotuner).
- * Load-time keys (block_permute, perm_block, perm_seed) take effect at the next
- * dpdlp_load_lp.  Unknown key or out-of-range value: DPDLP_ERR_INVALID. */
+ * Load-time keys (block_permute, perm_block, perm_seed, precond, ruiz_passes,
+ * pock_chambolle) take effect at the next dpdlp_load_lp / dpdlp_load_batch.  Unknown key or out-of-range value: DPDLP_ERR_INVALID. */
 int dpdlp_set_param(dpdlp_t* h, const char* key, double v);
 
 /* Read a parameter's current value. */

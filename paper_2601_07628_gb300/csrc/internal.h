@@ -160,6 +160,8 @@ struct DevVecs {
   const int32_t* inst_chunk_rows = nullptr;           // ninst + 1: chunks of each instance
   const int32_t* inst_chunk_cols = nullptr;
   int g_rows = 1, g_cols = 1;                         // number of chunks
+  const double* row_w = nullptr;                      // [m] KKT weights 1/D_r (nullptr: 1)
+  const double* col_w = nullptr;                      // [n] KKT weights 1/D_c (nullptr: 1)
   const int32_t* inst_of_row = nullptr;               // [m]
   const int32_t* inst_of_col = nullptr;               // [n]
   InstScalars* inst = nullptr;                        // [ninst]
@@ -189,6 +191,12 @@ void transpose_csr(int rows, int cols, const std::vector<int64_t>& ptr,
                    const std::vector<int32_t>& idx, const std::vector<double>& val,
                    std::vector<int64_t>& tptr, std::vector<int32_t>& tidx,
                    std::vector<double>& tval);
+// Optional diagonal preconditioning (the paper defines none): Ruiz infinity-norm passes,
+// then one Pock-Chambolle pass (alpha = 1), every factor rounded to the nearest power of
+// two so scaling is exact.  Scales val in place to D_r A D_c and returns D_r, D_c.
+void precondition(int rows, int cols, const std::vector<int64_t>& ptr,
+                  const std::vector<int32_t>& idx, std::vector<double>& val, int ruiz_passes,
+                  bool pock_chambolle, std::vector<double>& dr, std::vector<double>& dc);
 // Pack the rows of one orientation into lanes and slots (best-fit decreasing on row
 // lengths); decides the new row order.
 void plan_packing(int rows, const std::vector<int64_t>& ptr, PackPlan& plan);
@@ -220,10 +228,12 @@ cudaError_t launch_check(const DevPacked& csr, const DevPacked& csc, const DevVe
                          DevScalars* sc, unsigned long long cond_handle, int use_cond,
                          cudaStream_t s);
 cudaError_t launch_fill_start(const DevVecs& v, int fresh_x, int fresh_y, cudaStream_t s);
-cudaError_t launch_gather(const double* in, const int32_t* perm, double* out, int len,
-                          cudaStream_t s);  // out[i] = in[perm[i]]
-cudaError_t launch_scatter(const double* in, const int32_t* perm, double* out, int len,
-                           cudaStream_t s);  // out[perm[i]] = in[i]
+// out[i] = in[perm[i]] * scale[i] (scale may be nullptr: 1)
+cudaError_t launch_gather(const double* in, const int32_t* perm, const double* scale,
+                          double* out, int len, cudaStream_t s);
+// out[perm[i]] = in[i] * scale[i] (scale may be nullptr: 1)
+cudaError_t launch_scatter(const double* in, const int32_t* perm, const double* scale,
+                           double* out, int len, cudaStream_t s);
 cudaError_t launch_fill(double* p, double v, int len, cudaStream_t s);
 // One power-iteration round for every instance: w = A v, lam_i = w_i.w_i, u = A^T w,
 // v_i = u_i / ||u_i||; pw[4 i] = lam_i, pw[4 i + 1] = ||u_i||.

@@ -784,7 +784,8 @@ __global__ void __launch_bounds__(TPB) reduce_rows_kernel(DevVecs v) {
     for (int i = ch.y + threadIdx.x; i < ch.y + ch.z; i += TPB) {
       const double lc = -v.hi[i], uc = -v.lo[i];
       const double ax = v.axh[i];
-      const double d = ax - clampd(ax, lc, uc);
+      double d = ax - clampd(ax, lc, uc);
+      if (v.row_w) d *= v.row_w[i];  // residual of the original LP (preconditioned solve)
       q[0] = fma(d, d, q[0]);
       const double yh = v.yh[i];
       double p = 0.0;  // u (-y)^+ - l (-y)^-, a term vanishing when its multiplier is 0
@@ -820,7 +821,8 @@ __global__ void __launch_bounds__(TPB) reduce_cols_kernel(DevVecs v) {
       const double g = v.c[j] - v.aty[j];
       const double xt = fma(-tau, g, xhj);
       const double px = clampd(xt, v.lv[j], v.uv[j]);
-      const double d = px - xhj;
+      double d = px - xhj;
+      if (v.col_w) d *= v.col_w[j];
       q[0] = fma(d, d, q[0]);
       q[1] = fma(px - xt, xhj, q[1]);
       q[2] = fma(v.c[j], xhj, q[2]);
@@ -1102,29 +1104,31 @@ cudaError_t launch_fill_start(const DevVecs& v, int fresh_x, int fresh_y, cudaSt
   return cudaGetLastError();
 }
 
-__global__ void gather_kernel(const double* in, const int32_t* perm, double* out, int len) {
+__global__ void gather_kernel(const double* in, const int32_t* perm, const double* scale,
+                              double* out, int len) {
   const int i = blockIdx.x * TPB + threadIdx.x;
-  if (i < len) out[i] = in[perm[i]];
+  if (i < len) out[i] = scale ? in[perm[i]] * scale[i] : in[perm[i]];
 }
-__global__ void scatter_kernel(const double* in, const int32_t* perm, double* out, int len) {
+__global__ void scatter_kernel(const double* in, const int32_t* perm, const double* scale,
+                               double* out, int len) {
   const int i = blockIdx.x * TPB + threadIdx.x;
-  if (i < len) out[perm[i]] = in[i];
+  if (i < len) out[perm[i]] = scale ? in[i] * scale[i] : in[i];
 }
 __global__ void fill_kernel(double* p, double val, int len) {
   const int i = blockIdx.x * TPB + threadIdx.x;
   if (i < len) p[i] = val;
 }
 
-cudaError_t launch_gather(const double* in, const int32_t* perm, double* out, int len,
-                          cudaStream_t s) {
+cudaError_t launch_gather(const double* in, const int32_t* perm, const double* scale,
+                          double* out, int len, cudaStream_t s) {
   if (len == 0) return cudaSuccess;
-  gather_kernel<<<(len + TPB - 1) / TPB, TPB, 0, s>>>(in, perm, out, len);
+  gather_kernel<<<(len + TPB - 1) / TPB, TPB, 0, s>>>(in, perm, scale, out, len);
   return cudaGetLastError();
 }
-cudaError_t launch_scatter(const double* in, const int32_t* perm, double* out, int len,
-                           cudaStream_t s) {
+cudaError_t launch_scatter(const double* in, const int32_t* perm, const double* scale,
+                           double* out, int len, cudaStream_t s) {
   if (len == 0) return cudaSuccess;
-  scatter_kernel<<<(len + TPB - 1) / TPB, TPB, 0, s>>>(in, perm, out, len);
+  scatter_kernel<<<(len + TPB - 1) / TPB, TPB, 0, s>>>(in, perm, scale, out, len);
   return cudaGetLastError();
 }
 cudaError_t launch_fill(double* p, double val, int len, cudaStream_t s) {

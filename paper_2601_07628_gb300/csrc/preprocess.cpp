@@ -5,6 +5,7 @@
 //    B indices (B = 256 by default) are shuffled, the order inside a block is kept.
 //  * The CSC copy of A (the paper keeps both CSR and CSC in device memory so that A^T y
 //    needs no atomics, Appendix E.2), built as the CSR of A^T by a stable counting sort.
+//  * Optional diagonal preconditioning (Ruiz, Pock-Chambolle) with power-of-two factors.
 //  * (packing.cpp) nonzero-aware partitioning (Section 4.3) down to warp lanes.
 #include <algorithm>
 #include <cmath>
@@ -106,6 +107,52 @@ void transpose_csr(int rows, int cols, const std::vector<int64_t>& ptr,
       tidx[p] = r;
       tval[p] = val[e];
     }
+}
+
+// 2^k with k the integer nearest to log2(v) (v > 0 finite): v = f 2^e with 0.5 <= f < 1,
+// and log2(v) rounds up to e exactly when f >= 2^-1/2.
+static double pow2_nearest(double v) {
+  int e = 0;
+  const double f = std::frexp(v, &e);
+  return std::ldexp(1.0, f >= std::sqrt(0.5) ? e : e - 1);
+}
+
+void precondition(int rows, int cols, const std::vector<int64_t>& ptr,
+                  const std::vector<int32_t>& idx, std::vector<double>& val, int ruiz_passes,
+                  bool pock_chambolle, std::vector<double>& dr, std::vector<double>& dc) {
+  dr.assign(rows, 1.0);
+  dc.assign(cols, 1.0);
+  std::vector<double> rn(rows), cn(cols);
+  auto apply = [&]() {  // factors from the norms rn, cn; scale the values and accumulate
+    for (int i = 0; i < rows; ++i) rn[i] = rn[i] > 0.0 ? pow2_nearest(1.0 / std::sqrt(rn[i])) : 1.0;
+    for (int j = 0; j < cols; ++j) cn[j] = cn[j] > 0.0 ? pow2_nearest(1.0 / std::sqrt(cn[j])) : 1.0;
+    for (int i = 0; i < rows; ++i)
+      for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) val[k] = val[k] * rn[i] * cn[idx[k]];
+    for (int i = 0; i < rows; ++i) dr[i] *= rn[i];
+    for (int j = 0; j < cols; ++j) dc[j] *= cn[j];
+  };
+  for (int pass = 0; pass < ruiz_passes; ++pass) {
+    std::fill(rn.begin(), rn.end(), 0.0);
+    std::fill(cn.begin(), cn.end(), 0.0);
+    for (int i = 0; i < rows; ++i)
+      for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+        const double a = std::fabs(val[k]);
+        rn[i] = std::max(rn[i], a);
+        cn[idx[k]] = std::max(cn[idx[k]], a);
+      }
+    apply();
+  }
+  if (pock_chambolle) {
+    std::fill(rn.begin(), rn.end(), 0.0);
+    std::fill(cn.begin(), cn.end(), 0.0);
+    for (int i = 0; i < rows; ++i)
+      for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+        const double a = std::fabs(val[k]);
+        rn[i] += a;
+        cn[idx[k]] += a;
+      }
+    apply();
+  }
 }
 
 }  // namespace pdhg

@@ -61,6 +61,9 @@ std::map<std::string, Param> default_params() {
       {"spmv_fp32", {0, 0, 2, true}},
       {"fp32_switch_tol", {1e-6, 0.0, 1.0, false}},
       {"fp32_stall_checks", {64, 1, 1 << 30, true}},
+      {"precond", {0, 0, 1, true}},
+      {"ruiz_passes", {10, 0, 100, true}},
+      {"pock_chambolle", {1, 0, 1, true}},
       {"cta_slots_primal", {4, 2, 8, true}},
       {"cta_slots_dual", {4, 2, 8, true}},
   };
@@ -90,7 +93,12 @@ struct dpdlp {
   int ninst = 1;
   std::vector<int32_t> row_off, col_off;    // instance ranges (caller = internal ranges)
   std::vector<InstScalars> h_inst;          // host mirror of the instance scalars
-  std::vector<double> inst_bnorm, inst_cnorm;
+  std::vector<double> inst_bnorm, inst_cnorm;       // original LP (KKT denominators)
+  std::vector<double> inst_bnorm_s, inst_cnorm_s;   // the LP PDHG runs on (initial omega)
+  // diagonal preconditioning (internal order; empty / nullptr when off): the solver works
+  // on D_r A D_c, x = D_c xs, y = D_r ys; every factor is a power of two
+  std::vector<double> dr, dc;
+  double *d_dr = nullptr, *d_dc = nullptr, *d_rw = nullptr, *d_cw = nullptr;
   std::vector<double> eta_inst;             // power-iteration step size per instance
   bool eta_valid = false;
   std::vector<double> eta_user;             // per-instance step sizes set by the caller
@@ -157,6 +165,9 @@ void free_problem(dpdlp* h) {
   h->v = DevVecs{};
   h->xs = h->ys = nullptr;
   h->d_sc = nullptr;
+  h->d_dr = h->d_dc = h->d_rw = h->d_cw = nullptr;
+  h->dr.clear();
+  h->dc.clear();
   h->loaded = false;
   h->eta_valid = false;
   h->pending_state = false;
@@ -237,20 +248,29 @@ double bound_norm(const std::vector<double>& lc, const std::vector<double>& uc, 
   return std::sqrt(s);
 }
 
+// The -S box of the LP the solver iterates on (rows scaled by D_r when preconditioned),
+// and the bound norms of the original and of the scaled LP.
 int upload_row_bounds(dpdlp* h) {
-  std::vector<double> lo(h->m), hi(h->m);
+  std::vector<double> lo(h->m), hi(h->m), lcs(h->h_lc), ucs(h->h_uc);
   for (int i = 0; i < h->m; ++i) {
     const int o = h->prow[i];
-    lo[i] = -h->h_uc[o];
-    hi[i] = -h->h_lc[o];
+    if (!h->dr.empty()) {
+      lcs[o] = h->h_lc[o] * h->dr[i];
+      ucs[o] = h->h_uc[o] * h->dr[i];
+    }
+    lo[i] = -ucs[o];
+    hi[i] = -lcs[o];
   }
   if (h->m) {
     CK(cudaMemcpy(h->v.lo, lo.data(), h->m * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->v.hi, hi.data(), h->m * sizeof(double), cudaMemcpyHostToDevice));
   }
   h->inst_bnorm.assign(h->ninst, 0.0);
-  for (int i = 0; i < h->ninst; ++i)
+  h->inst_bnorm_s.assign(h->ninst, 0.0);
+  for (int i = 0; i < h->ninst; ++i) {
     h->inst_bnorm[i] = bound_norm(h->h_lc, h->h_uc, h->row_off[i], h->row_off[i + 1]);
+    h->inst_bnorm_s[i] = bound_norm(lcs, ucs, h->row_off[i], h->row_off[i + 1]);
+  }
   return 0;
 }
 
@@ -258,25 +278,25 @@ bool ptr_device(const dpdlp* h) { return h->P("ptr_mode_device") != 0.0; }
 
 // Caller vector (caller order, host or device) -> internal-order device vector `dst`.
 int import_vec(dpdlp* h, const double* src, double* dst, const int32_t* perm, int len,
-               double* staging) {
+               double* staging, const double* scale) {
   if (len == 0) return 0;
   const double* dsrc = src;
   if (!ptr_device(h)) {
     CK(cudaMemcpyAsync(staging, src, len * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     dsrc = staging;
   }
-  CK(launch_gather(dsrc, perm, dst, len, h->stream));
+  CK(launch_gather(dsrc, perm, scale, dst, len, h->stream));
   return 0;
 }
 
 // Internal-order device vector -> caller vector (caller order, host or device).
 int export_vec(dpdlp* h, const double* src, double* dst, const int32_t* perm, int len,
-               double* staging) {
+               double* staging, const double* scale) {
   if (len == 0 || !dst) return 0;
   if (ptr_device(h)) {
-    CK(launch_scatter(src, perm, dst, len, h->stream));
+    CK(launch_scatter(src, perm, scale, dst, len, h->stream));
   } else {
-    CK(launch_scatter(src, perm, staging, len, h->stream));
+    CK(launch_scatter(src, perm, scale, staging, len, h->stream));
     CK(cudaMemcpyAsync(dst, staging, len * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   }
   CK(cudaStreamSynchronize(h->stream));
@@ -409,7 +429,7 @@ int init_fresh(dpdlp* h) {
   h->h_inst.resize(h->ninst);
   for (int i = 0; i < h->ninst; ++i) {
     const double eta = pe > 0.0 ? pe : (!h->eta_user.empty() ? h->eta_user[i] : h->eta_inst[i]);
-    const double cn = h->inst_cnorm[i], bn = h->inst_bnorm[i];
+    const double cn = h->inst_cnorm_s[i], bn = h->inst_bnorm_s[i];  // of the LP iterated on
     const double omega = po > 0.0 ? po : ((cn > 0.0 && bn > 0.0) ? cn / bn : 1.0);
     h->h_inst[i] = fresh_inst(h, i, eta, omega, fp32);
   }
@@ -612,6 +632,10 @@ int load_impl(dpdlp* h, int32_t count, const int32_t* row_off, const int32_t* co
   std::vector<int32_t> pidx, tidx;
   std::vector<double> pval, tval;
   permute_csr(m, n, row_ptr, col_idx, val, h->prow, h->pcol, pptr, pidx, pval);
+  std::vector<double> drp, dcp;  // preconditioner factors, pre-packing order
+  if (h->P("precond") != 0.0)
+    precondition(m, n, pptr, pidx, pval, (int)h->P("ruiz_passes"), h->P("pock_chambolle") != 0.0,
+                 drp, dcp);
   transpose_csr(m, n, pptr, pidx, pval, tptr, tidx, tval);
   // pack rows of A and rows of A^T into warp lanes; each packing fixes one index order
   PackPlan rplan, cplan;
@@ -637,6 +661,12 @@ int load_impl(dpdlp* h, int32_t count, const int32_t* row_off, const int32_t* co
     for (int j = 0; j < n; ++j) pc[j] = h->pcol[cplan.old_of_new[j]];
     h->prow.swap(pr);
     h->pcol.swap(pc);
+    if (!drp.empty() || !dcp.empty()) {
+      h->dr.resize(m);
+      h->dc.resize(n);
+      for (int i = 0; i < m; ++i) h->dr[i] = drp[rplan.old_of_new[i]];
+      for (int j = 0; j < n; ++j) h->dc[j] = dcp[cplan.old_of_new[j]];
+    }
   }
 
   int rc;
@@ -704,22 +734,54 @@ int load_impl(dpdlp* h, int32_t count, const int32_t* row_off, const int32_t* co
   h->trace_cap = (int)h->P("trace_capacity");
   if ((rc = dalloc(h, (dpdlp_trace_t**)&v.trace, h->trace_cap > 0 ? h->trace_cap : 1))) return rc;
   if ((rc = dalloc(h, &h->d_sc, 1))) return rc;
+  const bool pre = !h->dr.empty();
+  std::vector<double> cs_int;  // the cost vector the solver iterates with (internal order)
   if (n) {
     std::vector<double> tmp = permuted(c, h->pcol);
+    if (pre)
+      for (int j = 0; j < n; ++j) tmp[j] *= h->dc[j];
+    cs_int = tmp;
     CK(cudaMemcpy(v.c, tmp.data(), n * sizeof(double), cudaMemcpyHostToDevice));
     tmp = permuted(lv, h->pcol);
+    if (pre)
+      for (int j = 0; j < n; ++j) tmp[j] /= h->dc[j];
     CK(cudaMemcpy(v.lv, tmp.data(), n * sizeof(double), cudaMemcpyHostToDevice));
     tmp = permuted(uv, h->pcol);
+    if (pre)
+      for (int j = 0; j < n; ++j) tmp[j] /= h->dc[j];
     CK(cudaMemcpy(v.uv, tmp.data(), n * sizeof(double), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(v.perm_col, h->pcol.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+  }
+  if (pre) {  // factors and their inverses (exact: powers of two) for the boundary and KKT
+    std::vector<double> rw(m), cw(n);
+    for (int i = 0; i < m; ++i) rw[i] = 1.0 / h->dr[i];
+    for (int j = 0; j < n; ++j) cw[j] = 1.0 / h->dc[j];
+    if ((rc = dalloc(h, &h->d_dr, m)) || (rc = dalloc(h, &h->d_dc, n)) ||
+        (rc = dalloc(h, &h->d_rw, m)) || (rc = dalloc(h, &h->d_cw, n)))
+      return rc;
+    if (m) {
+      CK(cudaMemcpy(h->d_dr, h->dr.data(), m * sizeof(double), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(h->d_rw, rw.data(), m * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    if (n) {
+      CK(cudaMemcpy(h->d_dc, h->dc.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(h->d_cw, cw.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    v.row_w = h->d_rw;
+    v.col_w = h->d_cw;
   }
   if (m) CK(cudaMemcpy(v.perm_row, h->prow.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice));
   if ((rc = upload_row_bounds(h))) return rc;
   h->inst_cnorm.assign(count, 0.0);
+  h->inst_cnorm_s.assign(count, 0.0);
   for (int i = 0; i < count; ++i) {
-    double cs = 0.0;
-    for (int j = col_off[i]; j < col_off[i + 1]; ++j) cs += c[j] * c[j];
+    double cs = 0.0, css = 0.0;
+    for (int j = col_off[i]; j < col_off[i + 1]; ++j) {
+      cs += c[j] * c[j];
+      css += cs_int[j] * cs_int[j];  // instance ranges are the same in both orders
+    }
     h->inst_cnorm[i] = std::sqrt(cs);
+    h->inst_cnorm_s[i] = pre ? std::sqrt(css) : h->inst_cnorm[i];
   }
   h->loaded = true;
   const auto t1 = std::chrono::steady_clock::now();
@@ -781,8 +843,8 @@ int dpdlp_set_start(dpdlp_t* h, const double* x0, const double* y0) {
   int rc;
   h->have_start_x = x0 != nullptr;
   h->have_start_y = y0 != nullptr;
-  if (x0 && (rc = import_vec(h, x0, h->xs, h->v.perm_col, h->n, h->v.tmp_n))) return rc;
-  if (y0 && (rc = import_vec(h, y0, h->ys, h->v.perm_row, h->m, h->v.tmp_m))) return rc;
+  if (x0 && (rc = import_vec(h, x0, h->xs, h->v.perm_col, h->n, h->v.tmp_n, h->d_cw))) return rc;
+  if (y0 && (rc = import_vec(h, y0, h->ys, h->v.perm_row, h->m, h->v.tmp_m, h->d_rw))) return rc;
   CK(cudaStreamSynchronize(h->stream));
   return 0;
 }
@@ -840,8 +902,8 @@ int dpdlp_get_solution(dpdlp_t* h, double* x, double* y) {
   if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
   CK(cudaSetDevice(h->device));
   int rc;
-  if ((rc = export_vec(h, h->v.xh, x, h->v.perm_col, h->n, h->v.tmp_n))) return rc;
-  if ((rc = export_vec(h, h->v.yh, y, h->v.perm_row, h->m, h->v.tmp_m))) return rc;
+  if ((rc = export_vec(h, h->v.xh, x, h->v.perm_col, h->n, h->v.tmp_n, h->d_dc))) return rc;
+  if ((rc = export_vec(h, h->v.yh, y, h->v.perm_row, h->m, h->v.tmp_m, h->d_dr))) return rc;
   return 0;
 }
 
@@ -952,10 +1014,10 @@ int dpdlp_get_state(dpdlp_t* h, double* x, double* y, double* x0, double* y0,
   if (h->ninst != 1) return fail(h, DPDLP_ERR_INVALID, "checkpoints hold a single LP, not a batch");
   CK(cudaSetDevice(h->device));
   int rc;
-  if ((rc = export_vec(h, h->v.x, x, h->v.perm_col, h->n, h->v.tmp_n))) return rc;
-  if ((rc = export_vec(h, h->v.y, y, h->v.perm_row, h->m, h->v.tmp_m))) return rc;
-  if ((rc = export_vec(h, h->v.x0, x0, h->v.perm_col, h->n, h->v.tmp_n))) return rc;
-  if ((rc = export_vec(h, h->v.y0, y0, h->v.perm_row, h->m, h->v.tmp_m))) return rc;
+  if ((rc = export_vec(h, h->v.x, x, h->v.perm_col, h->n, h->v.tmp_n, h->d_dc))) return rc;
+  if ((rc = export_vec(h, h->v.y, y, h->v.perm_row, h->m, h->v.tmp_m, h->d_dr))) return rc;
+  if ((rc = export_vec(h, h->v.x0, x0, h->v.perm_col, h->n, h->v.tmp_n, h->d_dc))) return rc;
+  if ((rc = export_vec(h, h->v.y0, y0, h->v.perm_row, h->m, h->v.tmp_m, h->d_dr))) return rc;
   if (st) {
     const InstScalars& s = h->h_inst[0];
     st->T = h->h_sc.T_base;
@@ -986,10 +1048,10 @@ int dpdlp_set_state(dpdlp_t* h, const double* x, const double* y, const double* 
   if (h->ninst != 1) return fail(h, DPDLP_ERR_INVALID, "checkpoints hold a single LP, not a batch");
   CK(cudaSetDevice(h->device));
   int rc;
-  if ((rc = import_vec(h, x, h->v.x, h->v.perm_col, h->n, h->v.tmp_n))) return rc;
-  if ((rc = import_vec(h, y, h->v.y, h->v.perm_row, h->m, h->v.tmp_m))) return rc;
-  if ((rc = import_vec(h, x0, h->v.x0, h->v.perm_col, h->n, h->v.tmp_n))) return rc;
-  if ((rc = import_vec(h, y0, h->v.y0, h->v.perm_row, h->m, h->v.tmp_m))) return rc;
+  if ((rc = import_vec(h, x, h->v.x, h->v.perm_col, h->n, h->v.tmp_n, h->d_cw))) return rc;
+  if ((rc = import_vec(h, y, h->v.y, h->v.perm_row, h->m, h->v.tmp_m, h->d_rw))) return rc;
+  if ((rc = import_vec(h, x0, h->v.x0, h->v.perm_col, h->n, h->v.tmp_n, h->d_cw))) return rc;
+  if ((rc = import_vec(h, y0, h->v.y0, h->v.perm_row, h->m, h->v.tmp_m, h->d_rw))) return rc;
   if (h->n) CK(cudaMemcpyAsync(h->v.xh, h->v.x, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   if (h->m) CK(cudaMemcpyAsync(h->v.yh, h->v.y, h->m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -1044,9 +1106,9 @@ int dpdlp_apply_A(dpdlp_t* h, const double* x, double* out) {
   if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
   CK(cudaSetDevice(h->device));
   int rc;
-  if ((rc = import_vec(h, x, h->v.tmp_n2, h->v.perm_col, h->n, h->v.tmp_n))) return rc;
+  if ((rc = import_vec(h, x, h->v.tmp_n2, h->v.perm_col, h->n, h->v.tmp_n, h->d_cw))) return rc;
   CK(launch_spmv(h->csr, h->v.tmp_n2, nullptr, h->v.axh, nullptr, h->stream));
-  return export_vec(h, h->v.axh, out, h->v.perm_row, h->m, h->v.tmp_m);
+  return export_vec(h, h->v.axh, out, h->v.perm_row, h->m, h->v.tmp_m, h->d_rw);
 }
 
 int dpdlp_apply_AT(dpdlp_t* h, const double* y, double* out) {
@@ -1054,9 +1116,9 @@ int dpdlp_apply_AT(dpdlp_t* h, const double* y, double* out) {
   if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
   CK(cudaSetDevice(h->device));
   int rc;
-  if ((rc = import_vec(h, y, h->v.axh, h->v.perm_row, h->m, h->v.tmp_m))) return rc;
+  if ((rc = import_vec(h, y, h->v.axh, h->v.perm_row, h->m, h->v.tmp_m, h->d_rw))) return rc;
   CK(launch_spmv(h->csc, h->v.axh, nullptr, h->v.tmp_n2, nullptr, h->stream));
-  return export_vec(h, h->v.tmp_n2, out, h->v.perm_col, h->n, h->v.tmp_n);
+  return export_vec(h, h->v.tmp_n2, out, h->v.perm_col, h->n, h->v.tmp_n, h->d_cw);
 }
 
 int dpdlp_time_kernel(dpdlp_t* h, const char* which, int32_t reps, double* avg_ms) {
