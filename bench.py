@@ -244,6 +244,7 @@ def time_to_tol(s, tol, max_iter, fp32_mode=0):
     tr = s.trace(1 << 16)
     switch = next((r["T"] for r in tr if r["spmv_mode"] == 0), None) if fp32_mode else None
     return {"tol": tol, "form": ["fp64", "mixed_fp32", "fp32_values"][fp32_mode], "status": st,
+            "precond": int(s.get_param("precond")),
             "seconds": dt, "iterations": k["iterations"], "restarts": k["restarts"],
             "rel_kkt": max(k["r_primal"], k["r_dual"], k["r_gap"]),
             "fp64_from_iteration": switch}
@@ -281,8 +282,9 @@ def launches_per_body(info, ninst):
 def run_batch(args, dev, stream, peak):
     """Batched form: the LPs in one handle (per-instance step sizes, weights, restarts and
     statuses; converged instances are skipped), against the same LPs solved one after
-    another with the plain single-LP path.  Power iteration and graph capture happen in an
-    untimed 64-iteration solve before each timed solve, on both sides."""
+    another with the single-LP path, both preconditioned.  Power iteration and graph
+    capture happen in an untimed 64-iteration solve before each timed solve, on both
+    sides."""
     import numpy as np
     import torch
 
@@ -296,8 +298,11 @@ def run_batch(args, dev, stream, peak):
     n = sum(lp.n for lp in lps)
     m = sum(lp.m for lp in lps)
     nnz = sum(lp.nnz for lp in lps)
+    # both sides run the optional preconditioning: without it a few of these LPs need more
+    # than 10^6 iterations to reach 1e-8, with it all converge; the comparison is batching
     s = Solver(dev)
     s.set_stream(stream)
+    s.set_param("precond", 1)
     t0 = time.perf_counter()
     s.load_batch(lps)
     load_s = time.perf_counter() - t0
@@ -324,30 +329,45 @@ def run_batch(args, dev, stream, peak):
     kt = {k: s.time_kernel(k, 20) for k in ("primal", "dual")}
     kern = {k: {"ms": kt[k], "GB/s": kb[k] / (kt[k] * 1e-3) / 1e9,
                 "hbm_frac": kb[k] / (kt[k] * 1e-3) / 1e9 / peak} for k in kt}
-    # batched solve to tolerance
-    tol = args.batch_tol
-    s.set_param("resume", 0)
-    s.solve(tol, K_CHECK)
-    t0 = time.perf_counter()
-    st = s.solve(tol, 500_000)
-    batched_s = time.perf_counter() - t0
-    bk = s.batch_kkt()
-    iters = np.array([k["iterations"] for k in bk], dtype=np.float64)
+    # batched solves to tolerance, then the same LPs one by one (plain FP64 PDHG)
+    tols = sorted({args.batch_tol, 1e-8}, reverse=True)
+    res_tol = {}
+    for tol in tols:
+        s.set_param("resume", 0)
+        s.solve(tol, K_CHECK)
+        t0 = time.perf_counter()
+        st = s.solve(tol, 1_000_000)
+        batched_s = time.perf_counter() - t0
+        bk = s.batch_kkt()
+        iters = np.array([k["iterations"] for k in bk], dtype=np.float64)
+        res_tol[tol] = dict(batched_s=batched_s, st=st, iters=iters,
+                            conv=int(sum(k["status"] == 0 for k in bk)))
     s.close()
-    # the same LPs one by one
-    seq_s, seq_iters, seq_status, seq_load = 0.0, [], [], 0.0
     one = Solver(dev)
     one.set_stream(stream)
+    one.set_param("precond", 1)
+    seq = {tol: dict(s=0.0, iters=[], status=[]) for tol in tols}
+    seq_load = 0.0
     for lp in lps:
         t0 = time.perf_counter()
         one.load(lp)
         seq_load += time.perf_counter() - t0
-        r = time_to_tol(one, tol, 500_000, 0)
-        seq_s += r["seconds"]
-        seq_iters.append(r["iterations"])
-        seq_status.append(r["status"])
+        for tol in tols:
+            r = time_to_tol(one, tol, 1_000_000, 0)
+            seq[tol]["s"] += r["seconds"]
+            seq[tol]["iters"].append(r["iterations"])
+            seq[tol]["status"].append(r["status"])
     one.close()
-    sgm10 = float(np.exp(np.mean(np.log(iters + 10.0))) - 10.0)
+    per_tol = {}
+    for tol in tols:
+        R, Q = res_tol[tol], seq[tol]
+        per_tol[f"{tol:.0e}"] = {
+            "batched": {"seconds": R["batched_s"], "status": R["st"], "converged": R["conv"],
+                        "max_iterations": int(R["iters"].max()),
+                        "sgm10_iterations": float(np.exp(np.mean(np.log(R["iters"] + 10.0))) - 10.0)},
+            "sequential": {"seconds": Q["s"], "converged": int(sum(x == 0 for x in Q["status"])),
+                           "max_iterations": int(max(Q["iters"]))},
+            "speedup_vs_sequential": Q["s"] / R["batched_s"] if R["batched_s"] > 0 else None}
     return {
         "workload": f"{len(lps)} uneven LPs (m_i ~ U{{500..50000}}, n_i = 2 m_i, 5-15 nnz/col, seed 3): "
                     f"n={n:,} m={m:,} nnz={nnz:,}",
@@ -355,13 +375,7 @@ def run_batch(args, dev, stream, peak):
         "autotune": {k: tune[k] for k in ("cta_slots_primal", "cta_slots_dual", "ms")},
         "iter_per_s_all_running": it_s, "kernels": kern,
         "gpu_launches_per_body": launches_per_body(info, len(lps)),
-        "tol": tol, "batched": {"seconds": batched_s, "status": st,
-                                "converged": int(sum(k["status"] == 0 for k in bk)),
-                                "max_iterations": int(iters.max()), "sgm10_iterations": sgm10},
-        "sequential": {"seconds": seq_s, "load_s": seq_load,
-                       "converged": int(sum(x == 0 for x in seq_status)),
-                       "max_iterations": int(max(seq_iters))},
-        "speedup_vs_sequential": seq_s / batched_s if batched_s > 0 else None,
+        "precond": 1, "sequential_load_s": seq_load, "to_tol": per_tol,
     }
 
 
@@ -591,6 +605,18 @@ def main():
                 ttt[key] = time_to_tol(s, 1e-4, 400_000, mode)
             if args.tol_runs == "all":
                 ttt["powerlaw_1e-8_fp64"] = time_to_tol(s, 1e-8, 2_000_000, 0)
+            # the same LP with the optional diagonal preconditioning (loaded again: the
+            # scaling is a load-time step, reported in preprocess_ms)
+            sp_ = Solver(dev)
+            sp_.set_stream(stream)
+            sp_.set_param("precond", 1)
+            sp_.load(lp)
+            runs = [(1e-4, 0), (1e-6, 0), (1e-8, 0)] + ([(1e-8, 1)] if args.tol_runs == "all" else [])
+            for tol, mode in runs:
+                r = time_to_tol(sp_, tol, 2_000_000, mode)
+                r["preprocess_ms"] = sp_.info()["preprocess_ms"]
+                ttt[f"powerlaw_{tol:.0e}_precond_{['fp64', 'mixed_fp32'][mode]}"] = r
+            sp_.close()
         import lpgen
 
         sm = Solver(dev)
