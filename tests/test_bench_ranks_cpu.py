@@ -1,0 +1,67 @@
+"""Multi-rank host logic of bench.py on the CPU: two gloo ranks (replicas, no GPU).
+
+Every rank times its own copy of the work; the job's time is the slowest rank's (every
+rank gets the maximum), the job's rate counts the units of all ranks, and only rank 0 of
+the reference arm does any work.
+"""
+import json
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank), BENCH_GLOO="1")
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import bench
+
+    w, r, _ = bench.dist_setup()
+    local_ms = [120.0, 300.0][r]
+    ms = bench.max_over_ranks(local_ms, w)
+    rate = bench.job_throughput(64 * 10, w, ms)
+    dist.barrier()
+    with open(os.path.join(out_dir, f"r{r}.json"), "w") as f:
+        json.dump({"world": w, "rank": r, "ms": ms, "rate": rate}, f)
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks(tmp_path):
+    port = _free_port()
+    mp.start_processes(_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True,
+                       start_method="spawn")
+    res = [json.load(open(tmp_path / f"r{r}.json")) for r in range(2)]
+    for r in res:
+        assert r["world"] == 2 and r["ms"] == 300.0
+        assert r["rate"] == pytest.approx(2 * 640 / 0.3)
+
+
+def test_single_rank_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.max_over_ranks(12.5, 1) == 12.5
+    assert bench.job_throughput(640, 1, 250.0) == pytest.approx(2560.0)
+
+
+def test_reference_arm_other_ranks_do_nothing(capsys):
+    sys.path.insert(0, ROOT)
+    import argparse
+
+    import bench
+
+    bench.run_reference(argparse.Namespace(workload="small", steps=1, warmup=0), 2, 1)
+    assert capsys.readouterr().out == ""
