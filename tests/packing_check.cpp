@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "internal.h"
@@ -33,8 +34,19 @@ int main(int argc, char** argv) {
   if (cols && std::fread(x.data(), 8, cols, f) != (size_t)cols) return fail("x");
   std::fclose(f);
 
+  // optional argv[2]: instance row offsets (comma separated, first 0, last rows) -> batch
+  std::vector<int32_t> offsets;
+  if (argc > 2) {
+    const char* q = argv[2];
+    while (*q) {
+      offsets.push_back((int32_t)std::strtol(q, (char**)&q, 10));
+      if (*q == ',') ++q;
+    }
+    if (offsets.size() < 2 || offsets.front() != 0 || offsets.back() != rows) return fail("offsets");
+  }
   PackPlan P;
-  plan_packing(rows, ptr, P);
+  if (offsets.empty()) plan_packing(rows, ptr, P);
+  else plan_packing_batch(rows, ptr, offsets, P);
   std::vector<int32_t> ident(cols);
   for (int j = 0; j < cols; ++j) ident[j] = j;
   HostPacked H;
@@ -47,18 +59,50 @@ int main(int argc, char** argv) {
     if (nr < 0 || nr >= rows || seen[nr]++) return fail("new_of_old not a permutation", r, nr);
     if (P.old_of_new[nr] != r) return fail("old_of_new", r, nr);
   }
-  // slots partition the short rows in order, within the row budget
+  // slots (in increasing row order, within the row budget) and long rows cover every row
+  // exactly once; for one LP the slots come first and are consecutive
+  std::vector<int> cover(rows, 0);
   int expect = 0;
   for (int s = 0; s < H.nslots; ++s) {
-    if (H.slots[s].row_base != expect) return fail("slot row_base", s, H.slots[s].row_base);
-    if (H.slots[s].nrows > MAX_SLOT_ROWS) return fail("slot rows", s, H.slots[s].nrows);
-    expect += H.slots[s].nrows;
+    const SlotDesc d = H.slots[s];
+    if (d.row_base < expect || (offsets.empty() && d.row_base != expect))
+      return fail("slot row_base", s, d.row_base);
+    if (d.nrows > MAX_SLOT_ROWS) return fail("slot rows", s, d.nrows);
+    for (int r = d.row_base; r < d.row_base + d.nrows; ++r) {
+      if (r >= rows) return fail("slot past the rows", s, r);
+      ++cover[r];
+    }
+    expect = d.row_base + d.nrows;
   }
-  if (expect != H.nshort || H.nshort + H.nlong != rows) return fail("row counts", expect, H.nshort);
-  for (int r = 0; r < rows; ++r) {
-    const int64_t L = ptr[r + 1] - ptr[r];
-    const bool is_long = L > LANE_ITEMS;
-    if (is_long != (P.new_of_old[r] >= H.nshort)) return fail("long/short class", r, L);
+  for (int i = 0; i < H.nlong; ++i) ++cover[H.long_row[i]];
+  for (int r = 0; r < rows; ++r)
+    if (cover[r] != 1) return fail("row not covered exactly once", r, cover[r]);
+  if (H.nshort + H.nlong != rows) return fail("row counts", H.nshort, H.nlong);
+  if (offsets.empty()) {
+    for (int r = 0; r < rows; ++r) {
+      const int64_t L = ptr[r + 1] - ptr[r];
+      const bool is_long = L > LANE_ITEMS;
+      if (is_long != (P.new_of_old[r] >= H.nshort)) return fail("long/short class", r, L);
+    }
+  } else {
+    // a batch: rows keep their instance's range, slots and long rows know their instance
+    auto inst_of = [&](int r) {
+      int i = 0;
+      while (offsets[i + 1] <= r) ++i;
+      return i;
+    };
+    for (int r = 0; r < rows; ++r)
+      if (inst_of(P.new_of_old[r]) != inst_of(r)) return fail("row left its instance", r, 0);
+    for (int s = 0; s < H.nslots; ++s) {
+      const SlotDesc d = H.slots[s];
+      if (d.nrows && (inst_of(d.row_base) != d.inst || inst_of(d.row_base + d.nrows - 1) != d.inst))
+        return fail("slot instance", s, d.inst);
+    }
+    for (int i = 0; i < H.nlong; ++i)
+      if (inst_of(H.long_row[i]) != H.long_inst[i]) return fail("long row instance", i, 0);
+    for (int i = 1; i < H.nlong; ++i)
+      if (H.long_ptr[i + 1] - H.long_ptr[i] > H.long_ptr[i] - H.long_ptr[i - 1])
+        return fail("long rows not longest first", i, 0);
   }
   // replay the lanes
   std::vector<double> out(rows, NAN), piece(H.npieces, NAN);

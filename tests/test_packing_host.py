@@ -30,7 +30,7 @@ def checker(tmp_path_factory):
     return exe, d
 
 
-def run(checker, row_ptr, col, val, ncols, seed=0):
+def run(checker, row_ptr, col, val, ncols, seed=0, offsets=None):
     exe, d = checker
     rows = len(row_ptr) - 1
     x = np.random.default_rng(seed).standard_normal(ncols)
@@ -41,7 +41,8 @@ def run(checker, row_ptr, col, val, ncols, seed=0):
         np.asarray(col, dtype=np.int32).tofile(f)
         np.asarray(val, dtype=np.float64).tofile(f)
         x.tofile(f)
-    out = subprocess.run([exe, path], capture_output=True, text=True).stdout.strip()
+    cmd = [exe, path] + ([",".join(str(int(o)) for o in offsets)] if offsets is not None else [])
+    out = subprocess.run(cmd, capture_output=True, text=True).stdout.strip()
     assert out.startswith("ok"), out
     return dict(kv.split("=") for kv in out.split()[1:])
 
@@ -83,3 +84,20 @@ def test_powerlaw_fill(checker):
     lp = lpgen.scaled_powerlaw_lp(1, 0.01)
     st = run(checker, lp.row_ptr, lp.col, lp.val, lp.n, seed=5)
     assert float(st["fill"]) > 0.85, st
+
+
+def test_batch_packing(checker):
+    """Several instances (block-diagonal stack, one of them empty): each instance's rows are
+    packed into its own slots and keep their instance's index range."""
+    import scipy.sparse as sp
+
+    parts = [lpgen.row_length_stress_lp(20, LENGTHS, n=4000),
+             lpgen.small_random_lp(21, n=300, m=0),
+             lpgen.uneven_lp(22, 700),
+             lpgen.row_length_stress_lp(23, [40, 0, 3, 33, 100, 1] * 20, n=500)]
+    mats = [sp.csr_matrix((p.val, p.col, p.row_ptr), shape=(p.m, p.n)) for p in parts]
+    B = sp.block_diag(mats).tocsr()
+    B.sort_indices()
+    offs = np.concatenate([[0], np.cumsum([p.m for p in parts])])
+    st = run(checker, B.indptr, B.indices, B.data, B.shape[1], seed=7, offsets=offs)
+    assert int(st["nlong"]) > 0
