@@ -173,6 +173,9 @@ struct StoreEpi1 {
       out0[r0 + r] = sr[0][r];
     }
   }
+  struct Row {};
+  __device__ Row load_row(int) const { return Row{}; }
+  __device__ void apply_loaded(int r, const double* v, const Row&) { apply_direct(r, v); }
 };
 struct StoreEpi2 {
   static constexpr bool kTunable = false;
@@ -192,6 +195,9 @@ struct StoreEpi2 {
       out1[r0 + r] = sr[1][r];
     }
   }
+  struct Row {};
+  __device__ Row load_row(int) const { return Row{}; }
+  __device__ void apply_loaded(int r, const double* v, const Row&) { apply_direct(r, v); }
 };
 
 // Per-iteration scalars read from device memory by the fused epilogues: the global part
@@ -292,6 +298,22 @@ struct PrimalEpi {
     step(j, s[0], ld_once(c + j), ld_once(lv + j), ld_once(uv + j), ld_once(x + j),
          need_anchor() ? ld_once(x0 + j) : 0.0);
   }
+  // the row's inputs loaded ahead of its product (long-row pass), then the step
+  struct Row {
+    double a[5];
+  };
+  __device__ Row load_row(int j) const {
+    Row r;
+    r.a[0] = ld_once(c + j);
+    r.a[1] = ld_once(lv + j);
+    r.a[2] = ld_once(uv + j);
+    r.a[3] = ld_once(x + j);
+    r.a[4] = need_anchor() ? ld_once(x0 + j) : 0.0;
+    return r;
+  }
+  __device__ void apply_loaded(int j, const double* s, const Row& r) {
+    step(j, s[0], r.a[0], r.a[1], r.a[2], r.a[3], r.a[4]);
+  }
   // Epilogue of a slot's rows r0 + r (r = lane + 32 k < nr): every load first, then the
   // updates, so the loads of all rows are in flight together.
   __device__ void apply_rows(int r0, int nr, int lane, const double (*sr)[MAX_SLOT_ROWS]) {
@@ -373,6 +395,20 @@ struct DualEpi {
     step(i, s[0], ld_once(lo + i), ld_once(hi + i), ld_once(y + i),
          need_anchor() ? ld_once(y0 + i) : 0.0);
   }
+  struct Row {
+    double a[4];
+  };
+  __device__ Row load_row(int i) const {
+    Row r;
+    r.a[0] = ld_once(lo + i);
+    r.a[1] = ld_once(hi + i);
+    r.a[2] = ld_once(y + i);
+    r.a[3] = need_anchor() ? ld_once(y0 + i) : 0.0;
+    return r;
+  }
+  __device__ void apply_loaded(int i, const double* s, const Row& r) {
+    step(i, s[0], r.a[0], r.a[1], r.a[2], r.a[3]);
+  }
   __device__ void apply_rows(int r0, int nr, int lane, const double (*sr)[MAX_SLOT_ROWS]) {
     constexpr int R = MAX_SLOT_ROWS / LANES;
     double lj[R], hj[R], yj[R], aj[R];
@@ -429,6 +465,8 @@ struct DualEpi {
 #endif
 static_assert(LANE_ITEMS % DPDLP_PK_BATCH == 0 && LANE_ITEMS / DPDLP_PK_BATCH >= 2,
               "a lane holds at least two pipeline batches (both are loaded before the sums)");
+static_assert(DPDLP_PK_BATCH % 4 == 0,
+              "indices (and FP32 values) of a batch are read four at a time with 16-byte loads");
 #ifndef DPDLP_EPI_BATCH
 #define DPDLP_EPI_BATCH 1
 #endif
@@ -667,6 +705,9 @@ __global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_i
   if (b < nb) {
     const int i = b;
     if (!epi.inst(M.long_inst[i])) return;  // uniform over the block
+    const int row = M.long_row[i];
+    typename Epi::Row in{};
+    if (threadIdx.x == 0) in = epi.load_row(row);  // in flight during the sums
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       double a = 0.0;
@@ -676,7 +717,7 @@ __global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_i
     }
     if (threadIdx.x == 0) {
       epi.prepare(M.long_inst[i]);
-      epi.apply_direct(M.long_row[i], v);
+      epi.apply_loaded(row, v, in);
     }
     return;
   }
@@ -686,6 +727,9 @@ __global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_i
     const int lane = threadIdx.x & 31;
     if (i >= nb + nw) return;
     if (!epi.inst(M.long_inst[i])) return;  // uniform over the warp
+    const int row = M.long_row[i];
+    typename Epi::Row in{};
+    if (lane == 0) in = epi.load_row(row);
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       double a = 0.0;
@@ -697,7 +741,7 @@ __global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_i
     }
     if (lane == 0) {
       epi.prepare(M.long_inst[i]);
-      epi.apply_direct(M.long_row[i], v);
+      epi.apply_loaded(row, v, in);
     }
     return;
   }
@@ -705,6 +749,8 @@ __global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_i
   const int i = nb + nw + b * TPB + threadIdx.x;
   if (i >= M.nlong) return;
   if (!epi.inst(M.long_inst[i])) return;
+  const int row = M.long_row[i];
+  const typename Epi::Row in = epi.load_row(row);
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
     double a = 0.0;
@@ -713,7 +759,7 @@ __global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_i
     v[k] = a;
   }
   epi.prepare(M.long_inst[i]);
-  epi.apply_direct(M.long_row[i], v);
+  epi.apply_loaded(row, v, in);
 }
 
 template <int NV, int W, class Epi>
