@@ -215,6 +215,42 @@ def job_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
     return units_per_rank * world / (ms_max / 1e3)
 
 
+def cusparse_reference(lp, dev, kb, reps=30):
+    """CUDA-event time of torch's CSR matrix-vector product (cuSPARSE SpMV) for A x and A^T y
+    on the LP's matrix (FP64 values, int32 indices), with the bytes of the product alone
+    (12 per nonzero + row pointers + the gathered and written vectors)."""
+    import numpy as np
+    import scipy.sparse as sp
+    import torch
+
+    d = f"cuda:{dev}"
+    A = sp.csr_matrix((lp.val, lp.col, lp.row_ptr), shape=(lp.m, lp.n))
+    At = A.T.tocsr()
+    out = {}
+    for name, M, nin in (("A_x", A, lp.n), ("AT_y", At, lp.m)):
+        T = torch.sparse_csr_tensor(torch.from_numpy(M.indptr.astype(np.int32)).to(d),
+                                    torch.from_numpy(M.indices.astype(np.int32)).to(d),
+                                    torch.from_numpy(M.data).to(d), size=M.shape, dtype=torch.float64)
+        v = torch.rand(nin, 1, dtype=torch.float64, device=d)
+        for _ in range(3):
+            T @ v
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            T @ v
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        by = 12 * M.nnz + 4 * (M.shape[0] + 1) + 8 * nin + 8 * M.shape[0]
+        out[name] = {"ms": ms, "GB/s": by / (ms * 1e-3) / 1e9}
+        del T, v
+    torch.cuda.empty_cache()
+    out["note"] = ("torch.sparse_csr_tensor @ dense (cuSPARSE SpMV); the solver's primal / dual "
+                   "kernels compute A^T y / A x_bar plus the whole primal / dual step")
+    return out
+
+
 def run_reference(args, world, rank):
     """The CPU oracle on the same workload and metric: one PDHG iteration per step."""
     if rank != 0:
@@ -566,6 +602,15 @@ def main():
                    "fp64_frac": fp64_ops[k] / (kt[k] * 1e-3) / 1e9 / fp64_peak}
                for k in kt}
 
+    # ---- library reference point: cuSPARSE CSR SpMV (through torch) on the same matrix,
+    # A x and A^T y in FP64, timed like the fused kernels (which do more: the product plus
+    # the primal or dual step).  Not on the solver's path.
+    spmv_ref = None
+    try:
+        spmv_ref = cusparse_reference(lp, dev, kb)
+    except Exception as exc:  # report, do not fail the benchmark
+        spmv_ref = {"error": str(exc)[:200]}
+
     # ---- mixed-precision form: FP32 matrix values (FP64 products), same steps
     s.set_param("spmv_fp32", 2)
     s.set_param("resume", 0)
@@ -672,7 +717,7 @@ def main():
                    "block_permute": 1, "tiles_csr": info["tiles_csr"], "tiles_csc": info["tiles_csc"],
                    "cta_slots": {"primal": tuned["cta_slots_primal"], "dual": tuned["cta_slots_dual"]}},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-        "roofline": roofline, "kernels": kernels, "forms": forms,
+        "roofline": roofline, "kernels": kernels, "spmv_cusparse": spmv_ref, "forms": forms,
         "fp64_peak_Gops": fp64_peak, "time_to_tol": ttt, "preprocess_ms": info["preprocess_ms"],
         "cpu_baseline": cpu, "batch": batch, "warm_start": warm,
     }
