@@ -84,6 +84,10 @@ struct DevPacked {
   const int32_t* long_ptr = nullptr;
   const int32_t* long_piece = nullptr;
   double* piece_sum = nullptr;  // 2 * npieces (room for two vectors)
+  // batches: slots of the running instances, rebuilt at every check (nullptr for one LP)
+  const int32_t* slot_off = nullptr;  // ninst + 1: instance i owns slots [slot_off[i], slot_off[i+1])
+  int32_t* active = nullptr;          // nslots: slot ids of running instances, instance order
+  int32_t* nactive = nullptr;         // 1: entries of active in use
 };
 
 // Row order chosen by the packing of one orientation (pre-order = after the block
@@ -167,6 +171,7 @@ struct DevVecs {
   InstScalars* inst = nullptr;                        // [ninst]
   double* wtab = nullptr;                             // [ninst][2][KMAX] Halpern weights
   int ninst = 1;
+  int32_t* act_off = nullptr;                         // 2 (ninst + 1): offsets into the active lists
   int32_t *perm_col = nullptr, *perm_row = nullptr;    // internal index -> caller index
   double *tmp_n = nullptr, *tmp_m = nullptr, *tmp_n2 = nullptr;  // scratch vectors
   double *pw = nullptr;                                // power-iteration scalars [ninst][4]
@@ -221,12 +226,16 @@ cudaError_t launch_primal(const DevPacked& csc, const DevVecs& v, const DevScala
                           IterPlan p, cudaStream_t s);
 cudaError_t launch_dual(const DevPacked& csr, const DevVecs& v, const DevScalars* sc,
                         IterPlan p, cudaStream_t s);
-// out0 = M x0 (and out1 = M x1 when x1 != nullptr) for one packed orientation M.
+// out0 = M x0 (and out1 = M x1 when x1 != nullptr) for one packed orientation M; with
+// `running` (a batch's instance scalars) only the rows of running instances are computed.
 cudaError_t launch_spmv(const DevPacked& M, const double* x0, const double* x1, double* out0,
-                        double* out1, cudaStream_t s);
+                        double* out1, cudaStream_t s, const InstScalars* running);
 cudaError_t launch_check(const DevPacked& csr, const DevPacked& csc, const DevVecs& v,
                          DevScalars* sc, unsigned long long cond_handle, int use_cond,
                          cudaStream_t s);
+// Batches: rebuild both orientations' lists of slots of running instances.
+cudaError_t launch_compact(const DevPacked& csr, const DevPacked& csc, const DevVecs& v,
+                           cudaStream_t s);
 cudaError_t launch_fill_start(const DevVecs& v, int fresh_x, int fresh_y, cudaStream_t s);
 // out[i] = in[perm[i]] * scale[i] (scale may be nullptr: 1)
 cudaError_t launch_gather(const double* in, const int32_t* perm, const double* scale,

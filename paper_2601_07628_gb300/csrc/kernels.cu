@@ -161,9 +161,13 @@ __device__ __forceinline__ void prefetch_rows(const double* const (&arr)[NA], in
 
 struct StoreEpi1 {
   static constexpr bool kTunable = false;
+  static constexpr bool kListable = true;
   double* out0;
+  const InstScalars* itab;  // nullptr: every row; else rows of running instances only
+  int listed;               // walk the active-slot list (batches)
   __device__ bool begin() { return true; }
-  __device__ bool inst(int) { return true; }
+  __device__ bool all_slots() const { return !listed; }
+  __device__ bool inst(int i) { return !itab || itab[i].status == -1; }
   __device__ void prepare(int) {}
   __device__ void prefetch(int, int, int) {}
   __device__ bool fp32() const { return false; }  // KKT and step-size products: FP64 values
@@ -179,9 +183,13 @@ struct StoreEpi1 {
 };
 struct StoreEpi2 {
   static constexpr bool kTunable = false;
+  static constexpr bool kListable = true;
   double *out0, *out1;
+  const InstScalars* itab;
+  int listed;
   __device__ bool begin() { return true; }
-  __device__ bool inst(int) { return true; }
+  __device__ bool all_slots() const { return !listed; }
+  __device__ bool inst(int i) { return !itab || itab[i].status == -1; }
   __device__ void prepare(int) {}
   __device__ void prefetch(int, int, int) {}
   __device__ bool fp32() const { return false; }
@@ -251,10 +259,12 @@ __device__ __forceinline__ void load_inst_steps(const InstScalars* tab, const do
 template <bool Single>
 struct PrimalEpi {
   static constexpr bool kTunable = true;
+  static constexpr bool kListable = !Single;  // one LP never uses the active-slot list
   const DevScalars* sc;
   const InstScalars* itab;
   const double* wtab;
   IterPlan plan;
+  int listed;  // batches: walk the active-slot list (all slots when timing)
   const double *c, *lv, *uv, *x0;
   double *x, *xbar, *xh, *dx;
   IterScalars q;
@@ -269,6 +279,7 @@ struct PrimalEpi {
     return go && (st == -1 || plan.force_regular);
   }
   __device__ bool inst(int i) { return Single || load_inst_mode(itab, i, plan, q); }
+  __device__ bool all_slots() const { return !listed || plan.force_regular; }
   __device__ void prepare(int i) {
     if (!Single) load_inst_steps(itab, wtab, i, plan, true, q);
   }
@@ -347,10 +358,12 @@ struct PrimalEpi {
 template <bool Single>
 struct DualEpi {
   static constexpr bool kTunable = true;
+  static constexpr bool kListable = !Single;  // one LP never uses the active-slot list
   const DevScalars* sc;
   const InstScalars* itab;
   const double* wtab;
   IterPlan plan;
+  int listed;  // batches: walk the active-slot list (all slots when timing)
   const double *lo, *hi, *y0;
   double *y, *yh;
   IterScalars q;
@@ -365,6 +378,7 @@ struct DualEpi {
     return go && (st == -1 || plan.force_regular);
   }
   __device__ bool inst(int i) { return Single || load_inst_mode(itab, i, plan, q); }
+  __device__ bool all_slots() const { return !listed || plan.force_regular; }
   __device__ void prepare(int i) {
     if (!Single) load_inst_steps(itab, wtab, i, plan, false, q);
   }
@@ -762,8 +776,78 @@ __global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_i
   epi.apply_loaded(row, v, in);
 }
 
+// Batches: a persistent form of the same slot computation.  One wave of resident blocks
+// walks the list of slots of running instances (rebuilt at every check), so once most
+// instances have converged an iteration costs what the running ones need, not a launch
+// over every slot of the batch.  all_slots() (timing, plain products) walks every slot.
+// The persistent loop needs more registers than one slot per warp: 6 resident blocks (80
+// registers) measured faster than 8 (64 registers, spills).
+#ifndef DPDLP_LIST_MIN_BLOCKS
+#define DPDLP_LIST_MIN_BLOCKS 6
+#endif
+#ifndef DPDLP_LIST_PERSISTENT
+#define DPDLP_LIST_PERSISTENT 1
+#endif
+template <int NV, int W, class Epi>
+__global__ void __launch_bounds__(W * LANES, (DPDLP_LIST_MIN_BLOCKS * PK_WARPS) / W)
+    packed_list_kernel(DevPacked M, GatherVecs<NV> g, Epi epi_in) {
+  __shared__ double srow[W][NV][MAX_SLOT_ROWS];
+  Epi epi = epi_in;
+  if (!epi.begin()) return;  // uniform over the launch
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int total = epi.all_slots() ? M.nslots : *M.nactive;
+  // with every instance running the list is the identity (instances keep their order and
+  // own consecutive slots): no indirection then
+  const bool all = total == M.nslots;
+  constexpr int B = DPDLP_PK_BATCH;
+  const unsigned long long pol = l2_evict_first_policy();
+  for (int k = blockIdx.x * W + w; k < total; k += gridDim.x * W) {  // uniform over the warp
+    const int s = all ? k : M.active[k];
+    const SlotDesc sd = M.slots[s];
+    const LaneMeta lm = M.lanes[(size_t)s * LANES + lane];
+    if (!epi.inst(sd.inst)) continue;
+    const size_t off = (size_t)s * SLOT_ITEMS;
+    const uint4* ip = reinterpret_cast<const uint4*>(M.idx + off) + lane;
+    uint32_t c0[B], c1[B];
+    load_idx<B>(ip, 0, c0, pol);
+    load_idx<B>(ip, 1, c1, pol);
+    if (epi.fp32() && M.val32)
+      lane_sums<float, NV, B>(M, g, off, lane, lm.row_local, lm.piece_base, srow[w], ip, pol, c0, c1);
+    else
+      lane_sums<double, NV, B>(M, g, off, lane, lm.row_local, lm.piece_base, srow[w], ip, pol, c0, c1);
+    __syncwarp();
+    epi.prepare(sd.inst);
+    epi.apply_rows(sd.row_base, sd.nrows, lane, srow[w]);
+    __syncwarp();  // the warp's row sums are read before its next slot writes them
+  }
+}
+
+static int sm_count() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached = v > 0 ? v : 1;
+  }
+  return cached;
+}
+
+#ifndef DPDLP_BATCH_LIST
+#define DPDLP_BATCH_LIST 1
+#endif
+
 template <int NV, int W, class Epi>
 static void launch_slots(const DevPacked& M, GatherVecs<NV> g, Epi epi, cudaStream_t s) {
+  if constexpr (Epi::kListable && DPDLP_BATCH_LIST) {
+    if (M.active && epi.listed) {
+      const int resident = sm_count() * ((DPDLP_LIST_MIN_BLOCKS * PK_WARPS) / W);
+      const int need = (M.nslots + W - 1) / W;
+      const int grid = DPDLP_LIST_PERSISTENT && need > resident ? resident : need;
+      packed_list_kernel<NV, W, Epi><<<grid, W * LANES, 0, s>>>(M, g, epi);
+      return;
+    }
+  }
   packed_spmv_kernel<NV, W, Epi><<<(M.nslots + W - 1) / W, W * LANES, 0, s>>>(M, g, epi);
 }
 
@@ -794,26 +878,27 @@ cudaError_t launch_primal(const DevPacked& csc, const DevVecs& v, const DevScala
                           IterPlan p, cudaStream_t s) {
   GatherVecs<1> g{{v.y}};
   if (v.ninst == 1)
-    return launch_packed<1>(csc, g, PrimalEpi<true>{sc, v.inst, v.wtab, p, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, {}}, s);
-  return launch_packed<1>(csc, g, PrimalEpi<false>{sc, v.inst, v.wtab, p, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, {}}, s);
+    return launch_packed<1>(csc, g, PrimalEpi<true>{sc, v.inst, v.wtab, p, 0, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, {}}, s);
+  return launch_packed<1>(csc, g, PrimalEpi<false>{sc, v.inst, v.wtab, p, 1, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, {}}, s);
 }
 
 cudaError_t launch_dual(const DevPacked& csr, const DevVecs& v, const DevScalars* sc,
                         IterPlan p, cudaStream_t s) {
   GatherVecs<1> g{{v.xbar}};
   if (v.ninst == 1)
-    return launch_packed<1>(csr, g, DualEpi<true>{sc, v.inst, v.wtab, p, v.lo, v.hi, v.y0, v.y, v.yh, {}}, s);
-  return launch_packed<1>(csr, g, DualEpi<false>{sc, v.inst, v.wtab, p, v.lo, v.hi, v.y0, v.y, v.yh, {}}, s);
+    return launch_packed<1>(csr, g, DualEpi<true>{sc, v.inst, v.wtab, p, 0, v.lo, v.hi, v.y0, v.y, v.yh, {}}, s);
+  return launch_packed<1>(csr, g, DualEpi<false>{sc, v.inst, v.wtab, p, 1, v.lo, v.hi, v.y0, v.y, v.yh, {}}, s);
 }
 
 cudaError_t launch_spmv(const DevPacked& M, const double* x0, const double* x1, double* out0,
-                        double* out1, cudaStream_t s) {
+                        double* out1, cudaStream_t s, const InstScalars* running) {
+  const int listed = running != nullptr;
   if (x1) {
     GatherVecs<2> g{{x0, x1}};
-    return launch_packed<2>(M, g, StoreEpi2{out0, out1}, s);
+    return launch_packed<2>(M, g, StoreEpi2{out0, out1, running, listed}, s);
   }
   GatherVecs<1> g{{x0}};
-  return launch_packed<1>(M, g, StoreEpi1{out0}, s);
+  return launch_packed<1>(M, g, StoreEpi1{out0, running, listed}, s);
 }
 
 // ---------------------------------------------------------------- check reductions
@@ -1115,14 +1200,93 @@ cudaError_t launch_check(const DevPacked& csr, const DevPacked& csc, const DevVe
                          DevScalars* sc, unsigned long long cond_handle, int use_cond,
                          cudaStream_t s) {
   cudaError_t e;
-  if ((e = launch_spmv(csr, v.xh, v.dx, v.axh, v.adx, s)) != cudaSuccess) return e;
-  if ((e = launch_spmv(csc, v.yh, nullptr, v.aty, nullptr, s)) != cudaSuccess) return e;
+  const InstScalars* running = v.ninst > 1 ? v.inst : nullptr;  // batches: running rows only
+  if ((e = launch_spmv(csr, v.xh, v.dx, v.axh, v.adx, s, running)) != cudaSuccess) return e;
+  if ((e = launch_spmv(csc, v.yh, nullptr, v.aty, nullptr, s, running)) != cudaSuccess) return e;
   if (v.g_rows > 0) reduce_rows_kernel<<<v.g_rows, TPB, 0, s>>>(v);
   if (v.g_cols > 0) reduce_cols_kernel<<<v.g_cols, TPB, 0, s>>>(v);
   control_kernel<<<v.ninst, TPB, 0, s>>>(v, sc);
   finalize_kernel<<<1, TPB, 0, s>>>(v, sc, cond_handle, use_cond);
   const int len = v.n > v.m ? v.n : v.m;
   if (len > 0) apply_kernel<<<(len + TPB - 1) / TPB, TPB, 0, s>>>(v, sc);
+  if (v.ninst > 1) return launch_compact(csr, csc, v, s);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- active-slot lists
+// Exclusive prefix sum over a block (fixed order); *total receives the block's sum.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* sm, int* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sm[w] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int k = 0; k < TPB / 32; ++k) {
+      const int t = sm[k];
+      sm[k] = acc;
+      acc += t;
+    }
+    sm[TPB / 32] = acc;
+  }
+  __syncthreads();
+  const int r = sm[w] + x - v;
+  *total = sm[TPB / 32];
+  __syncthreads();
+  return r;
+}
+
+// act_off[o][i]: first entry of instance i in orientation o's list (o = 0 rows of A, 1 rows
+// of A^T), counting the slots of running instances only; the list lengths go to nactive.
+__global__ void __launch_bounds__(TPB) active_offsets_kernel(DevVecs v, const int32_t* soff_r,
+                                                             const int32_t* soff_c, int32_t* nact_r,
+                                                             int32_t* nact_c) {
+  __shared__ int sm[TPB / 32 + 1];
+  const int N = v.ninst;
+  int carry_r = 0, carry_c = 0;
+  for (int base = 0; base < N; base += TPB) {
+    const int i = base + threadIdx.x;
+    const bool run = i < N && v.inst[i].status == -1;
+    const int cr = run ? soff_r[i + 1] - soff_r[i] : 0;
+    const int cc = run ? soff_c[i + 1] - soff_c[i] : 0;
+    int tr, tc;
+    const int er = block_exclusive_scan(cr, sm, &tr);
+    const int ec = block_exclusive_scan(cc, sm, &tc);
+    if (i < N) {
+      v.act_off[i] = carry_r + er;
+      v.act_off[N + 1 + i] = carry_c + ec;
+    }
+    carry_r += tr;
+    carry_c += tc;
+  }
+  if (threadIdx.x == 0) {
+    v.act_off[N] = carry_r;
+    v.act_off[2 * N + 1] = carry_c;
+    *nact_r = carry_r;
+    *nact_c = carry_c;
+  }
+}
+
+// One block per instance: a running instance's slot ids go to its place in the list.
+__global__ void __launch_bounds__(TPB) active_fill_kernel(DevVecs v, const int32_t* soff,
+                                                          const int32_t* off, int32_t* active) {
+  const int i = blockIdx.x;
+  if (v.inst[i].status != -1) return;
+  const int first = soff[i], count = soff[i + 1] - soff[i], base = off[i];
+  for (int t = threadIdx.x; t < count; t += TPB) active[base + t] = first + t;
+}
+
+cudaError_t launch_compact(const DevPacked& csr, const DevPacked& csc, const DevVecs& v,
+                           cudaStream_t s) {
+  if (!csr.active || !csc.active) return cudaSuccess;
+  active_offsets_kernel<<<1, TPB, 0, s>>>(v, csr.slot_off, csc.slot_off, csr.nactive, csc.nactive);
+  active_fill_kernel<<<v.ninst, TPB, 0, s>>>(v, csr.slot_off, v.act_off, csr.active);
+  active_fill_kernel<<<v.ninst, TPB, 0, s>>>(v, csc.slot_off, v.act_off + v.ninst + 1, csc.active);
   return cudaGetLastError();
 }
 
@@ -1223,8 +1387,8 @@ __global__ void scale_kernel(double* vv, const double* u, const double* pw, cons
 cudaError_t launch_power_round(const DevPacked& csr, const DevPacked& csc, const DevVecs& v,
                                double* vec_v, double* vec_w, double* vec_u, cudaStream_t s) {
   cudaError_t e;
-  if ((e = launch_spmv(csr, vec_v, nullptr, vec_w, nullptr, s)) != cudaSuccess) return e;
-  if ((e = launch_spmv(csc, vec_w, nullptr, vec_u, nullptr, s)) != cudaSuccess) return e;
+  if ((e = launch_spmv(csr, vec_v, nullptr, vec_w, nullptr, s, nullptr)) != cudaSuccess) return e;
+  if ((e = launch_spmv(csc, vec_w, nullptr, vec_u, nullptr, s, nullptr)) != cudaSuccess) return e;
   // partials live in the check-reduction buffers (NRED doubles per chunk)
   if (v.g_rows > 0) sumsq_kernel<<<v.g_rows, TPB, 0, s>>>(vec_w, v.chunk_rows, v.red_rows);
   if (v.g_cols > 0) sumsq_kernel<<<v.g_cols, TPB, 0, s>>>(vec_u, v.chunk_cols, v.red_cols);

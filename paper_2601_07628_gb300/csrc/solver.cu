@@ -672,6 +672,24 @@ int load_impl(dpdlp* h, int32_t count, const int32_t* row_off, const int32_t* co
   int rc;
   if ((rc = upload_packed(h, Hr, h->csr))) return rc;
   if ((rc = upload_packed(h, Hc, h->csc))) return rc;
+  if (count > 1) {  // per-instance slot ranges and the active-slot lists of a batch
+    for (int o = 0; o < 2; ++o) {
+      const HostPacked& Hp = o == 0 ? Hr : Hc;
+      DevPacked& D = o == 0 ? h->csr : h->csc;
+      std::vector<int32_t> soff(count + 1, 0);
+      for (const SlotDesc& d : Hp.slots) ++soff[d.inst + 1];
+      for (int i = 0; i < count; ++i) soff[i + 1] += soff[i];
+      int32_t *d_soff, *d_act, *d_nact;
+      if ((rc = dalloc(h, &d_soff, count + 1)) || (rc = dalloc(h, &d_act, Hp.slots.size())) ||
+          (rc = dalloc(h, &d_nact, 1)))
+        return rc;
+      CK(cudaMemcpy(d_soff, soff.data(), (count + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+      CK(cudaMemset(d_nact, 0, sizeof(int32_t)));
+      D.slot_off = d_soff;
+      D.active = d_act;
+      D.nactive = d_nact;
+    }
+  }
   h->csc.cta_slots = (int)h->P("cta_slots_primal");
   h->csr.cta_slots = (int)h->P("cta_slots_dual");
   DevVecs& v = h->v;
@@ -729,6 +747,7 @@ int load_impl(dpdlp* h, int32_t count, const int32_t* row_off, const int32_t* co
   if ((rc = dalloc(h, &v.perm_row, m))) return rc;
   if ((rc = dalloc(h, &v.pw, 4 * (size_t)count))) return rc;
   if ((rc = dalloc(h, &v.inst, count))) return rc;
+  if ((rc = dalloc(h, &v.act_off, 2 * ((size_t)count + 1)))) return rc;
   if ((rc = dalloc(h, &v.wtab, (size_t)count * 2 * KMAX))) return rc;
   if ((rc = dalloc(h, &v.sched, 1))) return rc;
   h->trace_cap = (int)h->P("trace_capacity");
@@ -880,6 +899,7 @@ int dpdlp_solve(dpdlp_t* h, double tol, int64_t max_iter) {
   CK(cudaMemcpyAsync(h->d_sc, &s, sizeof(DevScalars), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->v.inst, h->h_inst.data(), h->ninst * sizeof(InstScalars),
                      cudaMemcpyHostToDevice, h->stream));
+  CK(launch_compact(h->csr, h->csc, h->v, h->stream));  // a batch: every instance is running
   if (h->P("use_graph") != 0.0) {
     if (h->graph_K != s.K || !h->exec) {
       CK(cudaStreamSynchronize(h->stream));
@@ -1107,7 +1127,7 @@ int dpdlp_apply_A(dpdlp_t* h, const double* x, double* out) {
   CK(cudaSetDevice(h->device));
   int rc;
   if ((rc = import_vec(h, x, h->v.tmp_n2, h->v.perm_col, h->n, h->v.tmp_n, h->d_cw))) return rc;
-  CK(launch_spmv(h->csr, h->v.tmp_n2, nullptr, h->v.axh, nullptr, h->stream));
+  CK(launch_spmv(h->csr, h->v.tmp_n2, nullptr, h->v.axh, nullptr, h->stream, nullptr));
   return export_vec(h, h->v.axh, out, h->v.perm_row, h->m, h->v.tmp_m, h->d_rw);
 }
 
@@ -1117,7 +1137,7 @@ int dpdlp_apply_AT(dpdlp_t* h, const double* y, double* out) {
   CK(cudaSetDevice(h->device));
   int rc;
   if ((rc = import_vec(h, y, h->v.axh, h->v.perm_row, h->m, h->v.tmp_m, h->d_rw))) return rc;
-  CK(launch_spmv(h->csc, h->v.axh, nullptr, h->v.tmp_n2, nullptr, h->stream));
+  CK(launch_spmv(h->csc, h->v.axh, nullptr, h->v.tmp_n2, nullptr, h->stream, nullptr));
   return export_vec(h, h->v.tmp_n2, out, h->v.perm_col, h->n, h->v.tmp_n, h->d_cw);
 }
 
