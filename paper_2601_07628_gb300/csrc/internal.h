@@ -220,6 +220,7 @@ void build_packed(int rows, int cols, const std::vector<int64_t>& ptr,
 struct IterPlan {
   int i;              // iteration index inside the graph body
   int force_regular;  // 1: run as a regular iteration regardless of the scalars (timing)
+  int list;           // batches: 1 walk the active-slot list, 0 one launch over every slot
 };
 
 cudaError_t launch_primal(const DevPacked& csc, const DevVecs& v, const DevScalars* sc,
@@ -233,6 +234,10 @@ cudaError_t launch_spmv(const DevPacked& M, const double* x0, const double* x1, 
 cudaError_t launch_check(const DevPacked& csr, const DevPacked& csc, const DevVecs& v,
                          DevScalars* sc, unsigned long long cond_handle, int use_cond,
                          cudaStream_t s);
+// Batches: set the graph conditional `handle` to 1 when fewer than half of the slots are
+// active (the next body walks the lists), else 0.
+cudaError_t launch_select(const DevPacked& csr, const DevPacked& csc, unsigned long long handle,
+                          cudaStream_t s);
 // Batches: rebuild both orientations' lists of slots of running instances.
 cudaError_t launch_compact(const DevPacked& csr, const DevPacked& csc, const DevVecs& v,
                            cudaStream_t s);

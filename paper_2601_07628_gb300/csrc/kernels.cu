@@ -879,7 +879,7 @@ cudaError_t launch_primal(const DevPacked& csc, const DevVecs& v, const DevScala
   GatherVecs<1> g{{v.y}};
   if (v.ninst == 1)
     return launch_packed<1>(csc, g, PrimalEpi<true>{sc, v.inst, v.wtab, p, 0, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, {}}, s);
-  return launch_packed<1>(csc, g, PrimalEpi<false>{sc, v.inst, v.wtab, p, 1, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, {}}, s);
+  return launch_packed<1>(csc, g, PrimalEpi<false>{sc, v.inst, v.wtab, p, p.list, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, {}}, s);
 }
 
 cudaError_t launch_dual(const DevPacked& csr, const DevVecs& v, const DevScalars* sc,
@@ -887,7 +887,7 @@ cudaError_t launch_dual(const DevPacked& csr, const DevVecs& v, const DevScalars
   GatherVecs<1> g{{v.xbar}};
   if (v.ninst == 1)
     return launch_packed<1>(csr, g, DualEpi<true>{sc, v.inst, v.wtab, p, 0, v.lo, v.hi, v.y0, v.y, v.yh, {}}, s);
-  return launch_packed<1>(csr, g, DualEpi<false>{sc, v.inst, v.wtab, p, 1, v.lo, v.hi, v.y0, v.y, v.yh, {}}, s);
+  return launch_packed<1>(csr, g, DualEpi<false>{sc, v.inst, v.wtab, p, p.list, v.lo, v.hi, v.y0, v.y, v.yh, {}}, s);
 }
 
 cudaError_t launch_spmv(const DevPacked& M, const double* x0, const double* x1, double* out0,
@@ -1279,6 +1279,19 @@ __global__ void __launch_bounds__(TPB) active_fill_kernel(DevVecs v, const int32
   if (v.inst[i].status != -1) return;
   const int first = soff[i], count = soff[i + 1] - soff[i], base = off[i];
   for (int t = threadIdx.x; t < count; t += TPB) active[base + t] = first + t;
+}
+
+__global__ void select_kernel(const int32_t* nact_r, int nslots_r, const int32_t* nact_c,
+                              int nslots_c, unsigned long long handle) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const long long active = (long long)*nact_r + *nact_c, total = (long long)nslots_r + nslots_c;
+  cudaGraphSetConditional((cudaGraphConditionalHandle)handle, 2 * active < total ? 1u : 0u);
+}
+
+cudaError_t launch_select(const DevPacked& csr, const DevPacked& csc, unsigned long long handle,
+                          cudaStream_t s) {
+  select_kernel<<<1, 32, 0, s>>>(csr.nactive, csr.nslots, csc.nactive, csc.nslots, handle);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_compact(const DevPacked& csr, const DevPacked& csc, const DevVecs& v,

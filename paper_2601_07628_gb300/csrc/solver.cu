@@ -450,19 +450,62 @@ int build_graph(dpdlp* h, int K) {
   cudaGraphNode_t node;
   CK(cudaGraphAddNode(&node, h->graph, nullptr, nullptr, 0, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  CK(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
-                                   cudaStreamCaptureModeThreadLocal));
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  // K iterations captured into graph g after `deps`
+  auto capture_iters = [&](cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps, int list) {
+    cudaError_t e = cudaStreamBeginCaptureToGraph(h->cap_stream, g, deps, nullptr, ndeps, mode);
+    for (int i = 0; i < K && e == cudaSuccess; ++i) {
+      e = launch_primal(h->csc, h->v, h->d_sc, IterPlan{i, 0, list}, h->cap_stream);
+      if (e == cudaSuccess) e = launch_dual(h->csr, h->v, h->d_sc, IterPlan{i, 0, list}, h->cap_stream);
+    }
+    cudaGraph_t captured = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &captured);
+    return e != cudaSuccess ? e : e2;
+  };
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < K && e == cudaSuccess; ++i) {
-    e = launch_primal(h->csc, h->v, h->d_sc, IterPlan{i, 0}, h->cap_stream);
-    if (e == cudaSuccess) e = launch_dual(h->csr, h->v, h->d_sc, IterPlan{i, 0}, h->cap_stream);
+  if (h->ninst == 1) {  // one capture: the iterations, then the check
+    e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, mode);
+    for (int i = 0; i < K && e == cudaSuccess; ++i) {
+      e = launch_primal(h->csc, h->v, h->d_sc, IterPlan{i, 0, 0}, h->cap_stream);
+      if (e == cudaSuccess) e = launch_dual(h->csr, h->v, h->d_sc, IterPlan{i, 0, 0}, h->cap_stream);
+    }
+    if (e == cudaSuccess)
+      e = launch_check(h->csr, h->csc, h->v, h->d_sc, (unsigned long long)handle, 1, h->cap_stream);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &captured);
+    if (e == cudaSuccess) e = e2;
+  } else {
+    // a batch: a select kernel sets the IF condition from the active-slot counts, then the
+    // body's iterations walk the lists (IF) or launch over every slot (ELSE), then the check
+    cudaGraphConditionalHandle sel;
+    CK(cudaGraphConditionalHandleCreate(&sel, body, 0, 0));
+    e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, mode);
+    if (e == cudaSuccess) e = launch_select(h->csr, h->csc, (unsigned long long)sel, h->cap_stream);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &captured);
+    if (e == cudaSuccess) e = e2;
+    cudaGraphNode_t sel_node = nullptr, if_node = nullptr;
+    if (e == cudaSuccess) {
+      size_t nn = 1;
+      CK(cudaGraphGetNodes(body, &sel_node, &nn));
+      cudaGraphNodeParams ip{};
+      ip.type = cudaGraphNodeTypeConditional;
+      ip.conditional.handle = sel;
+      ip.conditional.type = cudaGraphCondTypeIf;
+      ip.conditional.size = 2;
+      CK(cudaGraphAddNode(&if_node, body, &sel_node, nullptr, 1, &ip));
+      e = capture_iters(ip.conditional.phGraph_out[0], nullptr, 0, 1);
+      if (e == cudaSuccess) e = capture_iters(ip.conditional.phGraph_out[1], nullptr, 0, 0);
+    }
+    if (e == cudaSuccess) {
+      e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, &if_node, nullptr, 1, mode);
+      if (e == cudaSuccess)
+        e = launch_check(h->csr, h->csc, h->v, h->d_sc, (unsigned long long)handle, 1, h->cap_stream);
+      const cudaError_t e3 = cudaStreamEndCapture(h->cap_stream, &captured);
+      if (e == cudaSuccess) e = e3;
+    }
   }
-  if (e == cudaSuccess)
-    e = launch_check(h->csr, h->csc, h->v, h->d_sc, (unsigned long long)handle, 1, h->cap_stream);
-  cudaGraph_t captured = nullptr;
-  cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &captured);
   if (e != cudaSuccess) return fail(h, DPDLP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  if (e2 != cudaSuccess) return fail(h, DPDLP_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e2));
   CK(cudaGraphInstantiate(&h->exec, h->graph, 0));
   h->graph_K = K;
   return 0;
@@ -471,9 +514,17 @@ int build_graph(dpdlp* h, int K) {
 int run_host_loop(dpdlp* h) {
   const int K = h->h_sc.K;
   for (;;) {
+    int list = 0;
+    if (h->ninst > 1) {  // the same choice the graph's select kernel makes
+      int32_t na[2] = {0, 0};
+      CK(cudaMemcpyAsync(&na[0], h->csr.nactive, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaMemcpyAsync(&na[1], h->csc.nactive, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      list = 2LL * (na[0] + na[1]) < (long long)h->csr.nslots + h->csc.nslots ? 1 : 0;
+    }
     for (int i = 0; i < K; ++i) {
-      CK(launch_primal(h->csc, h->v, h->d_sc, IterPlan{i, 0}, h->stream));
-      CK(launch_dual(h->csr, h->v, h->d_sc, IterPlan{i, 0}, h->stream));
+      CK(launch_primal(h->csc, h->v, h->d_sc, IterPlan{i, 0, list}, h->stream));
+      CK(launch_dual(h->csr, h->v, h->d_sc, IterPlan{i, 0, list}, h->stream));
     }
     CK(launch_check(h->csr, h->csc, h->v, h->d_sc, 0ULL, 0, h->stream));
     int status = -1;
@@ -1155,7 +1206,7 @@ int dpdlp_time_kernel(dpdlp_t* h, const char* which, int32_t reps, double* avg_m
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const IterPlan p{0, 1};
+  const IterPlan p{0, 1, 0};
   CK(cudaEventRecord(e0, h->stream));
   for (int r = 0; r < reps; ++r) {
     if (w == "primal") CK(launch_primal(h->csc, h->v, h->d_sc, p, h->stream));

@@ -231,3 +231,19 @@ def test_autotune_applies_and_caches(Solver, tmp_path):
     assert r2["cached"] and r2["cta_slots_primal"] == r["cta_slots_primal"]
     s.close()
     s2.close()
+
+
+def test_batch_graph_and_host_loop_agree(Solver):
+    """The graph's device-side choice between the active-slot lists and one launch over every
+    slot, and the host loop's choice of the same, give bit-identical results (the choice
+    changes the launch, never the arithmetic)."""
+    lps = small_batch()
+    out = []
+    for use_graph in (1, 0):
+        s = Solver()
+        s.set_param("use_graph", use_graph)
+        s.load_batch(lps)
+        assert s.solve(1e-6, 200_000) == 0
+        out.append(s.solution())
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
