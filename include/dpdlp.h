@@ -37,6 +37,7 @@
 #ifndef DPDLP_H
 #define DPDLP_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -124,6 +125,17 @@ void dpdlp_destroy(dpdlp_t* h);
 
 /* Description of the last error on this handle ("" if none); valid until the next call. */
 const char* dpdlp_last_error(const dpdlp_t* h);
+
+/* Device allocator hook: every device buffer of the loaded LP (matrix copies, vectors,
+ * scalars, trace) comes from alloc(bytes, ctx) and goes back through
+ * release(ptr, bytes, ctx) instead of cudaMalloc / cudaFree -- for instance a framework's
+ * caching allocator.  alloc returns memory on the handle's device aligned to 256 bytes
+ * (else the load fails with DPDLP_ERR_INVALID), or NULL (DPDLP_ERR_OOM).  Setting an
+ * allocator unloads the current LP (its memory goes back to the allocator it came from);
+ * NULL, NULL restores cudaMalloc.  The library synchronises its stream before releasing. */
+typedef void* (*dpdlp_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*dpdlp_release_fn)(void* ptr, size_t bytes, void* ctx);
+int dpdlp_set_allocator(dpdlp_t* h, dpdlp_alloc_fn alloc, dpdlp_release_fn release, void* ctx);
 
 /* Use `cuda_stream` (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream) for
  * all later work of the handle; NULL restores the handle's own stream.  The caller keeps

@@ -110,8 +110,11 @@ struct dpdlp {
   cudaGraphExec_t exec = nullptr;
   int graph_K = -1;
 
-  std::vector<void*> allocs;
+  std::vector<std::pair<void*, size_t>> allocs;
   int64_t dev_bytes = 0;
+  dpdlp_alloc_fn alloc_fn = nullptr;  // caller's allocator (nullptr: cudaMalloc)
+  dpdlp_release_fn release_fn = nullptr;
+  void* alloc_ctx = nullptr;
   dpdlp_info_t info{};
 
   double P(const char* k) const { return params.at(k).value; }
@@ -136,12 +139,22 @@ template <class T>
 int dalloc(dpdlp* h, T** p, size_t count) {
   *p = nullptr;
   const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
-  cudaError_t e = cudaMalloc((void**)p, bytes);
-  if (e != cudaSuccess) {
-    *p = nullptr;
-    return fail(h, DPDLP_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  if (h->alloc_fn) {
+    void* q = h->alloc_fn(bytes, h->alloc_ctx);
+    if (!q) return fail(h, DPDLP_ERR_OOM, "the allocator hook returned NULL");
+    if (reinterpret_cast<uintptr_t>(q) % 256 != 0) {
+      h->release_fn(q, bytes, h->alloc_ctx);
+      return fail(h, DPDLP_ERR_INVALID, "the allocator hook returned memory not aligned to 256 bytes");
+    }
+    *p = static_cast<T*>(q);
+  } else {
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) {
+      *p = nullptr;
+      return fail(h, DPDLP_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
   }
-  h->allocs.push_back(*p);
+  h->allocs.emplace_back(*p, bytes);
   h->dev_bytes += bytes;
   return 0;
 }
@@ -157,7 +170,10 @@ void free_graph(dpdlp* h) {
 void free_problem(dpdlp* h) {
   free_graph(h);
   if (h->stream) cudaStreamSynchronize(h->stream);
-  for (void* p : h->allocs) cudaFree(p);
+  for (const auto& a : h->allocs) {
+    if (h->release_fn) h->release_fn(a.first, a.second, h->alloc_ctx);
+    else cudaFree(a.first);
+  }
   h->allocs.clear();
   h->dev_bytes = 0;
   h->csr = DevPacked{};
@@ -569,6 +585,17 @@ void dpdlp_destroy(dpdlp_t* h) {
 }
 
 const char* dpdlp_last_error(const dpdlp_t* h) { return h ? h->err.c_str() : "null handle"; }
+
+int dpdlp_set_allocator(dpdlp_t* h, dpdlp_alloc_fn alloc, dpdlp_release_fn release, void* ctx) {
+  if (!h || (alloc == nullptr) != (release == nullptr))
+    return fail(h, DPDLP_ERR_INVALID, "allocator: give both functions or neither");
+  cudaSetDevice(h->device);
+  free_problem(h);  // buffers go back to the allocator they came from
+  h->alloc_fn = alloc;
+  h->release_fn = release;
+  h->alloc_ctx = ctx;
+  return 0;
+}
 
 int dpdlp_set_stream(dpdlp_t* h, void* s) {
   if (!h) return DPDLP_ERR_INVALID;

@@ -59,11 +59,15 @@ class Info(C.Structure):
                 ("device_bytes", C.c_int64), ("preprocess_ms", C.c_double)]
 
 
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+RELEASE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+
 EXPORTS = {
     "dpdlp_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int]),
     "dpdlp_destroy": (None, [C.c_void_p]),
     "dpdlp_last_error": (C.c_char_p, [C.c_void_p]),
     "dpdlp_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dpdlp_set_allocator": (C.c_int, [C.c_void_p, ALLOC_FN, RELEASE_FN, C.c_void_p]),
     "dpdlp_load_lp": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dpdlp_load_batch": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
@@ -140,6 +144,7 @@ class Solver:
         rc = self.lib.dpdlp_create(C.byref(h), int(device))
         if rc < 0:
             raise DpdlpError(rc, "dpdlp_create failed (no CUDA device?)")
+        self.device = int(device)
         self.h = h
         self.device = int(device)
         self.n = self.m = 0
@@ -258,6 +263,34 @@ class Solver:
         buf = (KKT * cnt)()
         self._check(self.lib.dpdlp_get_batch_kkt(self.h, buf, cnt))
         return [{f: getattr(buf[i], f) for f, _ in KKT._fields_} for i in range(cnt)]
+
+    def use_torch_allocator(self, on: bool = True):
+        """Take the device buffers of the LP from torch's caching allocator (on=True) or from
+        cudaMalloc (on=False).  Unloads the current LP; call before load / load_batch."""
+        if not on:
+            self._check(self.lib.dpdlp_set_allocator(self.h, ALLOC_FN(), RELEASE_FN(), None))
+            self._alloc_cbs = None
+            return self
+        import torch
+
+        dev = self.device
+
+        def _alloc(nbytes, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), device=dev)
+            except Exception:
+                return None
+
+        def _release(ptr, nbytes, ctx):
+            try:
+                torch.cuda.caching_allocator_delete(ptr)
+            except Exception:
+                pass
+
+        cbs = (ALLOC_FN(_alloc), RELEASE_FN(_release))  # kept alive with the solver
+        self._check(self.lib.dpdlp_set_allocator(self.h, cbs[0], cbs[1], None))
+        self._alloc_cbs = cbs
+        return self
 
     def set_row_bounds(self, lc, uc):
         lc, uc = _host_f64(lc, self.m), _host_f64(uc, self.m)
