@@ -25,6 +25,7 @@ import dataclasses
 import math
 
 import numpy as np
+import scipy.sparse as sp
 
 EQ, LE, GE = 0, 1, 2
 
@@ -49,6 +50,7 @@ class LP:
     y_star: np.ndarray | None = None
     z_star: np.ndarray | None = None
     name: str = "lp"
+    q: np.ndarray | None = None  # float64 [n] >= 0: diagonal QP objective 1/2 x^T diag(q) x + c^T x
 
     @property
     def nnz(self) -> int:
@@ -393,3 +395,36 @@ def transport_lp(fam: dict, seed: int) -> LP:
     lc, uc = bounds_from_types(ctype, b)
     return LP(n, m, c, row_ptr, col, val, lc, uc, lv, uv, ctype, b, None, None, None,
               name=f"transport_lp(S={S},D={D},R={R},seed={seed})")
+
+
+# ---------------------------------------------------------------- diagonal QP (LASSO)
+def lasso_qp(seed: int, rows: int, cols: int, density: float = 0.1, lam: float = 0.1):
+    """LASSO min 1/2 ||M x - d||^2 + lam ||x||_1 written as a diagonal QP over (x, r, t):
+    min 1/2 r^T r + lam 1^T t  s.t.  M x - r = d,  x - t <= 0,  x + t >= 0,  t >= 0
+    (Q = I on r, 0 elsewhere).  M is sparse N(0,1) with the given density, d = M x_true + noise
+    for a sparse x_true.  Returns (LP with q set, {"M", "d", "lam", "x": indices of x})."""
+    rng = np.random.default_rng(seed)
+    Msp = sp.random(rows, cols, density=density, random_state=np.random.RandomState(seed),
+                    data_rvs=rng.standard_normal, format="csr")
+    M = Msp.toarray()
+    xt = np.where(rng.random(cols) < 0.2, rng.standard_normal(cols), 0.0)
+    d = M @ xt + 0.1 * rng.standard_normal(rows)
+    I_c, I_r = sp.identity(cols, format="csr"), sp.identity(rows, format="csr")
+    Z_rc = sp.csr_matrix((rows, cols))
+    Z_cr = sp.csr_matrix((cols, rows))
+    A = sp.vstack([sp.hstack([Msp, -I_r, Z_rc]),      # M x - r = d
+                   sp.hstack([I_c, Z_cr, -I_c]),      # x - t <= 0
+                   sp.hstack([I_c, Z_cr, I_c])]).tocsr()  # x + t >= 0
+    A.sort_indices()
+    n = 2 * cols + rows
+    m = rows + 2 * cols
+    ctype = np.concatenate([np.full(rows, EQ), np.full(cols, LE), np.full(cols, GE)]).astype(np.int8)
+    b = np.concatenate([d, np.zeros(2 * cols)])
+    c = np.concatenate([np.zeros(cols + rows), np.full(cols, lam)])
+    q = np.concatenate([np.zeros(cols), np.ones(rows), np.zeros(cols)])
+    lv = np.concatenate([np.full(cols + rows, -np.inf), np.zeros(cols)])
+    uv = np.full(n, np.inf)
+    lc, uc = bounds_from_types(ctype, b)
+    lp = LP(n, m, c, A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data.astype(np.float64),
+            lc, uc, lv, uv, ctype, b, name=f"lasso_qp(seed={seed},rows={rows},cols={cols})", q=q)
+    return lp, {"M": M, "d": d, "lam": lam, "x": np.arange(cols)}

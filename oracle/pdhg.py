@@ -75,10 +75,14 @@ DEFAULTS = dict(
 
 # ----------------------------------------------------------------------------- problem data
 class OracleLP:
-    """LP of Eq. prob:primal: min c^T x, lc <= A x <= uc, lv <= x <= uv (CSR input)."""
+    """LP of Eq. prob:primal: min c^T x, lc <= A x <= uc, lv <= x <= uv (CSR input).
 
-    def __init__(self, n, m, c, row_ptr, col, val, lc, uc, lv, uv):
+    With ``q`` (the diagonal of a positive semidefinite Q, Section "Extensions to Diagonal
+    QPs") the objective is 1/2 x^T Q x + c^T x: the diagonal QP the same iteration solves."""
+
+    def __init__(self, n, m, c, row_ptr, col, val, lc, uc, lv, uv, q=None):
         self.n, self.m = int(n), int(m)
+        self.q = None if q is None else np.asarray(q, dtype=np.float64).copy()
         self.c = np.asarray(c, dtype=np.float64).copy()
         self.lc = np.asarray(lc, dtype=np.float64).copy()
         self.uc = np.asarray(uc, dtype=np.float64).copy()
@@ -189,7 +193,10 @@ def pdhg_step(lp: OracleLP, x, y, tau, sigma):
 
     Returns (x^, y^, x_bar, z)."""
     g = lp.c - lp.ATy(y)
-    xh = proj_X(x - tau * g, lp.lv, lp.uv)
+    if lp.q is None:
+        xh = proj_X(x - tau * g, lp.lv, lp.uv)
+    else:  # diagonal QP (Eq. primal_update): per coordinate a clamped 1-D quadratic minimum
+        xh = proj_X((x - tau * g) / (1.0 + tau * lp.q), lp.lv, lp.uv)
     xbar = 2.0 * xh - x
     z = lp.Ax(xbar)
     w = y / sigma - z
@@ -224,11 +231,12 @@ def kkt(lp: OracleLP, x, y, tau, bnorm=None, cnorm=None, row_w=None, col_w=None)
     if cnorm is None:
         cnorm = float(np.linalg.norm(lp.c))
     ax = lp.Ax(x)
+    quad = 0.0 if lp.q is None else float(np.dot(lp.q * x, x))  # x^T Q x of a diagonal QP
     rp_vec = ax - proj_S(ax, lp.lc, lp.uc)
     if row_w is not None:
         rp_vec = rp_vec * row_w
     r_p = float(np.linalg.norm(rp_vec)) / (1.0 + bnorm)
-    g = lp.c - lp.ATy(y)
+    g = lp.c - lp.ATy(y) if lp.q is None else lp.c + lp.q * x - lp.ATy(y)  # objective gradient
     xt = x - tau * g
     px = proj_X(xt, lp.lv, lp.uv)
     rd_vec = px - x
@@ -236,8 +244,8 @@ def kkt(lp: OracleLP, x, y, tau, bnorm=None, cnorm=None, row_w=None, col_w=None)
         rd_vec = rd_vec * col_w
     r_d = float(np.linalg.norm(rd_vec)) / tau / (1.0 + cnorm)
     s = (px - xt) / tau
-    obj_p = float(np.dot(lp.c, x))
-    obj_d = -p_fun(-y, lp.lc, lp.uc) + float(np.dot(s, x))
+    obj_p = float(np.dot(lp.c, x)) + 0.5 * quad
+    obj_d = -p_fun(-y, lp.lc, lp.uc) + float(np.dot(s, x)) - 0.5 * quad
     r_g = abs(obj_p - obj_d) / (1.0 + max(abs(obj_p), abs(obj_d)))
     return dict(r_primal=r_p, r_dual=r_d, r_gap=r_g, obj_p=obj_p, obj_d=obj_d)
 

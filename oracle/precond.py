@@ -63,7 +63,8 @@ def scaled_lp(lp: pdhg.OracleLP, dr, dc) -> pdhg.OracleLP:
     A = (sp.diags(dr) @ lp.A @ sp.diags(dc)).tocsr()
     A.sort_indices()
     return pdhg.OracleLP(lp.n, lp.m, dc * lp.c, A.indptr, A.indices, A.data, dr * lp.lc,
-                         dr * lp.uc, lp.lv / dc, lp.uv / dc)
+                         dr * lp.uc, lp.lv / dc, lp.uv / dc,
+                         None if lp.q is None else dc * dc * lp.q)
 
 
 def solve(lp: pdhg.OracleLP, eps=1e-8, max_iter=100_000, params=None, x_start=None,
