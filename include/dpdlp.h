@@ -184,6 +184,15 @@ int dpdlp_load_batch(dpdlp_t* h, int32_t count, const int32_t* row_off, const in
  * "eta" parameter, when > 0, still takes precedence. */
 int dpdlp_set_batch_eta(dpdlp_t* h, const double* eta, int32_t count);
 
+/* Diagonal QP (Section "Extensions to Diagonal QPs"): objective 1/2 x^T diag(q) x + c^T x
+ * with q[n] >= 0 finite (HOST array, caller order); q = NULL restores the LP.  The primal
+ * step becomes the clamped minimum of the separable quadratic (Eq. primal_update),
+ * x^ = proj_X((x - tau (c - A^T y)) / (1 + tau q)); KKT errors use the objective gradient
+ * c + Q x^ - A^T y^ and the objectives carry the quadratic term.  Resets the solver
+ * state; a later dpdlp_load_lp / dpdlp_load_batch clears it.  For a batch, q covers the
+ * stacked variables (zeros for the instances that are LPs). */
+int dpdlp_set_objective_diag(dpdlp_t* h, const double* q);
+
 /* Replace the row bounds with general ranges lc[m] <= A x <= uc[m] (HOST arrays, +-inf
  * allowed, lc <= uc, no NaN).  Resets the solver state. */
 int dpdlp_set_row_bounds(dpdlp_t* h, const double* lc, const double* uc);

@@ -37,7 +37,7 @@ constexpr int LONG_WARP_PIECES = 32;
 // Thread-block size of the element-wise and reduction kernels.
 constexpr int TPB = 256;
 constexpr int KMAX = 1024;  // largest check period (iterations per graph body)
-constexpr int NRED = 5;     // quantities per check reduction (rows and columns)
+constexpr int NRED = 6;     // quantities per check reduction (rows and columns)
 
 // Slot s: its short rows have the new indices [row_base, row_base + nrows); all belong to
 // LP instance `inst` (a slot never mixes instances of a batch).
@@ -156,6 +156,7 @@ struct DevVecs {
   double *lo = nullptr, *hi = nullptr;                // [m]: the box -S = [-uc, -lc]
   double *x = nullptr, *x0 = nullptr, *xbar = nullptr, *xh = nullptr, *dx = nullptr;  // [n]
   double *aty = nullptr;                               // [n]
+  double *q = nullptr;                                 // [n] diagonal of Q (nullptr: an LP)
   double *y = nullptr, *y0 = nullptr, *yh = nullptr;   // [m]
   double *axh = nullptr, *adx = nullptr;               // [m]
   double *red_rows = nullptr, *red_cols = nullptr;     // reduction partials [chunks][NRED]

@@ -256,7 +256,7 @@ __device__ __forceinline__ void load_inst_steps(const InstScalars* tab, const do
 //   Halpern: x <- w1 ((1+gamma) x^ - gamma x) + w0 x0   (with gamma = 1 the reflected point
 //   is x_bar itself), regular iterations;
 //   check iteration: keep x = x^k, store x^ and dx = x^k - x^.
-template <bool Single>
+template <bool Single, bool QP = false>
 struct PrimalEpi {
   static constexpr bool kTunable = true;
   static constexpr bool kListable = !Single;  // one LP never uses the active-slot list
@@ -267,6 +267,7 @@ struct PrimalEpi {
   int listed;  // batches: walk the active-slot list (all slots when timing)
   const double *c, *lv, *uv, *x0;
   double *x, *xbar, *xh, *dx;
+  const double* qd;  // diagonal of Q of a diagonal QP (nullptr: an LP)
   IterScalars q;
   // Single: one instance, whose scalars are loaded once per launch in begin()
   __device__ bool begin() {
@@ -292,7 +293,11 @@ struct PrimalEpi {
   __device__ bool need_anchor() const { return q.halpern && !q.check; }
   __device__ void step(int j, double s, double cj, double lvj, double uvj, double xj,
                        double x0j) {
-    const double xhj = clampd(fma(-q.step, cj - s, xj), lvj, uvj);
+    double t = fma(-q.step, cj - s, xj);
+    // diagonal QP: the minimum of 1/2 Q_jj x^2 + (c_j - s) x + (x - x_j)^2 / (2 tau) over the
+    // box is the clamped x = (x_j - tau (c_j - s)) / (1 + tau Q_jj)  (Eq. primal_update)
+    if constexpr (QP) t = t / fma(q.step, ld_once(qd + j), 1.0);
+    const double xhj = clampd(t, lvj, uvj);
     const double xb = fma(2.0, xhj, -xj);
     st_keep(xbar + j, xb);
     if (q.check) {
@@ -877,9 +882,14 @@ static cudaError_t launch_packed(const DevPacked& M, GatherVecs<NV> g, Epi epi, 
 cudaError_t launch_primal(const DevPacked& csc, const DevVecs& v, const DevScalars* sc,
                           IterPlan p, cudaStream_t s) {
   GatherVecs<1> g{{v.y}};
+  if (v.q) {  // a diagonal QP: the prox step divides by 1 + tau Q_jj
+    if (v.ninst == 1)
+      return launch_packed<1>(csc, g, PrimalEpi<true, true>{sc, v.inst, v.wtab, p, 0, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, v.q, {}}, s);
+    return launch_packed<1>(csc, g, PrimalEpi<false, true>{sc, v.inst, v.wtab, p, p.list, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, v.q, {}}, s);
+  }
   if (v.ninst == 1)
-    return launch_packed<1>(csc, g, PrimalEpi<true>{sc, v.inst, v.wtab, p, 0, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, {}}, s);
-  return launch_packed<1>(csc, g, PrimalEpi<false>{sc, v.inst, v.wtab, p, p.list, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, {}}, s);
+    return launch_packed<1>(csc, g, PrimalEpi<true>{sc, v.inst, v.wtab, p, 0, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, nullptr, {}}, s);
+  return launch_packed<1>(csc, g, PrimalEpi<false>{sc, v.inst, v.wtab, p, p.list, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, nullptr, {}}, s);
 }
 
 cudaError_t launch_dual(const DevPacked& csr, const DevVecs& v, const DevScalars* sc,
@@ -910,7 +920,7 @@ cudaError_t launch_spmv(const DevPacked& M, const double* x0, const double* x1, 
 __global__ void __launch_bounds__(TPB) reduce_rows_kernel(DevVecs v) {
   __shared__ double buf[TPB / 32];
   const int4 ch = v.chunk_rows[blockIdx.x];  // {instance, start, length, -}
-  double q[NRED] = {0, 0, 0, 0, 0};
+  double q[NRED] = {0, 0, 0, 0, 0, 0};
   if (v.inst[ch.x].status == -1) {
     for (int i = ch.y + threadIdx.x; i < ch.y + ch.z; i += TPB) {
       const double lc = -v.hi[i], uc = -v.lo[i];
@@ -937,19 +947,24 @@ __global__ void __launch_bounds__(TPB) reduce_rows_kernel(DevVecs v) {
   }
 }
 
-// Column terms at (x^, y^) with the instance's current tau: g = c - A^T y^,
-// xt = x^ - tau g, px = proj_X(xt): [0] (px - x^)^2, [1] (px - xt) x^ (= tau s_j x^_j),
-// [2] c x^, [3] dx^2, [4] (x^ - x0)^2.
+// Column terms at (x^, y^) with the instance's current tau: g = c + Q x^ - A^T y^ (Q = 0
+// for an LP), xt = x^ - tau g, px = proj_X(xt): [0] (px - x^)^2, [1] (px - xt) x^
+// (= tau s_j x^_j), [2] c x^, [3] dx^2, [4] (x^ - x0)^2, [5] Q_jj x^_j^2.
 __global__ void __launch_bounds__(TPB) reduce_cols_kernel(DevVecs v) {
   __shared__ double buf[TPB / 32];
   const int4 ch = v.chunk_cols[blockIdx.x];
-  double q[NRED] = {0, 0, 0, 0, 0};
+  double q[NRED] = {0, 0, 0, 0, 0, 0};
   const InstScalars& I = v.inst[ch.x];
   if (I.status == -1) {
     const double tau = I.tau;
     for (int j = ch.y + threadIdx.x; j < ch.y + ch.z; j += TPB) {
       const double xhj = v.xh[j];
-      const double g = v.c[j] - v.aty[j];
+      double g = v.c[j] - v.aty[j];
+      if (v.q) {
+        const double qx = v.q[j] * xhj;
+        g += qx;
+        q[5] = fma(qx, xhj, q[5]);
+      }
       const double xt = fma(-tau, g, xhj);
       const double px = clampd(xt, v.lv[j], v.uv[j]);
       double d = px - xhj;
@@ -1023,8 +1038,8 @@ __global__ void __launch_bounds__(TPB) control_kernel(DevVecs v, const DevScalar
       const double* C = S[1];
       const double r_p = sqrt(R[0]) / (1.0 + I.bnorm);
       const double r_d = sqrt(C[0]) / tau / (1.0 + I.cnorm);
-      const double obj_p = C[2];
-      const double obj_d = -R[1] + C[1] / tau;
+      const double obj_p = C[2] + 0.5 * C[5];  // C[5] = x^T Q x (0 for an LP)
+      const double obj_d = -R[1] + C[1] / tau - 0.5 * C[5];
       const double r_g = fabs(obj_p - obj_d) / (1.0 + fmax(fabs(obj_p), fabs(obj_d)));
       const double rsq = (omega / eta) * C[3] + (1.0 / (eta * omega)) * R[2] + 2.0 * R[3];
       const double r = sqrt(fmax(0.0, rsq));

@@ -99,6 +99,7 @@ struct dpdlp {
   // on D_r A D_c, x = D_c xs, y = D_r ys; every factor is a power of two
   std::vector<double> dr, dc;
   double *d_dr = nullptr, *d_dc = nullptr, *d_rw = nullptr, *d_cw = nullptr;
+  double* d_q = nullptr;  // diagonal of Q (a diagonal QP), internal order
   std::vector<double> eta_inst;             // power-iteration step size per instance
   bool eta_valid = false;
   std::vector<double> eta_user;             // per-instance step sizes set by the caller
@@ -182,6 +183,7 @@ void free_problem(dpdlp* h) {
   h->xs = h->ys = nullptr;
   h->d_sc = nullptr;
   h->d_dr = h->d_dc = h->d_rw = h->d_cw = nullptr;
+  h->d_q = nullptr;
   h->dr.clear();
   h->dc.clear();
   h->loaded = false;
@@ -915,6 +917,34 @@ int dpdlp_load_batch(dpdlp_t* h, int32_t count, const int32_t* row_off, const in
                      const double* lv, const double* uv, const int8_t* ctype) {
   if (!h) return DPDLP_ERR_INVALID;
   return load_impl(h, count, row_off, col_off, n, m, c, row_ptr, col_idx, val, b, lv, uv, ctype);
+}
+
+int dpdlp_set_objective_diag(dpdlp_t* h, const double* q) {
+  if (!h) return DPDLP_ERR_INVALID;
+  if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
+  CK(cudaSetDevice(h->device));
+  if (q)
+    for (int j = 0; j < h->n; ++j)
+      if (!(q[j] >= 0.0) || !std::isfinite(q[j]))
+        return fail(h, DPDLP_ERR_INVALID, "Q diagonal must be finite and >= 0 at " + std::to_string(j));
+  CK(cudaStreamSynchronize(h->stream));
+  free_graph(h);  // the captured kernels follow the LP / QP choice
+  h->has_state = false;
+  h->pending_state = false;
+  if (!q) {
+    h->v.q = nullptr;
+    return 0;
+  }
+  if (!h->d_q) {
+    int rc;
+    if ((rc = dalloc(h, &h->d_q, h->n))) return rc;
+  }
+  std::vector<double> qi(h->n);  // internal order; the scaled LP's Q is D_c Q D_c
+  for (int j = 0; j < h->n; ++j)
+    qi[j] = q[h->pcol[j]] * (h->dc.empty() ? 1.0 : h->dc[j] * h->dc[j]);
+  if (h->n) CK(cudaMemcpy(h->d_q, qi.data(), h->n * sizeof(double), cudaMemcpyHostToDevice));
+  h->v.q = h->d_q;
+  return 0;
 }
 
 int dpdlp_set_row_bounds(dpdlp_t* h, const double* lc, const double* uc) {

@@ -76,6 +76,7 @@ EXPORTS = {
     "dpdlp_set_batch_eta": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "dpdlp_get_batch_kkt": (C.c_int, [C.c_void_p, C.POINTER(KKT), C.c_int32]),
     "dpdlp_set_row_bounds": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dpdlp_set_objective_diag": (C.c_int, [C.c_void_p, C.c_void_p]),
     "dpdlp_set_param": (C.c_int, [C.c_void_p, C.c_char_p, C.c_double]),
     "dpdlp_get_param": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_double)]),
     "dpdlp_set_start": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -210,6 +211,16 @@ class Solver:
         self.col_off = np.array([0, n], np.int32)
         if ctype is None:
             self.set_row_bounds(lc, uc)
+        if lp is not None and getattr(lp, "q", None) is not None:
+            self.set_objective_diag(lp.q)
+        return self
+
+    def set_objective_diag(self, q):
+        """Diagonal QP: objective 1/2 x^T diag(q) x + c^T x (q = None: the LP again)."""
+        if q is None:
+            self._check(self.lib.dpdlp_set_objective_diag(self.h, None))
+        else:
+            self._check(self.lib.dpdlp_set_objective_diag(self.h, _ptr(_host_f64(q, self.n))))
         return self
 
     def load_batch(self, lps):
@@ -247,6 +258,9 @@ class Solver:
         self.row_off, self.col_off = row_off, col_off
         if not typed:
             self.set_row_bounds(np.concatenate([lp.lc for lp in lps]), np.concatenate([lp.uc for lp in lps]))
+        if any(getattr(lp, "q", None) is not None for lp in lps):
+            self.set_objective_diag(np.concatenate(
+                [lp.q if getattr(lp, "q", None) is not None else np.zeros(lp.n) for lp in lps]))
         return self
 
     def split(self, x, y):
