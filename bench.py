@@ -684,6 +684,16 @@ def main():
             sp_.close()
         import lpgen
 
+        # diagonal QP: a LASSO instance (min 1/2 ||M x - d||^2 + lam ||x||_1 as a QP), 20,000 x
+        # 10,000 M with 0.2 % nonzeros
+        qlp, _ = lpgen.lasso_qp(11, rows=20_000, cols=10_000, density=0.002, lam=0.5)
+        sq = Solver(dev)
+        sq.set_stream(stream)
+        sq.load(qlp)
+        for tol in (1e-4, 1e-6):
+            ttt[f"lasso_qp_{tol:.0e}_fp64"] = time_to_tol(sq, tol, 400_000, 0)
+        sq.close()
+
         sm = Solver(dev)
         sm.set_stream(stream)
         sm.load(lpgen.small_random_lp(0))

@@ -402,13 +402,12 @@ def lasso_qp(seed: int, rows: int, cols: int, density: float = 0.1, lam: float =
     """LASSO min 1/2 ||M x - d||^2 + lam ||x||_1 written as a diagonal QP over (x, r, t):
     min 1/2 r^T r + lam 1^T t  s.t.  M x - r = d,  x - t <= 0,  x + t >= 0,  t >= 0
     (Q = I on r, 0 elsewhere).  M is sparse N(0,1) with the given density, d = M x_true + noise
-    for a sparse x_true.  Returns (LP with q set, {"M", "d", "lam", "x": indices of x})."""
+    for a sparse x_true.  Returns (LP with q set, {"M" (CSR), "d", "lam", "x": indices of x})."""
     rng = np.random.default_rng(seed)
     Msp = sp.random(rows, cols, density=density, random_state=np.random.RandomState(seed),
                     data_rvs=rng.standard_normal, format="csr")
-    M = Msp.toarray()
     xt = np.where(rng.random(cols) < 0.2, rng.standard_normal(cols), 0.0)
-    d = M @ xt + 0.1 * rng.standard_normal(rows)
+    d = Msp @ xt + 0.1 * rng.standard_normal(rows)
     I_c, I_r = sp.identity(cols, format="csr"), sp.identity(rows, format="csr")
     Z_rc = sp.csr_matrix((rows, cols))
     Z_cr = sp.csr_matrix((cols, rows))
@@ -427,4 +426,4 @@ def lasso_qp(seed: int, rows: int, cols: int, density: float = 0.1, lam: float =
     lc, uc = bounds_from_types(ctype, b)
     lp = LP(n, m, c, A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data.astype(np.float64),
             lc, uc, lv, uv, ctype, b, name=f"lasso_qp(seed={seed},rows={rows},cols={cols})", q=q)
-    return lp, {"M": M, "d": d, "lam": lam, "x": np.arange(cols)}
+    return lp, {"M": Msp, "d": d, "lam": lam, "x": np.arange(cols)}

@@ -84,7 +84,7 @@ def test_lasso_reaches_its_optimum(Solver):
     x, _ = s.solution()
     k = s.kkt()
     assert max(k["r_primal"], k["r_dual"], k["r_gap"]) <= 1e-8
-    M, d, lam = meta["M"], meta["d"], meta["lam"]
+    M, d, lam = meta["M"].toarray(), meta["d"], meta["lam"]
     L = np.linalg.norm(M, 2) ** 2
     z = np.zeros(M.shape[1])
     for _ in range(100_000):

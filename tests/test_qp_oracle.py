@@ -111,7 +111,7 @@ def test_lasso_reformulation_matches_ista():
     o = O.OracleLP(lp.n, lp.m, lp.c, lp.row_ptr, lp.col, lp.val, lp.lc, lp.uc, lp.lv, lp.uv, lp.q)
     res = O.solve(o, eps=1e-9, max_iter=2_000_000)
     assert res.status == 0
-    M, d, lam = meta["M"], meta["d"], meta["lam"]
+    M, d, lam = meta["M"].toarray(), meta["d"], meta["lam"]
     x = np.zeros(M.shape[1])
     L = np.linalg.norm(M, 2) ** 2
     for _ in range(200_000):
