@@ -401,11 +401,15 @@ def transport_lp(fam: dict, seed: int) -> LP:
 def lasso_qp(seed: int, rows: int, cols: int, density: float = 0.1, lam: float = 0.1):
     """LASSO min 1/2 ||M x - d||^2 + lam ||x||_1 written as a diagonal QP over (x, r, t):
     min 1/2 r^T r + lam 1^T t  s.t.  M x - r = d,  x - t <= 0,  x + t >= 0,  t >= 0
-    (Q = I on r, 0 elsewhere).  M is sparse N(0,1) with the given density, d = M x_true + noise
+    (Q = I on r, 0 elsewhere).  M is sparse N(0,1), round(density * rows) distinct uniform
+    rows per column, d = M x_true + noise
     for a sparse x_true.  Returns (LP with q set, {"M" (CSR), "d", "lam", "x": indices of x})."""
     rng = np.random.default_rng(seed)
-    Msp = sp.random(rows, cols, density=density, random_state=np.random.RandomState(seed),
-                    data_rvs=rng.standard_normal, format="csr")
+    k = np.full(cols, max(1, int(round(density * rows))))  # nonzeros per column of M
+    ri = _distinct_rows_per_column(rng, rows, k)
+    ci = np.repeat(np.arange(cols), k)
+    Msp = sp.csr_matrix((rng.standard_normal(ri.shape[0]), (ri, ci)), shape=(rows, cols))
+    Msp.sort_indices()
     xt = np.where(rng.random(cols) < 0.2, rng.standard_normal(cols), 0.0)
     d = Msp @ xt + 0.1 * rng.standard_normal(rows)
     I_c, I_r = sp.identity(cols, format="csr"), sp.identity(rows, format="csr")
