@@ -45,10 +45,10 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="powerlaw", choices=["powerlaw", "powerlaw_quarter", "small"])
     p.add_argument("--e2e-steps", type=int, default=20)
-    p.add_argument("--tol-runs", default="default", choices=["none", "default", "all"],
+    p.add_argument("--tol-runs", default="default", choices=["none", "small", "default", "all"],
                    help="time-to-tolerance runs: default = small LP to 1e-4 and 1e-8 and the "
                         "benchmark LP to 1e-4 (FP64 and mixed precision); all adds the "
-                        "benchmark LP to 1e-8; none")
+                        "benchmark LP to 1e-8; small = only the small and tiny LPs; none")
     p.add_argument("--cpu-sample-iters", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batch", action="store_true",
@@ -664,7 +664,7 @@ def main():
     # ---- time to tolerance (plain FP64 and mixed precision)
     ttt = {}
     if args.tol_runs != "none" and rank == 0:
-        if args.workload == "powerlaw":
+        if args.workload == "powerlaw" and args.tol_runs != "small":
             for mode in (0, 1):
                 key = f"powerlaw_1e-4_{['fp64', 'mixed_fp32'][mode]}"
                 ttt[key] = time_to_tol(s, 1e-4, 400_000, mode)
@@ -686,13 +686,14 @@ def main():
 
         # diagonal QP: a LASSO instance (min 1/2 ||M x - d||^2 + lam ||x||_1 as a QP), 20,000 x
         # 10,000 M with 0.2 % nonzeros
-        qlp, _ = lpgen.lasso_qp(11, rows=20_000, cols=10_000, density=0.002, lam=0.5)
-        sq = Solver(dev)
-        sq.set_stream(stream)
-        sq.load(qlp)
-        for tol in (1e-4, 1e-6):
-            ttt[f"lasso_qp_{tol:.0e}_fp64"] = time_to_tol(sq, tol, 400_000, 0)
-        sq.close()
+        if args.tol_runs != "small":
+            qlp, _ = lpgen.lasso_qp(11, rows=20_000, cols=10_000, density=0.002, lam=0.5)
+            sq = Solver(dev)
+            sq.set_stream(stream)
+            sq.load(qlp)
+            for tol in (1e-4, 1e-6):
+                ttt[f"lasso_qp_{tol:.0e}_fp64"] = time_to_tol(sq, tol, 400_000, 0)
+            sq.close()
 
         sm = Solver(dev)
         sm.set_stream(stream)
@@ -701,6 +702,18 @@ def main():
             for mode in (0, 1):
                 ttt[f"small_lp_{tol:.0e}_{['fp64', 'mixed_fp32'][mode]}"] = time_to_tol(sm, tol, 1_000_000, mode)
         sm.close()
+        # a tiny LP (n=250, m=125, 2 warp slots per packed copy) takes the fused body (one
+        # launch per 64 iterations); the same solve with separate primal / dual launches
+        st_ = Solver(dev)
+        st_.set_stream(stream)
+        st_.load(lpgen.small_random_lp(7, n=250, m=125))
+        for fused in (1, 0):
+            st_.set_param("fused_body", fused)
+            r = time_to_tol(st_, 1e-8, 1_000_000, 0)
+            r["fused_body"] = st_.info()["fused_body"]
+            r["us_per_iteration"] = 1e6 * r["seconds"] / max(r["iterations"], 1)
+            ttt[f"tiny_lp_1e-08_fp64_{['separate_launches', 'fused_body'][fused]}"] = r
+        st_.close()
     s.close()
     batch = None
     if rank == 0 and args.workload == "powerlaw" and not args.no_batch:

@@ -113,6 +113,10 @@ typedef struct dpdlp_info {
   int32_t long_rows, long_cols;           /* rows / columns longer than one lane (32 nonzeros) */
   int64_t device_bytes;
   double preprocess_ms;
+  int32_t fused_body;  /* 1: each graph body (check_every iterations) runs as one launch of one
+                          thread block (parameters fused_body, fused_max_slots); results are
+                          bitwise those of the separate primal / dual launches */
+  int32_t reserved;
 } dpdlp_info_t;
 
 /* Create a handle bound to CUDA device `device`.  Work goes to a stream the handle creates
@@ -222,6 +226,15 @@ int dpdlp_set_row_bounds(dpdlp_t* h, const double* lc, const double* uc);
  *   cta_slots_primal, cta_slots_dual (4): warp slots per thread block of the primal (A^T y)
  *   and dual (A x_bar) iteration kernels, 2, 4 or 8 (64, 128 or 256 threads); a launch
  *   shape only, results do not depend on it (set by the autotuner).
+ *   fused_body (1), fused_max_slots (6, at most 64): a single LP whose packed copies have
+ *   at most fused_max_slots warp slots each (a slot holds 1,024 stored nonzeros) runs each
+ *   graph body -- check_every iterations -- as one launch of one thread block, with block
+ *   barriers between the primal and dual phases, instead of two or three launches per
+ *   iteration.  On a tiny LP an iteration costs launch latency; one SM's FP64 issue rate
+ *   bounds the fused block, so it is faster only up to a few slots per copy.  The sums and
+ *   their order are those of the separate launches, so results are bitwise the same;
+ *   fused_body = 0 always launches the kernels separately.  dpdlp_get_info reports which
+ *   form the next solve takes.
  * Load-time keys (block_permute, perm_block, perm_seed, precond, ruiz_passes,
  * pock_chambolle) take effect at the next dpdlp_load_lp / dpdlp_load_batch.  Unknown key or out-of-range value: DPDLP_ERR_INVALID. */
 int dpdlp_set_param(dpdlp_t* h, const char* key, double v);

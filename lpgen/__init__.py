@@ -279,6 +279,31 @@ def row_length_stress_lp(seed: int, lengths, n: int) -> LP:
               name=f"row_length_stress_lp({seed})")
 
 
+def cross_stress_lp(seed: int, lengths, n: int, dense_cols: dict) -> LP:
+    """LP whose rows have the given lengths (distinct uniform columns, as
+    ``row_length_stress_lp``) and whose columns ``j`` in ``dense_cols`` additionally hold
+    ``dense_cols[j]`` distinct uniform rows, so both A and A^T have rows of chosen lengths;
+    N(0,1) values, '=' / '<=' rows and a planted optimum."""
+    rng = np.random.default_rng(seed)
+    lengths = np.asarray(lengths, dtype=np.int64)
+    m = lengths.shape[0]
+    pairs = set()
+    for i, L in enumerate(lengths):
+        for j in rng.choice(n, size=int(min(L, n)), replace=False):
+            pairs.add((i, int(j)))
+    for j, k in dense_cols.items():
+        for i in rng.choice(m, size=int(min(k, m)), replace=False):
+            pairs.add((int(i), int(j)))
+    pr = np.array(sorted(pairs), dtype=np.int64).reshape(-1, 2)
+    vals = rng.standard_normal(pr.shape[0])
+    row_ptr, col, val = _csr_from_coo(m, n, pr[:, 0], pr[:, 1], vals)
+    ctype = rng.integers(0, 2, size=m).astype(np.int8)  # EQ / LE rows
+    lv, uv, xs, ys, zs, b, c = _planted_optimum(rng, n, m, row_ptr, col, val, ctype)
+    lc, uc = bounds_from_types(ctype, b)
+    return LP(n, m, c, row_ptr, col, val, lc, uc, lv, uv, ctype, b, xs, ys, zs,
+              name=f"cross_stress_lp({seed})")
+
+
 def scaled_powerlaw_lp(seed: int, scale: float) -> LP:
     """The power-law workload shrunk by ``scale`` in n, m and nnz (same recipe, cap scaled)."""
     n = max(2, int(round(4_000_000 * scale)))

@@ -228,6 +228,15 @@ cudaError_t launch_primal(const DevPacked& csc, const DevVecs& v, const DevScala
                           IterPlan p, cudaStream_t s);
 cudaError_t launch_dual(const DevPacked& csr, const DevVecs& v, const DevScalars* sc,
                         IterPlan p, cudaStream_t s);
+// Small single LPs: all K iterations of a graph body in one launch of one thread block,
+// bitwise equal to K pairs of launch_primal / launch_dual.  Applies when both orientations
+// have at most max_slots (<= FUSED_MAX_SLOTS) slots and no block-class long rows.
+constexpr int FUSED_MAX_SLOTS = 64;
+bool fused_body_fits(const DevPacked& csc, const DevPacked& csr, int ninst, int max_slots);
+// Sets the fused kernel's shared-memory limit; called before the first launch or capture.
+cudaError_t fused_body_prepare();
+cudaError_t launch_body_fused(const DevPacked& csc, const DevPacked& csr, const DevVecs& v,
+                              const DevScalars* sc, int K, cudaStream_t s);
 // out0 = M x0 (and out1 = M x1 when x1 != nullptr) for one packed orientation M; with
 // `running` (a batch's instance scalars) only the rows of running instances are computed.
 cudaError_t launch_spmv(const DevPacked& M, const double* x0, const double* x1, double* out0,

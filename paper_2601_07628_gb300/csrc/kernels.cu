@@ -360,7 +360,7 @@ struct PrimalEpi {
 //   w = y / sigma - z,  d = w - proj_{-S}(w),  y^ = sigma d,  -S_i = [lo_i, hi_i] = [-uc_i, -lc_i];
 //   Halpern: y <- w1 ((1+gamma) y^ - gamma y) + w0 y0, with gamma = 1 evaluated as
 //   w1 (2 sigma d - y) + w0 y0; check iteration: keep y = y^k, store y^.
-template <bool Single>
+template <bool Single, bool MirrorY = false>
 struct DualEpi {
   static constexpr bool kTunable = true;
   static constexpr bool kListable = !Single;  // one LP never uses the active-slot list
@@ -372,6 +372,7 @@ struct DualEpi {
   const double *lo, *hi, *y0;
   double *y, *yh;
   IterScalars q;
+  double* ys;  // MirrorY: every new y_i is also written here (the fused body's shared copy)
   // Single: one instance, whose scalars are loaded once per launch in begin()
   __device__ bool begin() {
     if (!Single) return load_global(sc, plan, q);
@@ -405,9 +406,12 @@ struct DualEpi {
       } else {
         r = fma(1.0 + q.gamma, q.step * d, -q.gamma * yi);
       }
-      st_keep(y + i, fma(q.w1, r, q.w0 * y0i));
+      const double yn = fma(q.w1, r, q.w0 * y0i);
+      st_keep(y + i, yn);
+      if constexpr (MirrorY) ys[i] = yn;
     } else {
       st_keep(y + i, q.step * d);
+      if constexpr (MirrorY) ys[i] = q.step * d;
     }
   }
   __device__ void apply_direct(int i, const double* s) {
@@ -496,7 +500,11 @@ struct GatherVecs {
   const double* x[NV];
 };
 
+// Coh: the gathered vector is written earlier in the same launch (fused small-LP body), so
+// it is read with a coherent load instead of the read-only path.
+template <bool Coh = false>
 __device__ __forceinline__ double gather(const double* p) {
+  if constexpr (Coh) return *p;
 #if DPDLP_L2_HINTS && !DPDLP_GATHER_NOALLOC
   double r;
   asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(p), "l"(l2_evict_last_policy()));
@@ -580,7 +588,7 @@ __device__ __forceinline__ void load_idx(const uint4* ip, int b, uint32_t (&c)[B
 // sums (short rows) or to the piece array (long-row pieces).  Three-stage pipeline of
 // batches: indices two batches ahead, values and the x[col] gathers one batch ahead, so
 // gathers are in flight while the FMA chain runs.
-template <typename V, int NV, int B>
+template <typename V, int NV, int B, bool Coh = false>
 __device__ __forceinline__ void lane_sums(const DevPacked& M, const GatherVecs<NV>& g, size_t off,
                                           int lane, int rl, int pid,
                                           double (*srow)[MAX_SLOT_ROWS], const uint4* ip,
@@ -597,7 +605,7 @@ __device__ __forceinline__ void lane_sums(const DevPacked& M, const GatherVecs<N
 #pragma unroll
   for (int j = 0; j < B; ++j) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) x0v[k][j] = gather(g.x[k] + (c0[j] & IDX_MASK));
+    for (int k = 0; k < NV; ++k) x0v[k][j] = gather<Coh>(g.x[k] + (c0[j] & IDX_MASK));
   }
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
@@ -610,7 +618,7 @@ __device__ __forceinline__ void lane_sums(const DevPacked& M, const GatherVecs<N
 #pragma unroll
       for (int j = 0; j < B; ++j) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) x1v[k][j] = gather(g.x[k] + (c1[j] & IDX_MASK));
+        for (int k = 0; k < NV; ++k) x1v[k][j] = gather<Coh>(g.x[k] + (c1[j] & IDX_MASK));
       }
     }
 #pragma unroll
@@ -909,6 +917,149 @@ cudaError_t launch_spmv(const DevPacked& M, const double* x0, const double* x1, 
   }
   GatherVecs<1> g{{x0}};
   return launch_packed<1>(M, g, StoreEpi1{out0, running, listed}, s);
+}
+
+// ---------------------------------------------------------------- fused body (small LPs)
+// On a small LP an iteration costs launch latency, not bandwidth: its two products touch
+// a few hundred kilobytes.  fused_body_kernel runs every iteration of a graph body in one
+// thread block of FB_WARPS warps, phases separated by block barriers: the primal slots
+// (one warp per slot, slots strided over the warps), the long columns, the dual slots, the
+// long rows.  Each phase is the device code of the separate kernels (lane_sums, the
+// epilogues, finish_long_kernel's row classes with the same reduction trees), so the
+// sums, their order and hence the results are bitwise those of the separate launches.  One
+// SM's L2 bandwidth bounds this form, and most of its traffic would be the random gathers
+// (one 32-byte sector per 8-byte value), so the gathered vectors live in shared memory: x_bar
+// only there, y in global memory and mirrored there.  Gathers read them with plain
+// (coherent) loads, and the block barriers order every write before its reads.
+static_assert(!DPDLP_L2_HINTS, "the fused body stores x_bar through a shared-memory pointer");
+constexpr int FB_WARPS = 16;
+constexpr int FB_TPB = FB_WARPS * LANES;
+
+// One product-and-step phase over every slot of M (the packed_spmv_kernel body).
+template <class Epi>
+__device__ __forceinline__ void fused_slots(const DevPacked& M, const GatherVecs<1>& g, Epi& epi,
+                                            double (*srow)[MAX_SLOT_ROWS], int w, int lane) {
+  constexpr int B = DPDLP_PK_BATCH;
+  const unsigned long long pol = l2_evict_first_policy();
+  for (int s = w; s < M.nslots; s += FB_WARPS) {  // uniform over the warp
+    const SlotDesc sd = M.slots[s];
+    const LaneMeta lm = M.lanes[(size_t)s * LANES + lane];
+    const size_t off = (size_t)s * SLOT_ITEMS;
+    const uint4* ip = reinterpret_cast<const uint4*>(M.idx + off) + lane;
+    uint32_t c0[B], c1[B];
+    load_idx<B>(ip, 0, c0, pol);
+    load_idx<B>(ip, 1, c1, pol);
+    if (epi.fp32() && M.val32)
+      lane_sums<float, 1, B, true>(M, g, off, lane, lm.row_local, lm.piece_base, srow, ip, pol, c0, c1);
+    else
+      lane_sums<double, 1, B, true>(M, g, off, lane, lm.row_local, lm.piece_base, srow, ip, pol, c0, c1);
+    __syncwarp();
+    epi.prepare(sd.inst);
+    epi.apply_rows(sd.row_base, sd.nrows, lane, srow);
+    __syncwarp();  // the row sums are read before the warp's next slot writes them
+  }
+}
+
+// The long rows of M with finish_long_kernel's warp-class and thread-class sums (an LP that
+// fits the fused body has no block-class rows: one would need more than 8,192 entries, so
+// the other orientation would have more than FUSED_MAX_SLOTS slots).
+template <class Epi>
+__device__ __forceinline__ void fused_long(const DevPacked& M, Epi& epi, int w, int lane) {
+  const int nw = M.nlong_warp;
+  const double* ps = M.piece_sum;
+  for (int i = w; i < nw; i += FB_WARPS) {  // uniform over the warp
+    const int row = M.long_row[i];
+    typename Epi::Row in{};
+    if (lane == 0) in = epi.load_row(row);
+    double a = 0.0;
+    for (int q = M.long_ptr[i] + lane; q < M.long_ptr[i + 1]; q += LANES) a += ps[M.long_piece[q]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    double v[1];
+    v[0] = a;
+    if (lane == 0) epi.apply_loaded(row, v, in);
+  }
+  for (int i = nw + (int)threadIdx.x; i < M.nlong; i += FB_TPB) {
+    const int row = M.long_row[i];
+    const typename Epi::Row in = epi.load_row(row);
+    double a = 0.0;
+    for (int q = M.long_ptr[i]; q < M.long_ptr[i + 1]; ++q) a += ps[M.long_piece[q]];
+    double v[1];
+    v[0] = a;
+    epi.apply_loaded(row, v, in);
+  }
+}
+
+template <class PEpi>
+__global__ void __launch_bounds__(FB_TPB, 1)
+    fused_body_kernel(DevPacked Mc, DevPacked Mr, PEpi pe_in, DualEpi<true, true> de_in, int K) {
+  __shared__ double srow[FB_WARPS][1][MAX_SLOT_ROWS];
+  extern __shared__ double fb_vecs[];  // y [m], then x_bar [n]
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = Mr.rows, n = Mc.rows;
+  double* ys = fb_vecs;
+  double* xs = fb_vecs + m;
+  for (int i = threadIdx.x; i < m; i += FB_TPB) ys[i] = de_in.y[i];
+  __syncthreads();
+  // x_bar lives only in shared memory (nothing after the body reads it); y is written to
+  // global memory and mirrored here
+  const GatherVecs<1> gp{{ys}}, gd{{xs}};
+  for (int i = 0; i < K; ++i) {
+    // the scalars read by begin() change only at checks, so every thread takes the same
+    // branch, and once the iteration limit is passed it stays passed
+    PEpi pe = pe_in;
+    pe.plan.i = i;
+    pe.xbar = xs;
+    if (!pe.begin()) break;
+    fused_slots(Mc, gp, pe, srow[w], w, lane);
+    __syncthreads();
+    if (Mc.nlong > 0) {
+      fused_long(Mc, pe, w, lane);
+      __syncthreads();
+    }
+    DualEpi<true, true> de = de_in;
+    de.plan.i = i;
+    de.ys = ys;
+    if (!de.begin()) break;
+    fused_slots(Mr, gd, de, srow[w], w, lane);
+    __syncthreads();
+    if (Mr.nlong > 0) {
+      fused_long(Mr, de, w, lane);
+      __syncthreads();
+    }
+  }
+}
+
+// x_bar and y in shared memory: at most FB_VEC_MAX entries together
+constexpr int FB_VEC_MAX = 20480;
+constexpr int FB_DYN_MAX = FB_VEC_MAX * (int)sizeof(double);
+
+bool fused_body_fits(const DevPacked& csc, const DevPacked& csr, int ninst, int max_slots) {
+  return ninst == 1 && max_slots <= FUSED_MAX_SLOTS && csc.nslots <= max_slots &&
+         csr.nslots <= max_slots && csc.nlong_block == 0 && csr.nlong_block == 0 &&
+         (long long)csc.rows + csr.rows <= FB_VEC_MAX;
+}
+
+cudaError_t fused_body_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(fused_body_kernel<PrimalEpi<true>>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, FB_DYN_MAX);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fused_body_kernel<PrimalEpi<true, true>>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, FB_DYN_MAX);
+  return e;
+}
+
+cudaError_t launch_body_fused(const DevPacked& csc, const DevPacked& csr, const DevVecs& v,
+                              const DevScalars* sc, int K, cudaStream_t s) {
+  if (v.ninst != 1 || csc.rows + csr.rows > FB_VEC_MAX) return cudaErrorInvalidValue;
+  const IterPlan p{0, 0, 0};
+  const size_t dyn = (size_t)(csc.rows + csr.rows) * sizeof(double);
+  const DualEpi<true, true> de{sc, v.inst, v.wtab, p, 0, v.lo, v.hi, v.y0, v.y, v.yh, {}, nullptr};
+  if (v.q)
+    fused_body_kernel<<<1, FB_TPB, dyn, s>>>(csc, csr, PrimalEpi<true, true>{sc, v.inst, v.wtab, p, 0, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, v.q, {}}, de, K);
+  else
+    fused_body_kernel<<<1, FB_TPB, dyn, s>>>(csc, csr, PrimalEpi<true>{sc, v.inst, v.wtab, p, 0, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, nullptr, {}}, de, K);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- check reductions

@@ -56,7 +56,8 @@ class Info(C.Structure):
                 ("nnz_padded_csr", C.c_int64), ("nnz_padded_csc", C.c_int64),
                 ("tiles_csr", C.c_int32), ("tiles_csc", C.c_int32),
                 ("long_rows", C.c_int32), ("long_cols", C.c_int32),
-                ("device_bytes", C.c_int64), ("preprocess_ms", C.c_double)]
+                ("device_bytes", C.c_int64), ("preprocess_ms", C.c_double),
+                ("fused_body", C.c_int32), ("reserved", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)

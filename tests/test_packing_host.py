@@ -101,3 +101,30 @@ def test_batch_packing(checker):
     offs = np.concatenate([[0], np.cumsum([p.m for p in parts])])
     st = run(checker, B.indptr, B.indices, B.data, B.shape[1], seed=7, offsets=offs)
     assert int(st["nlong"]) > 0
+
+
+def test_cross_stress_fits_the_fused_body(checker):
+    """The LP the fused-body GPU tests use: long rows of both classes the fused body runs
+    (warp-class, more than 32 pieces, and thread-class) in A and in A^T, within 64 slots per
+    orientation and without block-class rows (more than 256 pieces)."""
+    import scipy.sparse as sp
+
+    lp = lpgen.cross_stress_lp(5, [1500, 1100, 200, 40, 0, 1, 33] + [12] * 1493, 2000,
+                               {5: 1200, 7: 600, 9: 40})
+    A = sp.csr_matrix((lp.val, lp.col, lp.row_ptr), shape=(lp.m, lp.n))
+    assert np.all(np.diff(lp.row_ptr)[:7] >= [1500, 1100, 200, 40, 0, 1, 33])
+    assert np.all(np.diff(A.tocsc().indptr)[[5, 7, 9]] >= [1200, 600, 40])
+    T = A.T.tocsr()
+    T.sort_indices()
+    for k, M in enumerate((A, T)):
+        st = run(checker, M.indptr, M.indices, M.data, M.shape[1], seed=30 + k)
+        lens = np.diff(M.indptr)
+        assert int(st["slots"]) <= 64
+        assert int(st["nlong"]) == int((lens > 32).sum())
+        assert (lens > 32 * 32).any() and ((lens > 32) & (lens <= 32 * 32)).any()
+        assert not (lens > 256 * 32).any()
+    # planted optimum: feasible, and A^T y* + z* = c
+    ax = A @ lp.x_star
+    eq = lp.ctype == lpgen.EQ
+    assert np.allclose(ax[eq], lp.b[eq]) and np.all(ax[~eq] <= lp.b[~eq] + 1e-12)
+    assert np.allclose(A.T @ lp.y_star + lp.z_star, lp.c)
