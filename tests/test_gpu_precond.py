@@ -4,7 +4,6 @@ The GPU scales the LP on the host at load (power-of-two Ruiz and Pock-Chambolle 
 iterates on the scaled LP and reports solutions and KKT errors of the original one; the
 oracle does the same with its own code.  Same 1e-9 parity bar as the plain path.
 """
-import math
 
 import numpy as np
 import pytest

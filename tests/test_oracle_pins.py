@@ -10,7 +10,6 @@ import itertools
 import math
 
 import numpy as np
-import pytest
 
 import lpgen
 import oracle

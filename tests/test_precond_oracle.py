@@ -6,7 +6,6 @@ scaling (the primal residual and both objectives are those of the original LP at
 mapped point); the identity case reproducing the plain solve bit for bit; and convergence
 to the planted optimum of a generator LP at 1e-8.
 """
-import math
 
 import numpy as np
 import pytest
