@@ -12,6 +12,7 @@
 #include <cmath>
 #include <numeric>
 
+#include "host_parallel.h"
 #include "internal.h"
 
 namespace pdhg {
@@ -68,8 +69,13 @@ void plan_packing(int rows, const std::vector<int64_t>& ptr, PackPlan& P) {
       piece_lanes.push_back(lane);
     }
   }
-  std::stable_sort(to_fit.begin(), to_fit.end(),
-                   [&](int32_t a, int32_t b) { return segs[a].usage > segs[b].usage; });
+  {  // stable order by decreasing usage (1..LANE_ITEMS): one bucket per usage value
+    std::vector<int32_t> start(LANE_ITEMS + 2, 0), sorted(to_fit.size());
+    for (int32_t g : to_fit) ++start[LANE_ITEMS + 1 - segs[g].usage];
+    for (int u = 1; u <= LANE_ITEMS + 1; ++u) start[u] += start[u - 1];
+    for (int32_t g : to_fit) sorted[start[LANE_ITEMS - segs[g].usage]++] = g;
+    to_fit.swap(sorted);
+  }
   std::vector<std::vector<int32_t>> bucket(LANE_ITEMS);  // open lanes by free room 1..31
   for (int32_t s : to_fit) {
     const int u = segs[s].usage;
@@ -235,43 +241,61 @@ void build_packed(int rows, int cols, const std::vector<int64_t>& ptr,
   out.idx.assign(out.stored, 0u);
   out.slots = P.slots;
   out.lanes.assign((size_t)out.nslots * LANES, LaneMeta{0, 0});
-  int32_t piece_counter = 0;
+  // global id of the first piece in each slot (pieces are numbered in slot / lane order),
+  // so that slots can be filled independently
+  std::vector<int32_t> slot_piece(out.nslots + 1, 0);
   for (int s = 0; s < out.nslots; ++s) {
-    double* sv = out.val.data() + (size_t)s * SLOT_ITEMS;
-    uint32_t* si = out.idx.data() + (size_t)s * SLOT_ITEMS;
-    int32_t rows_before = 0;
+    int32_t c = 0;
     for (int l = 0; l < LANES; ++l) {
-      LaneMeta& lm = out.lanes[(size_t)s * LANES + l];
-      lm.row_local = rows_before;
-      lm.piece_base = piece_counter;
       const int32_t lane = P.slot_lanes[(size_t)s * LANES + l];
       if (lane < 0) continue;
-      int p = 0;
+      for (int k = P.lane_ptr[lane]; k < P.lane_ptr[lane + 1]; ++k) c += P.segs[k].piece >= 0;
+    }
+    slot_piece[s + 1] = slot_piece[s] + c;
+  }
+  const std::vector<int64_t> parts = even_parts(out.nslots, host_threads());
+  std::vector<char> exact(parts.size() - 1, 1);  // per part: every value fits FP32 exactly
+  run_parts(parts, [&](int part, int64_t s0, int64_t s1) {
+    bool ok = true;
+    for (int64_t s = s0; s < s1; ++s) {
+      double* sv = out.val.data() + (size_t)s * SLOT_ITEMS;
+      uint32_t* si = out.idx.data() + (size_t)s * SLOT_ITEMS;
       float* sf = out.val32.data() + (size_t)s * SLOT_ITEMS;
-      auto put = [&](double v, uint32_t c) {
-        sv[((p >> 1) * LANES + l) * 2 + (p & 1)] = v;
-        si[((p >> 2) * LANES + l) * 4 + (p & 3)] = c;
-        const float f = (float)v;
-        if (v != 0.0 && !(std::isfinite(f) && std::fabs(f) >= FLT_MIN)) out.fp32_exact_range = false;
-        sf[((p >> 2) * LANES + l) * 4 + (p & 3)] = f;
-        ++p;
-      };
-      for (int k = P.lane_ptr[lane]; k < P.lane_ptr[lane + 1]; ++k) {
-        const PackPlan::Seg& g = P.segs[k];
-        const uint32_t end = END_BIT | (g.piece >= 0 ? PIECE_BIT : 0u);
-        if (g.piece >= 0) ++piece_counter; else ++rows_before;
-        if (g.count == 0) {  // empty row: one stored zero carries its end flag
-          put(0.0, end);
-          continue;
-        }
-        const int64_t e0 = ptr[g.row] + g.first;
-        for (int q = 0; q < g.count; ++q) {
-          const uint32_t c = (uint32_t)col_new_of_old[idx[e0 + q]];
-          put(val[e0 + q], c | (q == g.count - 1 ? end : 0u));
+      int32_t rows_before = 0, piece_counter = slot_piece[s];
+      for (int l = 0; l < LANES; ++l) {
+        LaneMeta& lm = out.lanes[(size_t)s * LANES + l];
+        lm.row_local = rows_before;
+        lm.piece_base = piece_counter;
+        const int32_t lane = P.slot_lanes[(size_t)s * LANES + l];
+        if (lane < 0) continue;
+        int p = 0;
+        auto put = [&](double v, uint32_t c) {
+          sv[((p >> 1) * LANES + l) * 2 + (p & 1)] = v;
+          si[((p >> 2) * LANES + l) * 4 + (p & 3)] = c;
+          const float f = (float)v;
+          if (v != 0.0 && !(std::isfinite(f) && std::fabs(f) >= FLT_MIN)) ok = false;
+          sf[((p >> 2) * LANES + l) * 4 + (p & 3)] = f;
+          ++p;
+        };
+        for (int k = P.lane_ptr[lane]; k < P.lane_ptr[lane + 1]; ++k) {
+          const PackPlan::Seg& g = P.segs[k];
+          const uint32_t end = END_BIT | (g.piece >= 0 ? PIECE_BIT : 0u);
+          if (g.piece >= 0) ++piece_counter; else ++rows_before;
+          if (g.count == 0) {  // empty row: one stored zero carries its end flag
+            put(0.0, end);
+            continue;
+          }
+          const int64_t e0 = ptr[g.row] + g.first;
+          for (int q = 0; q < g.count; ++q) {
+            const uint32_t c = (uint32_t)col_new_of_old[idx[e0 + q]];
+            put(val[e0 + q], c | (q == g.count - 1 ? end : 0u));
+          }
         }
       }
     }
-  }
+    exact[part] = ok;
+  });
+  for (char e : exact) out.fp32_exact_range = out.fp32_exact_range && e;
   out.long_row.resize(P.nlong);
   for (int i = 0; i < P.nlong; ++i) out.long_row[i] = P.new_of_old[P.long_rows[i]];
   out.long_inst = P.long_inst;

@@ -12,6 +12,7 @@
 #include <cstring>
 #include <numeric>
 
+#include "host_parallel.h"
 #include "internal.h"
 
 namespace pdhg {
@@ -70,43 +71,90 @@ void permute_csr(int rows, int cols, const int64_t* ptr, const int32_t* idx, con
   const int64_t nnz = optr[rows];
   oidx.resize(nnz);
   oval.resize(nnz);
-  std::vector<std::pair<int32_t, double>> buf;
-  for (int r = 0; r < rows; ++r) {
-    const int64_t s = ptr[prow[r]], e = ptr[prow[r] + 1];
-    buf.resize(e - s);
-    bool sorted = true;
-    for (int64_t k = s; k < e; ++k) {
-      buf[k - s] = {inv_col[idx[k]], val[k]};
-      if (k > s && buf[k - s].first < buf[k - s - 1].first) sorted = false;
+  // rows are independent: threads take ranges of new rows of about equal nonzeros
+  run_parts(balanced_rows(rows, optr.data(), host_threads()), [&](int, int64_t r0, int64_t r1) {
+    std::vector<std::pair<int32_t, double>> buf;
+    for (int64_t r = r0; r < r1; ++r) {
+      const int64_t s = ptr[prow[r]], e = ptr[prow[r] + 1];
+      buf.resize(e - s);
+      bool sorted = true;
+      for (int64_t k = s; k < e; ++k) {
+        buf[k - s] = {inv_col[idx[k]], val[k]};
+        if (k > s && buf[k - s].first < buf[k - s - 1].first) sorted = false;
+      }
+      if (!sorted)
+        std::stable_sort(buf.begin(), buf.end(),
+                         [](const std::pair<int32_t, double>& a,
+                            const std::pair<int32_t, double>& b) { return a.first < b.first; });
+      for (size_t k = 0; k < buf.size(); ++k) {
+        oidx[optr[r] + k] = buf[k].first;
+        oval[optr[r] + k] = buf[k].second;
+      }
     }
-    if (!sorted)
-      std::stable_sort(buf.begin(), buf.end(),
-                       [](const std::pair<int32_t, double>& a,
-                          const std::pair<int32_t, double>& b) { return a.first < b.first; });
-    for (size_t k = 0; k < buf.size(); ++k) {
-      oidx[optr[r] + k] = buf[k].first;
-      oval[optr[r] + k] = buf[k].second;
-    }
-  }
+  });
 }
 
+// Stable counting sort by column.  In parallel: each thread counts the columns of its own
+// range of rows, a thread's entries of column j go after those of the earlier threads'
+// rows, and each thread then places its rows in order -- the sequential result exactly.
 void transpose_csr(int rows, int cols, const std::vector<int64_t>& ptr,
                    const std::vector<int32_t>& idx, const std::vector<double>& val,
                    std::vector<int64_t>& tptr, std::vector<int32_t>& tidx,
                    std::vector<double>& tval) {
   const int64_t nnz = ptr[rows];
   tptr.assign(cols + 1, 0);
-  for (int64_t e = 0; e < nnz; ++e) tptr[idx[e] + 1]++;
-  for (int j = 0; j < cols; ++j) tptr[j + 1] += tptr[j];
-  std::vector<int64_t> pos(tptr.begin(), tptr.end() - 1);
   tidx.resize(nnz);
   tval.resize(nnz);
-  for (int r = 0; r < rows; ++r)
-    for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) {
-      const int64_t p = pos[idx[e]]++;
-      tidx[p] = r;
-      tval[p] = val[e];
+  // per-thread column counts cost threads x cols x 4 bytes: at most one thread per cols
+  // nonzeros, and at most 256 MB of counts
+  int T = (int)std::min<int64_t>(host_threads(), nnz / std::max(cols, 1));
+  T = (int)std::min<int64_t>(T, ((int64_t)1 << 26) / std::max(cols, 1));
+  if (nnz >= INT32_MAX) T = 1;  // the parallel form keeps positions in 32 bits
+  if (T <= 1) {
+    for (int64_t e = 0; e < nnz; ++e) tptr[idx[e] + 1]++;
+    for (int j = 0; j < cols; ++j) tptr[j + 1] += tptr[j];
+    std::vector<int64_t> pos(tptr.begin(), tptr.end() - 1);
+    for (int r = 0; r < rows; ++r)
+      for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) {
+        const int64_t p = pos[idx[e]]++;
+        tidx[p] = r;
+        tval[p] = val[e];
+      }
+    return;
+  }
+  const std::vector<int64_t> rb = balanced_rows(rows, ptr.data(), T);
+  T = (int)rb.size() - 1;
+  std::vector<std::vector<int32_t>> cnt(T);
+  run_parts(rb, [&](int t, int64_t r0, int64_t r1) {
+    std::vector<int32_t>& c = cnt[t];
+    c.assign(cols, 0);
+    for (int64_t e = ptr[r0]; e < ptr[r1]; ++e) c[idx[e]]++;
+  });
+  for (int j = 0; j < cols; ++j) {
+    int64_t a = 0;
+    for (int t = 0; t < T; ++t) a += cnt[t][j];
+    tptr[j + 1] = tptr[j] + a;
+  }
+  // counts -> first position of each thread's entries in each column
+  run_parts(even_parts(cols, T), [&](int, int64_t j0, int64_t j1) {
+    for (int64_t j = j0; j < j1; ++j) {
+      int64_t p = tptr[j];
+      for (int t = 0; t < T; ++t) {
+        const int32_t c = cnt[t][j];
+        cnt[t][j] = (int32_t)p;
+        p += c;
+      }
     }
+  });
+  run_parts(rb, [&](int t, int64_t r0, int64_t r1) {
+    std::vector<int32_t>& pos = cnt[t];
+    for (int64_t r = r0; r < r1; ++r)
+      for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) {
+        const int32_t p = pos[idx[e]]++;
+        tidx[p] = (int32_t)r;
+        tval[p] = val[e];
+      }
+  });
 }
 
 // 2^k with k the integer nearest to log2(v) (v > 0 finite): v = f 2^e with 0.5 <= f < 1,

@@ -19,6 +19,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/dpdlp.h"
@@ -741,12 +742,14 @@ int load_impl(dpdlp* h, int32_t count, const int32_t* row_off, const int32_t* co
   transpose_csr(m, n, pptr, pidx, pval, tptr, tidx, tval);
   // pack rows of A and rows of A^T into warp lanes; each packing fixes one index order
   PackPlan rplan, cplan;
-  if (count == 1) {
-    plan_packing(m, pptr, rplan);
-    plan_packing(n, tptr, cplan);
-  } else {
-    plan_packing_batch(m, pptr, h->row_off, rplan);
-    plan_packing_batch(n, tptr, h->col_off, cplan);
+  {  // the two orientations are planned independently: the columns on a second thread
+    std::thread cols_thread([&] {
+      if (count == 1) plan_packing(n, tptr, cplan);
+      else plan_packing_batch(n, tptr, h->col_off, cplan);
+    });
+    if (count == 1) plan_packing(m, pptr, rplan);
+    else plan_packing_batch(m, pptr, h->row_off, rplan);
+    cols_thread.join();
   }
   HostPacked Hr, Hc;
   build_packed(m, n, pptr, pidx, pval, rplan, cplan.new_of_old, Hr);

@@ -1,7 +1,11 @@
 // Host check of the lane packing (no GPU): reads a CSR matrix and a vector x from a binary
 // file, packs the rows, replays what the warp lanes and the long-row pass compute from the
 // stored arrays, and compares with a plain CSR product.  Also checks the structural
-// invariants of the layout.  Prints "ok <stats>" or "FAIL <reason>".
+// invariants of the layout, the (threaded) transpose and row / column permutation against
+// plain sequential definitions, and prints a hash of every output so that runs with
+// different host thread counts (DPDLP_HOST_THREADS) can be compared.
+// Prints "ok <stats> hash=<hex>" or "FAIL <reason>".
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -159,8 +163,76 @@ int main(int argc, char** argv) {
   if (maxrel > 1e-13) return fail("product mismatch (1e-15 units)", (long)(maxrel * 1e15), 0);
   if (stored_nonpad != nz_vals) return fail("stored nonzeros", stored_nonpad, nz_vals);
   if (stored_flags != H.nshort + H.npieces) return fail("end flags", stored_flags, H.nshort + H.npieces);
-  std::printf("ok slots=%d nshort=%d nlong=%d npieces=%d fill=%.4f maxrel=%.3g\n", H.nslots,
-              H.nshort, H.nlong, H.npieces,
-              H.stored ? (double)nnz / (double)H.stored : 1.0, maxrel);
+
+  // transpose: a stable counting sort by column, written out plainly
+  std::vector<int64_t> tptr, rptr(cols + 1, 0);
+  std::vector<int32_t> tidx, ridx(nnz);
+  std::vector<double> tval, rval(nnz);
+  transpose_csr(rows, cols, ptr, idx, val, tptr, tidx, tval);
+  for (int64_t e = 0; e < nnz; ++e) rptr[idx[e] + 1]++;
+  for (int j = 0; j < cols; ++j) rptr[j + 1] += rptr[j];
+  {
+    std::vector<int64_t> next(rptr.begin(), rptr.end() - 1);
+    for (int r = 0; r < rows; ++r)
+      for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) {
+        ridx[next[idx[e]]] = r;
+        rval[next[idx[e]]++] = val[e];
+      }
+  }
+  if (tptr != rptr || tidx != ridx ||
+      std::memcmp(tval.data(), rval.data(), nnz * sizeof(double)) != 0)
+    return fail("transpose");
+  // permutation: new row r is old row prow[r], columns renamed and sorted (stable)
+  const std::vector<int32_t> prow = block_permutation(rows, 3, 7, true);
+  const std::vector<int32_t> pcol = block_permutation(cols, 5, 8, true);
+  std::vector<int64_t> pptr;
+  std::vector<int32_t> pidx;
+  std::vector<double> pval;
+  permute_csr(rows, cols, ptr.data(), idx.data(), val.data(), prow, pcol, pptr, pidx, pval);
+  {
+    std::vector<int32_t> inv(cols);
+    for (int j = 0; j < cols; ++j) inv[pcol[j]] = j;
+    int64_t k = 0;
+    for (int r = 0; r < rows; ++r) {
+      if (pptr[r] != k) return fail("permuted row_ptr", r, 0);
+      std::vector<std::pair<int32_t, double>> row;
+      for (int64_t e = ptr[prow[r]]; e < ptr[prow[r] + 1]; ++e) row.push_back({inv[idx[e]], val[e]});
+      std::stable_sort(row.begin(), row.end(), [](const std::pair<int32_t, double>& a,
+                                                  const std::pair<int32_t, double>& b) {
+        return a.first < b.first;
+      });
+      for (const auto& q : row) {
+        if (pidx[k] != q.first || std::memcmp(&pval[k], &q.second, sizeof(double)) != 0)
+          return fail("permuted entry", r, (long)k);
+        ++k;
+      }
+    }
+    if (pptr[rows] != k) return fail("permuted nnz");
+  }
+
+  unsigned long long h = 1469598103934665603ull;  // FNV-1a over every output
+  auto mix = [&](const void* p, size_t b) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < b; ++i) {
+      h ^= c[i];
+      h *= 1099511628211ull;
+    }
+  };
+  mix(H.val.data(), H.val.size() * sizeof(double));
+  mix(H.val32.data(), H.val32.size() * sizeof(float));
+  mix(H.idx.data(), H.idx.size() * sizeof(uint32_t));
+  mix(H.slots.data(), H.slots.size() * sizeof(SlotDesc));
+  mix(H.lanes.data(), H.lanes.size() * sizeof(LaneMeta));
+  mix(H.long_row.data(), H.long_row.size() * sizeof(int32_t));
+  mix(H.long_ptr.data(), H.long_ptr.size() * sizeof(int32_t));
+  mix(H.long_piece.data(), H.long_piece.size() * sizeof(int32_t));
+  mix(P.old_of_new.data(), P.old_of_new.size() * sizeof(int32_t));
+  mix(tidx.data(), tidx.size() * sizeof(int32_t));
+  mix(tval.data(), tval.size() * sizeof(double));
+  mix(pidx.data(), pidx.size() * sizeof(int32_t));
+  mix(pval.data(), pval.size() * sizeof(double));
+  std::printf("ok slots=%d nshort=%d nlong=%d npieces=%d fill=%.4f maxrel=%.3g exact32=%d hash=%016llx\n",
+              H.nslots, H.nshort, H.nlong, H.npieces,
+              H.stored ? (double)nnz / (double)H.stored : 1.0, maxrel, (int)H.fp32_exact_range, h);
   return 0;
 }

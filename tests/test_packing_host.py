@@ -25,12 +25,13 @@ def checker(tmp_path_factory):
     cuda_inc = "/usr/local/cuda/include"
     cmd = ["g++", "-O2", "-std=c++17", "-I", CSRC, "-I", os.path.join(ROOT, "include"), "-I",
            cuda_inc, os.path.join(os.path.dirname(__file__), "packing_check.cpp"),
-           os.path.join(CSRC, "packing.cpp"), "-o", exe]
+           os.path.join(CSRC, "packing.cpp"), os.path.join(CSRC, "preprocess.cpp"), "-o", exe,
+           "-pthread"]
     subprocess.run(cmd, check=True)
     return exe, d
 
 
-def run(checker, row_ptr, col, val, ncols, seed=0, offsets=None):
+def run(checker, row_ptr, col, val, ncols, seed=0, offsets=None, threads=None):
     exe, d = checker
     rows = len(row_ptr) - 1
     x = np.random.default_rng(seed).standard_normal(ncols)
@@ -42,7 +43,10 @@ def run(checker, row_ptr, col, val, ncols, seed=0, offsets=None):
         np.asarray(val, dtype=np.float64).tofile(f)
         x.tofile(f)
     cmd = [exe, path] + ([",".join(str(int(o)) for o in offsets)] if offsets is not None else [])
-    out = subprocess.run(cmd, capture_output=True, text=True).stdout.strip()
+    env = dict(os.environ)
+    if threads is not None:
+        env["DPDLP_HOST_THREADS"] = str(threads)
+    out = subprocess.run(cmd, capture_output=True, text=True, env=env).stdout.strip()
     assert out.startswith("ok"), out
     return dict(kv.split("=") for kv in out.split()[1:])
 
@@ -128,3 +132,31 @@ def test_cross_stress_fits_the_fused_body(checker):
     eq = lp.ctype == lpgen.EQ
     assert np.allclose(ax[eq], lp.b[eq]) and np.all(ax[~eq] <= lp.b[~eq] + 1e-12)
     assert np.allclose(A.T @ lp.y_star + lp.z_star, lp.c)
+
+
+@pytest.mark.parametrize("case", ["stress", "batch", "powerlaw"])
+def test_results_do_not_depend_on_host_threads(checker, case):
+    """The load-time loops (transpose, permutation, packed arrays) run on host threads; every
+    output is the same, bit for bit, with 1, 3 and 7 threads."""
+    import scipy.sparse as sp
+
+    offs = None
+    if case == "stress":
+        lp = lpgen.row_length_stress_lp(11, LENGTHS, n=12000)
+        A = sp.csr_matrix((lp.val, lp.col, lp.row_ptr), shape=(lp.m, lp.n))
+    elif case == "batch":
+        parts = [lpgen.uneven_lp(40 + i, 300 + 97 * i) for i in range(12)]
+        A = sp.block_diag([sp.csr_matrix((p.val, p.col, p.row_ptr), shape=(p.m, p.n))
+                           for p in parts]).tocsr()
+        A.sort_indices()
+        offs = np.concatenate([[0], np.cumsum([p.m for p in parts])])
+    else:
+        lp = lpgen.scaled_powerlaw_lp(1, 0.01)
+        A = sp.csr_matrix((lp.val, lp.col, lp.row_ptr), shape=(lp.m, lp.n))
+    hashes = set()
+    for t in (1, 3, 7):
+        for M, off in ((A, offs), (A.T.tocsr(), None)):
+            st = run(checker, M.indptr, M.indices, M.data, M.shape[1], seed=40 + t, offsets=off,
+                     threads=t)
+            hashes.add((M.shape, st["hash"]))
+    assert len(hashes) == 2, hashes
