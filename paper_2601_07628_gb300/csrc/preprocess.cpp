@@ -94,17 +94,17 @@ void permute_csr(int rows, int cols, const int64_t* ptr, const int32_t* idx, con
   });
 }
 
-// Stable counting sort by column.  In parallel: each thread counts the columns of its own
-// range of rows, a thread's entries of column j go after those of the earlier threads'
-// rows, and each thread then places its rows in order -- the sequential result exactly.
-void transpose_csr(int rows, int cols, const std::vector<int64_t>& ptr,
-                   const std::vector<int32_t>& idx, const std::vector<double>& val,
-                   std::vector<int64_t>& tptr, std::vector<int32_t>& tidx,
-                   std::vector<double>& tval) {
+// Stable counting sort of the entries of a CSR matrix by column: tptr (cols + 1) gets the
+// column offsets and emit(p, r, e) is called once per entry e (of row r) with its place p
+// in column order, entries of a column in row order.  In parallel: each thread counts the
+// columns of its own range of rows, a thread's entries of column j go after those of the
+// earlier threads' rows, and each thread then places its rows in order -- the sequential
+// placement exactly.
+template <class Emit>
+static void column_sort(int rows, int cols, const int64_t* ptr, const int32_t* idx,
+                        std::vector<int64_t>& tptr, Emit&& emit) {
   const int64_t nnz = ptr[rows];
   tptr.assign(cols + 1, 0);
-  tidx.resize(nnz);
-  tval.resize(nnz);
   // per-thread column counts cost threads x cols x 4 bytes: at most one thread per cols
   // nonzeros, and at most 256 MB of counts
   int T = (int)std::min<int64_t>(host_threads(), nnz / std::max(cols, 1));
@@ -115,14 +115,10 @@ void transpose_csr(int rows, int cols, const std::vector<int64_t>& ptr,
     for (int j = 0; j < cols; ++j) tptr[j + 1] += tptr[j];
     std::vector<int64_t> pos(tptr.begin(), tptr.end() - 1);
     for (int r = 0; r < rows; ++r)
-      for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) {
-        const int64_t p = pos[idx[e]]++;
-        tidx[p] = r;
-        tval[p] = val[e];
-      }
+      for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) emit(pos[idx[e]]++, r, e);
     return;
   }
-  const std::vector<int64_t> rb = balanced_rows(rows, ptr.data(), T);
+  const std::vector<int64_t> rb = balanced_rows(rows, ptr, T);
   T = (int)rb.size() - 1;
   std::vector<std::vector<int32_t>> cnt(T);
   run_parts(rb, [&](int t, int64_t r0, int64_t r1) {
@@ -149,11 +145,20 @@ void transpose_csr(int rows, int cols, const std::vector<int64_t>& ptr,
   run_parts(rb, [&](int t, int64_t r0, int64_t r1) {
     std::vector<int32_t>& pos = cnt[t];
     for (int64_t r = r0; r < r1; ++r)
-      for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) {
-        const int32_t p = pos[idx[e]]++;
-        tidx[p] = (int32_t)r;
-        tval[p] = val[e];
-      }
+      for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) emit((int64_t)pos[idx[e]]++, (int)r, e);
+  });
+}
+
+void transpose_csr(int rows, int cols, const std::vector<int64_t>& ptr,
+                   const std::vector<int32_t>& idx, const std::vector<double>& val,
+                   std::vector<int64_t>& tptr, std::vector<int32_t>& tidx,
+                   std::vector<double>& tval) {
+  const int64_t nnz = ptr[rows];
+  tidx.resize(nnz);
+  tval.resize(nnz);
+  column_sort(rows, cols, ptr.data(), idx.data(), tptr, [&](int64_t p, int r, int64_t e) {
+    tidx[p] = r;
+    tval[p] = val[e];
   });
 }
 
@@ -171,34 +176,55 @@ void precondition(int rows, int cols, const std::vector<int64_t>& ptr,
   dr.assign(rows, 1.0);
   dc.assign(cols, 1.0);
   std::vector<double> rn(rows), cn(cols);
+  // column lists of entry positions (entries of a column in row order), so that column
+  // norms can be taken per column, on threads, in the order a row-by-row pass adds them
+  std::vector<int64_t> cptr;
+  std::vector<int64_t> cpos(ptr[rows]);
+  column_sort(rows, cols, ptr.data(), idx.data(), cptr,
+              [&](int64_t p, int, int64_t e) { cpos[p] = e; });
+  const int T = host_threads();
+  const std::vector<int64_t> rparts = balanced_rows(rows, ptr.data(), T);
+  const std::vector<int64_t> cparts = balanced_rows(cols, cptr.data(), T);
+  // row and column norms of |A|: the maximum (Ruiz) or the sum (Pock-Chambolle)
+  auto norms = [&](bool sum) {
+    run_parts(rparts, [&](int, int64_t i0, int64_t i1) {
+      for (int64_t i = i0; i < i1; ++i) {
+        double a = 0.0;
+        for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k)
+          a = sum ? a + std::fabs(val[k]) : std::max(a, std::fabs(val[k]));
+        rn[i] = a;
+      }
+    });
+    run_parts(cparts, [&](int, int64_t j0, int64_t j1) {
+      for (int64_t j = j0; j < j1; ++j) {
+        double a = 0.0;
+        for (int64_t q = cptr[j]; q < cptr[j + 1]; ++q)
+          a = sum ? a + std::fabs(val[cpos[q]]) : std::max(a, std::fabs(val[cpos[q]]));
+        cn[j] = a;
+      }
+    });
+  };
   auto apply = [&]() {  // factors from the norms rn, cn; scale the values and accumulate
-    for (int i = 0; i < rows; ++i) rn[i] = rn[i] > 0.0 ? pow2_nearest(1.0 / std::sqrt(rn[i])) : 1.0;
-    for (int j = 0; j < cols; ++j) cn[j] = cn[j] > 0.0 ? pow2_nearest(1.0 / std::sqrt(cn[j])) : 1.0;
-    for (int i = 0; i < rows; ++i)
-      for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) val[k] = val[k] * rn[i] * cn[idx[k]];
-    for (int i = 0; i < rows; ++i) dr[i] *= rn[i];
-    for (int j = 0; j < cols; ++j) dc[j] *= cn[j];
+    run_parts(even_parts(cols, T), [&](int, int64_t j0, int64_t j1) {
+      for (int64_t j = j0; j < j1; ++j) {
+        cn[j] = cn[j] > 0.0 ? pow2_nearest(1.0 / std::sqrt(cn[j])) : 1.0;
+        dc[j] *= cn[j];
+      }
+    });
+    run_parts(rparts, [&](int, int64_t i0, int64_t i1) {
+      for (int64_t i = i0; i < i1; ++i) {
+        rn[i] = rn[i] > 0.0 ? pow2_nearest(1.0 / std::sqrt(rn[i])) : 1.0;
+        dr[i] *= rn[i];
+        for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) val[k] = val[k] * rn[i] * cn[idx[k]];
+      }
+    });
   };
   for (int pass = 0; pass < ruiz_passes; ++pass) {
-    std::fill(rn.begin(), rn.end(), 0.0);
-    std::fill(cn.begin(), cn.end(), 0.0);
-    for (int i = 0; i < rows; ++i)
-      for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
-        const double a = std::fabs(val[k]);
-        rn[i] = std::max(rn[i], a);
-        cn[idx[k]] = std::max(cn[idx[k]], a);
-      }
+    norms(false);
     apply();
   }
   if (pock_chambolle) {
-    std::fill(rn.begin(), rn.end(), 0.0);
-    std::fill(cn.begin(), cn.end(), 0.0);
-    for (int i = 0; i < rows; ++i)
-      for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
-        const double a = std::fabs(val[k]);
-        rn[i] += a;
-        cn[idx[k]] += a;
-      }
+    norms(true);
     apply();
   }
 }

@@ -210,6 +210,37 @@ int main(int argc, char** argv) {
     if (pptr[rows] != k) return fail("permuted nnz");
   }
 
+  // preconditioning (10 Ruiz passes, then Pock-Chambolle) against the plain row-by-row loops
+  std::vector<double> sval(val), dr, dc;
+  precondition(rows, cols, ptr, idx, sval, 10, true, dr, dc);
+  {
+    std::vector<double> v(val), er(rows, 1.0), ec(cols, 1.0), rn(rows), cn(cols);
+    auto p2 = [](double x) {  // the power of two nearest to x in log scale
+      int e = 0;
+      const double f = std::frexp(x, &e);
+      return std::ldexp(1.0, f >= std::sqrt(0.5) ? e : e - 1);
+    };
+    for (int pass = 0; pass < 11; ++pass) {
+      const bool sum = pass == 10;
+      std::fill(rn.begin(), rn.end(), 0.0);
+      std::fill(cn.begin(), cn.end(), 0.0);
+      for (int r = 0; r < rows; ++r)
+        for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) {
+          const double a = std::fabs(v[e]);
+          rn[r] = sum ? rn[r] + a : std::max(rn[r], a);
+          cn[idx[e]] = sum ? cn[idx[e]] + a : std::max(cn[idx[e]], a);
+        }
+      for (int r = 0; r < rows; ++r) rn[r] = rn[r] > 0.0 ? p2(1.0 / std::sqrt(rn[r])) : 1.0;
+      for (int j = 0; j < cols; ++j) cn[j] = cn[j] > 0.0 ? p2(1.0 / std::sqrt(cn[j])) : 1.0;
+      for (int r = 0; r < rows; ++r)
+        for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) v[e] = v[e] * rn[r] * cn[idx[e]];
+      for (int r = 0; r < rows; ++r) er[r] *= rn[r];
+      for (int j = 0; j < cols; ++j) ec[j] *= cn[j];
+    }
+    if (std::memcmp(v.data(), sval.data(), nnz * sizeof(double)) != 0 || er != dr || ec != dc)
+      return fail("preconditioning");
+  }
+
   unsigned long long h = 1469598103934665603ull;  // FNV-1a over every output
   auto mix = [&](const void* p, size_t b) {
     const unsigned char* c = static_cast<const unsigned char*>(p);
@@ -231,6 +262,9 @@ int main(int argc, char** argv) {
   mix(tval.data(), tval.size() * sizeof(double));
   mix(pidx.data(), pidx.size() * sizeof(int32_t));
   mix(pval.data(), pval.size() * sizeof(double));
+  mix(sval.data(), sval.size() * sizeof(double));
+  mix(dr.data(), dr.size() * sizeof(double));
+  mix(dc.data(), dc.size() * sizeof(double));
   std::printf("ok slots=%d nshort=%d nlong=%d npieces=%d fill=%.4f maxrel=%.3g exact32=%d hash=%016llx\n",
               H.nslots, H.nshort, H.nlong, H.npieces,
               H.stored ? (double)nnz / (double)H.stored : 1.0, maxrel, (int)H.fp32_exact_range, h);
