@@ -54,7 +54,8 @@ extern "C" {
 #define DPDLP_ERR_OOM (-2)        /* device or host allocation failed */
 #define DPDLP_ERR_CUDA (-3)       /* a CUDA runtime call failed */
 #define DPDLP_ERR_NOT_LOADED (-4) /* no LP loaded on this handle */
-#define DPDLP_ERR_TIMEOUT (-5)    /* a bounded device wait gave up */
+#define DPDLP_ERR_TIMEOUT (-5)    /* reserved for a bounded device wait that gives up; this
+                                     build has no device-side wait and never returns it */
 #define DPDLP_ERR_TOO_LARGE (-6)  /* size beyond dpdlp_csr_spmv_noalloc's fixed scratch */
 
 typedef struct dpdlp dpdlp_t; /* opaque solver handle, one LP per handle */

@@ -403,3 +403,15 @@ def test_resume_from_state_is_exact():
     rest = O.solve(o, eps=0.0, max_iter=256, params=dict(check_every=64), state=half.state)
     assert np.array_equal(full.x, rest.x) and np.array_equal(full.y, rest.y)
     assert full.omega == rest.omega and full.restarts == rest.restarts
+
+
+def test_diverging_step_is_reported_at_the_first_check():
+    """eta far above 1 / ||A|| makes the iterates overflow; the first check must stop the
+    solve with status 2 (non-finite iterate), not report convergence or run on."""
+    lp = lpgen.small_random_lp(0, n=200, m=100)
+    o = O.OracleLP.from_lpgen(lp)
+    with np.errstate(all="ignore"):
+        bad = O.solve(o, eps=1e-8, max_iter=640, params=dict(eta=1e300))
+    assert bad.status == 2 and bad.iterations == 64
+    ok = O.solve(o, eps=1e-4, max_iter=100_000, params=dict(eta=O.default_eta(o)))
+    assert ok.status == 0
