@@ -11,6 +11,7 @@
 #include <cfloat>
 #include <cmath>
 #include <numeric>
+#include <utility>
 
 #include "host_parallel.h"
 #include "internal.h"
@@ -176,12 +177,25 @@ void plan_packing_batch(int rows, const std::vector<int64_t>& ptr,
   std::vector<int32_t> lrow, linst, lcount;
   std::vector<std::vector<int32_t>> lpieces;
   const int ninst = (int)offsets.size() - 1;
+  // the instances are planned independently (on threads, ranges of instances of about equal
+  // nonzeros), then concatenated in instance order
+  std::vector<PackPlan> plans(ninst);
+  {
+    std::vector<int64_t> inst_nnz(ninst + 1);
+    for (int i = 0; i <= ninst; ++i) inst_nnz[i] = ptr[offsets[i]];
+    run_parts(balanced_rows(ninst, inst_nnz.data(), host_threads()),
+              [&](int, int64_t i0, int64_t i1) {
+                for (int64_t i = i0; i < i1; ++i) {
+                  const int off = offsets[i], len = offsets[i + 1] - offsets[i];
+                  std::vector<int64_t> sub(len + 1);
+                  for (int r = 0; r <= len; ++r) sub[r] = ptr[off + r] - ptr[off];
+                  plan_packing(len, sub, plans[i]);
+                }
+              });
+  }
   for (int i = 0; i < ninst; ++i) {
     const int off = offsets[i], len = offsets[i + 1] - offsets[i];
-    std::vector<int64_t> sub(len + 1);
-    for (int r = 0; r <= len; ++r) sub[r] = ptr[off + r] - ptr[off];
-    PackPlan Q;
-    plan_packing(len, sub, Q);
+    const PackPlan Q = std::move(plans[i]);  // freed at the end of this instance
     const int32_t lane_off = (int32_t)P.lane_ptr.size() - 1;
     const int32_t seg_off = (int32_t)P.segs.size();
     const int32_t piece_off = P.npieces;

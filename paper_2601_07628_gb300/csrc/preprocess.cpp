@@ -106,9 +106,9 @@ static void column_sort(int rows, int cols, const int64_t* ptr, const int32_t* i
   const int64_t nnz = ptr[rows];
   tptr.assign(cols + 1, 0);
   // per-thread column counts cost threads x cols x 4 bytes: at most one thread per cols
-  // nonzeros, and at most 256 MB of counts
+  // nonzeros, and at most 512 MB of counts
   int T = (int)std::min<int64_t>(host_threads(), nnz / std::max(cols, 1));
-  T = (int)std::min<int64_t>(T, ((int64_t)1 << 26) / std::max(cols, 1));
+  T = (int)std::min<int64_t>(T, ((int64_t)1 << 27) / std::max(cols, 1));
   if (nnz >= INT32_MAX) T = 1;  // the parallel form keeps positions in 32 bits
   if (T <= 1) {
     for (int64_t e = 0; e < nnz; ++e) tptr[idx[e] + 1]++;
