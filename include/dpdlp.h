@@ -300,12 +300,14 @@ int dpdlp_get_info(dpdlp_t* h, dpdlp_info_t* out);
 
 /* y[m] = A x[n] for a plain CSR matrix already in DEVICE memory, allocating nothing.
  * The paper has no counterpart: this is a service for callers that cannot allocate device
- * memory where they need the product -- code recording a CUDA graph by stream capture
- * (cudaMalloc is not a stream operation and may synchronize the device), frameworks
- * whose pool owns all device memory, allocation-free latency-critical loops.
+ * memory where they need the product -- frameworks whose own pool has reserved the
+ * device's memory (a cudaMalloc behind its back fails or fragments it), and
+ * latency-critical loops that must not stall on the allocator (cudaMalloc and cudaFree
+ * may synchronize the device).
  *   row_ptr[m+1] (int32, row_ptr[0] = 0, non-decreasing, row_ptr[m] = nnz), col_idx[nnz]
  *   (int32 in [0, n)), val[nnz], x[n], y[m]: device pointers on the current device; the
- *   caller guarantees a valid CSR (it is not checked on the device).
+ *   caller guarantees a valid CSR (it is not checked on the device).  In particular nnz
+ *   must equal row_ptr[m]: a smaller nnz leaves the last rows with truncated sums.
  *   cuda_stream: a cudaStream_t or NULL; the call only enqueues work, y is ready when the
  *   stream reaches this point.
  * Scratch: one fixed array of 192 KB per device (static device storage, reserved when the
@@ -314,7 +316,9 @@ int dpdlp_get_info(dpdlp_t* h, dpdlp_info_t* out);
  * concurrently on the GPU (different streams without ordering) race and must not overlap;
  * each call rewrites every slot it reads, so nothing needs clearing between calls.  The
  * first call on a device looks up the array's device address (once per device, with that
- * device current); make that first call before any stream capture.
+ * device current) and keeps it for the life of the process; make that first call before
+ * any stream capture.  A device reset (cudaDeviceReset) unloads the array and leaves the
+ * kept address stale: do not call this entry point on a device after resetting it.
  * Limits: nnz <= 2^30 (DPDLP_ERR_TOO_LARGE beyond it); negative sizes or NULL pointers:
  * DPDLP_ERR_INVALID; a failed launch or lookup: DPDLP_ERR_CUDA.  Results are deterministic
  * (fixed summation order) and agree with dpdlp_apply_A to rounding. */

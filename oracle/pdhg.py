@@ -41,9 +41,10 @@ Readings of passages the paper leaves open (the same readings the CUDA path take
   d_x or d_y is zero or not finite.
 
 Parity unpinned: the numeric values of the restart thresholds (beta_sufficient = 0.2,
-beta_necessary = 0.8, beta_artificial = 0.36) and of the PID gains (K_P = 0.99,
-K_I = 0.01, K_D = 0) are not given by the paper; nothing but agreement with the CUDA path
-pins them.  The decision rules and the PID formula themselves are pinned by tests.
+beta_necessary = 0.8, beta_artificial = 0.36), of the PID gains (K_P = 0.99, K_I = 0.01,
+K_D = 0) and of the step-size safety factor (0.998) are not given by the paper; nothing but
+agreement with the CUDA path pins them.  The decision rules, the epoch bookkeeping, the PID
+formula and distances, omega_0 and eta = safety / sigma_max are pinned by tests.
 """
 from __future__ import annotations
 
@@ -301,6 +302,21 @@ def pid_omega(omega, d_x, d_y, e_sum, e_prev, kp, ki, kd):
     return math.exp(log_w), e_sum, e
 
 
+def anchor_distances(xh, yh, x0, y0):
+    """The PID's distances (Appendix B.3): d_x = ||x^ - x^{n,0}||, d_y = ||y^ - y^{n,0}||,
+    measured from the anchor of the epoch that ends (the start point in the first epoch)."""
+    return float(np.linalg.norm(xh - x0)), float(np.linalg.norm(yh - y0))
+
+
+def new_epoch(S):
+    """Start a restart epoch (Appendix B.2): the inner count k restarts at 0, and the
+    epoch's reference r(z^{n,0}) and previous-check residual are unset until its first
+    check sets both."""
+    S["k"] = 0
+    S["r_anchor"] = None
+    S["r_prev"] = None
+
+
 # ----------------------------------------------------------------------------- the solve
 @dataclass
 class OracleResult:
@@ -385,6 +401,7 @@ def solve(lp: OracleLP, eps=1e-8, max_iter=100_000, params=None, x_start=None, y
         if first:
             S["r_anchor"] = r
             S["r_prev"] = r
+        rec.update(first=first, r_anchor=S["r_anchor"], r_prev=S["r_prev"])
         kind = 0
         if P["restart"]:
             kind = restart_decision(r, S["r_anchor"], S["r_prev"], first, S["k"], S["T"],
@@ -394,15 +411,13 @@ def solve(lp: OracleLP, eps=1e-8, max_iter=100_000, params=None, x_start=None, y
             rec["restart"] = kind
             S["restarts"] += 1
             if P["pid"]:
-                d_x = float(np.linalg.norm(xh - x0))
-                d_y = float(np.linalg.norm(yh - y0))
+                d_x, d_y = anchor_distances(xh, yh, x0, y0)
+                rec.update(d_x=d_x, d_y=d_y)
                 omega, S["e_sum"], S["e_prev"] = pid_omega(
                     omega, d_x, d_y, S["e_sum"], S["e_prev"], P["pid_kp"], P["pid_ki"], P["pid_kd"])
             x0, y0 = xh.copy(), yh.copy()
             x, y = xh.copy(), yh.copy()
-            S["k"] = 0
-            S["r_anchor"] = None
-            S["r_prev"] = None
+            new_epoch(S)
             tau, sigma = eta / omega, eta * omega
         else:
             x, y = xn, yn

@@ -2,13 +2,12 @@
 // nothing.
 //
 // Some callers cannot allocate device memory at the point where they need a product:
-// code that is recording a CUDA graph by stream capture (cudaMalloc is not a stream
-// operation, may synchronize the device and is refused in the strictest capture mode),
-// frameworks whose own pool owns all device memory and forbid allocations behind its back,
-// and latency-critical loops that must not stall on the allocator.  For them this entry
-// point keeps its only scratch -- the partial sums of rows that cross thread-block
-// boundaries -- in one file-scope device array of fixed size, reserved once per device
-// when the library is loaded and held until the process exits.
+// frameworks whose own pool has reserved the device's memory and forbid allocations behind
+// its back, and latency-critical loops that must not stall on the allocator (cudaMalloc and
+// cudaFree may synchronize the device).  For them this entry point keeps its only scratch
+// -- the partial sums of rows that cross thread-block boundaries -- in one file-scope
+// device array of fixed size, reserved once per device when the library is loaded and held
+// until the process exits.
 //
 // Work split: the nonzeros are cut into P equal parts (P <= NA_MAX_PARTS), one thread block
 // per part.  A block owns the rows that start inside its part and sums them completely,
@@ -112,7 +111,8 @@ noalloc_fixup_kernel(int m, long long nnz, int P, long long S, const int32_t* __
 std::mutex g_scratch_mu;
 NoAllocScratch* g_scratch_ptr[64] = {};  // device address of the array, per device ordinal
 
-// Device address of the scratch array on the current device, looked up once per device.
+// Device address of the scratch array on the current device, looked up once per device and
+// kept for the life of the process (a device reset would make it stale; the header says so).
 cudaError_t scratch_address(int dev, NoAllocScratch** out) {
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_scratch_mu);

@@ -416,15 +416,29 @@ class Solver:
 
 def csr_spmv_noalloc(row_ptr, col_idx, val, x, y, n, stream=None) -> int:
     """y = A x through ``dpdlp_csr_spmv_noalloc`` (no device allocation).  All arrays are
-    CUDA tensors (int32 row_ptr/col_idx, float64 val/x/y) on the current device; ``stream``
-    is a raw cudaStream_t handle (default: torch's current stream).  Returns the ABI code."""
-    lib = load_library()
-    if stream is None:
-        import torch
+    contiguous CUDA tensors on the current device: int32 row_ptr [m+1] and col_idx [nnz],
+    float64 val [nnz], x [>= n] and y [>= m]; ``stream`` is a raw cudaStream_t handle
+    (default: torch's current stream).  Returns the ABI code; arguments of the wrong type,
+    layout, device or length return DPDLP_ERR_INVALID (-1) without calling the library.
+    The CSR contents themselves (row_ptr[m] = nnz, indices in range) are the caller's
+    guarantee, as in the C ABI."""
+    import torch
 
-        stream = torch.cuda.current_stream().cuda_stream
+    lib = load_library()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    want = ((row_ptr, torch.int32), (col_idx, torch.int32), (val, torch.float64),
+            (x, torch.float64), (y, torch.float64))
+    for t, dt in want:
+        if not isinstance(t, torch.Tensor) or t.dtype != dt or t.device != dev or t.dim() != 1 \
+                or not t.is_contiguous():
+            return -1
     m = int(row_ptr.numel()) - 1
-    return lib.dpdlp_csr_spmv_noalloc(m, int(n), int(col_idx.numel()), C.c_void_p(row_ptr.data_ptr()),
+    nnz = int(col_idx.numel())
+    if m < 0 or val.numel() != nnz or x.numel() < int(n) or y.numel() < m:
+        return -1
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    return lib.dpdlp_csr_spmv_noalloc(m, int(n), nnz, C.c_void_p(row_ptr.data_ptr()),
                                       C.c_void_p(col_idx.data_ptr()), C.c_void_p(val.data_ptr()),
                                       C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
                                       C.c_void_p(stream) if stream else None)

@@ -1,0 +1,35 @@
+"""Vector comparisons shared by the GPU parity tests (no oracle arithmetic here).
+
+The parity bar compares the GPU's iterates with the oracle's two ways:
+* relative 2-norm: ||g - r|| / ||r|| <= tol, the bar of the whole vector;
+* element by element: max_i |g_i - r_i| <= tol * max(||r||_inf, 1), so that a few wrong
+  entries (one bad row of a slot, one long row) cannot hide inside a 2-norm over millions.
+"""
+import numpy as np
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def max_elem_err(a, b):
+    """max_i |a_i - b_i| / max(||b||_inf, 1)."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    if b.size == 0:
+        return 0.0
+    return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1.0))
+
+
+def vec_errors(a, b):
+    return rel(a, b) if np.asarray(b).size else 0.0, max_elem_err(a, b)
+
+
+def assert_vec_parity(a, b, tol, what=""):
+    e2, ei = vec_errors(a, b)
+    assert e2 <= tol and ei <= tol, (what, e2, ei)
+
+
+def assert_xy_parity(x, y, xr, yr, tol, what=""):
+    assert_vec_parity(x, xr, tol, f"{what} x")
+    assert_vec_parity(y, yr, tol, f"{what} y")

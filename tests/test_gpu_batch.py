@@ -11,6 +11,7 @@ import pytest
 
 import lpgen
 from oracle import pdhg as O
+from parity_util import assert_vec_parity, assert_xy_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -23,10 +24,6 @@ def Solver():
 
     build()
     return dpdlp.Solver
-
-
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 def small_batch():
@@ -56,7 +53,7 @@ def test_batch_matches_oracle_per_instance(Solver, T):
     x, y = s.solution()
     kk = s.batch_kkt()
     for i, ((xi, yi), res) in enumerate(zip(s.split(x, y), ores)):
-        assert rel(xi, res.x) <= TOL and rel(yi, res.y) <= TOL, i
+        assert_xy_parity(xi, yi, res.x, res.y, TOL, f"instance {i}")
         assert kk[i]["restarts"] == res.restarts, i
         for key in ("r_primal", "r_dual", "r_gap"):
             assert kk[i][key] == pytest.approx(res.kkt[key], rel=1e-6, abs=1e-14), (i, key)
@@ -160,9 +157,9 @@ def test_batch_with_empty_instance(Solver):
     s.solve(0.0, 300)
     x, y = s.solution()
     for (xi, yi), res in zip(s.split(x, y), ores):
-        assert rel(xi, res.x) <= TOL
+        assert_vec_parity(xi, res.x, TOL, "x")
         if yi.size:
-            assert rel(yi, res.y) <= TOL
+            assert_vec_parity(yi, res.y, TOL, "y")
     s.close()
 
 
@@ -190,7 +187,7 @@ def test_full_batch_sampled_parity(Solver, full_batch):
         o = O.OracleLP.from_lpgen(lps[i])
         res = O.solve(o, eps=0.0, max_iter=T, params=dict(eta=eta))
         xi, yi = parts[i]
-        assert rel(xi, res.x) <= TOL and rel(yi, res.y) <= TOL, i
+        assert_xy_parity(xi, yi, res.x, res.y, TOL, f"instance {i}")
         assert kk[i]["restarts"] == res.restarts
     s.close()
 

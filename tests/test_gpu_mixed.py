@@ -13,6 +13,7 @@ import pytest
 
 import lpgen
 from oracle import pdhg as O
+from parity_util import assert_xy_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -29,10 +30,6 @@ def rounded(lp):
     return dataclasses.replace(lp, val=lp.val.astype(np.float32).astype(np.float64))
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-
-
 @pytest.mark.parametrize("T", [1, 64, 500])
 def test_fp32_values_match_oracle_on_rounded_matrix(Solver, T):
     lp = lpgen.small_random_lp(0)
@@ -47,7 +44,7 @@ def test_fp32_values_match_oracle_on_rounded_matrix(Solver, T):
     s.set_schedule([r["restart"] for r in ores.trace])
     s.solve(0.0, T)
     x, y = s.solution()
-    assert rel(x, ores.x) <= 1e-9 and rel(y, ores.y) <= 1e-9
+    assert_xy_parity(x, y, ores.x, ores.y, 1e-9)
     assert all(r["spmv_mode"] == 1 for r in s.trace())
     assert s.kkt()["spmv_mode"] == 1
 
@@ -101,4 +98,4 @@ def test_fp32_values_full_size(Solver):
     s.set_param("eta", eta)
     s.solve(0.0, 2)
     x, y = s.solution()
-    assert rel(x, ores.x) <= 1e-9 and rel(y, ores.y) <= 1e-9
+    assert_xy_parity(x, y, ores.x, ores.y, 1e-9)

@@ -14,6 +14,7 @@ import pytest
 
 import lpgen
 from oracle import pdhg as O
+from parity_util import assert_xy_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -26,10 +27,6 @@ def Solver():
 
     build()
     return dpdlp.Solver
-
-
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 ORACLE_KEYS = ("gamma", "halpern", "check_every", "restart", "beta_sufficient", "beta_necessary",
@@ -57,8 +54,7 @@ def run_pair(Solver, lp, T, params=None, eta=None, eps=0.0, forced=True, permute
 
 
 def assert_parity(ores, x, y, tol=TOL):
-    ex, ey = rel(x, ores.x), rel(y, ores.y) if ores.y.size else 0.0
-    assert ex <= tol and ey <= tol, (ex, ey)
+    assert_xy_parity(x, y, ores.x, ores.y, tol)
 
 
 # --------------------------------------------------------------------------- small LP

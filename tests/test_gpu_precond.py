@@ -10,6 +10,7 @@ import pytest
 
 import lpgen
 from oracle import pdhg as O
+from parity_util import assert_xy_parity, rel
 from oracle import precond as P
 
 pytestmark = pytest.mark.gpu
@@ -21,10 +22,6 @@ def Solver():
 
     build()
     return dpdlp.Solver
-
-
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 def oracle_run(lp, T, eps=0.0):
@@ -46,7 +43,7 @@ def test_precond_matches_oracle(Solver, T):
     s.set_schedule([r["restart"] for r in res.trace])
     s.solve(0.0, T)
     x, y = s.solution()
-    assert rel(x, res.x) <= 1e-9 and rel(y, res.y) <= 1e-9
+    assert_xy_parity(x, y, res.x, res.y, 1e-9)
     k = s.kkt()
     for key in ("r_primal", "r_dual", "r_gap", "obj_p", "obj_d"):
         assert k[key] == pytest.approx(res.kkt[key], rel=1e-6, abs=1e-14), key
@@ -132,5 +129,5 @@ def test_precond_full_size_two_iterations(Solver):
     s.set_param("eta", eta)
     s.solve(0.0, 2)
     x, y = s.solution()
-    assert rel(x, res.x) <= 1e-9 and rel(y, res.y) <= 1e-9
+    assert_xy_parity(x, y, res.x, res.y, 1e-9)
     s.close()

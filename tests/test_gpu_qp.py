@@ -11,6 +11,7 @@ import pytest
 
 import lpgen
 from oracle import pdhg as O
+from parity_util import assert_xy_parity, rel
 from oracle import precond as P
 
 pytestmark = pytest.mark.gpu
@@ -22,10 +23,6 @@ def Solver():
 
     build()
     return dpdlp.Solver
-
-
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 def oracle_lp(lp):
@@ -53,7 +50,7 @@ def test_qp_matches_oracle(Solver, case, T):
     s.set_schedule([r["restart"] for r in res.trace])
     s.solve(0.0, T)
     x, y = s.solution()
-    assert rel(x, res.x) <= 1e-9 and rel(y, res.y) <= 1e-9
+    assert_xy_parity(x, y, res.x, res.y, 1e-9)
     k = s.kkt()
     for key in ("r_primal", "r_dual", "r_gap", "obj_p", "obj_d"):
         assert k[key] == pytest.approx(res.kkt[key], rel=1e-6, abs=1e-13), key
@@ -108,7 +105,7 @@ def test_preconditioned_qp_matches_oracle(Solver):
     s.set_schedule([r["restart"] for r in res.trace])
     s.solve(0.0, 200)
     x, y = s.solution()
-    assert rel(x, res.x) <= 1e-9 and rel(y, res.y) <= 1e-9
+    assert_xy_parity(x, y, res.x, res.y, 1e-9)
     s.close()
 
 

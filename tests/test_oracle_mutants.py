@@ -18,7 +18,8 @@ ALL_CHECKS = [
     pins.check_planted_optimum_is_fixed, pins.check_p_norm_dense, pins.check_kkt_hand,
     pins.check_kkt_zero_at_planted, pins.check_power_iteration, pins.check_restart_rules,
     pins.check_pid, pins.check_box_only, pins.check_knapsack,
-    lambda: pins.check_brute_force(seeds=range(2)),
+    pins.check_eta_closed_form, pins.check_default_omega, pins.check_epoch_hand,
+    lambda: pins.check_brute_force(seeds=range(2)), pins.check_epoch_trace,
 ]
 
 
@@ -141,6 +142,36 @@ def m_proj_X_unbounded_above(v, lv, uv):
     return np.maximum(v, lv)
 
 
+def m_epoch_keeps_anchor(S):
+    S["k"] = 0  # r_anchor and r_prev carried over from the epoch that ended
+
+
+def m_epoch_keeps_k(S):
+    S["r_anchor"] = None
+    S["r_prev"] = None  # inner count k not reset
+
+
+def m_distances_from_origin(xh, yh, x0, y0):
+    return float(np.linalg.norm(xh)), float(np.linalg.norm(yh))
+
+
+def m_omega_inverted(lp):
+    cn = float(np.linalg.norm(lp.c))
+    bn = O.finite_bound_norm(lp.lc, lp.uc)
+    return bn / cn if (cn > 0.0 and bn > 0.0) else 1.0
+
+
+def m_bound_norm_with_infinities(lc, uc):
+    eq = lc == uc
+    return math.sqrt(float(np.sum(np.where(eq, lc, 0.0) ** 2) + np.sum(lc[~eq] ** 2)
+                           + np.sum(uc[~eq] ** 2)))
+
+
+def m_eta_no_safety(lp, safety=0.998, iters=200, tol=1e-8):
+    s = O.power_sigma_max(lp, iters, tol)
+    return 1.0 / s if s > 0.0 else 1.0
+
+
 MUTANTS = {
     "primal step sign of A^T y": ("pdhg_step", m_primal_sign),
     "dropped reflection 2x+ - x": ("pdhg_step", m_no_reflection),
@@ -158,6 +189,12 @@ MUTANTS = {
     "necessary decay with >= instead of >": ("restart_decision", m_necessary_strict),
     "power iteration returns sigma^2": ("power_sigma_max", m_power_no_sqrt),
     "box projection ignores upper bound": ("proj_X", m_proj_X_unbounded_above),
+    "restart keeps the epoch's reference residual": ("new_epoch", m_epoch_keeps_anchor),
+    "restart keeps the inner iteration count": ("new_epoch", m_epoch_keeps_k),
+    "PID distances from the origin, not the anchor": ("anchor_distances", m_distances_from_origin),
+    "omega_0 ratio inverted": ("default_omega", m_omega_inverted),
+    "infinite bounds counted in ||b||": ("finite_bound_norm", m_bound_norm_with_infinities),
+    "eta without the safety factor": ("default_eta", m_eta_no_safety),
 }
 
 

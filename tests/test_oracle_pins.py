@@ -326,6 +326,114 @@ def test_power_iteration_matches_svd():
     check_power_iteration()
 
 
+def check_eta_closed_form():
+    """eta = safety / sigma_max(A) (the step-size condition eta ||A||_2 < 1 of Section 2.2,
+    with the documented safety factor 0.998): on A = diag(3, 4) sigma_max is 4, so
+    eta = 0.998 / 4; an LP without nonzeros gets eta = 1."""
+    lp = O.OracleLP(2, 2, [1.0, 1.0], [0, 1, 2], [0, 1], [3.0, 4.0], [0.0, 0.0], [1.0, 1.0],
+                    [0.0, 0.0], [1.0, 1.0])
+    eta = O.default_eta(lp)
+    assert abs(eta - 0.998 / 4.0) <= 1e-8 * eta, eta
+    empty = O.OracleLP(3, 1, [1.0, 2.0, 3.0], [0, 0], [], [], [0.0], [1.0], [0.0] * 3, [1.0] * 3)
+    assert O.default_eta(empty) == 1.0
+
+
+def test_eta_closed_form():
+    check_eta_closed_form()
+
+
+def check_default_omega():
+    """omega_0 = ||c|| / ||b_fin|| (the reading of the initial primal weight): with
+    c = (6, 8), ||c|| = 10, and rows '=' (b = 1, counted once), '<=' (u = 2), '>=' (l = 2),
+    free, and ranged [0, 4] (two finite entries), ||b_fin||^2 = 1 + 4 + 4 + 0 + 16 = 25, so
+    omega_0 = 10 / 5 = 2 exactly.  A zero cost vector or rows without finite bounds give 1."""
+    lc = [1.0, -INF, 2.0, -INF, 0.0]
+    uc = [1.0, 2.0, INF, INF, 4.0]
+    rp = [0, 1, 2, 3, 4, 5]
+    lp = O.OracleLP(2, 5, [6.0, 8.0], rp, [0, 1, 0, 1, 0], [1.0] * 5, lc, uc, [0.0, 0.0],
+                    [INF, INF])
+    assert O.default_omega(lp) == 2.0
+    zero_c = O.OracleLP(2, 5, [0.0, 0.0], rp, [0, 1, 0, 1, 0], [1.0] * 5, lc, uc, [0.0, 0.0],
+                        [INF, INF])
+    assert O.default_omega(zero_c) == 1.0
+    free = O.OracleLP(2, 1, [6.0, 8.0], [0, 1], [0], [1.0], [-INF], [INF], [0.0, 0.0], [1.0, 1.0])
+    assert O.default_omega(free) == 1.0
+
+
+def test_default_omega_hand_computed():
+    check_default_omega()
+
+
+def check_epoch_hand():
+    """Two checks of the restarted, reflected-Halpern solve, worked by hand (Appendix B.2,
+    B.3) on  min -x  s.t.  x <= 1/4,  0 <= x <= 5,  eta = 1/2, omega_0 = 1, a check after
+    every iteration.
+
+    T = 1 from (0, 0), tau = sigma = 1/2: x^ = 1/2, x_bar = 1, y^ = min(0, 0 + (1/4 - 1)/2)
+    = -3/8.  P-norm of (dx, dy) = (-1/2, 3/8): 1/2 + 9/32 - 3/8 = 13/32.  First check of
+    the epoch (anchor residual = r), artificial restart since k = 1 >= 0.36 T.  PID with
+    d_x = 1/2, d_y = 3/8 (distances from the start): omega = d_y / d_x = 3/4.
+    T = 2 from the new anchor (1/2, -3/8), tau = 2/3, sigma = 3/8: x^ = 1/2 + 5/12 = 11/12,
+    x_bar = 4/3, y^ = -3/8 + (3/8)(1/4 - 4/3) = -25/32.  P-norm^2 of (-5/12, 13/32) with
+    omega = 3/4: 75/288 + 169/384 - 130/384 = 139/384.  Again the epoch's first check, so
+    the anchor residual is this r, and an artificial restart (k = 1 >= 0.72).  PID with the
+    distances from the anchor set at T = 1: d_x = 5/12, d_y = 13/32, error log(10/13),
+    integral log(4/3) + log(10/13): omega = (3/4)(13/10)(4/3)^(-0.01)."""
+    lp = O.OracleLP(1, 1, [-1.0], [0, 1], [0], [1.0], [-INF], [0.25], [0.0], [5.0])
+    prm = dict(eta=0.5, omega0=1.0, check_every=1)
+    r1 = O.solve(lp, eps=0.0, max_iter=1, params=prm)
+    assert r1.x[0] == 0.5 and r1.y[0] == -0.375
+    r2 = O.solve(lp, eps=0.0, max_iter=2, params=prm)
+    assert abs(r2.x[0] - 11.0 / 12.0) <= 1e-15 and abs(r2.y[0] + 25.0 / 32.0) <= 1e-15
+    t0, t1 = r2.trace
+    assert abs(t0["r"] - math.sqrt(13.0 / 32.0)) <= 1e-15
+    assert abs(t1["r"] - math.sqrt(139.0 / 384.0)) <= 1e-14
+    for t in (t0, t1):
+        assert t["first"] and t["r_anchor"] == t["r"] and t["r_prev"] == t["r"]
+        assert t["restart"] == 3 and t["k"] == 1
+    assert t0["d_x"] == 0.5 and t0["d_y"] == 0.375
+    assert abs(t1["d_x"] - 5.0 / 12.0) <= 1e-15 and abs(t1["d_y"] - 13.0 / 32.0) <= 1e-15
+    assert t0["omega"] == 1.0 and abs(t1["omega"] - 0.75) <= 1e-15
+    want = 0.75 * 1.3 * (4.0 / 3.0) ** -0.01
+    assert abs(r2.omega - want) <= 1e-14 * want, (r2.omega, want)
+    assert r2.restarts == 2
+
+
+def test_epoch_bookkeeping_hand_computed():
+    check_epoch_hand()
+
+
+def check_epoch_trace(T=4000):
+    """The restart test's inputs at every check follow their definitions (Appendix B.2,
+    readings O10 and O18): an epoch's first check is the first check after a restart (or
+    of the solve); its residual is the epoch's reference r(z^{n,0}) until the next restart;
+    the previous-check residual is the last check's r within the epoch (the check's own r at
+    the first one); the decision is the printed rule applied to those; omega changes only at
+    a restart."""
+    lp = lpgen.small_random_lp(4, n=300, m=150, nnz_per_col=5)
+    o = O.OracleLP.from_lpgen(lp)
+    res = O.solve(o, eps=0.0, max_iter=T, params=dict(check_every=16))
+    tr = res.trace
+    kinds = {t["restart"] for t in tr}
+    assert {1, 3} <= kinds and len(tr) == T // 16, kinds  # several epochs, several kinds
+    anchor = prev = None
+    for i, t in enumerate(tr):
+        first = i == 0 or tr[i - 1]["restart"] != 0
+        assert t["first"] == first, i
+        if first:
+            anchor = prev = t["r"]
+        assert t["r_anchor"] == anchor and t["r_prev"] == prev, i
+        want = O.restart_decision(t["r"], anchor, prev, first, t["k"], t["T"], 0.2, 0.8, 0.36)
+        assert t["restart"] == want, i
+        prev = t["r"]
+        if i and tr[i - 1]["restart"] == 0:
+            assert t["omega"] == tr[i - 1]["omega"], i
+
+
+def test_epoch_bookkeeping_follows_definitions():
+    check_epoch_trace()
+
+
 # --------------------------------------------------------------------------- restarts, PID
 def check_restart_rules():
     """Appendix B.2 criteria as printed, with ties as printed (<= and >)."""
