@@ -222,6 +222,7 @@ struct IterPlan {
   int i;              // iteration index inside the graph body
   int force_regular;  // 1: run as a regular iteration regardless of the scalars (timing)
   int list;           // batches: 1 walk the active-slot list, 0 one launch over every slot
+  int pdl;            // launch as a programmatic dependent of the previous kernel
 };
 
 cudaError_t launch_primal(const DevPacked& csc, const DevVecs& v, const DevScalars* sc,
@@ -259,6 +260,10 @@ cudaError_t launch_gather(const double* in, const int32_t* perm, const double* s
 cudaError_t launch_scatter(const double* in, const int32_t* perm, const double* scale,
                            double* out, int len, cudaStream_t s);
 cudaError_t launch_fill(double* p, double v, int len, cudaStream_t s);
+// Access probes of one packed orientation (no arithmetic, for the roofline): mode 0 the
+// index stream and the gathers of x, mode 1 plus the value stream, mode 2 the streams only.
+cudaError_t launch_access_probe(const DevPacked& M, const double* x, int mode,
+                                unsigned long long* sink, cudaStream_t s);
 // One power-iteration round for every instance: w = A v, lam_i = w_i.w_i, u = A^T w,
 // v_i = u_i / ||u_i||; pw[4 i] = lam_i, pw[4 i + 1] = ||u_i||.
 cudaError_t launch_power_round(const DevPacked& csr, const DevPacked& csc, const DevVecs& v,

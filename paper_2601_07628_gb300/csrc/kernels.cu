@@ -35,6 +35,30 @@ __device__ __forceinline__ double clampd(double v, double lo, double hi) {
   return v < lo ? lo : (v > hi ? hi : v);
 }
 
+// The same clamp without FP64 instructions, for the iteration epilogues (GB300 issues about
+// two FP64 operations per clock per SM, and the epilogues share that pipe with one FMA per
+// stored nonzero).  Doubles compare as integers after mapping their bit patterns to keys
+// that grow with the value (negative values: magnitude bits flipped).  A NaN input is
+// returned unchanged, as clampd does; for any other input the result equals clampd's value
+// (only the sign of a zero result may differ: -0 sorts below +0 here).
+#ifndef DPDLP_INT_CLAMP
+#define DPDLP_INT_CLAMP 1
+#endif
+__device__ __forceinline__ long long order_key(long long b) {
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double clampd_int(double v, double lo, double hi) {
+#if DPDLP_INT_CLAMP
+  const long long bv = __double_as_longlong(v);
+  const long long kv = order_key(bv);
+  if ((bv & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) return v;  // NaN
+  return kv < order_key(__double_as_longlong(lo)) ? lo
+                                                 : (kv > order_key(__double_as_longlong(hi)) ? hi : v);
+#else
+  return clampd(v, lo, hi);
+#endif
+}
+
 __device__ __forceinline__ unsigned long long l2_evict_first_policy() {
   unsigned long long p;
   asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
@@ -133,6 +157,16 @@ __device__ __forceinline__ double block_sum(double v, double* buf) {
   }
   return r;
 }
+
+// Programmatic dependent launch (griddepcontrol, sm_90 and later).  An iteration kernel
+// launched with the programmatic-serialization attribute may start while the kernel before
+// it drains: its blocks load what no earlier kernel writes (slot descriptors, the first
+// index batches), then pdl_wait() blocks until every earlier kernel has finished and its
+// writes are visible.  Each block calls pdl_trigger() at its start, so the next kernel is
+// released once all of this kernel's blocks are resident.  Launched without the attribute
+// (plain products, the timing path) both instructions do nothing.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
 
 // ---------------------------------------------------------------- epilogues
 // An epilogue turns finished row sums into outputs: `apply_direct(row, sums)`.
@@ -297,7 +331,7 @@ struct PrimalEpi {
     // diagonal QP: the minimum of 1/2 Q_jj x^2 + (c_j - s) x + (x - x_j)^2 / (2 tau) over the
     // box is the clamped x = (x_j - tau (c_j - s)) / (1 + tau Q_jj)  (Eq. primal_update)
     if constexpr (QP) t = t / fma(q.step, ld_once(qd + j), 1.0);
-    const double xhj = clampd(t, lvj, uvj);
+    const double xhj = clampd_int(t, lvj, uvj);
     const double xb = fma(2.0, xhj, -xj);
     st_keep(xbar + j, xb);
     if (q.check) {
@@ -396,7 +430,7 @@ struct DualEpi {
   __device__ bool need_anchor() const { return q.halpern && !q.check; }
   __device__ void step(int i, double s, double loi, double hii, double yi, double y0i) {
     const double w = fma(yi, q.inv_step, -s);
-    const double d = w - clampd(w, loi, hii);
+    const double d = w - clampd_int(w, loi, hii);
     if (q.check) {
       yh[i] = q.step * d;
     } else if (q.halpern) {
@@ -653,6 +687,13 @@ __device__ __forceinline__ void lane_sums(const DevPacked& M, const GatherVecs<N
   }
 }
 
+// Whether this launch is an iteration kernel launched as a programmatic dependent.
+template <class Epi>
+__device__ __forceinline__ bool launched_dependent(const Epi& epi) {
+  if constexpr (Epi::kTunable) return epi.plan.pdl != 0;
+  return false;
+}
+
 // One warp per slot, PK_WARPS slots per block, no block-level barrier: the lanes sum their
 // rows (lane_sums), then apply the epilogue to the slot's short rows, one row per lane.
 // W slots (warps) per block; the register cap keeps the same number of resident warps per
@@ -669,12 +710,13 @@ __global__ void __launch_bounds__(W * LANES, (DPDLP_PK_MIN_BLOCKS * PK_WARPS) / 
   const uint4* ip = reinterpret_cast<const uint4*>(M.idx + off) + lane;
   const unsigned long long pol = l2_evict_first_policy();
   uint32_t c0[B], c1[B];
-#if DPDLP_HOIST_IDX
-  if (s < M.nslots) {  // the first index batches depend on the slot only
+  // with programmatic dependent launch the first index batches (which no kernel writes)
+  // load before the wait, while the previous kernel drains
+  const bool early_idx = DPDLP_HOIST_IDX || launched_dependent(epi);
+  if (early_idx && s < M.nslots) {
     load_idx<B>(ip, 0, c0, pol);
     load_idx<B>(ip, 1, c1, pol);
   }
-#endif
 #if DPDLP_HOIST_SLOT
   // the slot's descriptors are loaded while the launch scalars are in flight
   SlotDesc sd{0, 0, 0, 0};
@@ -683,9 +725,13 @@ __global__ void __launch_bounds__(W * LANES, (DPDLP_PK_MIN_BLOCKS * PK_WARPS) / 
     sd = M.slots[s];
     lm = M.lanes[(size_t)s * LANES + lane];
   }
+  pdl_trigger();
+  pdl_wait();
   if (!epi.begin()) return;   // uniform over the launch
   if (s >= M.nslots) return;  // uniform over the warp
 #else
+  pdl_trigger();
+  pdl_wait();
   if (!epi.begin()) return;
   if (s >= M.nslots) return;
   const SlotDesc sd = M.slots[s];
@@ -695,10 +741,10 @@ __global__ void __launch_bounds__(W * LANES, (DPDLP_PK_MIN_BLOCKS * PK_WARPS) / 
 #if DPDLP_EPI_PREFETCH
   epi.prefetch(sd.row_base, sd.nrows, lane);
 #endif
-#if !DPDLP_HOIST_IDX
-  load_idx<B>(ip, 0, c0, pol);
-  load_idx<B>(ip, 1, c1, pol);
-#endif
+  if (!early_idx) {
+    load_idx<B>(ip, 0, c0, pol);
+    load_idx<B>(ip, 1, c1, pol);
+  }
   if (epi.fp32() && M.val32)  // uniform over the warp
     lane_sums<float, NV, B>(M, g, off, lane, lm.row_local, lm.piece_base, srow[w], ip, pol, c0, c1);
   else
@@ -724,6 +770,8 @@ template <int NV, class Epi>
 __global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_in) {
   __shared__ double red[TPB / 32];
   Epi epi = epi_in;
+  pdl_trigger();
+  pdl_wait();  // the pieces and scalars come from the kernels before
   if (!epi.begin()) return;
   const int nb = M.nlong_block, nw = M.nlong_warp;
   const int wblocks = (nw + TPB / 32 - 1) / (TPB / 32);
@@ -806,6 +854,8 @@ __global__ void __launch_bounds__(W * LANES, (DPDLP_LIST_MIN_BLOCKS * PK_WARPS) 
     packed_list_kernel(DevPacked M, GatherVecs<NV> g, Epi epi_in) {
   __shared__ double srow[W][NV][MAX_SLOT_ROWS];
   Epi epi = epi_in;
+  pdl_trigger();
+  pdl_wait();  // the slot list and scalars come from the kernels before
   if (!epi.begin()) return;  // uniform over the launch
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int total = epi.all_slots() ? M.nslots : *M.nactive;
@@ -850,41 +900,66 @@ static int sm_count() {
 #define DPDLP_BATCH_LIST 1
 #endif
 
+// A launch, as a programmatic dependent of the previous work in the stream when `pdl`.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_k(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s,
+                            bool pdl, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? at : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <class Epi>
+static bool pdl_of(const Epi& epi) {
+  if constexpr (Epi::kTunable) return epi.plan.pdl != 0;
+  return false;
+}
+
 template <int NV, int W, class Epi>
-static void launch_slots(const DevPacked& M, GatherVecs<NV> g, Epi epi, cudaStream_t s) {
+static cudaError_t launch_slots(const DevPacked& M, GatherVecs<NV> g, Epi epi, cudaStream_t s) {
+  const bool pdl = pdl_of(epi);
   if constexpr (Epi::kListable && DPDLP_BATCH_LIST) {
     if (M.active && epi.listed) {
       const int resident = sm_count() * ((DPDLP_LIST_MIN_BLOCKS * PK_WARPS) / W);
       const int need = (M.nslots + W - 1) / W;
       const int grid = DPDLP_LIST_PERSISTENT && need > resident ? resident : need;
-      packed_list_kernel<NV, W, Epi><<<grid, W * LANES, 0, s>>>(M, g, epi);
-      return;
+      return launch_k(packed_list_kernel<NV, W, Epi>, grid, W * LANES, s, pdl, M, g, epi);
     }
   }
-  packed_spmv_kernel<NV, W, Epi><<<(M.nslots + W - 1) / W, W * LANES, 0, s>>>(M, g, epi);
+  return launch_k(packed_spmv_kernel<NV, W, Epi>, (M.nslots + W - 1) / W, W * LANES, s, pdl, M, g,
+                  epi);
 }
 
 // Iteration kernels (Epi::kTunable) run with the orientation's chosen slots per block;
 // the plain products of the checks and the power iteration use PK_WARPS.
 template <int NV, class Epi>
 static cudaError_t launch_packed(const DevPacked& M, GatherVecs<NV> g, Epi epi, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
   if (M.nslots > 0) {
     if constexpr (Epi::kTunable) {
       switch (M.cta_slots) {
-        case 2: launch_slots<NV, 2>(M, g, epi, s); break;
-        case 8: launch_slots<NV, 8>(M, g, epi, s); break;
-        default: launch_slots<NV, 4>(M, g, epi, s); break;
+        case 2: e = launch_slots<NV, 2>(M, g, epi, s); break;
+        case 8: e = launch_slots<NV, 8>(M, g, epi, s); break;
+        default: e = launch_slots<NV, 4>(M, g, epi, s); break;
       }
     } else {
-      launch_slots<NV, PK_WARPS>(M, g, epi, s);
+      e = launch_slots<NV, PK_WARPS>(M, g, epi, s);
     }
   }
-  if (M.nlong > 0) {
+  if (e == cudaSuccess && M.nlong > 0) {
     const int rest = M.nlong - M.nlong_block - M.nlong_warp;
     const int grid = M.nlong_block + (M.nlong_warp + TPB / 32 - 1) / (TPB / 32) + (rest + TPB - 1) / TPB;
-    finish_long_kernel<NV, Epi><<<grid, TPB, 0, s>>>(M, epi);
+    e = launch_k(finish_long_kernel<NV, Epi>, grid, TPB, s, pdl_of(epi), M, epi);
   }
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_primal(const DevPacked& csc, const DevVecs& v, const DevScalars* sc,
@@ -917,6 +992,81 @@ cudaError_t launch_spmv(const DevPacked& M, const double* x0, const double* x1, 
   }
   GatherVecs<1> g{{x0}};
   return launch_packed<1>(M, g, StoreEpi1{out0, running, listed}, s);
+}
+
+// ---------------------------------------------------------------- access probes
+// The packed kernels' memory accesses per stored entry without their arithmetic, to place
+// the iteration kernels against what their access pattern allows (the roofline's ceilings):
+//   mode 0  the index stream and the x[col] gathers (random 8-byte gathers, each its own
+//           32-byte L2 sector: the gather ceiling of this layout);
+//   mode 1  mode 0 plus the value stream (every load the product makes per stored entry);
+//   mode 2  the index and value streams without gathers (the coalesced-stream ceiling).
+// Same slots, warps, cache policies and pipeline depth as packed_spmv_kernel.  Loaded words
+// are folded with integer xor (no FP64 work) and the fold is stored only if it equals a
+// constant it practically never takes, so every load stays live.
+template <int Mode>
+__global__ void __launch_bounds__(PK_TPB, DPDLP_PK_MIN_BLOCKS)
+    access_probe_kernel(DevPacked M, const double* __restrict__ x, unsigned long long* sink) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.x * PK_WARPS + w;
+  if (s >= M.nslots) return;  // uniform over the warp
+  constexpr int B = DPDLP_PK_BATCH;
+  constexpr int NB = LANE_ITEMS / B;
+  const size_t off = (size_t)s * SLOT_ITEMS;
+  const uint4* ip = reinterpret_cast<const uint4*>(M.idx + off) + lane;
+  const double2* vp = Vals<double>::base(M, off, lane);
+  const unsigned long long pol = l2_evict_first_policy();
+  unsigned long long acc = 0;
+  uint32_t c0[B], c1[B];
+  load_idx<B>(ip, 0, c0, pol);
+  load_idx<B>(ip, 1, c1, pol);
+  unsigned long long g0[B];
+  double v0[B];
+  if (Mode >= 1) Vals<double>::load<B>(vp, 0, v0, pol);
+#pragma unroll
+  for (int j = 0; j < B; ++j)
+    g0[j] = Mode == 2 ? c0[j] : (unsigned long long)__double_as_longlong(__ldg(x + (c0[j] & IDX_MASK)));
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    uint32_t c2[B];
+    unsigned long long g1[B];
+    double v1[B];
+    if (b + 2 < NB) load_idx<B>(ip, b + 2, c2, pol);
+    if (b + 1 < NB) {
+      if (Mode >= 1) Vals<double>::load<B>(vp, b + 1, v1, pol);
+#pragma unroll
+      for (int j = 0; j < B; ++j)
+        g1[j] = Mode == 2 ? c1[j]
+                          : (unsigned long long)__double_as_longlong(__ldg(x + (c1[j] & IDX_MASK)));
+    }
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      acc ^= g0[j];
+      if (Mode >= 1) acc ^= (unsigned long long)__double_as_longlong(v0[j]);
+    }
+    if (b + 1 < NB) {
+#pragma unroll
+      for (int j = 0; j < B; ++j) {
+        g0[j] = g1[j];
+        v0[j] = v1[j];
+        c1[j] = c2[j];
+      }
+    }
+  }
+  if (acc == 0x9e3779b97f4a7c15ull) sink[0] = acc;
+}
+
+cudaError_t launch_access_probe(const DevPacked& M, const double* x, int mode,
+                                unsigned long long* sink, cudaStream_t s) {
+  if (M.nslots <= 0) return cudaSuccess;
+  const int grid = (M.nslots + PK_WARPS - 1) / PK_WARPS;
+  switch (mode) {
+    case 0: access_probe_kernel<0><<<grid, PK_TPB, 0, s>>>(M, x, sink); break;
+    case 1: access_probe_kernel<1><<<grid, PK_TPB, 0, s>>>(M, x, sink); break;
+    case 2: access_probe_kernel<2><<<grid, PK_TPB, 0, s>>>(M, x, sink); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- fused body (small LPs)

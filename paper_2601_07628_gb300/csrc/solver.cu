@@ -56,6 +56,7 @@ std::map<std::string, Param> default_params() {
       {"perm_block", {256, 1, 1 << 30, true}},
       {"perm_seed", {1, 0, 9007199254740992.0, true}},
       {"use_graph", {1, 0, 1, true}},
+      {"pdl", {1, 0, 1, true}},
       {"ptr_mode_device", {0, 0, 1, true}},
       {"resume", {0, 0, 1, true}},
       {"trace_capacity", {4096, 0, 1 << 20, true}},
@@ -481,12 +482,13 @@ int build_graph(dpdlp* h, int K) {
   CK(cudaGraphAddNode(&node, h->graph, nullptr, nullptr, 0, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  const int pdl = (int)h->P("pdl");
   // K iterations captured into graph g after `deps`
   auto capture_iters = [&](cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps, int list) {
     cudaError_t e = cudaStreamBeginCaptureToGraph(h->cap_stream, g, deps, nullptr, ndeps, mode);
     for (int i = 0; i < K && e == cudaSuccess; ++i) {
-      e = launch_primal(h->csc, h->v, h->d_sc, IterPlan{i, 0, list}, h->cap_stream);
-      if (e == cudaSuccess) e = launch_dual(h->csr, h->v, h->d_sc, IterPlan{i, 0, list}, h->cap_stream);
+      e = launch_primal(h->csc, h->v, h->d_sc, IterPlan{i, 0, list, pdl}, h->cap_stream);
+      if (e == cudaSuccess) e = launch_dual(h->csr, h->v, h->d_sc, IterPlan{i, 0, list, pdl}, h->cap_stream);
     }
     cudaGraph_t captured = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &captured);
@@ -500,8 +502,8 @@ int build_graph(dpdlp* h, int K) {
       if (e == cudaSuccess) e = launch_body_fused(h->csc, h->csr, h->v, h->d_sc, K, h->cap_stream);
     } else {
       for (int i = 0; i < K && e == cudaSuccess; ++i) {
-        e = launch_primal(h->csc, h->v, h->d_sc, IterPlan{i, 0, 0}, h->cap_stream);
-        if (e == cudaSuccess) e = launch_dual(h->csr, h->v, h->d_sc, IterPlan{i, 0, 0}, h->cap_stream);
+        e = launch_primal(h->csc, h->v, h->d_sc, IterPlan{i, 0, 0, pdl}, h->cap_stream);
+        if (e == cudaSuccess) e = launch_dual(h->csr, h->v, h->d_sc, IterPlan{i, 0, 0, pdl}, h->cap_stream);
       }
     }
     if (e == cudaSuccess)
@@ -549,6 +551,7 @@ int build_graph(dpdlp* h, int K) {
 int run_host_loop(dpdlp* h) {
   const int K = h->h_sc.K;
   if (use_fused(h)) CK(fused_body_prepare());
+  const int pdl = (int)h->P("pdl");
   for (;;) {
     int list = 0;
     if (h->ninst > 1) {  // the same choice the graph's select kernel makes
@@ -562,8 +565,8 @@ int run_host_loop(dpdlp* h) {
       CK(launch_body_fused(h->csc, h->csr, h->v, h->d_sc, K, h->stream));
     } else {
       for (int i = 0; i < K; ++i) {
-        CK(launch_primal(h->csc, h->v, h->d_sc, IterPlan{i, 0, list}, h->stream));
-        CK(launch_dual(h->csr, h->v, h->d_sc, IterPlan{i, 0, list}, h->stream));
+        CK(launch_primal(h->csc, h->v, h->d_sc, IterPlan{i, 0, list, pdl}, h->stream));
+        CK(launch_dual(h->csr, h->v, h->d_sc, IterPlan{i, 0, list, pdl}, h->stream));
       }
     }
     CK(launch_check(h->csr, h->csc, h->v, h->d_sc, 0ULL, 0, h->stream));
@@ -640,7 +643,7 @@ int dpdlp_set_param(dpdlp_t* h, const char* key, double v) {
   if ((k == "cta_slots_primal" || k == "cta_slots_dual") && v != 2 && v != 4 && v != 8)
     return fail(h, DPDLP_ERR_INVALID, k + " must be 2, 4 or 8");
   if ((k == "check_every" || k == "cta_slots_primal" || k == "cta_slots_dual" ||
-       k == "fused_body" || k == "fused_max_slots") && v != p.value)
+       k == "fused_body" || k == "fused_max_slots" || k == "pdl") && v != p.value)
     free_graph(h);  // the captured graph holds the launch shapes
   if (std::string(key) == "eta_safety" || std::string(key) == "power_iters" ||
       std::string(key) == "power_tol")
@@ -1278,7 +1281,21 @@ int dpdlp_time_kernel(dpdlp_t* h, const char* which, int32_t reps, double* avg_m
   if (!h || !which || reps <= 0 || !avg_ms) return DPDLP_ERR_INVALID;
   if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
   const std::string w(which);
-  if (w != "primal" && w != "dual") return fail(h, DPDLP_ERR_INVALID, "kernel must be primal or dual");
+  // the iteration kernels, or an access probe of one orientation's product (its loads
+  // without arithmetic): gather_* indices + gathers, access_* plus values, stream_* the
+  // index and value streams only
+  int probe = -1;
+  bool primal = w == "primal";
+  if (w != "primal" && w != "dual") {
+    const size_t us = w.find('_');
+    const std::string kind = us == std::string::npos ? w : w.substr(0, us);
+    const std::string side = us == std::string::npos ? "" : w.substr(us + 1);
+    probe = kind == "gather" ? 0 : kind == "access" ? 1 : kind == "stream" ? 2 : -1;
+    if (probe < 0 || (side != "primal" && side != "dual"))
+      return fail(h, DPDLP_ERR_INVALID,
+                  "kernel must be primal, dual, or gather_/access_/stream_ + primal or dual");
+    primal = side == "primal";
+  }
   if (!h->has_state) return fail(h, DPDLP_ERR_INVALID, "solve or set a start first");
   CK(cudaSetDevice(h->device));
   // keep the state: snapshot the vectors the kernels update in place
@@ -1291,8 +1308,15 @@ int dpdlp_time_kernel(dpdlp_t* h, const char* which, int32_t reps, double* avg_m
   const IterPlan p{0, 1, 0};
   CK(cudaEventRecord(e0, h->stream));
   for (int r = 0; r < reps; ++r) {
-    if (w == "primal") CK(launch_primal(h->csc, h->v, h->d_sc, p, h->stream));
-    else CK(launch_dual(h->csr, h->v, h->d_sc, p, h->stream));
+    if (probe >= 0) {
+      // the primal product gathers y over the rows of A^T, the dual one x_bar over A
+      CK(launch_access_probe(primal ? h->csc : h->csr, primal ? h->v.y : h->v.xbar, probe,
+                             reinterpret_cast<unsigned long long*>(h->v.pw), h->stream));
+    } else if (primal) {
+      CK(launch_primal(h->csc, h->v, h->d_sc, p, h->stream));
+    } else {
+      CK(launch_dual(h->csr, h->v, h->d_sc, p, h->stream));
+    }
   }
   CK(cudaEventRecord(e1, h->stream));
   CK(cudaEventSynchronize(e1));
