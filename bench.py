@@ -57,12 +57,17 @@ def parse():
                    help="tolerances of the batched-vs-sequential comparison (1e-8: several "
                         "minutes; a few of the 256 LPs need more than 10^6 iterations)")
     p.add_argument("--batch-precond", type=int, default=0, choices=[0, 1])
+    p.add_argument("--batch-tol8-count", type=int, default=64,
+                   help="the smallest instances of the batch solved to 1e-8, batched and one by one")
     p.add_argument("--no-warm-start", action="store_true",
                    help="skip the learned warm start (train on solver solutions, warm vs cold)")
+    p.add_argument("--ws-train", type=int, default=400,
+                   help="warm start: training instances of the transportation family")
+    p.add_argument("--ws-test", type=int, default=32, help="warm start: held-out instances")
+    p.add_argument("--ws-epochs", type=int, default=8, help="warm start: training epochs")
     p.add_argument("--x3-full", action="store_true",
-                   help="learned warm start on the full transportation family (300 x 300 arcs, "
-                        "20,000 side rows; 2,000 training and 200 test instances) instead of "
-                        "the 100 x 100 one; several minutes")
+                   help="learned warm start with 2,000 training and 200 held-out instances of "
+                        "the transportation family (default: --ws-train / --ws-test); several minutes")
     p.add_argument("--host-loop", action="store_true",
                    help="launch the iteration kernels from a host loop instead of the CUDA graph "
                         "(same kernels; for profilers that do not descend into graph loops)")
@@ -446,19 +451,70 @@ def run_batch(args, dev, stream, peak):
         "workload": f"{len(lps)} uneven LPs (m_i ~ U{{500..50000}}, n_i = 2 m_i, 5-15 nnz/col, seed 3): "
                     f"n={n:,} m={m:,} nnz={nnz:,}",
         "generate_s": gen_s, "load_s": load_s, "preprocess_ms": info["preprocess_ms"],
-        "autotune": {k: tune[k] for k in ("cta_slots_primal", "cta_slots_dual", "ms")},
+        "autotune": {k: tune[k] for k in ("cta_slots_primal", "cta_slots_dual", "list_fraction",
+                                          "list_warps_per_sm", "ms") if k in tune},
         "iter_per_s_all_running": it_s, "kernels": kern,
         "gpu_launches_per_body": launches_per_body(info, len(lps)),
         "precond": args.batch_precond, "sequential_load_s": seq_load, "to_tol": per_tol,
+        "to_1e-08_smallest": batch_tol8_smallest(args, lps, dev, stream),
     }
 
 
+def batch_tol8_smallest(args, lps, dev, stream):
+    """Relative KKT 1e-8 for the ``--batch-tol8-count`` smallest instances of the batch
+    workload: batched (tuned launch choices) against the same LPs solved one after another."""
+    import numpy as np
+
+    from paper_2601_07628_gb300 import autotune
+    from paper_2601_07628_gb300.dpdlp import Solver
+
+    k = min(args.batch_tol8_count, len(lps))
+    if k <= 0:
+        return None
+    pick = sorted(range(len(lps)), key=lambda i: (lps[i].nnz, i))[:k]
+    sub = [lps[i] for i in pick]
+    s = Solver(dev)
+    s.set_stream(stream)
+    s.load_batch(sub)
+    tune = autotune.tune(s, cache=os.path.join(tempfile.gettempdir(), "dpdlp_autotune.json"),
+                         reps=10, rounds=2, force=True)
+    s.solve(1e-8, K_CHECK)
+    s.set_param("resume", 0)
+    t0 = time.perf_counter()
+    st = s.solve(1e-8, 2_000_000)
+    bs = time.perf_counter() - t0
+    bk = s.batch_kkt()
+    s.close()
+    one = Solver(dev)
+    one.set_stream(stream)
+    seq_s, seq_it, seq_st = 0.0, [], []
+    for lp in sub:
+        one.load(lp)
+        r = time_to_tol(one, 1e-8, 2_000_000, 0)
+        seq_s += r["seconds"]
+        seq_it.append(r["iterations"])
+        seq_st.append(r["status"])
+    one.close()
+    it = np.array([q["iterations"] for q in bk], dtype=np.float64)
+    return {"instances": k, "nnz": int(sum(lp.nnz for lp in sub)),
+            "batched": {"seconds": bs, "status": st, "converged": int(sum(q["status"] == 0 for q in bk)),
+                        "max_iterations": int(it.max())},
+            "sequential": {"seconds": seq_s, "converged": int(sum(x == 0 for x in seq_st)),
+                           "max_iterations": int(max(seq_it))},
+            "speedup_vs_sequential": seq_s / bs if bs > 0 else None,
+            "autotune": {q: tune[q] for q in ("cta_slots_primal", "cta_slots_dual", "list_fraction",
+                                              "list_warps_per_sm") if q in tune}}
+
+
 def run_warm_start(args, dev, stream):
-    """Learned warm start: solve a family of transportation LPs (shared A, perturbed b and
-    c) with the plain solver, train the network on those solutions with the library's own
-    kernels, then solve held-out instances from zero and from the network's prediction.
-    Solves run batched (every instance with its own restarts and status); the warm time
-    includes the network's inference."""
+    """Learned warm start on the transportation family (300 sources x 300 sinks, 20,000 side
+    rows: shared A, perturbed b and c): solve training instances with the plain solver,
+    train the network on those solutions with the library's own kernels, then solve
+    held-out instances from zero and from the network's prediction, guarded per instance
+    (``gnn.guard_starts``: a prediction is kept only where its KKT error after 64 iterations
+    is no worse than the cold start's).  Solves run batched (every instance with its own
+    restarts and status).  The warm time includes inference and the guard's probes; power
+    iteration and graph capture are outside both timings."""
     import numpy as np
     import torch
 
@@ -466,38 +522,40 @@ def run_warm_start(args, dev, stream):
     from paper_2601_07628_gb300 import gnn
     from paper_2601_07628_gb300.dpdlp import Solver
 
+    fam = lpgen.transport_family(seed=4)
     if args.x3_full:
-        fam = lpgen.transport_family(seed=4)
-        ntrain, ntest, tol_train, epochs, chunk = 2000, 200, 1e-4, 8, 250
+        ntrain, ntest, epochs = 2000, 200, 8
     else:
-        fam = lpgen.transport_family(seed=12, S=100, D=100, side_rows=2000, arcs_per_side=10)
-        ntrain, ntest, tol_train, epochs, chunk = 256, 32, 1e-6, 30, 256
+        ntrain, ntest, epochs = args.ws_train, args.ws_test, args.ws_epochs
+    tol_train, chunk = 1e-4, 200
 
-    def solve(lps, tol, starts=None):
+    def solve(lps, tol, starts=None, guard=False):
         s = Solver(dev)
         s.set_stream(stream)
         s.load_batch(lps)
-        if starts is not None:
-            s.set_start(np.concatenate([x for x, _ in starts]), np.concatenate([y for _, y in starts]))
         s.solve(tol, 64)  # power iteration and graph capture, untimed
         s.set_param("resume", 0)
-        if starts is not None:
-            s.set_start(np.concatenate([x for x, _ in starts]), np.concatenate([y for _, y in starts]))
         t0 = time.perf_counter()
+        keep = None
+        if starts is not None:
+            if guard:
+                starts, keep, _, _ = gnn.guard_starts(s, lps, starts)
+            else:
+                s.set_start(np.concatenate([x for x, _ in starts]), np.concatenate([y for _, y in starts]))
         st = s.solve(tol, 2_000_000)
         dt = time.perf_counter() - t0
         x, y = s.solution()
         its = [k["iterations"] for k in s.batch_kkt()]
         parts = s.split(x, y)
         s.close()
-        return st, dt, parts, its
+        return st, dt, parts, its, keep
 
     t0 = time.perf_counter()
     train = [lpgen.transport_lp(fam, 100 + i) for i in range(ntrain)]
     test = [lpgen.transport_lp(fam, 1_000_000 + i) for i in range(ntest)]
     xs, ys, data_s = [], [], 0.0
     for a in range(0, ntrain, chunk):
-        st, dt, parts, _ = solve(train[a:a + chunk], tol_train)
+        st, dt, parts, _, _ = solve(train[a:a + chunk], tol_train)
         data_s += dt
         xs += [x.copy() for x, _ in parts]
         ys += [y.copy() for _, y in parts]
@@ -529,16 +587,20 @@ def run_warm_start(args, dev, stream):
            "train_instances": ntrain, "train_tol": tol_train, "solve_train_s": data_s,
            "generate_and_solve_s": gen_s, "epochs": epochs, "train_s": train_s,
            "train_ms_per_step": 1e3 * train_s / steps, "loss_first_last": [hist[0], hist[-1]],
-           "test_instances": ntest, "inference_s": infer_s}
+           "test_instances": ntest, "inference_s": infer_s,
+           "guard": "a prediction is kept where its KKT error after 64 iterations is no worse "
+                    "than the cold start's; the probes are inside the warm time"}
     for tol in (1e-6, 1e-8):
-        stc, tc, _, itc = solve(test, tol)
-        stw, tw, _, itw = solve(test, tol, starts)
+        stc, tc, _, itc, _ = solve(test, tol)
+        stw, tw, _, itw, keep = solve(test, tol, starts, guard=True)
         out[f"{tol:.0e}"] = {
             "cold": {"status": stc, "seconds": tc, "median_iterations": float(np.median(itc)),
-                     "mean_iterations": float(np.mean(itc))},
+                     "mean_iterations": float(np.mean(itc)), "max_iterations": int(max(itc))},
             "warm": {"status": stw, "seconds": tw + infer_s, "median_iterations": float(np.median(itw)),
-                     "mean_iterations": float(np.mean(itw))},
+                     "mean_iterations": float(np.mean(itw)), "max_iterations": int(max(itw)),
+                     "predictions_kept": int(sum(keep))},
             "instances_faster_warm": int(sum(w < c for w, c in zip(itw, itc))),
+            "per_instance_iterations": {"cold": [int(v) for v in itc], "warm": [int(v) for v in itw]},
         }
     return out
 

@@ -236,6 +236,14 @@ int dpdlp_set_row_bounds(dpdlp_t* h, const double* lc, const double* uc);
  *   their order are those of the separate launches, so results are bitwise the same;
  *   fused_body = 0 always launches the kernels separately.  dpdlp_get_info reports which
  *   form the next solve takes.
+ *   pdl (1): the iteration kernels launch as programmatic dependents of the kernel before
+ *   them (they load what no kernel writes -- slot descriptors, first index batches -- while
+ *   it drains, then wait for it); 0 = plain stream order.  Results do not depend on it.
+ *   list_fraction (0.5, 0..2), list_warps_per_sm (0 = the most the list kernel's register
+ *   budget allows): batches only.  A graph body walks the lists of slots of running
+ *   instances (a persistent kernel with list_warps_per_sm resident warps per SM) when fewer
+ *   than list_fraction of all slots are active, else launches over every slot (stopped
+ *   instances' warps exit at once).  Launch choices only, set by the autotuner.
  * Load-time keys (block_permute, perm_block, perm_seed, precond, ruiz_passes,
  * pock_chambolle) take effect at the next dpdlp_load_lp / dpdlp_load_batch.  Unknown key or out-of-range value: DPDLP_ERR_INVALID. */
 int dpdlp_set_param(dpdlp_t* h, const char* key, double v);
@@ -292,7 +300,13 @@ int dpdlp_apply_AT(dpdlp_t* h, const double* y, double* out);
 /* Time `reps` back-to-back launches of one iteration kernel ("primal": fused CSC SpMV +
  * primal update, "dual": fused CSR SpMV + dual update) on the handle's stream with CUDA
  * events, on the current state (the state is left as it was).  *avg_ms = mean duration of
- * one launch.  Needs a solve or dpdlp_set_start beforehand. */
+ * one launch.  Needs a solve or dpdlp_set_start beforehand.  Other names:
+ *   "gather_primal", "access_primal", "stream_primal" (and _dual): access probes of the
+ *   orientation's product -- its index stream and x[col] gathers; plus its value stream;
+ *   its two streams alone -- without arithmetic (ceilings of the access pattern);
+ *   "primal_list", "primal_idle", "primal_list_idle" (and dual_), batches only: the
+ *   persistent kernel walking the list of every slot, a launch over every slot with all
+ *   instances stopped, the list kernel over an empty list (costs the autotuner compares). */
 int dpdlp_time_kernel(dpdlp_t* h, const char* which, int32_t reps, double* avg_ms);
 
 /* Sizes and layout of the loaded LP. */

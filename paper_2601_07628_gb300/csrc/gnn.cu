@@ -3,10 +3,12 @@
 // Four kinds of kernel carry the whole network:
 //   spmm_kernel       sparse aggregation over A's pattern, H = 64 features per node
 //                     (warp per row, two features per lane, sums in stored order);
-//   linear_kernel     relu(X1 W1^T + X2 W2^T + b) for 64-row tiles (BF16 weights widened
-//                     into shared memory, FP32 products and sums);
-//   linear_bwd_kernel the ReLU mask and the products with W1 and W2 for the backward pass;
-//   wgrad_kernel      weight and bias gradients dZ^T X as fixed per-block partial sums,
+//   linear_mma_kernel relu(X1 W1^T + X2 W2^T + b) of the 64 x 64 layers on the tensor
+//                     cores (mma.sync BF16, FP32 accumulation, FP32 activations split into
+//                     BF16 hi + lo); linear_kernel the same on the FP32 pipe for the 8-wide
+//                     input encoders;
+//   linear_bwd_*      the ReLU mask and the products with W1 and W2 for the backward pass;
+//   wgrad_*           weight and bias gradients dZ^T X as fixed per-block partial sums,
 //                     added in block order by reduce_partials_kernel.
 // No floating-point atomics anywhere: every result is bitwise reproducible.
 #include <cuda_bf16.h>
@@ -72,11 +74,29 @@ __global__ void __launch_bounds__(TPB) spmm_kernel(int rows, const int64_t* __re
   const int lane = threadIdx.x & 31;
   if (r >= rows) return;
   float2 acc = make_float2(0.f, 0.f);
-  for (int64_t k = ptr[r]; k < ptr[r + 1]; ++k) {
-    const float a = val[k];
-    const float2 h = reinterpret_cast<const float2*>(in + (size_t)idx[k] * H)[lane];
-    acc.x = fmaf(a, h.x, acc.x);
-    acc.y = fmaf(a, h.y, acc.y);
+  // the row's entries SPMM_BATCH at a time: indices and values, then the gathers, all in
+  // flight together; the products are added in stored order
+  constexpr int SPMM_BATCH = 8;
+  const int64_t k1 = ptr[r + 1];
+  for (int64_t k = ptr[r]; k < k1; k += SPMM_BATCH) {
+    int j[SPMM_BATCH];
+    float a[SPMM_BATCH];
+    float2 h[SPMM_BATCH];
+#pragma unroll
+    for (int u = 0; u < SPMM_BATCH; ++u) {
+      j[u] = k + u < k1 ? idx[k + u] : -1;
+      a[u] = k + u < k1 ? val[k + u] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < SPMM_BATCH; ++u)
+      h[u] = j[u] >= 0 ? reinterpret_cast<const float2*>(in + (size_t)j[u] * H)[lane]
+                       : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < SPMM_BATCH; ++u) {
+      if (j[u] < 0) break;
+      acc.x = fmaf(a[u], h[u].x, acc.x);
+      acc.y = fmaf(a[u], h[u].y, acc.y);
+    }
   }
   float2* o = reinterpret_cast<float2*>(out + (size_t)r * H) + lane;
   if (accumulate) {
@@ -230,6 +250,265 @@ __global__ void __launch_bounds__(TPB) linear_bwd_kernel(int N, const float* __r
   }
 }
 
+// ---------------------------------------------------------------- tensor-core dense layers
+// The 64 x 64 layers run on the tensor cores: mma.sync m16n8k16, BF16 operands, FP32
+// accumulation.  Weights are BF16 already.  Activations are FP32; each is split into
+// hi = bf16(v) and lo = bf16(v - hi), and a product with a weight is taken as hi*w + lo*w
+// (both exact in FP32), which keeps 16 significant bits of v.  In the weight gradient both
+// operands are FP32 activations: dZ^T X is taken as Zhi Xhi + Zhi Xlo + Zlo Xhi.
+// Fragment layout of m16n8k16 (g = lane / 4, t = lane % 4):
+//   A (16 x 16, row-major)  a0 = A[g][2t..2t+1], a1 = A[g+8][2t..], a2 = A[g][2t+8..], a3 = A[g+8][2t+8..]
+//   B (16 x 8, k-major)     b0 = B[2t..2t+1][g], b1 = B[2t+8..2t+9][g]
+//   C (16 x 8, FP32)        c0, c1 = C[g][2t], C[g][2t+1];  c2, c3 = C[g+8][2t], C[g+8][2t+1]
+// (a register holds two BF16, the lower column / row index in the low half).
+constexpr int MMA_WARPS = 8;                     // warps per block, 16 rows each
+constexpr int MMA_ROWS = MMA_WARPS * 16;         // rows per block of the dense kernels
+constexpr int WPAD = H + 8;                      // shared row stride (BF16): conflict-free fragments
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+      "{%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat162 v) {
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// hi and lo BF16 pairs of two FP32 values (the first in the low half)
+__device__ __forceinline__ void split2(float2 v, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+  const float2 hf = __bfloat1622float2(h);
+  hi = pack_bf16(h);
+  lo = pack_bf16(__floats2bfloat162_rn(v.x - hf.x, v.y - hf.y));
+}
+
+// Stage W[H][H] (BF16) as S[n][k] = W[n][k] (transpose = false) or W[k][n] (true).
+__device__ __forceinline__ void stage_w_bf16(__nv_bfloat16 (*S)[WPAD], const __nv_bfloat16* W,
+                                             bool transpose) {
+  for (int e = threadIdx.x; e < H * H; e += MMA_WARPS * 32) {
+    const int r = e / H, c = e % H;
+    if (transpose) S[c][r] = W[e];
+    else S[r][c] = W[e];
+  }
+}
+
+// B fragments of n-tile j, k-step kk from S[n][k]
+__device__ __forceinline__ void b_frag(const __nv_bfloat16 (*S)[WPAD], int j, int kk, int g,
+                                       int t, uint32_t& b0, uint32_t& b1) {
+  b0 = *reinterpret_cast<const uint32_t*>(&S[8 * j + g][16 * kk + 2 * t]);
+  b1 = *reinterpret_cast<const uint32_t*>(&S[8 * j + g][16 * kk + 2 * t + 8]);
+}
+
+// A fragments (hi, lo) of k-step kk of the 16-row tile at row r0 of X[N][H] (rows >= N: 0)
+__device__ __forceinline__ void a_frag_split(const float* X, int r0, int N, int kk, int g, int t,
+                                             uint32_t (&hi)[4], uint32_t (&lo)[4]) {
+  const int ra = r0 + g, rb = r0 + g + 8, c = 16 * kk + 2 * t;
+  const float2 z = make_float2(0.f, 0.f);
+  const float2 v0 = ra < N ? *reinterpret_cast<const float2*>(X + (size_t)ra * H + c) : z;
+  const float2 v1 = rb < N ? *reinterpret_cast<const float2*>(X + (size_t)rb * H + c) : z;
+  const float2 v2 = ra < N ? *reinterpret_cast<const float2*>(X + (size_t)ra * H + c + 8) : z;
+  const float2 v3 = rb < N ? *reinterpret_cast<const float2*>(X + (size_t)rb * H + c + 8) : z;
+  split2(v0, hi[0], lo[0]);
+  split2(v1, hi[1], lo[1]);
+  split2(v2, hi[2], lo[2]);
+  split2(v3, hi[3], lo[3]);
+}
+
+// out = relu(X1 W1^T + X2 W2^T + b) for X1, X2 [N][H], W1, W2 [H][H]: each warp one 16-row
+// tile, all 64 output columns (8 n-tiles), both products into the same accumulators.
+__global__ void __launch_bounds__(MMA_WARPS * 32) linear_mma_kernel(
+    int N, const float* __restrict__ X1, const __nv_bfloat16* __restrict__ W1,
+    const float* __restrict__ X2, const __nv_bfloat16* __restrict__ W2,
+    const float* __restrict__ b, float* out) {
+  __shared__ __align__(16) __nv_bfloat16 S1[H][WPAD];
+  __shared__ __align__(16) __nv_bfloat16 S2[H][WPAD];
+  stage_w_bf16(S1, W1, false);
+  stage_w_bf16(S2, W2, false);
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = blockIdx.x * MMA_ROWS + w * 16;
+  if (r0 >= N) return;
+  float acc[8][4];
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+#pragma unroll
+  for (int which = 0; which < 2; ++which) {
+    const float* X = which ? X2 : X1;
+    const __nv_bfloat16(*S)[WPAD] = which ? S2 : S1;
+#pragma unroll
+    for (int kk = 0; kk < H / 16; ++kk) {
+      uint32_t hi[4], lo[4];
+      a_frag_split(X, r0, N, kk, g, t, hi, lo);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        uint32_t b0, b1;
+        b_frag(S, j, kk, g, t, b0, b1);
+        mma_bf16(acc[j], hi, b0, b1);
+        mma_bf16(acc[j], lo, b0, b1);
+      }
+    }
+  }
+  const int ra = r0 + g, rb = r0 + g + 8;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int c = 8 * j + 2 * t;
+    const float b0 = b[c], b1 = b[c + 1];
+    if (ra < N)
+      *reinterpret_cast<float2*>(out + (size_t)ra * H + c) =
+          make_float2(fmaxf(acc[j][0] + b0, 0.f), fmaxf(acc[j][1] + b1, 0.f));
+    if (rb < N)
+      *reinterpret_cast<float2*>(out + (size_t)rb * H + c) =
+          make_float2(fmaxf(acc[j][2] + b0, 0.f), fmaxf(acc[j][3] + b1, 0.f));
+  }
+}
+
+// Backward of out = relu(X1 W1^T + X2 W2^T + b): dZ = dOut * [out > 0] (stored), then
+// dX1 = dZ W1 and dX2 = dZ W2 ([N][H] each) on the tensor cores.
+__global__ void __launch_bounds__(MMA_WARPS * 32) linear_bwd_mma_kernel(
+    int N, const float* __restrict__ dOut, const float* __restrict__ Hout,
+    const __nv_bfloat16* __restrict__ W1, const __nv_bfloat16* __restrict__ W2, float* dZ,
+    float* dX1, float* dX2) {
+  __shared__ __align__(16) __nv_bfloat16 S1[H][WPAD];
+  __shared__ __align__(16) __nv_bfloat16 S2[H][WPAD];
+  stage_w_bf16(S1, W1, true);  // B[o][k] = W[o][k] read as S[n = k][o]
+  stage_w_bf16(S2, W2, true);
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = blockIdx.x * MMA_ROWS + w * 16;
+  if (r0 >= N) return;
+  const int ra = r0 + g, rb = r0 + g + 8;
+  uint32_t hi[H / 16][4], lo[H / 16][4];
+#pragma unroll
+  for (int kk = 0; kk < H / 16; ++kk) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = (q & 1) ? rb : ra;
+      const int c = 16 * kk + 2 * t + ((q & 2) ? 8 : 0);
+      float2 z = make_float2(0.f, 0.f);
+      if (r < N) {
+        const size_t e = (size_t)r * H + c;
+        const float2 d = *reinterpret_cast<const float2*>(dOut + e);
+        const float2 h = *reinterpret_cast<const float2*>(Hout + e);
+        z = make_float2(h.x > 0.f ? d.x : 0.f, h.y > 0.f ? d.y : 0.f);
+        *reinterpret_cast<float2*>(dZ + e) = z;
+      }
+      split2(z, hi[kk][q], lo[kk][q]);
+    }
+  }
+#pragma unroll
+  for (int which = 0; which < 2; ++which) {
+    float* dX = which ? dX2 : dX1;
+    const __nv_bfloat16(*S)[WPAD] = which ? S2 : S1;
+    float acc[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < H / 16; ++kk) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        uint32_t b0, b1;
+        b_frag(S, j, kk, g, t, b0, b1);
+        mma_bf16(acc[j], hi[kk], b0, b1);
+        mma_bf16(acc[j], lo[kk], b0, b1);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = 8 * j + 2 * t;
+      if (ra < N) *reinterpret_cast<float2*>(dX + (size_t)ra * H + c) = make_float2(acc[j][0], acc[j][1]);
+      if (rb < N) *reinterpret_cast<float2*>(dX + (size_t)rb * H + c) = make_float2(acc[j][2], acc[j][3]);
+    }
+  }
+}
+
+// Weight gradient dW = dZ^T X (H x H) and bias gradient sum_r dZ[r] on the tensor cores:
+// partial[block][o * H + k] and partial[block][H * H + o] over the block's 64-row tiles
+// (tiles t = block, block + grid, ...), added in block order by reduce_partials_kernel.
+// Each 64-row tile is staged transposed in shared memory as BF16 hi / lo pairs (ZT[o][r],
+// XT[k][r]); warp w owns the output rows o = 16 (w % 4) .. + 15 and the n-tiles 4 (w / 4) .. + 3.
+constexpr int WG_TILE = 64;
+__global__ void __launch_bounds__(MMA_WARPS * 32) wgrad_mma_kernel(int N,
+                                                                  const float* __restrict__ dZ,
+                                                                  const float* __restrict__ X,
+                                                                  float* __restrict__ partial) {
+  __shared__ __align__(16) __nv_bfloat16 ZTh[H][WPAD], ZTl[H][WPAD], XTh[H][WPAD], XTl[H][WPAD];
+  __shared__ float bsum[4][H];
+  const int tid = threadIdx.x;
+  const int w = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  const int mt = w & 3, nh = w >> 2;
+  // staging: thread (col = tid % 64, pair = tid / 64) moves rows 2p, 2p + 1 for p = pair, pair + 4, ...
+  const int col = tid & (H - 1), pr = tid >> 6;
+  float acc[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+  float bacc = 0.f;
+  for (int tile = blockIdx.x; tile * WG_TILE < N; tile += gridDim.x) {
+    const int r0 = tile * WG_TILE;
+    __syncthreads();  // the previous tile's fragments are read
+    for (int p = pr; p < WG_TILE / 2; p += 4) {
+      const int ra = r0 + 2 * p, rb = ra + 1;
+      const float za = ra < N ? dZ[(size_t)ra * H + col] : 0.f;
+      const float zb = rb < N ? dZ[(size_t)rb * H + col] : 0.f;
+      const float xa = ra < N ? X[(size_t)ra * H + col] : 0.f;
+      const float xb = rb < N ? X[(size_t)rb * H + col] : 0.f;
+      bacc += za;
+      bacc += zb;
+      uint32_t h, l;
+      split2(make_float2(za, zb), h, l);
+      *reinterpret_cast<uint32_t*>(&ZTh[col][2 * p]) = h;
+      *reinterpret_cast<uint32_t*>(&ZTl[col][2 * p]) = l;
+      split2(make_float2(xa, xb), h, l);
+      *reinterpret_cast<uint32_t*>(&XTh[col][2 * p]) = h;
+      *reinterpret_cast<uint32_t*>(&XTl[col][2 * p]) = l;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < WG_TILE / 16; ++kk) {
+      uint32_t ah[4], al[4];
+      const int o = 16 * mt + g, c = 16 * kk + 2 * t;
+      ah[0] = *reinterpret_cast<const uint32_t*>(&ZTh[o][c]);
+      ah[1] = *reinterpret_cast<const uint32_t*>(&ZTh[o + 8][c]);
+      ah[2] = *reinterpret_cast<const uint32_t*>(&ZTh[o][c + 8]);
+      ah[3] = *reinterpret_cast<const uint32_t*>(&ZTh[o + 8][c + 8]);
+      al[0] = *reinterpret_cast<const uint32_t*>(&ZTl[o][c]);
+      al[1] = *reinterpret_cast<const uint32_t*>(&ZTl[o + 8][c]);
+      al[2] = *reinterpret_cast<const uint32_t*>(&ZTl[o][c + 8]);
+      al[3] = *reinterpret_cast<const uint32_t*>(&ZTl[o + 8][c + 8]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = 8 * (4 * nh + j) + g;
+        const uint32_t bh0 = *reinterpret_cast<const uint32_t*>(&XTh[k][c]);
+        const uint32_t bh1 = *reinterpret_cast<const uint32_t*>(&XTh[k][c + 8]);
+        const uint32_t bl0 = *reinterpret_cast<const uint32_t*>(&XTl[k][c]);
+        const uint32_t bl1 = *reinterpret_cast<const uint32_t*>(&XTl[k][c + 8]);
+        mma_bf16(acc[j], ah, bh0, bh1);
+        mma_bf16(acc[j], ah, bl0, bl1);
+        mma_bf16(acc[j], al, bh0, bh1);
+      }
+    }
+  }
+  float* p = partial + (size_t)blockIdx.x * (H * H + H);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int k = 8 * (4 * nh + j) + 2 * t, o = 16 * mt + g;
+    *reinterpret_cast<float2*>(p + (size_t)o * H + k) = make_float2(acc[j][0], acc[j][1]);
+    *reinterpret_cast<float2*>(p + (size_t)(o + 8) * H + k) = make_float2(acc[j][2], acc[j][3]);
+  }
+  bsum[pr][col] = bacc;
+  __syncthreads();
+  if (tid < H) p[H * H + tid] = ((bsum[0][tid] + bsum[1][tid]) + bsum[2][tid]) + bsum[3][tid];
+}
+
 // partial[block][o * K + k] = sum over the block's rows r of dZ[r][o] X[r][k], and
 // partial[block][H * K + o] = sum of dZ[r][o] (bias); tiles t = block, block + grid, ...
 template <int K>
@@ -266,14 +545,39 @@ __global__ void __launch_bounds__(TPB) wgrad_kernel(int N, const float* __restri
 }
 
 // grad[e] += sum over blocks g (in order) of partial[g * stride + e], e < len.
-__global__ void reduce_partials_kernel(int G, int len, int stride,
-                                       const float* __restrict__ partial, float* grad) {
-  const int e = blockIdx.x * TPB + threadIdx.x;
-  if (e >= len) return;
-  float s = 0.f;
-  for (int g = 0; g < G; ++g) s += partial[(size_t)g * stride + e];
-  grad[e] += s;
+// grad[e] += sum over blocks g of partial[g * stride + e], e < len: a block takes 32
+// consecutive e and RP_SLICES slices of g (slice q: g = q, q + RP_SLICES, ... in order, loads
+// batched), then adds the slices' sums in slice order.  Fixed order: reproducible.
+constexpr int RP_E = 32, RP_SLICES = 8, RP_BATCH = 8;
+__global__ void __launch_bounds__(RP_E * RP_SLICES) reduce_partials_kernel(
+    int G, int len, int stride, const float* __restrict__ partial, float* grad) {
+  __shared__ float part[RP_SLICES][RP_E];
+  const int ex = threadIdx.x % RP_E, q = threadIdx.x / RP_E;
+  const int e = blockIdx.x * RP_E + ex;
+  float acc = 0.f;
+  if (e < len) {
+    for (int g = q; g < G; g += RP_SLICES * RP_BATCH) {
+      float v[RP_BATCH];
+#pragma unroll
+      for (int u = 0; u < RP_BATCH; ++u) {
+        const int gg = g + u * RP_SLICES;
+        v[u] = gg < G ? partial[(size_t)gg * stride + e] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < RP_BATCH; ++u)
+        if (g + u * RP_SLICES < G) acc += v[u];
+    }
+  }
+  part[q][ex] = acc;
+  __syncthreads();
+  if (q == 0 && e < len) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < RP_SLICES; ++k) s += part[k][ex];
+    grad[e] += s;
+  }
 }
+int reduce_grid(int len) { return (len + RP_E - 1) / RP_E; }
 
 // out[r] = Hm[r] . w + b (warp per row, fixed shuffle tree).
 __global__ void __launch_bounds__(TPB) head_kernel(int N, const float* __restrict__ Hm,
@@ -319,26 +623,73 @@ __global__ void __launch_bounds__(TPB) head_bwd_kernel(int N, const float* __res
 }
 
 // partial[block][k] = sum over the block's rows of d[r] Hm[r][k] (k < H), [H] = sum d[r].
+// Thread (rg, c) of the 4 x 64 threads sums, over the block's tiles, the rows r = tile
+// start + rg, + 4, ... of d[r] Hm[r][c] (and thread c = 0 also d[r], the bias gradient), the
+// rows' loads batched; the four row groups are then added in order.  Fixed order.
+constexpr int HW_GROUPS = TPB / H;  // 4 row groups of 64 columns
 __global__ void __launch_bounds__(TPB) head_wgrad_kernel(int N, const float* __restrict__ d,
                                                          const float* __restrict__ Hm,
                                                          float* __restrict__ partial) {
-  const int t = threadIdx.x;
-  float acc = 0.f;
+  __shared__ float part[HW_GROUPS][H + 1];
+  const int c = threadIdx.x % H, rg = threadIdx.x / H;
+  constexpr int BATCH = 4;
+  float acc = 0.f, bacc = 0.f;
   for (int tile = blockIdx.x; tile * TILE < N; tile += gridDim.x) {
     const int r1 = min(N, (tile + 1) * TILE);
-    for (int r = tile * TILE; r < r1; ++r) {
-      if (t < H) acc = fmaf(d[r], Hm[(size_t)r * H + t], acc);
-      else if (t == H) acc += d[r];
+    for (int r = tile * TILE + rg; r < r1; r += HW_GROUPS * BATCH) {
+      float dv[BATCH], hv[BATCH];
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u) {
+        const int rr = r + u * HW_GROUPS;
+        dv[u] = rr < r1 ? d[rr] : 0.f;
+        hv[u] = rr < r1 ? Hm[(size_t)rr * H + c] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u) {
+        if (r + u * HW_GROUPS >= r1) break;
+        acc = fmaf(dv[u], hv[u], acc);
+        bacc += dv[u];
+      }
     }
   }
-  if (t <= H) partial[(size_t)blockIdx.x * (H + 1) + t] = acc;
+  part[rg][c] = acc;
+  if (c == 0) part[rg][H] = bacc;
+  __syncthreads();
+  if (threadIdx.x <= H) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < HW_GROUPS; ++k) s += part[k][threadIdx.x];
+    partial[(size_t)blockIdx.x * (H + 1) + threadIdx.x] = s;
+  }
 }
 
-__global__ void sum_parts_kernel(int G, const float* __restrict__ parts, double* out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// *out = sum of parts[0 .. G) in FP64: thread t adds parts t, t + SP_THREADS, ... in order
+// (loads batched), then a fixed tree over the threads.
+constexpr int SP_THREADS = 1024;
+__global__ void __launch_bounds__(SP_THREADS) sum_parts_kernel(int G, const float* __restrict__ parts,
+                                                               double* out) {
+  __shared__ double red[SP_THREADS / 32];
   double s = 0.0;
-  for (int g = 0; g < G; ++g) s += parts[g];
-  *out = s;
+  constexpr int BATCH = 8;
+  for (int g = threadIdx.x; g < G; g += SP_THREADS * BATCH) {
+    float v[BATCH];
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      const int gg = g + u * SP_THREADS;
+      v[u] = gg < G ? parts[gg] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) s += (double)v[u];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < SP_THREADS / 32; ++k) t += red[k];
+    *out = t;
+  }
 }
 
 __global__ void adam_kernel(int64_t P, float* theta, float* grad, float* m1, float* m2,
@@ -428,6 +779,7 @@ void free_graph_buffers(dpdlp_gnn* g) {
 }
 
 int blocks_for_rows(int rows) { return (rows + TILE - 1) / TILE; }
+int mma_blocks(int rows) { return (rows + MMA_ROWS - 1) / MMA_ROWS; }
 int warp_blocks(int rows) { return (int)(((size_t)rows * 32 + TPB - 1) / TPB); }
 int wg_grid(int rows) {
   const int b = blocks_for_rows(rows);
@@ -449,8 +801,9 @@ int add_wgrad(dpdlp_gnn* g, int N, const float* dZ, const float* X, int64_t off,
   const int G = wg_grid(N);
   const int stride = H * K + H;
   const int len = with_bias ? stride : H * K;
-  wgrad_kernel<K><<<G, TPB, 0, g->stream>>>(N, dZ, X, g->partial);
-  reduce_partials_kernel<<<(len + TPB - 1) / TPB, TPB, 0, g->stream>>>(G, len, stride, g->partial,
+  if constexpr (K == H) wgrad_mma_kernel<<<G, MMA_WARPS * 32, 0, g->stream>>>(N, dZ, X, g->partial);
+  else wgrad_kernel<K><<<G, TPB, 0, g->stream>>>(N, dZ, X, g->partial);
+  reduce_partials_kernel<<<reduce_grid(len), RP_E * RP_SLICES, 0, g->stream>>>(G, len, stride, g->partial,
                                                                         g->grad + off);
   GCK(cudaGetLastError());
   return 0;
@@ -662,11 +1015,11 @@ int dpdlp_gnn_forward(dpdlp_gnn_t* g, float* x_hat, float* y_hat) {
   for (int l = 0; l < L; ++l) {
     if (m) {
       spmm_kernel<<<warp_blocks(m), TPB, 0, s>>>(m, g->a_ptr, g->a_idx, g->a_R, g->hv[l], g->gc[l], 0);
-      linear_kernel<H, true><<<blocks_for_rows(m), TPB, 0, s>>>(m, g->hc[l], w + LAY.Uc[l], g->gc[l], w + LAY.Vc[l], th + LAY.bc[l], g->hc[l + 1]);
+      linear_mma_kernel<<<mma_blocks(m), MMA_WARPS * 32, 0, s>>>(m, g->hc[l], w + LAY.Uc[l], g->gc[l], w + LAY.Vc[l], th + LAY.bc[l], g->hc[l + 1]);
     }
     if (n) {
       spmm_kernel<<<warp_blocks(n), TPB, 0, s>>>(n, g->t_ptr, g->t_idx, g->t_C, g->hc[l + 1], g->gv[l], 0);
-      linear_kernel<H, true><<<blocks_for_rows(n), TPB, 0, s>>>(n, g->hv[l], w + LAY.Uv[l], g->gv[l], w + LAY.Vv[l], th + LAY.bv[l], g->hv[l + 1]);
+      linear_mma_kernel<<<mma_blocks(n), MMA_WARPS * 32, 0, s>>>(n, g->hv[l], w + LAY.Uv[l], g->gv[l], w + LAY.Vv[l], th + LAY.bv[l], g->hv[l + 1]);
     }
   }
   if (n) head_kernel<<<warp_blocks(n), TPB, 0, s>>>(n, g->hv[L], w + LAY.wx, th + LAY.bx, g->xhat);
@@ -694,20 +1047,20 @@ int dpdlp_gnn_backward(dpdlp_gnn_t* g, const float* tx, const float* ty, double*
     head_bwd_kernel<<<gx, TPB, 0, s>>>(n, g->xhat, g->tx, w + LAY.wx, g->dx, g->dhv[0], g->loss_part);
     const int G = wg_grid(n);
     head_wgrad_kernel<<<G, TPB, 0, s>>>(n, g->dx, g->hv[L], g->partial);
-    reduce_partials_kernel<<<1, TPB, 0, s>>>(G, H + 1, H + 1, g->partial, g->grad + LAY.wx);
+    reduce_partials_kernel<<<reduce_grid(H + 1), RP_E * RP_SLICES, 0, s>>>(G, H + 1, H + 1, g->partial, g->grad + LAY.wx);
   }
   if (m) {
     head_bwd_kernel<<<gy, TPB, 0, s>>>(m, g->yhat, g->ty, w + LAY.wy, g->dy, g->dhc[0], g->loss_part + gx);
     const int G = wg_grid(m);
     head_wgrad_kernel<<<G, TPB, 0, s>>>(m, g->dy, g->hc[L], g->partial);
-    reduce_partials_kernel<<<1, TPB, 0, s>>>(G, H + 1, H + 1, g->partial, g->grad + LAY.wy);
+    reduce_partials_kernel<<<reduce_grid(H + 1), RP_E * RP_SLICES, 0, s>>>(G, H + 1, H + 1, g->partial, g->grad + LAY.wy);
   }
-  sum_parts_kernel<<<1, 32, 0, s>>>(gx + gy, g->loss_part, g->loss_d);
+  sum_parts_kernel<<<1, SP_THREADS, 0, s>>>(gx + gy, g->loss_part, g->loss_d);
   int rc;
   for (int l = L - 1; l >= 0; --l) {
     // variable update of round l: hv[l+1] = relu(hv[l] Uv^T + gv[l] Vv^T + bv), gv = C hc[l+1]
     if (n) {
-      linear_bwd_kernel<<<blocks_for_rows(n), TPB, 0, s>>>(n, g->dhv[cv], g->hv[l + 1], w + LAY.Uv[l], w + LAY.Vv[l], g->dzv, g->dhv[1 - cv], g->dgv);
+      linear_bwd_mma_kernel<<<mma_blocks(n), MMA_WARPS * 32, 0, s>>>(n, g->dhv[cv], g->hv[l + 1], w + LAY.Uv[l], w + LAY.Vv[l], g->dzv, g->dhv[1 - cv], g->dgv);
       if ((rc = add_wgrad<H>(g, n, g->dzv, g->hv[l], LAY.Uv[l], false))) return rc;
       if ((rc = add_wgrad<H>(g, n, g->dzv, g->gv[l], LAY.Vv[l], true))) return rc;
       if (m) spmm_kernel<<<warp_blocks(m), TPB, 0, s>>>(m, g->a_ptr, g->a_idx, g->a_Ct, g->dgv, g->dhc[cc], 1);
@@ -715,7 +1068,7 @@ int dpdlp_gnn_backward(dpdlp_gnn_t* g, const float* tx, const float* ty, double*
     }
     // constraint update of round l: hc[l+1] = relu(hc[l] Uc^T + gc[l] Vc^T + bc), gc = R hv[l]
     if (m) {
-      linear_bwd_kernel<<<blocks_for_rows(m), TPB, 0, s>>>(m, g->dhc[cc], g->hc[l + 1], w + LAY.Uc[l], w + LAY.Vc[l], g->dzc, g->dhc[1 - cc], g->dgc);
+      linear_bwd_mma_kernel<<<mma_blocks(m), MMA_WARPS * 32, 0, s>>>(m, g->dhc[cc], g->hc[l + 1], w + LAY.Uc[l], w + LAY.Vc[l], g->dzc, g->dhc[1 - cc], g->dgc);
       if ((rc = add_wgrad<H>(g, m, g->dzc, g->hc[l], LAY.Uc[l], false))) return rc;
       if ((rc = add_wgrad<H>(g, m, g->dzc, g->gc[l], LAY.Vc[l], true))) return rc;
       if (n) spmm_kernel<<<warp_blocks(n), TPB, 0, s>>>(n, g->t_ptr, g->t_idx, g->t_Rt, g->dgc, g->dhv[cv], 1);

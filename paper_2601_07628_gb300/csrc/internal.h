@@ -74,6 +74,7 @@ struct DevPacked {
   int rows = 0, cols = 0, nslots = 0, nlong = 0, npieces = 0;
   int nlong_block = 0, nlong_warp = 0;
   int cta_slots = PK_WARPS;  // slots per block of this orientation's iteration kernel (2, 4, 8)
+  int list_warps_per_sm = 0;  // resident warps per SM of the persistent list kernel (0: most)
   const double* val = nullptr;
   const float* val32 = nullptr;  // FP32 copy of the values (nullptr: not representable)
   const uint32_t* idx = nullptr;
@@ -223,6 +224,7 @@ struct IterPlan {
   int force_regular;  // 1: run as a regular iteration regardless of the scalars (timing)
   int list;           // batches: 1 walk the active-slot list, 0 one launch over every slot
   int pdl;            // launch as a programmatic dependent of the previous kernel
+  int idle;           // timing only: every instance counts as stopped (an empty slot list)
 };
 
 cudaError_t launch_primal(const DevPacked& csc, const DevVecs& v, const DevScalars* sc,
@@ -236,8 +238,12 @@ constexpr int FUSED_MAX_SLOTS = 64;
 bool fused_body_fits(const DevPacked& csc, const DevPacked& csr, int ninst, int max_slots);
 // Sets the fused kernel's shared-memory limit; called before the first launch or capture.
 cudaError_t fused_body_prepare();
+// cluster > 1: the body spread over a thread-block cluster of that many CTAs (at most 8),
+// bitwise the same results.
 cudaError_t launch_body_fused(const DevPacked& csc, const DevPacked& csr, const DevVecs& v,
-                              const DevScalars* sc, int K, cudaStream_t s);
+                              const DevScalars* sc, int K, int cluster, cudaStream_t s);
+// CTAs of the cluster form: `requested` (>= 1), or 0 = about two slots per CTA, at most 8.
+int fused_cluster_ctas(const DevPacked& csc, const DevPacked& csr, int requested);
 // out0 = M x0 (and out1 = M x1 when x1 != nullptr) for one packed orientation M; with
 // `running` (a batch's instance scalars) only the rows of running instances are computed.
 cudaError_t launch_spmv(const DevPacked& M, const double* x0, const double* x1, double* out0,
@@ -245,10 +251,12 @@ cudaError_t launch_spmv(const DevPacked& M, const double* x0, const double* x1, 
 cudaError_t launch_check(const DevPacked& csr, const DevPacked& csc, const DevVecs& v,
                          DevScalars* sc, unsigned long long cond_handle, int use_cond,
                          cudaStream_t s);
-// Batches: set the graph conditional `handle` to 1 when fewer than half of the slots are
-// active (the next body walks the lists), else 0.
+// Batches: set the graph conditional `handle` to 1 when fewer than `fraction` of the slots
+// are active (the next body walks the lists), else 0.
 cudaError_t launch_select(const DevPacked& csr, const DevPacked& csc, unsigned long long handle,
-                          cudaStream_t s);
+                          double fraction, cudaStream_t s);
+// Most resident warps per SM of the persistent list kernel (its register budget).
+int list_max_warps_per_sm();
 // Batches: rebuild both orientations' lists of slots of running instances.
 cudaError_t launch_compact(const DevPacked& csr, const DevPacked& csc, const DevVecs& v,
                            cudaStream_t s);

@@ -21,6 +21,7 @@
 //                     CUDA-graph loop condition.
 //  apply_kernel       after a check: restart (anchor and iterate <- PDHG output) or the
 //                     Halpern step of the check iteration.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "../../include/dpdlp.h"
@@ -168,6 +169,17 @@ __device__ __forceinline__ double block_sum(double v, double* buf) {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
 
+// Store v at shared-memory address p (a generic pointer into this CTA's shared memory) of
+// every CTA 0 .. ncta-1 of the thread-block cluster, through distributed shared memory.
+__device__ __forceinline__ void st_cluster_all(double* p, double v, unsigned ncta) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  for (unsigned c = 0; c < ncta; ++c) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(c));
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(r), "d"(v) : "memory");
+  }
+}
+
 // ---------------------------------------------------------------- epilogues
 // An epilogue turns finished row sums into outputs: `apply_direct(row, sums)`.
 
@@ -269,6 +281,7 @@ __device__ __forceinline__ bool load_global(const DevScalars* sc, IterPlan p, It
 __device__ __forceinline__ bool load_inst_mode(const InstScalars* tab, int inst, IterPlan p,
                                                IterScalars& o) {
   const InstScalars& I = tab[inst];
+  if (p.idle) return false;                                // timing an idle launch
   if (I.status != -1 && !p.force_regular) return false;  // converged instance: skip its rows
   o.fp32 = I.spmv_fp32;
   return true;
@@ -290,7 +303,9 @@ __device__ __forceinline__ void load_inst_steps(const InstScalars* tab, const do
 //   Halpern: x <- w1 ((1+gamma) x^ - gamma x) + w0 x0   (with gamma = 1 the reflected point
 //   is x_bar itself), regular iterations;
 //   check iteration: keep x = x^k, store x^ and dx = x^k - x^.
-template <bool Single, bool QP = false>
+// Bcast: x_bar is a shared-memory vector copied in every CTA of a cluster (the cluster
+// form of the fused body); each new x_bar_j is stored into all ncta copies.
+template <bool Single, bool QP = false, bool Bcast = false>
 struct PrimalEpi {
   static constexpr bool kTunable = true;
   static constexpr bool kListable = !Single;  // one LP never uses the active-slot list
@@ -303,6 +318,7 @@ struct PrimalEpi {
   double *x, *xbar, *xh, *dx;
   const double* qd;  // diagonal of Q of a diagonal QP (nullptr: an LP)
   IterScalars q;
+  unsigned ncta = 0;  // Bcast: CTAs of the cluster
   // Single: one instance, whose scalars are loaded once per launch in begin()
   __device__ bool begin() {
     if (!Single) return load_global(sc, plan, q);
@@ -333,7 +349,8 @@ struct PrimalEpi {
     if constexpr (QP) t = t / fma(q.step, ld_once(qd + j), 1.0);
     const double xhj = clampd_int(t, lvj, uvj);
     const double xb = fma(2.0, xhj, -xj);
-    st_keep(xbar + j, xb);
+    if constexpr (Bcast) st_cluster_all(xbar + j, xb, ncta);
+    else st_keep(xbar + j, xb);
     if (q.check) {
       xh[j] = xhj;
       dx[j] = xj - xhj;
@@ -394,7 +411,9 @@ struct PrimalEpi {
 //   w = y / sigma - z,  d = w - proj_{-S}(w),  y^ = sigma d,  -S_i = [lo_i, hi_i] = [-uc_i, -lc_i];
 //   Halpern: y <- w1 ((1+gamma) y^ - gamma y) + w0 y0, with gamma = 1 evaluated as
 //   w1 (2 sigma d - y) + w0 y0; check iteration: keep y = y^k, store y^.
-template <bool Single, bool MirrorY = false>
+// Mirror: 1 = every new y_i is also written to the shared copy ys (the fused body), 2 = to
+// the shared copy ys of every CTA of a cluster (the cluster form of the fused body).
+template <bool Single, int Mirror = 0>
 struct DualEpi {
   static constexpr bool kTunable = true;
   static constexpr bool kListable = !Single;  // one LP never uses the active-slot list
@@ -406,7 +425,8 @@ struct DualEpi {
   const double *lo, *hi, *y0;
   double *y, *yh;
   IterScalars q;
-  double* ys;  // MirrorY: every new y_i is also written here (the fused body's shared copy)
+  double* ys;  // Mirror: the shared copy of y
+  unsigned ncta = 0;  // Mirror 2: CTAs of the cluster
   // Single: one instance, whose scalars are loaded once per launch in begin()
   __device__ bool begin() {
     if (!Single) return load_global(sc, plan, q);
@@ -442,11 +462,15 @@ struct DualEpi {
       }
       const double yn = fma(q.w1, r, q.w0 * y0i);
       st_keep(y + i, yn);
-      if constexpr (MirrorY) ys[i] = yn;
+      mirror(i, yn);
     } else {
       st_keep(y + i, q.step * d);
-      if constexpr (MirrorY) ys[i] = q.step * d;
+      mirror(i, q.step * d);
     }
+  }
+  __device__ void mirror(int i, double v) {
+    if constexpr (Mirror == 1) ys[i] = v;
+    if constexpr (Mirror == 2) st_cluster_all(ys + i, v, ncta);
   }
   __device__ void apply_direct(int i, const double* s) {
     step(i, s[0], ld_once(lo + i), ld_once(hi + i), ld_once(y + i),
@@ -687,6 +711,13 @@ __device__ __forceinline__ void lane_sums(const DevPacked& M, const GatherVecs<N
   }
 }
 
+// Whether this launch times an idle iteration (no instance running).
+template <class Epi>
+__device__ __forceinline__ bool idle_launch(const Epi& epi) {
+  if constexpr (Epi::kTunable) return epi.plan.idle != 0;
+  return false;
+}
+
 // Whether this launch is an iteration kernel launched as a programmatic dependent.
 template <class Epi>
 __device__ __forceinline__ bool launched_dependent(const Epi& epi) {
@@ -763,6 +794,35 @@ __global__ void __launch_bounds__(W * LANES, (DPDLP_PK_MIN_BLOCKS * PK_WARPS) / 
 #endif
 }
 
+// Sum of piece sums k = q, q + step, q + 2 step, ... < q1 of vector `v`, added in that order.
+// The piece ids and then the sums are loaded PIECE_BATCH at a time before they are added,
+// so a row's loads overlap instead of forming a chain of dependent round trips; the order
+// of the additions is that of the plain loop.
+// L2: read the sums from L2 (ld.global.cg), for sums another SM of the cluster wrote.
+constexpr int PIECE_BATCH = 8;
+template <bool L2 = false>
+__device__ __forceinline__ double strided_piece_sum(const DevPacked& M, int k, int q, int q1,
+                                                    int step) {
+  const double* ps = M.piece_sum + (size_t)k * M.npieces;
+  double a = 0.0;
+  for (; q < q1; q += PIECE_BATCH * step) {
+    int pid[PIECE_BATCH];
+    double v[PIECE_BATCH];
+#pragma unroll
+    for (int u = 0; u < PIECE_BATCH; ++u) {
+      const int qq = q + u * step;
+      pid[u] = qq < q1 ? M.long_piece[qq] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < PIECE_BATCH; ++u)
+      v[u] = pid[u] >= 0 ? (L2 ? __ldcg(ps + pid[u]) : ps[pid[u]]) : 0.0;
+#pragma unroll
+    for (int u = 0; u < PIECE_BATCH; ++u)
+      if (pid[u] >= 0) a += v[u];
+  }
+  return a;
+}
+
 // Long rows: add each row's pieces, then its epilogue.  Rows come longest first: the first
 // nlong_block rows get a thread block each, the next nlong_warp rows a warp each (fixed
 // strided sums and fixed reduction trees), the rest a thread each (pieces in order).
@@ -783,13 +843,9 @@ __global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_i
     const int row = M.long_row[i];
     typename Epi::Row in{};
     if (threadIdx.x == 0) in = epi.load_row(row);  // in flight during the sums
+    const int q0 = M.long_ptr[i], q1 = M.long_ptr[i + 1];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double a = 0.0;
-      for (int q = M.long_ptr[i] + threadIdx.x; q < M.long_ptr[i + 1]; q += TPB)
-        a += M.piece_sum[(size_t)k * M.npieces + M.long_piece[q]];
-      v[k] = block_sum(a, red);
-    }
+    for (int k = 0; k < NV; ++k) v[k] = block_sum(strided_piece_sum(M, k, q0 + threadIdx.x, q1, TPB), red);
     if (threadIdx.x == 0) {
       epi.prepare(M.long_inst[i]);
       epi.apply_loaded(row, v, in);
@@ -805,11 +861,10 @@ __global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_i
     const int row = M.long_row[i];
     typename Epi::Row in{};
     if (lane == 0) in = epi.load_row(row);
+    const int q0 = M.long_ptr[i], q1 = M.long_ptr[i + 1];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      double a = 0.0;
-      for (int q = M.long_ptr[i] + lane; q < M.long_ptr[i + 1]; q += LANES)
-        a += M.piece_sum[(size_t)k * M.npieces + M.long_piece[q]];
+      double a = strided_piece_sum(M, k, q0 + lane, q1, LANES);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
       v[k] = a;
@@ -826,13 +881,9 @@ __global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_i
   if (!epi.inst(M.long_inst[i])) return;
   const int row = M.long_row[i];
   const typename Epi::Row in = epi.load_row(row);
+  const int q0 = M.long_ptr[i], q1 = M.long_ptr[i + 1];
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double a = 0.0;
-    for (int q = M.long_ptr[i]; q < M.long_ptr[i + 1]; ++q)
-      a += M.piece_sum[(size_t)k * M.npieces + M.long_piece[q]];
-    v[k] = a;
-  }
+  for (int k = 0; k < NV; ++k) v[k] = strided_piece_sum(M, k, q0, q1, 1);
   epi.prepare(M.long_inst[i]);
   epi.apply_loaded(row, v, in);
 }
@@ -858,7 +909,7 @@ __global__ void __launch_bounds__(W * LANES, (DPDLP_LIST_MIN_BLOCKS * PK_WARPS) 
   pdl_wait();  // the slot list and scalars come from the kernels before
   if (!epi.begin()) return;  // uniform over the launch
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int total = epi.all_slots() ? M.nslots : *M.nactive;
+  const int total = idle_launch(epi) ? 0 : epi.all_slots() ? M.nslots : *M.nactive;
   // with every instance running the list is the identity (instances keep their order and
   // own consecutive slots): no indirection then
   const bool all = total == M.nslots;
@@ -928,7 +979,9 @@ static cudaError_t launch_slots(const DevPacked& M, GatherVecs<NV> g, Epi epi, c
   const bool pdl = pdl_of(epi);
   if constexpr (Epi::kListable && DPDLP_BATCH_LIST) {
     if (M.active && epi.listed) {
-      const int resident = sm_count() * ((DPDLP_LIST_MIN_BLOCKS * PK_WARPS) / W);
+      const int most = (DPDLP_LIST_MIN_BLOCKS * PK_WARPS) / W;  // resident blocks per SM
+      const int want = M.list_warps_per_sm > 0 ? M.list_warps_per_sm / W : most;
+      const int resident = sm_count() * (want < 1 ? 1 : (want > most ? most : want));
       const int need = (M.nslots + W - 1) / W;
       const int grid = DPDLP_LIST_PERSISTENT && need > resident ? resident : need;
       return launch_k(packed_list_kernel<NV, W, Epi>, grid, W * LANES, s, pdl, M, g, epi);
@@ -1084,6 +1137,8 @@ cudaError_t launch_access_probe(const DevPacked& M, const double* x, int mode,
 static_assert(!DPDLP_L2_HINTS, "the fused body stores x_bar through a shared-memory pointer");
 constexpr int FB_WARPS = 16;
 constexpr int FB_TPB = FB_WARPS * LANES;
+constexpr int FB_MAX_CLUSTER = 8;     // CTAs of the cluster form (the portable cluster size)
+constexpr int FB_SLOTS_PER_CTA = 2;   // automatic cluster size: about this many slots per CTA
 
 // One product-and-step phase over every slot of M (the packed_spmv_kernel body).
 template <class Epi>
@@ -1116,13 +1171,11 @@ __device__ __forceinline__ void fused_slots(const DevPacked& M, const GatherVecs
 template <class Epi>
 __device__ __forceinline__ void fused_long(const DevPacked& M, Epi& epi, int w, int lane) {
   const int nw = M.nlong_warp;
-  const double* ps = M.piece_sum;
   for (int i = w; i < nw; i += FB_WARPS) {  // uniform over the warp
     const int row = M.long_row[i];
     typename Epi::Row in{};
     if (lane == 0) in = epi.load_row(row);
-    double a = 0.0;
-    for (int q = M.long_ptr[i] + lane; q < M.long_ptr[i + 1]; q += LANES) a += ps[M.long_piece[q]];
+    double a = strided_piece_sum(M, 0, M.long_ptr[i] + lane, M.long_ptr[i + 1], LANES);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     double v[1];
@@ -1132,8 +1185,7 @@ __device__ __forceinline__ void fused_long(const DevPacked& M, Epi& epi, int w, 
   for (int i = nw + (int)threadIdx.x; i < M.nlong; i += FB_TPB) {
     const int row = M.long_row[i];
     const typename Epi::Row in = epi.load_row(row);
-    double a = 0.0;
-    for (int q = M.long_ptr[i]; q < M.long_ptr[i + 1]; ++q) a += ps[M.long_piece[q]];
+    const double a = strided_piece_sum(M, 0, M.long_ptr[i], M.long_ptr[i + 1], 1);
     double v[1];
     v[0] = a;
     epi.apply_loaded(row, v, in);
@@ -1142,7 +1194,7 @@ __device__ __forceinline__ void fused_long(const DevPacked& M, Epi& epi, int w, 
 
 template <class PEpi>
 __global__ void __launch_bounds__(FB_TPB, 1)
-    fused_body_kernel(DevPacked Mc, DevPacked Mr, PEpi pe_in, DualEpi<true, true> de_in, int K) {
+    fused_body_kernel(DevPacked Mc, DevPacked Mr, PEpi pe_in, DualEpi<true, 1> de_in, int K) {
   __shared__ double srow[FB_WARPS][1][MAX_SLOT_ROWS];
   extern __shared__ double fb_vecs[];  // y [m], then x_bar [n]
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1167,7 +1219,7 @@ __global__ void __launch_bounds__(FB_TPB, 1)
       fused_long(Mc, pe, w, lane);
       __syncthreads();
     }
-    DualEpi<true, true> de = de_in;
+    DualEpi<true, 1> de = de_in;
     de.plan.i = i;
     de.ys = ys;
     if (!de.begin()) break;
@@ -1178,6 +1230,114 @@ __global__ void __launch_bounds__(FB_TPB, 1)
       __syncthreads();
     }
   }
+}
+
+// ---- cluster form: the same body spread over the CTAs of a thread-block cluster
+// One CTA bounds the single-block body by its SM's FP64 issue rate (about two FMAs per
+// clock) once an LP has more than a few slots.  Here C CTAs (one per SM) share the work:
+// CTA r takes the slots r, r + C, ... (its warps striding over them) and every C-th long row.
+// Each CTA keeps full shared-memory copies of x_bar and y for its gathers; a new x_bar_j or
+// y_i is stored into all C copies through distributed shared memory, and cluster barriers
+// separate the phases (and order the piece sums of long rows, which cross SMs through L2).
+// Each slot's lane sums, each epilogue and each long row's sum are the same code as the
+// separate launches, so results are bitwise theirs.
+template <class Epi>
+__device__ __forceinline__ void cluster_slots(const DevPacked& M, const GatherVecs<1>& g, Epi& epi,
+                                              double (*srow)[MAX_SLOT_ROWS], int w, int lane,
+                                              int rank, int C) {
+  constexpr int B = DPDLP_PK_BATCH;
+  const unsigned long long pol = l2_evict_first_policy();
+  for (int s = rank + C * w; s < M.nslots; s += C * FB_WARPS) {  // uniform over the warp
+    const SlotDesc sd = M.slots[s];
+    const LaneMeta lm = M.lanes[(size_t)s * LANES + lane];
+    const size_t off = (size_t)s * SLOT_ITEMS;
+    const uint4* ip = reinterpret_cast<const uint4*>(M.idx + off) + lane;
+    uint32_t c0[B], c1[B];
+    load_idx<B>(ip, 0, c0, pol);
+    load_idx<B>(ip, 1, c1, pol);
+    if (epi.fp32() && M.val32)
+      lane_sums<float, 1, B, true>(M, g, off, lane, lm.row_local, lm.piece_base, srow, ip, pol, c0, c1);
+    else
+      lane_sums<double, 1, B, true>(M, g, off, lane, lm.row_local, lm.piece_base, srow, ip, pol, c0, c1);
+    __syncwarp();
+    epi.prepare(sd.inst);
+    epi.apply_rows(sd.row_base, sd.nrows, lane, srow);
+    __syncwarp();
+  }
+}
+
+template <class Epi>
+__device__ __forceinline__ void cluster_long(const DevPacked& M, Epi& epi, int w, int lane,
+                                             int rank, int C) {
+  const int nw = M.nlong_warp;
+  for (int i = rank * FB_WARPS + w; i < nw; i += C * FB_WARPS) {  // uniform over the warp
+    const int row = M.long_row[i];
+    typename Epi::Row in{};
+    if (lane == 0) in = epi.load_row(row);
+    double a = strided_piece_sum<true>(M, 0, M.long_ptr[i] + lane, M.long_ptr[i + 1], LANES);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    double v[1];
+    v[0] = a;
+    if (lane == 0) epi.apply_loaded(row, v, in);
+  }
+  for (int i = nw + rank * FB_TPB + (int)threadIdx.x; i < M.nlong; i += C * FB_TPB) {
+    const int row = M.long_row[i];
+    const typename Epi::Row in = epi.load_row(row);
+    double v[1];
+    v[0] = strided_piece_sum<true>(M, 0, M.long_ptr[i], M.long_ptr[i + 1], 1);
+    epi.apply_loaded(row, v, in);
+  }
+}
+
+// Pieces written to global memory by this cluster's lanes become visible to the CTAs that
+// finish the long rows.
+__device__ __forceinline__ void cluster_sync_pieces(cooperative_groups::cluster_group& cl) {
+  __threadfence();
+  cl.sync();
+}
+
+template <class PEpi>
+__global__ void __launch_bounds__(FB_TPB, 1)
+    cluster_body_kernel(DevPacked Mc, DevPacked Mr, PEpi pe_in, DualEpi<true, 2> de_in, int K) {
+  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  __shared__ double srow[FB_WARPS][1][MAX_SLOT_ROWS];
+  extern __shared__ double fb_vecs[];  // y [m], then x_bar [n]: this CTA's copies
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = Mr.rows, n = Mc.rows;
+  double* ys = fb_vecs;
+  double* xs = fb_vecs + m;
+  for (int i = threadIdx.x; i < m; i += FB_TPB) ys[i] = de_in.y[i];
+  cl.sync();  // every CTA of the cluster runs before any stores into another's copies
+  const GatherVecs<1> gp{{ys}}, gd{{xs}};
+  for (int i = 0; i < K; ++i) {
+    // begin() reads scalars that change only at checks: every CTA takes the same branch
+    PEpi pe = pe_in;
+    pe.plan.i = i;
+    pe.xbar = xs;
+    pe.ncta = (unsigned)C;
+    if (!pe.begin()) break;
+    cluster_slots(Mc, gp, pe, srow[w], w, lane, rank, C);
+    if (Mc.nlong > 0) {
+      cluster_sync_pieces(cl);
+      cluster_long(Mc, pe, w, lane, rank, C);
+    }
+    cl.sync();  // x_bar complete in every copy
+    DualEpi<true, 2> de = de_in;
+    de.plan.i = i;
+    de.ys = ys;
+    de.ncta = (unsigned)C;
+    if (!de.begin()) break;
+    cluster_slots(Mr, gd, de, srow[w], w, lane, rank, C);
+    if (Mr.nlong > 0) {
+      cluster_sync_pieces(cl);
+      cluster_long(Mr, de, w, lane, rank, C);
+    }
+    cl.sync();  // y complete in every copy
+  }
+  cl.sync();  // no CTA exits while another may still store into its shared memory
+  (void)n;
 }
 
 // x_bar and y in shared memory: at most FB_VEC_MAX entries together
@@ -1196,15 +1356,53 @@ cudaError_t fused_body_prepare() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(fused_body_kernel<PrimalEpi<true, true>>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, FB_DYN_MAX);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(cluster_body_kernel<PrimalEpi<true, false, true>>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, FB_DYN_MAX);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(cluster_body_kernel<PrimalEpi<true, true, true>>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, FB_DYN_MAX);
   return e;
 }
 
+int fused_cluster_ctas(const DevPacked& csc, const DevPacked& csr, int requested) {
+  if (requested >= 1) return requested > FB_MAX_CLUSTER ? FB_MAX_CLUSTER : requested;
+  const int slots = csc.nslots > csr.nslots ? csc.nslots : csr.nslots;
+  const int c = (slots + FB_SLOTS_PER_CTA - 1) / FB_SLOTS_PER_CTA;
+  return c < 1 ? 1 : (c > FB_MAX_CLUSTER ? FB_MAX_CLUSTER : c);
+}
+
+template <class PEpi>
+static cudaError_t launch_cluster(const DevPacked& csc, const DevPacked& csr, PEpi pe,
+                                  DualEpi<true, 2> de, int K, int C, size_t dyn, cudaStream_t s) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(FB_TPB);
+  cfg.dynamicSmemBytes = dyn;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, cluster_body_kernel<PEpi>, csc, csr, pe, de, K);
+}
+
 cudaError_t launch_body_fused(const DevPacked& csc, const DevPacked& csr, const DevVecs& v,
-                              const DevScalars* sc, int K, cudaStream_t s) {
+                              const DevScalars* sc, int K, int cluster, cudaStream_t s) {
   if (v.ninst != 1 || csc.rows + csr.rows > FB_VEC_MAX) return cudaErrorInvalidValue;
   const IterPlan p{0, 0, 0};
   const size_t dyn = (size_t)(csc.rows + csr.rows) * sizeof(double);
-  const DualEpi<true, true> de{sc, v.inst, v.wtab, p, 0, v.lo, v.hi, v.y0, v.y, v.yh, {}, nullptr};
+  if (cluster > 1) {
+    const int C = cluster > FB_MAX_CLUSTER ? FB_MAX_CLUSTER : cluster;
+    const DualEpi<true, 2> de{sc, v.inst, v.wtab, p, 0, v.lo, v.hi, v.y0, v.y, v.yh, {}, nullptr, 0};
+    if (v.q)
+      return launch_cluster(csc, csr, PrimalEpi<true, true, true>{sc, v.inst, v.wtab, p, 0, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, v.q, {}, 0}, de, K, C, dyn, s);
+    return launch_cluster(csc, csr, PrimalEpi<true, false, true>{sc, v.inst, v.wtab, p, 0, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, nullptr, {}, 0}, de, K, C, dyn, s);
+  }
+  const DualEpi<true, 1> de{sc, v.inst, v.wtab, p, 0, v.lo, v.hi, v.y0, v.y, v.yh, {}, nullptr};
   if (v.q)
     fused_body_kernel<<<1, FB_TPB, dyn, s>>>(csc, csr, PrimalEpi<true, true>{sc, v.inst, v.wtab, p, 0, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, v.q, {}}, de, K);
   else
@@ -1598,17 +1796,21 @@ __global__ void __launch_bounds__(TPB) active_fill_kernel(DevVecs v, const int32
 }
 
 __global__ void select_kernel(const int32_t* nact_r, int nslots_r, const int32_t* nact_c,
-                              int nslots_c, unsigned long long handle) {
+                              int nslots_c, unsigned long long handle, double fraction) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const long long active = (long long)*nact_r + *nact_c, total = (long long)nslots_r + nslots_c;
-  cudaGraphSetConditional((cudaGraphConditionalHandle)handle, 2 * active < total ? 1u : 0u);
+  cudaGraphSetConditional((cudaGraphConditionalHandle)handle,
+                          (double)active < fraction * (double)total ? 1u : 0u);
 }
 
 cudaError_t launch_select(const DevPacked& csr, const DevPacked& csc, unsigned long long handle,
-                          cudaStream_t s) {
-  select_kernel<<<1, 32, 0, s>>>(csr.nactive, csr.nslots, csc.nactive, csc.nslots, handle);
+                          double fraction, cudaStream_t s) {
+  select_kernel<<<1, 32, 0, s>>>(csr.nactive, csr.nslots, csc.nactive, csc.nslots, handle,
+                                 fraction);
   return cudaGetLastError();
 }
+
+int list_max_warps_per_sm() { return DPDLP_LIST_MIN_BLOCKS * PK_WARPS; }
 
 cudaError_t launch_compact(const DevPacked& csr, const DevPacked& csc, const DevVecs& v,
                            cudaStream_t s) {

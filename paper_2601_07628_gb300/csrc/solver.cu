@@ -66,10 +66,13 @@ std::map<std::string, Param> default_params() {
       {"precond", {0, 0, 1, true}},
       {"ruiz_passes", {10, 0, 100, true}},
       {"pock_chambolle", {1, 0, 1, true}},
+      {"list_fraction", {0.5, 0.0, 2.0, false}},
+      {"list_warps_per_sm", {0, 0, 64, true}},
       {"cta_slots_primal", {4, 2, 8, true}},
       {"cta_slots_dual", {4, 2, 8, true}},
       {"fused_body", {1, 0, 1, true}},
       {"fused_max_slots", {6, 1, FUSED_MAX_SLOTS, true}},
+      {"fused_cluster", {0, 0, 8, true}},
   };
 }
 
@@ -499,7 +502,10 @@ int build_graph(dpdlp* h, int K) {
   if (h->ninst == 1) {  // one capture: the iterations, then the check
     e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, mode);
     if (use_fused(h)) {
-      if (e == cudaSuccess) e = launch_body_fused(h->csc, h->csr, h->v, h->d_sc, K, h->cap_stream);
+      if (e == cudaSuccess)
+        e = launch_body_fused(h->csc, h->csr, h->v, h->d_sc, K,
+                              fused_cluster_ctas(h->csc, h->csr, (int)h->P("fused_cluster")),
+                              h->cap_stream);
     } else {
       for (int i = 0; i < K && e == cudaSuccess; ++i) {
         e = launch_primal(h->csc, h->v, h->d_sc, IterPlan{i, 0, 0, pdl}, h->cap_stream);
@@ -517,7 +523,8 @@ int build_graph(dpdlp* h, int K) {
     cudaGraphConditionalHandle sel;
     CK(cudaGraphConditionalHandleCreate(&sel, body, 0, 0));
     e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, mode);
-    if (e == cudaSuccess) e = launch_select(h->csr, h->csc, (unsigned long long)sel, h->cap_stream);
+    if (e == cudaSuccess)
+      e = launch_select(h->csr, h->csc, (unsigned long long)sel, h->P("list_fraction"), h->cap_stream);
     cudaGraph_t captured = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &captured);
     if (e == cudaSuccess) e = e2;
@@ -559,10 +566,14 @@ int run_host_loop(dpdlp* h) {
       CK(cudaMemcpyAsync(&na[0], h->csr.nactive, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
       CK(cudaMemcpyAsync(&na[1], h->csc.nactive, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
       CK(cudaStreamSynchronize(h->stream));
-      list = 2LL * (na[0] + na[1]) < (long long)h->csr.nslots + h->csc.nslots ? 1 : 0;
+      list = (double)(na[0] + na[1]) <
+                     h->P("list_fraction") * (double)((long long)h->csr.nslots + h->csc.nslots)
+                 ? 1
+                 : 0;
     }
     if (use_fused(h)) {
-      CK(launch_body_fused(h->csc, h->csr, h->v, h->d_sc, K, h->stream));
+      CK(launch_body_fused(h->csc, h->csr, h->v, h->d_sc, K,
+                           fused_cluster_ctas(h->csc, h->csr, (int)h->P("fused_cluster")), h->stream));
     } else {
       for (int i = 0; i < K; ++i) {
         CK(launch_primal(h->csc, h->v, h->d_sc, IterPlan{i, 0, list, pdl}, h->stream));
@@ -643,7 +654,9 @@ int dpdlp_set_param(dpdlp_t* h, const char* key, double v) {
   if ((k == "cta_slots_primal" || k == "cta_slots_dual") && v != 2 && v != 4 && v != 8)
     return fail(h, DPDLP_ERR_INVALID, k + " must be 2, 4 or 8");
   if ((k == "check_every" || k == "cta_slots_primal" || k == "cta_slots_dual" ||
-       k == "fused_body" || k == "fused_max_slots" || k == "pdl") && v != p.value)
+       k == "fused_body" || k == "fused_max_slots" || k == "fused_cluster" || k == "pdl" ||
+       k == "list_fraction" ||
+       k == "list_warps_per_sm") && v != p.value)
     free_graph(h);  // the captured graph holds the launch shapes
   if (std::string(key) == "eta_safety" || std::string(key) == "power_iters" ||
       std::string(key) == "power_tol")
@@ -651,6 +664,7 @@ int dpdlp_set_param(dpdlp_t* h, const char* key, double v) {
   p.value = v;
   h->csc.cta_slots = (int)h->P("cta_slots_primal");
   h->csr.cta_slots = (int)h->P("cta_slots_dual");
+  h->csc.list_warps_per_sm = h->csr.list_warps_per_sm = (int)h->P("list_warps_per_sm");
   return 0;
 }
 
@@ -800,6 +814,7 @@ int load_impl(dpdlp* h, int32_t count, const int32_t* row_off, const int32_t* co
   }
   h->csc.cta_slots = (int)h->P("cta_slots_primal");
   h->csr.cta_slots = (int)h->P("cta_slots_dual");
+  h->csc.list_warps_per_sm = h->csr.list_warps_per_sm = (int)h->P("list_warps_per_sm");
   DevVecs& v = h->v;
   v.n = n;
   v.m = m;
@@ -1286,7 +1301,18 @@ int dpdlp_time_kernel(dpdlp_t* h, const char* which, int32_t reps, double* avg_m
   // index and value streams only
   int probe = -1;
   bool primal = w == "primal";
-  if (w != "primal" && w != "dual") {
+  // batches also time the iteration kernels as the solve may run them: walking the
+  // active-slot lists (*_list), and with every instance stopped (*_idle, *_list_idle)
+  IterPlan p{0, 1, 0, 0, 0};
+  const std::string side0 = w.substr(0, w.find('_'));
+  const std::string rest = w.find('_') == std::string::npos ? "" : w.substr(w.find('_') + 1);
+  if ((side0 == "primal" || side0 == "dual") &&
+      (rest == "list" || rest == "idle" || rest == "list_idle")) {
+    if (h->ninst < 2) return fail(h, DPDLP_ERR_INVALID, "list and idle timings need a batch");
+    primal = side0 == "primal";
+    p.list = rest != "idle";
+    p.idle = rest != "list";
+  } else if (w != "primal" && w != "dual") {
     const size_t us = w.find('_');
     const std::string kind = us == std::string::npos ? w : w.substr(0, us);
     const std::string side = us == std::string::npos ? "" : w.substr(us + 1);
@@ -1305,7 +1331,6 @@ int dpdlp_time_kernel(dpdlp_t* h, const char* which, int32_t reps, double* avg_m
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const IterPlan p{0, 1, 0};
   CK(cudaEventRecord(e0, h->stream));
   for (int r = 0; r < reps; ++r) {
     if (probe >= 0) {

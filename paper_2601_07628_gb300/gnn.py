@@ -237,8 +237,18 @@ def train(net: Network, data, epochs: int, lr: float = 1e-3, seed: int = 0, log=
     return hist
 
 
+def project_dual(lp, y):
+    """y projected onto the dual set Y of Section 2.1: a row with only an upper bound
+    (lc = -inf) has y <= 0, a row with only a lower bound (uc = +inf) has y >= 0, a free row
+    has y = 0, an equality or ranged row any sign."""
+    lc, uc = np.asarray(lp.lc, np.float64), np.asarray(lp.uc, np.float64)
+    y = np.where(np.isfinite(lc), y, np.minimum(y, 0.0))
+    return np.where(np.isfinite(uc), y, np.maximum(y, 0.0))
+
+
 def predict(net: Network, lp, sc: Scales):
-    """Start point for ``lp``: the network's (x, y), rescaled, x clipped into its bounds."""
+    """Start point for ``lp``: the network's (x, y), rescaled, x clipped into its bounds and
+    y projected onto the dual set."""
     fv, fc = features(lp, sc)
     was = net.dev
     if was:
@@ -248,5 +258,38 @@ def predict(net: Network, lp, sc: Scales):
     if was:
         net.device_arrays(True)
     x = np.clip(xh.astype(np.float64) * sc.x_scale, lp.lv, lp.uv)
-    y = yh.astype(np.float64) * sc.y_scale
+    y = project_dual(lp, yh.astype(np.float64) * sc.y_scale)
     return x, y
+
+
+def cold_start(lp):
+    """The solver's own start point: x = proj_X(0), y = 0."""
+    return np.clip(np.zeros(lp.n), lp.lv, lp.uv), np.zeros(lp.m)
+
+
+def _max_kkt(k):
+    return max(k["r_primal"], k["r_dual"], k["r_gap"])
+
+
+def guard_starts(solver, lps, starts, probe_iters: int = 64):
+    """Keep each predicted start only where it is no worse than the cold start.
+
+    ``solver`` holds ``lps`` as a batch (``load_batch``).  Both start sets are run for
+    ``probe_iters`` iterations on that handle; an instance keeps its predicted start when
+    its relative KKT error after them is at most that of the cold start, else it falls back
+    to the cold start (plain PDHG from zero stays the fallback and the judge of the
+    prediction).  The handle is left with the chosen start set and ``resume`` = 0, ready for
+    the real solve.  Returns (chosen starts, kept mask, KKT from the prediction, KKT cold)."""
+    cold = [cold_start(lp) for lp in lps]
+    resume0 = solver.get_param("resume")
+    solver.set_param("resume", 0)
+    errs = []
+    for st in (starts, cold):
+        solver.set_start(np.concatenate([x for x, _ in st]), np.concatenate([y for _, y in st]))
+        solver.solve(0.0, probe_iters)
+        errs.append([_max_kkt(k) for k in solver.batch_kkt()])
+    keep = [w <= c for w, c in zip(*errs)]
+    chosen = [s if k else c for s, k, c in zip(starts, keep, cold)]
+    solver.set_start(np.concatenate([x for x, _ in chosen]), np.concatenate([y for _, y in chosen]))
+    solver.set_param("resume", resume0)
+    return chosen, keep, errs[0], errs[1]

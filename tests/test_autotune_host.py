@@ -6,11 +6,17 @@ from paper_2601_07628_gb300 import autotune
 
 
 class FakeSolver:
-    def __init__(self, times, n=4000, m=2000, nnz=40000, ninst=1):
+    """Stand-in for dpdlp.Solver: launch times come from tables, a large single LP never
+    fits the fused body; batches answer the list and idle timings."""
+
+    def __init__(self, times, n=4000, m=2000, nnz=40000, ninst=1, batch_times=None):
         self.times = times  # {(kernel, w): ms}
-        self.params = {"cta_slots_primal": 4, "cta_slots_dual": 4, "spmv_fp32": 0}
+        self.batch_times = batch_times or {}  # {suffix: ms} or {("_list", warps): ms}
+        self.params = {"cta_slots_primal": 4, "cta_slots_dual": 4, "spmv_fp32": 0,
+                       "fused_body": 1, "fused_max_slots": 6, "list_fraction": 0.5,
+                       "list_warps_per_sm": 0}
         self.row_off = list(range(ninst + 1))
-        self._info = dict(n=n, m=m, nnz=nnz)
+        self._info = dict(n=n, m=m, nnz=nnz, fused_body=0, tiles_csr=40, tiles_csc=40)
         self.timed = 0
 
     def info(self):
@@ -24,7 +30,35 @@ class FakeSolver:
 
     def time_kernel(self, kern, reps):
         self.timed += 1
-        return self.times[(kern, self.params[autotune.PARAMS[kern]])]
+        side, _, suffix = kern.partition("_")
+        if not suffix:
+            return self.times[(kern, self.params[autotune.PARAMS[kern]])]
+        key = ("_list", self.params["list_warps_per_sm"]) if suffix == "list" else "_" + suffix
+        return self.batch_times[key] / 2  # the primal and the dual launch each half
+
+
+def test_crossover_rule():
+    # list walk: 10 % dearer per active slot, nearly free when idle; launch over every slot:
+    # its idle cost is a fifth of the full launch.  Lines 0.2 + 0.8 f and 0.01 + 1.09 f.
+    f = autotune.crossover(a=1.0, l=1.1, e=0.2, c=0.01)
+    assert abs(f - (0.2 - 0.01) / (1.09 - 0.8)) < 1e-12
+    assert autotune.crossover(1.0, 0.9, 0.2, 0.01) == 2.0  # list never dearer: always
+    assert autotune.crossover(1.0, 0.9, 0.01, 0.2) == 0.0  # list dearer when idle: never
+    assert abs(autotune.crossover(1.0, 5.0, 0.2, 0.19) - 0.01 / 4.01) < 1e-15
+
+
+def test_tune_batch_sets_list_parameters(tmp_path):
+    times = {(k, w): 1.0 for k in ("primal", "dual") for w in autotune.VARIANTS}
+    bt = {("_list", 8): 1.3, ("_list", 16): 1.1, ("_list", 24): 1.2, "_idle": 0.2,
+          "_list_idle": 0.01}
+    s = FakeSolver(times, ninst=8, batch_times=bt)
+    r = autotune.tune(s, cache=str(tmp_path / "c.json"), reps=1, rounds=1)
+    assert r["list_warps_per_sm"] == 16 and s.params["list_warps_per_sm"] == 16
+    want = autotune.crossover(2.0, 1.1, 0.2, 0.01)
+    assert abs(r["list_fraction"] - want) < 1e-12 and s.params["list_fraction"] == r["list_fraction"]
+    s2 = FakeSolver(times, ninst=8, batch_times=bt)
+    r2 = autotune.tune(s2, cache=str(tmp_path / "c.json"))
+    assert r2["cached"] and s2.timed == 0 and s2.params["list_warps_per_sm"] == 16
 
 
 def test_size_class_buckets():

@@ -193,21 +193,25 @@ def test_full_batch_sampled_parity(Solver, full_batch):
 
 
 def test_launch_shapes_do_not_change_results(Solver):
-    """Slots per block (2, 4, 8) of either iteration kernel is a launch shape only: the
-    batch solve gives bit-identical results under every combination."""
+    """Slots per block (2, 4, 8) of either iteration kernel, the list threshold (never /
+    always walk the active-slot lists) and the list kernel's warps per SM are launch choices
+    only: the batch solve gives bit-identical results under every combination."""
     lps = small_batch()
     ref = None
-    for wp, wd in ((4, 4), (2, 2), (8, 8), (2, 8), (8, 2)):
+    for wp, wd, frac, lw in ((4, 4, 0.5, 0), (2, 2, 0.5, 0), (8, 8, 0.5, 0), (2, 8, 0.0, 0),
+                             (8, 2, 2.0, 8), (4, 4, 2.0, 24), (4, 4, 0.9, 16)):
         s = Solver()
         s.set_param("cta_slots_primal", wp)
         s.set_param("cta_slots_dual", wd)
+        s.set_param("list_fraction", frac)
+        s.set_param("list_warps_per_sm", lw)
         s.load_batch(lps)
         assert s.solve(1e-6, 200_000) == 0
         x, y = s.solution()
         if ref is None:
             ref = (x, y)
         else:
-            assert np.array_equal(x, ref[0]) and np.array_equal(y, ref[1]), (wp, wd)
+            assert np.array_equal(x, ref[0]) and np.array_equal(y, ref[1]), (wp, wd, frac, lw)
         s.close()
 
 
@@ -221,6 +225,10 @@ def test_autotune_applies_and_caches(Solver, tmp_path):
     assert not r["cached"]
     for p in autotune.PARAMS.values():
         assert r[p] in autotune.VARIANTS and s.get_param(p) == r[p]
+    assert r["list_warps_per_sm"] in autotune.LIST_WARPS
+    assert 0.0 <= r["list_fraction"] <= 2.0 and s.get_param("list_fraction") == r["list_fraction"]
+    cr = r["ms"]["crossover"]
+    assert all(v > 0 for v in cr.values()) and cr["list_idle"] < cr["all_running"]
     assert s.solve(1e-6, 200_000) == 0
     s2 = Solver()
     s2.load_batch(small_batch())

@@ -1,9 +1,11 @@
-"""The fused body for small LPs (parameters ``fused_body``, ``fused_max_slots``): all
-iterations of a graph body in one launch of one thread block.
+"""The fused body for small LPs (parameters ``fused_body``, ``fused_max_slots``,
+``fused_cluster``): all iterations of a graph body in one launch of one thread block, or
+of one thread-block cluster whose CTAs share the slots and exchange x_bar and y through
+distributed shared memory.
 
-It runs the same lane sums, epilogues and long-row sums as the separate primal and dual
-launches, in the same order, so every result must be bitwise equal to the separate path
-(compared as raw 64-bit patterns), and at parity with the oracle like the separate path.
+Both forms run the same lane sums, epilogues and long-row sums as the separate primal and
+dual launches, in the same order, so every result must be bitwise equal to the separate
+path (compared as raw 64-bit patterns), and at parity with the oracle like the separate path.
 The tests force the fused form (``fused_max_slots`` = 64) on LPs larger than the default
 threshold, so that many slots per warp and long rows are covered: the cross-stress LP has
 long rows in both orientations (rows of A with 1,500 and 1,100 nonzeros, a column with
@@ -70,12 +72,13 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("cluster", [1, 3, 8])
 @pytest.mark.parametrize("case", list(CASES))
-def test_fused_body_is_bitwise_the_separate_path(Solver, case):
+def test_fused_body_is_bitwise_the_separate_path(Solver, case, cluster):
     make, params = CASES[case]
     lp = make()
     T = 333  # not a multiple of the check period: the last body stops early
-    a = run(Solver, lp, 1, T, **params)
+    a = run(Solver, lp, 1, T, fused_cluster=cluster, **params)
     b = run(Solver, lp, 0, T, **params)
     assert a["info"]["fused_body"] == 1 and b["info"]["fused_body"] == 0
     assert a["status"] == b["status"] == 1
@@ -138,3 +141,23 @@ def test_default_threshold(Solver):
     a = run(Solver, tiny, 1, 500)
     b = run(Solver, tiny, 0, 500)
     assert np.array_equal(bits(a["x"]), bits(b["x"])) and np.array_equal(bits(a["y"]), bits(b["y"]))
+
+
+def test_autotune_times_the_fused_body_and_keeps_the_state(Solver, tmp_path):
+    """For a tiny single LP the autotuner times one graph body fused and separate from a
+    saved state and restores it: the solver state is the same before and after."""
+    from paper_2601_07628_gb300 import autotune
+
+    lp = lpgen.small_random_lp(7, n=250, m=125)
+    s = Solver()
+    s.load(lp)
+    s.solve(0.0, 64)
+    before = s.get_state()
+    r = autotune.tune(s, cache=str(tmp_path / "t.json"), reps=3, rounds=1)
+    after = s.get_state()
+    assert 1 <= r["fused_max_slots"] <= 64 and s.get_param("fused_max_slots") == r["fused_max_slots"]
+    assert r["ms"]["body"]["fused"] > 0 and r["ms"]["body"]["separate"] > 0
+    for k in ("x", "y", "x0", "y0"):
+        assert np.array_equal(before[k], after[k]), k
+    assert before["scalars"] == after["scalars"]
+    s.close()
