@@ -227,15 +227,18 @@ int dpdlp_set_row_bounds(dpdlp_t* h, const double* lc, const double* uc);
  *   cta_slots_primal, cta_slots_dual (4): warp slots per thread block of the primal (A^T y)
  *   and dual (A x_bar) iteration kernels, 2, 4 or 8 (64, 128 or 256 threads); a launch
  *   shape only, results do not depend on it (set by the autotuner).
- *   fused_body (1), fused_max_slots (6, at most 64): a single LP whose packed copies have
- *   at most fused_max_slots warp slots each (a slot holds 1,024 stored nonzeros) runs each
- *   graph body -- check_every iterations -- as one launch of one thread block, with block
- *   barriers between the primal and dual phases, instead of two or three launches per
- *   iteration.  On a tiny LP an iteration costs launch latency; one SM's FP64 issue rate
- *   bounds the fused block, so it is faster only up to a few slots per copy.  The sums and
- *   their order are those of the separate launches, so results are bitwise the same;
- *   fused_body = 0 always launches the kernels separately.  dpdlp_get_info reports which
- *   form the next solve takes.
+ *   fused_body (1), fused_max_slots (40, at most 64), fused_cluster (0): a single LP whose
+ *   packed copies have at most fused_max_slots warp slots each (a slot holds 1,024 stored
+ *   nonzeros) runs each graph body -- check_every iterations -- as one launch instead of two
+ *   or three launches per iteration: one thread block with block barriers between the
+ *   primal and dual phases, or a thread-block cluster of fused_cluster CTAs (at most 8)
+ *   that share the slots, exchange x_bar and y through distributed shared memory and
+ *   synchronize with cluster barriers.  fused_cluster = 0 chooses: one CTA up to 6 slots per
+ *   copy, else about two slots per CTA.  On a tiny LP an iteration costs launch latency;
+ *   one SM's FP64 issue rate bounds a single block beyond a few slots.  The sums and their
+ *   order are those of the separate launches, so results are bitwise the same in every
+ *   form; fused_body = 0 always launches the kernels separately.  dpdlp_get_info reports
+ *   which form the next solve takes.
  *   pdl (1): the iteration kernels launch as programmatic dependents of the kernel before
  *   them (they load what no kernel writes -- slot descriptors, first index batches -- while
  *   it drains, then wait for it); 0 = plain stream order.  Results do not depend on it.

@@ -1,15 +1,18 @@
 // Warm-start network (include/dpdlp_gnn.h): forward and backward kernels and the C ABI.
 //
 // Four kinds of kernel carry the whole network:
-//   spmm_kernel       sparse aggregation over A's pattern, H = 64 features per node
-//                     (warp per row, two features per lane, sums in stored order);
+//   spmm_*            sparse aggregation over A's pattern, H = 64 features per node (a warp
+//                     per row, two features per lane, sums in stored order; a block of 16
+//                     warps per row longer than 64 entries, chunk sums added in order);
 //   linear_mma_kernel relu(X1 W1^T + X2 W2^T + b) of the 64 x 64 layers on the tensor
 //                     cores (mma.sync BF16, FP32 accumulation, FP32 activations split into
 //                     BF16 hi + lo); linear_kernel the same on the FP32 pipe for the 8-wide
 //                     input encoders;
-//   linear_bwd_*      the ReLU mask and the products with W1 and W2 for the backward pass;
-//   wgrad_*           weight and bias gradients dZ^T X as fixed per-block partial sums,
-//                     added in block order by reduce_partials_kernel.
+//   linear_bwd_mma_kernel the ReLU mask and the products with W1 and W2 for the backward
+//                     pass (the mask alone for the encoders);
+//   wgrad_mma_kernel, wgrad8_mma_kernel  weight and bias gradients dZ^T X on the tensor cores
+//                     as fixed per-block partial sums, added in block order by
+//                     reduce_partials_kernel.
 // No floating-point atomics anywhere: every result is bitwise reproducible.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -64,21 +67,17 @@ struct Layout {
 const Layout LAY;
 
 // ---------------------------------------------------------------- kernels
-// out[r][:] (=|+=) sum_k val[k] * in[idx[k]][:] over row r's stored entries, in order.
-__global__ void __launch_bounds__(TPB) spmm_kernel(int rows, const int64_t* __restrict__ ptr,
-                                                   const int* __restrict__ idx,
-                                                   const float* __restrict__ val,
-                                                   const float* __restrict__ in, float* out,
-                                                   int accumulate) {
-  const int r = (int)((blockIdx.x * (size_t)TPB + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (r >= rows) return;
+// Sum over entries k0 .. k1-1 of val[k] * in[idx[k]][2 lane .. 2 lane + 1], added in stored
+// order; SPMM_BATCH entries at a time (indices and values, then the gathers, all in flight
+// together).
+constexpr int SPMM_BATCH = 8;
+constexpr int SPMM_LONG = 64;        // rows with more entries: a thread block per row
+constexpr int SPMM_LONG_WARPS = 16;  // warps of that block, each a contiguous chunk
+__device__ __forceinline__ float2 spmm_range(int64_t k0, int64_t k1, const int* __restrict__ idx,
+                                             const float* __restrict__ val,
+                                             const float* __restrict__ in, int lane) {
   float2 acc = make_float2(0.f, 0.f);
-  // the row's entries SPMM_BATCH at a time: indices and values, then the gathers, all in
-  // flight together; the products are added in stored order
-  constexpr int SPMM_BATCH = 8;
-  const int64_t k1 = ptr[r + 1];
-  for (int64_t k = ptr[r]; k < k1; k += SPMM_BATCH) {
+  for (int64_t k = k0; k < k1; k += SPMM_BATCH) {
     int j[SPMM_BATCH];
     float a[SPMM_BATCH];
     float2 h[SPMM_BATCH];
@@ -98,6 +97,10 @@ __global__ void __launch_bounds__(TPB) spmm_kernel(int rows, const int64_t* __re
       acc.y = fmaf(a[u], h[u].y, acc.y);
     }
   }
+  return acc;
+}
+
+__device__ __forceinline__ void spmm_store(float* out, int r, int lane, float2 acc, int accumulate) {
   float2* o = reinterpret_cast<float2*>(out + (size_t)r * H) + lane;
   if (accumulate) {
     const float2 p = *o;
@@ -105,6 +108,87 @@ __global__ void __launch_bounds__(TPB) spmm_kernel(int rows, const int64_t* __re
     acc.y += p.y;
   }
   *o = acc;
+}
+
+// out[r][:] (=|+=) sum_k val[k] * in[idx[k]][:] over row r's stored entries, in order: eight
+// lanes per row (four rows per warp), eight features per lane, each feature summed by one
+// lane in stored order.  Rows longer than SPMM_LONG are left to spmm_long_kernel.
+constexpr int SPMM_ROW_LANES = 8;
+__global__ void __launch_bounds__(TPB) spmm_kernel(int rows, const int64_t* __restrict__ ptr,
+                                                   const int* __restrict__ idx,
+                                                   const float* __restrict__ val,
+                                                   const float* __restrict__ in, float* out,
+                                                   int accumulate) {
+  const size_t t = blockIdx.x * (size_t)TPB + threadIdx.x;
+  const int r = (int)(t / SPMM_ROW_LANES), sl = (int)(t % SPMM_ROW_LANES);
+  if (r >= rows) return;
+  const int64_t k0 = ptr[r], k1 = ptr[r + 1];
+  if (k1 - k0 > SPMM_LONG) return;
+  float acc[8];
+#pragma unroll
+  for (int f = 0; f < 8; ++f) acc[f] = 0.f;
+  constexpr int BATCH = 4;
+  for (int64_t k = k0; k < k1; k += BATCH) {
+    int j[BATCH];
+    float a[BATCH];
+    float4 h0[BATCH], h1[BATCH];
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      j[u] = k + u < k1 ? idx[k + u] : -1;
+      a[u] = k + u < k1 ? val[k + u] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      const float4* src = reinterpret_cast<const float4*>(in + (size_t)(j[u] < 0 ? 0 : j[u]) * H) + 2 * sl;
+      h0[u] = j[u] >= 0 ? src[0] : make_float4(0.f, 0.f, 0.f, 0.f);
+      h1[u] = j[u] >= 0 ? src[1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      if (j[u] < 0) break;
+      acc[0] = fmaf(a[u], h0[u].x, acc[0]);
+      acc[1] = fmaf(a[u], h0[u].y, acc[1]);
+      acc[2] = fmaf(a[u], h0[u].z, acc[2]);
+      acc[3] = fmaf(a[u], h0[u].w, acc[3]);
+      acc[4] = fmaf(a[u], h1[u].x, acc[4]);
+      acc[5] = fmaf(a[u], h1[u].y, acc[5]);
+      acc[6] = fmaf(a[u], h1[u].z, acc[6]);
+      acc[7] = fmaf(a[u], h1[u].w, acc[7]);
+    }
+  }
+  float4* o = reinterpret_cast<float4*>(out + (size_t)r * H) + 2 * sl;
+  if (accumulate) {
+    const float4 p0 = o[0], p1 = o[1];
+    acc[0] += p0.x; acc[1] += p0.y; acc[2] += p0.z; acc[3] += p0.w;
+    acc[4] += p1.x; acc[5] += p1.y; acc[6] += p1.z; acc[7] += p1.w;
+  }
+  o[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+  o[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+}
+int spmm_blocks(int rows) { return (int)(((size_t)rows * SPMM_ROW_LANES + TPB - 1) / TPB); }
+
+// The long rows (list `longs`): a block per row; warp w sums the w-th of SPMM_LONG_WARPS
+// contiguous chunks of the row's entries in order, then the chunk sums are added in chunk
+// order.  Fixed order: reproducible.
+__global__ void __launch_bounds__(SPMM_LONG_WARPS * 32) spmm_long_kernel(
+    const int* __restrict__ longs, const int64_t* __restrict__ ptr, const int* __restrict__ idx,
+    const float* __restrict__ val, const float* __restrict__ in, float* out, int accumulate) {
+  __shared__ float2 part[SPMM_LONG_WARPS][32];
+  const int r = longs[blockIdx.x];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t k0 = ptr[r], k1 = ptr[r + 1];
+  const int64_t len = k1 - k0, chunk = (len + SPMM_LONG_WARPS - 1) / SPMM_LONG_WARPS;
+  const int64_t a = k0 + w * chunk, b = a + chunk < k1 ? a + chunk : k1;
+  part[w][lane] = a < b ? spmm_range(a, b, idx, val, in, lane) : make_float2(0.f, 0.f);
+  __syncthreads();
+  if (w == 0) {
+    float2 acc = part[0][lane];
+    for (int q = 1; q < SPMM_LONG_WARPS; ++q) {
+      acc.x += part[q][lane].x;
+      acc.y += part[q][lane].y;
+    }
+    spmm_store(out, r, lane, acc, accumulate);
+  }
 }
 
 // Stage a 64-row tile of an N x K row-major matrix into shared memory (rows past N read 0).
@@ -188,68 +272,6 @@ __global__ void __launch_bounds__(TPB) linear_kernel(int N, const float* __restr
   }
 }
 
-// Backward of out = relu(X1 W1^T + X2 W2^T + b): dZ = dOut * [out > 0] (stored), then
-// dX1 = dZ W1 (H x H weights only) and dX2 = dZ W2 when requested.
-__device__ __forceinline__ void tile_times_w(const float (*Z)[H + 1], const float (*Ws)[H + 1],
-                                             float* dst, int r0, int N) {
-  const int t = threadIdx.x, rg = t >> 4, cg = t & 15;
-  float acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-#pragma unroll 8
-  for (int o = 0; o < H; ++o) {
-    float z[4], w[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) z[i] = Z[rg * 4 + i][o];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) w[j] = Ws[o][cg * 4 + j];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(z[i], w[j], acc[i][j]);
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int row = r0 + rg * 4 + i;
-    if (row < N)
-      reinterpret_cast<float4*>(dst + (size_t)row * H)[cg] =
-          make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-  }
-}
-
-__global__ void __launch_bounds__(TPB) linear_bwd_kernel(int N, const float* __restrict__ dOut,
-                                                         const float* __restrict__ Hout,
-                                                         const __nv_bfloat16* __restrict__ W1,
-                                                         const __nv_bfloat16* __restrict__ W2,
-                                                         float* dZ, float* dX1, float* dX2) {
-  __shared__ float Zs[TILE][H + 1];
-  __shared__ float Ws[H][H + 1];
-  const int r0 = blockIdx.x * TILE;
-  for (int e = threadIdx.x; e < TILE * H; e += TPB) {
-    const int rr = e / H, o = e % H, row = r0 + rr;
-    float z = 0.f;
-    if (row < N) {
-      const size_t g = (size_t)row * H + o;
-      z = Hout[g] > 0.f ? dOut[g] : 0.f;
-      dZ[g] = z;
-    }
-    Zs[rr][o] = z;
-  }
-  if (dX1) {
-    stage_weights<H>(Ws, W1);
-    __syncthreads();
-    tile_times_w(Zs, Ws, dX1, r0, N);
-  }
-  if (dX2) {
-    __syncthreads();
-    stage_weights<H>(Ws, W2);
-    __syncthreads();
-    tile_times_w(Zs, Ws, dX2, r0, N);
-  }
-}
-
 // ---------------------------------------------------------------- tensor-core dense layers
 // The 64 x 64 layers run on the tensor cores: mma.sync m16n8k16, BF16 operands, FP32
 // accumulation.  Weights are BF16 already.  Activations are FP32; each is split into
@@ -303,19 +325,16 @@ __device__ __forceinline__ void b_frag(const __nv_bfloat16 (*S)[WPAD], int j, in
   b1 = *reinterpret_cast<const uint32_t*>(&S[8 * j + g][16 * kk + 2 * t + 8]);
 }
 
-// A fragments (hi, lo) of k-step kk of the 16-row tile at row r0 of X[N][H] (rows >= N: 0)
-__device__ __forceinline__ void a_frag_split(const float* X, int r0, int N, int kk, int g, int t,
-                                             uint32_t (&hi)[4], uint32_t (&lo)[4]) {
+// The four FP32 pairs behind the A fragment of k-step kk of the 16-row tile at row r0 of
+// X[N][H] (rows >= N: 0), in fragment order.
+__device__ __forceinline__ void a_frag_load(const float* X, int r0, int N, int kk, int g, int t,
+                                            float2 (&v)[4]) {
   const int ra = r0 + g, rb = r0 + g + 8, c = 16 * kk + 2 * t;
   const float2 z = make_float2(0.f, 0.f);
-  const float2 v0 = ra < N ? *reinterpret_cast<const float2*>(X + (size_t)ra * H + c) : z;
-  const float2 v1 = rb < N ? *reinterpret_cast<const float2*>(X + (size_t)rb * H + c) : z;
-  const float2 v2 = ra < N ? *reinterpret_cast<const float2*>(X + (size_t)ra * H + c + 8) : z;
-  const float2 v3 = rb < N ? *reinterpret_cast<const float2*>(X + (size_t)rb * H + c + 8) : z;
-  split2(v0, hi[0], lo[0]);
-  split2(v1, hi[1], lo[1]);
-  split2(v2, hi[2], lo[2]);
-  split2(v3, hi[3], lo[3]);
+  v[0] = ra < N ? *reinterpret_cast<const float2*>(X + (size_t)ra * H + c) : z;
+  v[1] = rb < N ? *reinterpret_cast<const float2*>(X + (size_t)rb * H + c) : z;
+  v[2] = ra < N ? *reinterpret_cast<const float2*>(X + (size_t)ra * H + c + 8) : z;
+  v[3] = rb < N ? *reinterpret_cast<const float2*>(X + (size_t)rb * H + c + 8) : z;
 }
 
 // out = relu(X1 W1^T + X2 W2^T + b) for X1, X2 [N][H], W1, W2 [H][H]: each warp one 16-row
@@ -330,8 +349,10 @@ __global__ void __launch_bounds__(MMA_WARPS * 32) linear_mma_kernel(
   stage_w_bf16(S2, W2, false);
   __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int r0 = blockIdx.x * MMA_ROWS + w * 16;
-  if (r0 >= N) return;
+  // persistent over row tiles: the weights are staged once per block
+  for (int tile = blockIdx.x; tile * MMA_ROWS < N; tile += gridDim.x) {
+  const int r0 = tile * MMA_ROWS + w * 16;
+  if (r0 >= N) break;
   float acc[8][4];
 #pragma unroll
   for (int j = 0; j < 8; ++j)
@@ -341,10 +362,14 @@ __global__ void __launch_bounds__(MMA_WARPS * 32) linear_mma_kernel(
   for (int which = 0; which < 2; ++which) {
     const float* X = which ? X2 : X1;
     const __nv_bfloat16(*S)[WPAD] = which ? S2 : S1;
+    float2 v[H / 16][4];  // the warp's 16 rows of X, all loads in flight together
+#pragma unroll
+    for (int kk = 0; kk < H / 16; ++kk) a_frag_load(X, r0, N, kk, g, t, v[kk]);
 #pragma unroll
     for (int kk = 0; kk < H / 16; ++kk) {
       uint32_t hi[4], lo[4];
-      a_frag_split(X, r0, N, kk, g, t, hi, lo);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) split2(v[kk][q], hi[q], lo[q]);
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         uint32_t b0, b1;
@@ -366,6 +391,7 @@ __global__ void __launch_bounds__(MMA_WARPS * 32) linear_mma_kernel(
       *reinterpret_cast<float2*>(out + (size_t)rb * H + c) =
           make_float2(fmaxf(acc[j][2] + b0, 0.f), fmaxf(acc[j][3] + b1, 0.f));
   }
+  }
 }
 
 // Backward of out = relu(X1 W1^T + X2 W2^T + b): dZ = dOut * [out > 0] (stored), then
@@ -376,13 +402,24 @@ __global__ void __launch_bounds__(MMA_WARPS * 32) linear_bwd_mma_kernel(
     float* dX1, float* dX2) {
   __shared__ __align__(16) __nv_bfloat16 S1[H][WPAD];
   __shared__ __align__(16) __nv_bfloat16 S2[H][WPAD];
-  stage_w_bf16(S1, W1, true);  // B[o][k] = W[o][k] read as S[n = k][o]
-  stage_w_bf16(S2, W2, true);
+  const bool products = W1 != nullptr;  // without weights: the ReLU mask only (dZ)
+  if (products) {
+    stage_w_bf16(S1, W1, true);  // B[o][k] = W[o][k] read as S[n = k][o]
+    stage_w_bf16(S2, W2, true);
+  }
   __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int r0 = blockIdx.x * MMA_ROWS + w * 16;
-  if (r0 >= N) return;
+  // persistent over row tiles: the weights are staged once per block
+  for (int tile = blockIdx.x; tile * MMA_ROWS < N; tile += gridDim.x) {
+  const int r0 = tile * MMA_ROWS + w * 16;
+  if (r0 >= N) break;
   const int ra = r0 + g, rb = r0 + g + 8;
+  float2 dv[H / 16][4], hv[H / 16][4];  // every load of the warp's rows before any store
+#pragma unroll
+  for (int kk = 0; kk < H / 16; ++kk) {
+    a_frag_load(dOut, r0, N, kk, g, t, dv[kk]);
+    a_frag_load(Hout, r0, N, kk, g, t, hv[kk]);
+  }
   uint32_t hi[H / 16][4], lo[H / 16][4];
 #pragma unroll
   for (int kk = 0; kk < H / 16; ++kk) {
@@ -390,17 +427,13 @@ __global__ void __launch_bounds__(MMA_WARPS * 32) linear_bwd_mma_kernel(
     for (int q = 0; q < 4; ++q) {
       const int r = (q & 1) ? rb : ra;
       const int c = 16 * kk + 2 * t + ((q & 2) ? 8 : 0);
-      float2 z = make_float2(0.f, 0.f);
-      if (r < N) {
-        const size_t e = (size_t)r * H + c;
-        const float2 d = *reinterpret_cast<const float2*>(dOut + e);
-        const float2 h = *reinterpret_cast<const float2*>(Hout + e);
-        z = make_float2(h.x > 0.f ? d.x : 0.f, h.y > 0.f ? d.y : 0.f);
-        *reinterpret_cast<float2*>(dZ + e) = z;
-      }
+      const float2 d = dv[kk][q], h = hv[kk][q];
+      const float2 z = make_float2(h.x > 0.f ? d.x : 0.f, h.y > 0.f ? d.y : 0.f);
+      if (r < N) *reinterpret_cast<float2*>(dZ + (size_t)r * H + c) = z;
       split2(z, hi[kk][q], lo[kk][q]);
     }
   }
+  if (!products) continue;
 #pragma unroll
   for (int which = 0; which < 2; ++which) {
     float* dX = which ? dX2 : dX1;
@@ -427,124 +460,182 @@ __global__ void __launch_bounds__(MMA_WARPS * 32) linear_bwd_mma_kernel(
       if (rb < N) *reinterpret_cast<float2*>(dX + (size_t)rb * H + c) = make_float2(acc[j][2], acc[j][3]);
     }
   }
+  }
 }
 
-// Weight gradient dW = dZ^T X (H x H) and bias gradient sum_r dZ[r] on the tensor cores:
-// partial[block][o * H + k] and partial[block][H * H + o] over the block's 64-row tiles
-// (tiles t = block, block + grid, ...), added in block order by reduce_partials_kernel.
-// Each 64-row tile is staged transposed in shared memory as BF16 hi / lo pairs (ZT[o][r],
-// XT[k][r]); warp w owns the output rows o = 16 (w % 4) .. + 15 and the n-tiles 4 (w / 4) .. + 3.
+// Weight gradients dW1 = dZ^T X1, dW2 = dZ^T X2 (H x H each) and the bias gradient sum_r dZ[r]
+// of one layer on the tensor cores: partial[block] = [dW1 | dW2 | bias] (2 H H + H floats,
+// the parameter order of a round) over the block's 64-row tiles (tiles t = block, block +
+// grid, ...), added in block order by reduce_partials_kernel.  Each tile is staged transposed
+// in shared memory as BF16 hi / lo pairs: ZT[o][r] once, then X1T[k][r] and X2T[k][r] in turn
+// through the same buffer.  Warp w owns the output rows o = 16 (w % 4) .. + 15 and the
+// n-tiles 4 (w / 4) .. + 3 of both products.
 constexpr int WG_TILE = 64;
-__global__ void __launch_bounds__(MMA_WARPS * 32) wgrad_mma_kernel(int N,
-                                                                  const float* __restrict__ dZ,
-                                                                  const float* __restrict__ X,
-                                                                  float* __restrict__ partial) {
-  __shared__ __align__(16) __nv_bfloat16 ZTh[H][WPAD], ZTl[H][WPAD], XTh[H][WPAD], XTl[H][WPAD];
-  __shared__ float bsum[4][H];
-  const int tid = threadIdx.x;
-  const int w = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-  const int mt = w & 3, nh = w >> 2;
-  // staging: thread (col = tid % 64, pair = tid / 64) moves rows 2p, 2p + 1 for p = pair, pair + 4, ...
-  const int col = tid & (H - 1), pr = tid >> 6;
-  float acc[4][4];
+constexpr int WG_PAIRS = WG_TILE / 2 / 4;  // row pairs per staging thread (4 threads per column)
+__device__ __forceinline__ void wg_stage(__nv_bfloat16 (*Th)[WPAD], __nv_bfloat16 (*Tl)[WPAD],
+                                         const float* __restrict__ X, int r0, int N, int col,
+                                         int pr, float* colsum) {
+  float a[WG_PAIRS], b[WG_PAIRS];
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
+  for (int u = 0; u < WG_PAIRS; ++u) {  // every load first
+    const int ra = r0 + 2 * (pr + 4 * u), rb = ra + 1;
+    a[u] = ra < N ? X[(size_t)ra * H + col] : 0.f;
+    b[u] = rb < N ? X[(size_t)rb * H + col] : 0.f;
+  }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
-  float bacc = 0.f;
-  for (int tile = blockIdx.x; tile * WG_TILE < N; tile += gridDim.x) {
-    const int r0 = tile * WG_TILE;
-    __syncthreads();  // the previous tile's fragments are read
-    for (int p = pr; p < WG_TILE / 2; p += 4) {
-      const int ra = r0 + 2 * p, rb = ra + 1;
-      const float za = ra < N ? dZ[(size_t)ra * H + col] : 0.f;
-      const float zb = rb < N ? dZ[(size_t)rb * H + col] : 0.f;
-      const float xa = ra < N ? X[(size_t)ra * H + col] : 0.f;
-      const float xb = rb < N ? X[(size_t)rb * H + col] : 0.f;
-      bacc += za;
-      bacc += zb;
-      uint32_t h, l;
-      split2(make_float2(za, zb), h, l);
-      *reinterpret_cast<uint32_t*>(&ZTh[col][2 * p]) = h;
-      *reinterpret_cast<uint32_t*>(&ZTl[col][2 * p]) = l;
-      split2(make_float2(xa, xb), h, l);
-      *reinterpret_cast<uint32_t*>(&XTh[col][2 * p]) = h;
-      *reinterpret_cast<uint32_t*>(&XTl[col][2 * p]) = l;
+  for (int u = 0; u < WG_PAIRS; ++u) {
+    const int p = pr + 4 * u;
+    if (colsum) {
+      *colsum += a[u];
+      *colsum += b[u];
     }
-    __syncthreads();
+    uint32_t h, l;
+    split2(make_float2(a[u], b[u]), h, l);
+    *reinterpret_cast<uint32_t*>(&Th[col][2 * p]) = h;
+    *reinterpret_cast<uint32_t*>(&Tl[col][2 * p]) = l;
+  }
+}
+
+__device__ __forceinline__ void wg_mma(const __nv_bfloat16 (*ZTh)[WPAD], const __nv_bfloat16 (*ZTl)[WPAD],
+                                       const __nv_bfloat16 (*XTh)[WPAD], const __nv_bfloat16 (*XTl)[WPAD],
+                                       int mt, int nh, int g, int t, float (&acc)[4][4]) {
 #pragma unroll
-    for (int kk = 0; kk < WG_TILE / 16; ++kk) {
-      uint32_t ah[4], al[4];
-      const int o = 16 * mt + g, c = 16 * kk + 2 * t;
-      ah[0] = *reinterpret_cast<const uint32_t*>(&ZTh[o][c]);
-      ah[1] = *reinterpret_cast<const uint32_t*>(&ZTh[o + 8][c]);
-      ah[2] = *reinterpret_cast<const uint32_t*>(&ZTh[o][c + 8]);
-      ah[3] = *reinterpret_cast<const uint32_t*>(&ZTh[o + 8][c + 8]);
-      al[0] = *reinterpret_cast<const uint32_t*>(&ZTl[o][c]);
-      al[1] = *reinterpret_cast<const uint32_t*>(&ZTl[o + 8][c]);
-      al[2] = *reinterpret_cast<const uint32_t*>(&ZTl[o][c + 8]);
-      al[3] = *reinterpret_cast<const uint32_t*>(&ZTl[o + 8][c + 8]);
+  for (int kk = 0; kk < WG_TILE / 16; ++kk) {
+    uint32_t ah[4], al[4];
+    const int o = 16 * mt + g, c = 16 * kk + 2 * t;
+    ah[0] = *reinterpret_cast<const uint32_t*>(&ZTh[o][c]);
+    ah[1] = *reinterpret_cast<const uint32_t*>(&ZTh[o + 8][c]);
+    ah[2] = *reinterpret_cast<const uint32_t*>(&ZTh[o][c + 8]);
+    ah[3] = *reinterpret_cast<const uint32_t*>(&ZTh[o + 8][c + 8]);
+    al[0] = *reinterpret_cast<const uint32_t*>(&ZTl[o][c]);
+    al[1] = *reinterpret_cast<const uint32_t*>(&ZTl[o + 8][c]);
+    al[2] = *reinterpret_cast<const uint32_t*>(&ZTl[o][c + 8]);
+    al[3] = *reinterpret_cast<const uint32_t*>(&ZTl[o + 8][c + 8]);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int k = 8 * (4 * nh + j) + g;
-        const uint32_t bh0 = *reinterpret_cast<const uint32_t*>(&XTh[k][c]);
-        const uint32_t bh1 = *reinterpret_cast<const uint32_t*>(&XTh[k][c + 8]);
-        const uint32_t bl0 = *reinterpret_cast<const uint32_t*>(&XTl[k][c]);
-        const uint32_t bl1 = *reinterpret_cast<const uint32_t*>(&XTl[k][c + 8]);
-        mma_bf16(acc[j], ah, bh0, bh1);
-        mma_bf16(acc[j], ah, bl0, bl1);
-        mma_bf16(acc[j], al, bh0, bh1);
-      }
+    for (int j = 0; j < 4; ++j) {
+      const int k = 8 * (4 * nh + j) + g;
+      const uint32_t bh0 = *reinterpret_cast<const uint32_t*>(&XTh[k][c]);
+      const uint32_t bh1 = *reinterpret_cast<const uint32_t*>(&XTh[k][c + 8]);
+      const uint32_t bl0 = *reinterpret_cast<const uint32_t*>(&XTl[k][c]);
+      const uint32_t bl1 = *reinterpret_cast<const uint32_t*>(&XTl[k][c + 8]);
+      mma_bf16(acc[j], ah, bh0, bh1);
+      mma_bf16(acc[j], ah, bl0, bl1);
+      mma_bf16(acc[j], al, bh0, bh1);
     }
   }
-  float* p = partial + (size_t)blockIdx.x * (H * H + H);
+}
+
+__device__ __forceinline__ void wg_store(float* p, int mt, int nh, int g, int t,
+                                         const float (&acc)[4][4]) {
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int k = 8 * (4 * nh + j) + 2 * t, o = 16 * mt + g;
     *reinterpret_cast<float2*>(p + (size_t)o * H + k) = make_float2(acc[j][0], acc[j][1]);
     *reinterpret_cast<float2*>(p + (size_t)(o + 8) * H + k) = make_float2(acc[j][2], acc[j][3]);
   }
+}
+
+constexpr int WG_STRIDE = 2 * H * H + H;  // floats per block partial
+__global__ void __launch_bounds__(MMA_WARPS * 32) wgrad_mma_kernel(int N,
+                                                                  const float* __restrict__ dZ,
+                                                                  const float* __restrict__ X1,
+                                                                  const float* __restrict__ X2,
+                                                                  float* __restrict__ partial) {
+  __shared__ __align__(16) __nv_bfloat16 ZTh[H][WPAD], ZTl[H][WPAD], XTh[H][WPAD], XTl[H][WPAD];
+  __shared__ float bsum[4][H];
+  const int tid = threadIdx.x;
+  const int w = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  const int mt = w & 3, nh = w >> 2;
+  const int col = tid & (H - 1), pr = tid >> 6;  // staging: column, first row pair
+  float acc1[4][4], acc2[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc1[j][q] = acc2[j][q] = 0.f;
+  float bacc = 0.f;
+  for (int tile = blockIdx.x; tile * WG_TILE < N; tile += gridDim.x) {
+    const int r0 = tile * WG_TILE;
+    __syncthreads();  // the previous tile's fragments are read
+    wg_stage(ZTh, ZTl, dZ, r0, N, col, pr, &bacc);
+    wg_stage(XTh, XTl, X1, r0, N, col, pr, nullptr);
+    __syncthreads();
+    wg_mma(ZTh, ZTl, XTh, XTl, mt, nh, g, t, acc1);
+    __syncthreads();  // X1's fragments are read
+    wg_stage(XTh, XTl, X2, r0, N, col, pr, nullptr);
+    __syncthreads();
+    wg_mma(ZTh, ZTl, XTh, XTl, mt, nh, g, t, acc2);
+  }
+  float* p = partial + (size_t)blockIdx.x * WG_STRIDE;
+  wg_store(p, mt, nh, g, t, acc1);
+  wg_store(p + H * H, mt, nh, g, t, acc2);
   bsum[pr][col] = bacc;
   __syncthreads();
-  if (tid < H) p[H * H + tid] = ((bsum[0][tid] + bsum[1][tid]) + bsum[2][tid]) + bsum[3][tid];
+  if (tid < H) p[2 * H * H + tid] = ((bsum[0][tid] + bsum[1][tid]) + bsum[2][tid]) + bsum[3][tid];
 }
 
-// partial[block][o * K + k] = sum over the block's rows r of dZ[r][o] X[r][k], and
-// partial[block][H * K + o] = sum of dZ[r][o] (bias); tiles t = block, block + grid, ...
-template <int K>
-__global__ void __launch_bounds__(TPB) wgrad_kernel(int N, const float* __restrict__ dZ,
-                                                    const float* __restrict__ X,
-                                                    float* __restrict__ partial) {
-  __shared__ float Zs[TILE][H + 1];
-  __shared__ float Xs[TILE][K + 1];
-  constexpr int PER = H * K / TPB;  // outputs per thread: 16 (K = 64) or 2 (K = 8)
-  const int t = threadIdx.x;
-  float acc[PER];
-#pragma unroll
-  for (int q = 0; q < PER; ++q) acc[q] = 0.f;
+// The 8-wide input encoders' gradients: dW = dZ^T X (H x F) and the bias, partial[block] =
+// [dW | bias] (H F + H floats), read by reduce_partials_kernel; one n8 tile, warps 0..3 own
+// the output rows 16 w .. + 15, all warps stage.  Same BF16 splits as wgrad_mma_kernel.
+__global__ void __launch_bounds__(MMA_WARPS * 32) wgrad8_mma_kernel(int N,
+                                                                   const float* __restrict__ dZ,
+                                                                   const float* __restrict__ X,
+                                                                   float* __restrict__ partial) {
+  __shared__ __align__(16) __nv_bfloat16 ZTh[H][WPAD], ZTl[H][WPAD], XTh[F][WPAD], XTl[F][WPAD];
+  __shared__ float bsum[4][H];
+  const int tid = threadIdx.x;
+  const int w = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  const int col = tid & (H - 1), pr = tid >> 6;
+  const int c8 = tid & (F - 1), p8 = tid / F;  // X staging: column, row pair (256 = 8 x 32)
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
   float bacc = 0.f;
-  for (int tile = blockIdx.x; tile * TILE < N; tile += gridDim.x) {
-    const int r0 = tile * TILE;
+  for (int tile = blockIdx.x; tile * WG_TILE < N; tile += gridDim.x) {
+    const int r0 = tile * WG_TILE;
     __syncthreads();
-    stage_rows<H>(Zs, dZ, r0, N);
-    stage_rows<K>(Xs, X, r0, N);
+    wg_stage(ZTh, ZTl, dZ, r0, N, col, pr, &bacc);
+    {
+      const int ra = r0 + 2 * p8, rb = ra + 1;
+      const float xa = ra < N ? X[(size_t)ra * F + c8] : 0.f;
+      const float xb = rb < N ? X[(size_t)rb * F + c8] : 0.f;
+      uint32_t h, l;
+      split2(make_float2(xa, xb), h, l);
+      *reinterpret_cast<uint32_t*>(&XTh[c8][2 * p8]) = h;
+      *reinterpret_cast<uint32_t*>(&XTl[c8][2 * p8]) = l;
+    }
     __syncthreads();
-    for (int r = 0; r < TILE; ++r) {
+    if (w < 4) {
 #pragma unroll
-      for (int q = 0; q < PER; ++q) {
-        const int e = t * PER + q, o = e / K, k = e % K;
-        acc[q] = fmaf(Zs[r][o], Xs[r][k], acc[q]);
+      for (int kk = 0; kk < WG_TILE / 16; ++kk) {
+        uint32_t ah[4], al[4];
+        const int o = 16 * w + g, c = 16 * kk + 2 * t;
+        ah[0] = *reinterpret_cast<const uint32_t*>(&ZTh[o][c]);
+        ah[1] = *reinterpret_cast<const uint32_t*>(&ZTh[o + 8][c]);
+        ah[2] = *reinterpret_cast<const uint32_t*>(&ZTh[o][c + 8]);
+        ah[3] = *reinterpret_cast<const uint32_t*>(&ZTh[o + 8][c + 8]);
+        al[0] = *reinterpret_cast<const uint32_t*>(&ZTl[o][c]);
+        al[1] = *reinterpret_cast<const uint32_t*>(&ZTl[o + 8][c]);
+        al[2] = *reinterpret_cast<const uint32_t*>(&ZTl[o][c + 8]);
+        al[3] = *reinterpret_cast<const uint32_t*>(&ZTl[o + 8][c + 8]);
+        const uint32_t bh0 = *reinterpret_cast<const uint32_t*>(&XTh[g][c]);
+        const uint32_t bh1 = *reinterpret_cast<const uint32_t*>(&XTh[g][c + 8]);
+        const uint32_t bl0 = *reinterpret_cast<const uint32_t*>(&XTl[g][c]);
+        const uint32_t bl1 = *reinterpret_cast<const uint32_t*>(&XTl[g][c + 8]);
+        mma_bf16(acc, ah, bh0, bh1);
+        mma_bf16(acc, ah, bl0, bl1);
+        mma_bf16(acc, al, bh0, bh1);
       }
-      if (t < H) bacc += Zs[r][t];
     }
   }
-  float* p = partial + (size_t)blockIdx.x * (H * K + H);
-#pragma unroll
-  for (int q = 0; q < PER; ++q) p[t * PER + q] = acc[q];
-  if (t < H) p[H * K + t] = bacc;
+  float* pp = partial + (size_t)blockIdx.x * (H * F + H);
+  if (w < 4) {
+    const int o = 16 * w + g, k = 2 * t;
+    *reinterpret_cast<float2*>(pp + (size_t)o * F + k) = make_float2(acc[0], acc[1]);
+    *reinterpret_cast<float2*>(pp + (size_t)(o + 8) * F + k) = make_float2(acc[2], acc[3]);
+  }
+  bsum[pr][col] = bacc;
+  __syncthreads();
+  if (tid < H) pp[H * F + tid] = ((bsum[0][tid] + bsum[1][tid]) + bsum[2][tid]) + bsum[3][tid];
 }
 
-// grad[e] += sum over blocks g (in order) of partial[g * stride + e], e < len.
 // grad[e] += sum over blocks g of partial[g * stride + e], e < len: a block takes 32
 // consecutive e and RP_SLICES slices of g (slice q: g = q, q + RP_SLICES, ... in order, loads
 // batched), then adds the slices' sums in slice order.  Fixed order: reproducible.
@@ -719,6 +810,11 @@ __global__ void to_bf16_kernel(int64_t P, const float* theta, __nv_bfloat16* wbf
 struct dpdlp_gnn {
   int device = 0;
   cudaStream_t stream = nullptr;
+  // backward: the weight gradients (the users of `partial`) run on a second stream beside the
+  // data-gradient chain; ev_z* are recorded after a dZ buffer is written (main stream),
+  // ev_w* after the gradient pass that reads it (side stream)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_zv = nullptr, ev_zc = nullptr, ev_wv = nullptr, ev_wc = nullptr;
   std::string err;
   int ptr_dev = 0;
   int n = 0, m = 0;
@@ -727,6 +823,8 @@ struct dpdlp_gnn {
   // A (m rows): R values (row-normalised) and Ct values (A D_c^-1, for C^T in backward);
   // A^T (n rows): C values (column-normalised) and Rt values (A^T D_r^-1, for R^T)
   int64_t *a_ptr = nullptr, *t_ptr = nullptr;
+  int *a_long = nullptr, *t_long = nullptr;  // rows longer than SPMM_LONG of A and of A^T
+  int na_long = 0, nt_long = 0;
   int *a_idx = nullptr, *t_idx = nullptr;
   float *a_R = nullptr, *a_Ct = nullptr, *t_C = nullptr, *t_Rt = nullptr;
   float *Fv = nullptr, *Fc = nullptr, *tx = nullptr, *ty = nullptr;
@@ -779,7 +877,11 @@ void free_graph_buffers(dpdlp_gnn* g) {
 }
 
 int blocks_for_rows(int rows) { return (rows + TILE - 1) / TILE; }
-int mma_blocks(int rows) { return (rows + MMA_ROWS - 1) / MMA_ROWS; }
+// persistent dense kernels: at most two blocks per SM, each looping over 128-row tiles
+int mma_blocks(int rows) {
+  const int tiles = (rows + MMA_ROWS - 1) / MMA_ROWS;
+  return tiles < WG_BLOCKS ? (tiles > 0 ? tiles : 1) : WG_BLOCKS;
+}
 int warp_blocks(int rows) { return (int)(((size_t)rows * 32 + TPB - 1) / TPB); }
 int wg_grid(int rows) {
   const int b = blocks_for_rows(rows);
@@ -795,16 +897,40 @@ cudaMemcpyKind out_kind(const dpdlp_gnn* g) {
 
 // weight gradient of one layer: grad[off .. off + H*K) += dZ^T X and, with_bias, the next
 // H entries (the bias that follows the weight in the parameter order) += column sums of dZ
-template <int K>
-int add_wgrad(dpdlp_gnn* g, int N, const float* dZ, const float* X, int64_t off,
-              bool with_bias) {
+// out (=|+=) the aggregation over A's rows (transpose = false) or A^T's rows with the value
+// array `val`: a warp per short row, a block per long row.
+void spmm(dpdlp_gnn* g, bool transpose, const float* val, const float* in, float* out,
+          int accumulate) {
+  const int rows = transpose ? g->n : g->m;
+  if (rows == 0) return;
+  const int64_t* ptr = transpose ? g->t_ptr : g->a_ptr;
+  const int* idx = transpose ? g->t_idx : g->a_idx;
+  spmm_kernel<<<spmm_blocks(rows), TPB, 0, g->stream>>>(rows, ptr, idx, val, in, out, accumulate);
+  const int nl = transpose ? g->nt_long : g->na_long;
+  if (nl > 0)
+    spmm_long_kernel<<<nl, SPMM_LONG_WARPS * 32, 0, g->stream>>>(transpose ? g->t_long : g->a_long,
+                                                                ptr, idx, val, in, out, accumulate);
+}
+
+// both weight gradients and the bias gradient of a round's layer: grad[off ..) += [dZ^T X1 |
+// dZ^T X2 | column sums of dZ] (the parameter order U, V, b)
+int add_wgrad2(dpdlp_gnn* g, int N, const float* dZ, const float* X1, const float* X2, int64_t off) {
   const int G = wg_grid(N);
-  const int stride = H * K + H;
-  const int len = with_bias ? stride : H * K;
-  if constexpr (K == H) wgrad_mma_kernel<<<G, MMA_WARPS * 32, 0, g->stream>>>(N, dZ, X, g->partial);
-  else wgrad_kernel<K><<<G, TPB, 0, g->stream>>>(N, dZ, X, g->partial);
-  reduce_partials_kernel<<<reduce_grid(len), RP_E * RP_SLICES, 0, g->stream>>>(G, len, stride, g->partial,
-                                                                        g->grad + off);
+  wgrad_mma_kernel<<<G, MMA_WARPS * 32, 0, g->side>>>(N, dZ, X1, X2, g->partial);
+  reduce_partials_kernel<<<reduce_grid(WG_STRIDE), RP_E * RP_SLICES, 0, g->side>>>(
+      G, WG_STRIDE, WG_STRIDE, g->partial, g->grad + off);
+  GCK(cudaGetLastError());
+  return 0;
+}
+
+// an input encoder's weight and bias gradients: grad[off ..) += [dZ^T X | column sums of dZ]
+int add_wgrad8(dpdlp_gnn* g, int N, const float* dZ, const float* X, int64_t off) {
+  const int G = wg_grid(N);
+  const int stride = H * F + H;
+  const int len = stride;
+  wgrad8_mma_kernel<<<G, MMA_WARPS * 32, 0, g->side>>>(N, dZ, X, g->partial);
+  reduce_partials_kernel<<<reduce_grid(len), RP_E * RP_SLICES, 0, g->side>>>(G, len, stride, g->partial,
+                                                                      g->grad + off);
   GCK(cudaGetLastError());
   return 0;
 }
@@ -826,9 +952,14 @@ int dpdlp_gnn_create(dpdlp_gnn_t** out, int device) {
   if (!g) return DPDLP_ERR_OOM;
   g->device = device;
   const size_t P = (size_t)LAY.total;
-  const size_t part = (size_t)WG_BLOCKS * (H * H + H);
+  const size_t part = (size_t)WG_BLOCKS * WG_STRIDE;
   if (cudaSetDevice(device) != cudaSuccess ||
       cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->ev_zv, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->ev_zc, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->ev_wv, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->ev_wc, cudaEventDisableTiming) != cudaSuccess ||
       cudaMalloc(&g->theta, P * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&g->grad, P * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&g->m1, P * sizeof(float)) != cudaSuccess ||
@@ -858,6 +989,11 @@ void dpdlp_gnn_destroy(dpdlp_gnn_t* g) {
   void* ps[] = {g->theta, g->grad, g->m1, g->m2, g->wbf, g->partial};
   for (void* p : ps)
     if (p) cudaFree(p);
+  if (g->side) cudaStreamSynchronize(g->side);
+  cudaEvent_t evs[] = {g->ev_zv, g->ev_zc, g->ev_wv, g->ev_wc};
+  for (cudaEvent_t e : evs)
+    if (e) cudaEventDestroy(e);
+  if (g->side) cudaStreamDestroy(g->side);
   if (g->stream) cudaStreamDestroy(g->stream);
   delete g;
 }
@@ -955,8 +1091,17 @@ int dpdlp_gnn_set_graph(dpdlp_gnn_t* g, int32_t n, int32_t m, const int64_t* row
         tRt[q] = (float)(val[k] / rs[i]);
       }
   }
+  std::vector<int> along, tlong;
+  for (int i = 0; i < m; ++i)
+    if (row_ptr[i + 1] - row_ptr[i] > SPMM_LONG) along.push_back(i);
+  for (int j = 0; j < n; ++j)
+    if (tptr[j + 1] - tptr[j] > SPMM_LONG) tlong.push_back(j);
   int rc;
   const size_t nH = (size_t)n * H, mH = (size_t)m * H;
+  if ((rc = galloc(g, &g->a_long, along.size())) || (rc = galloc(g, &g->t_long, tlong.size())))
+    return rc;
+  g->na_long = (int)along.size();
+  g->nt_long = (int)tlong.size();
   if ((rc = galloc(g, &g->a_ptr, m + 1)) || (rc = galloc(g, &g->t_ptr, n + 1)) ||
       (rc = galloc(g, &g->a_idx, nnz)) || (rc = galloc(g, &g->t_idx, nnz)) ||
       (rc = galloc(g, &g->a_R, nnz)) || (rc = galloc(g, &g->a_Ct, nnz)) ||
@@ -988,6 +1133,8 @@ int dpdlp_gnn_set_graph(dpdlp_gnn_t* g, int32_t n, int32_t m, const int64_t* row
   GCK(up(g->a_Ct, aCt.data(), nnz * sizeof(float)));
   GCK(up(g->t_C, tC.data(), nnz * sizeof(float)));
   GCK(up(g->t_Rt, tRt.data(), nnz * sizeof(float)));
+  GCK(up(g->a_long, along.data(), along.size() * sizeof(int)));
+  GCK(up(g->t_long, tlong.data(), tlong.size() * sizeof(int)));
   g->graph = true;
   return 0;
 }
@@ -1014,11 +1161,11 @@ int dpdlp_gnn_forward(dpdlp_gnn_t* g, float* x_hat, float* y_hat) {
   if (m) linear_kernel<F, false><<<blocks_for_rows(m), TPB, 0, s>>>(m, g->Fc, w + LAY.Ec, nullptr, nullptr, th + LAY.ec, g->hc[0]);
   for (int l = 0; l < L; ++l) {
     if (m) {
-      spmm_kernel<<<warp_blocks(m), TPB, 0, s>>>(m, g->a_ptr, g->a_idx, g->a_R, g->hv[l], g->gc[l], 0);
+      spmm(g, false, g->a_R, g->hv[l], g->gc[l], 0);
       linear_mma_kernel<<<mma_blocks(m), MMA_WARPS * 32, 0, s>>>(m, g->hc[l], w + LAY.Uc[l], g->gc[l], w + LAY.Vc[l], th + LAY.bc[l], g->hc[l + 1]);
     }
     if (n) {
-      spmm_kernel<<<warp_blocks(n), TPB, 0, s>>>(n, g->t_ptr, g->t_idx, g->t_C, g->hc[l + 1], g->gv[l], 0);
+      spmm(g, true, g->t_C, g->hc[l + 1], g->gv[l], 0);
       linear_mma_kernel<<<mma_blocks(n), MMA_WARPS * 32, 0, s>>>(n, g->hv[l], w + LAY.Uv[l], g->gv[l], w + LAY.Vv[l], th + LAY.bv[l], g->hv[l + 1]);
     }
   }
@@ -1043,46 +1190,71 @@ int dpdlp_gnn_backward(dpdlp_gnn_t* g, const float* tx, const float* ty, double*
   if (m) GCK(cudaMemcpyAsync(g->ty, ty, m * sizeof(float), in_kind(g), s));
   int cv = 0, cc = 0;  // dhv[cv], dhc[cc]: gradients of the current hv, hc (the heads write all rows)
   const int gx = n ? warp_blocks(n) : 0, gy = m ? warp_blocks(m) : 0;
+  // The weight gradients run on g->side, in order (they share `partial`); before the main
+  // stream rewrites a dZ buffer it waits for the side pass that reads it.
+  cudaStream_t side = g->side;
+  GCK(cudaEventRecord(g->ev_zv, s));  // the side stream starts after the targets are in
+  GCK(cudaStreamWaitEvent(side, g->ev_zv, 0));
   if (n) {
     head_bwd_kernel<<<gx, TPB, 0, s>>>(n, g->xhat, g->tx, w + LAY.wx, g->dx, g->dhv[0], g->loss_part);
+    GCK(cudaEventRecord(g->ev_zv, s));
+    GCK(cudaStreamWaitEvent(side, g->ev_zv, 0));
     const int G = wg_grid(n);
-    head_wgrad_kernel<<<G, TPB, 0, s>>>(n, g->dx, g->hv[L], g->partial);
-    reduce_partials_kernel<<<reduce_grid(H + 1), RP_E * RP_SLICES, 0, s>>>(G, H + 1, H + 1, g->partial, g->grad + LAY.wx);
+    head_wgrad_kernel<<<G, TPB, 0, side>>>(n, g->dx, g->hv[L], g->partial);
+    reduce_partials_kernel<<<reduce_grid(H + 1), RP_E * RP_SLICES, 0, side>>>(G, H + 1, H + 1, g->partial, g->grad + LAY.wx);
   }
   if (m) {
     head_bwd_kernel<<<gy, TPB, 0, s>>>(m, g->yhat, g->ty, w + LAY.wy, g->dy, g->dhc[0], g->loss_part + gx);
+    GCK(cudaEventRecord(g->ev_zc, s));
+    GCK(cudaStreamWaitEvent(side, g->ev_zc, 0));
     const int G = wg_grid(m);
-    head_wgrad_kernel<<<G, TPB, 0, s>>>(m, g->dy, g->hc[L], g->partial);
-    reduce_partials_kernel<<<reduce_grid(H + 1), RP_E * RP_SLICES, 0, s>>>(G, H + 1, H + 1, g->partial, g->grad + LAY.wy);
+    head_wgrad_kernel<<<G, TPB, 0, side>>>(m, g->dy, g->hc[L], g->partial);
+    reduce_partials_kernel<<<reduce_grid(H + 1), RP_E * RP_SLICES, 0, side>>>(G, H + 1, H + 1, g->partial, g->grad + LAY.wy);
   }
+  GCK(cudaEventRecord(g->ev_wv, side));
+  GCK(cudaEventRecord(g->ev_wc, side));
   sum_parts_kernel<<<1, SP_THREADS, 0, s>>>(gx + gy, g->loss_part, g->loss_d);
   int rc;
   for (int l = L - 1; l >= 0; --l) {
     // variable update of round l: hv[l+1] = relu(hv[l] Uv^T + gv[l] Vv^T + bv), gv = C hc[l+1]
     if (n) {
+      GCK(cudaStreamWaitEvent(s, g->ev_wv, 0));  // the previous pass over dzv is done
       linear_bwd_mma_kernel<<<mma_blocks(n), MMA_WARPS * 32, 0, s>>>(n, g->dhv[cv], g->hv[l + 1], w + LAY.Uv[l], w + LAY.Vv[l], g->dzv, g->dhv[1 - cv], g->dgv);
-      if ((rc = add_wgrad<H>(g, n, g->dzv, g->hv[l], LAY.Uv[l], false))) return rc;
-      if ((rc = add_wgrad<H>(g, n, g->dzv, g->gv[l], LAY.Vv[l], true))) return rc;
-      if (m) spmm_kernel<<<warp_blocks(m), TPB, 0, s>>>(m, g->a_ptr, g->a_idx, g->a_Ct, g->dgv, g->dhc[cc], 1);
+      GCK(cudaEventRecord(g->ev_zv, s));
+      GCK(cudaStreamWaitEvent(side, g->ev_zv, 0));
+      if ((rc = add_wgrad2(g, n, g->dzv, g->hv[l], g->gv[l], LAY.Uv[l]))) return rc;
+      GCK(cudaEventRecord(g->ev_wv, side));
+      if (m) spmm(g, false, g->a_Ct, g->dgv, g->dhc[cc], 1);
       cv = 1 - cv;
     }
     // constraint update of round l: hc[l+1] = relu(hc[l] Uc^T + gc[l] Vc^T + bc), gc = R hv[l]
     if (m) {
+      GCK(cudaStreamWaitEvent(s, g->ev_wc, 0));  // the previous pass over dzc is done
       linear_bwd_mma_kernel<<<mma_blocks(m), MMA_WARPS * 32, 0, s>>>(m, g->dhc[cc], g->hc[l + 1], w + LAY.Uc[l], w + LAY.Vc[l], g->dzc, g->dhc[1 - cc], g->dgc);
-      if ((rc = add_wgrad<H>(g, m, g->dzc, g->hc[l], LAY.Uc[l], false))) return rc;
-      if ((rc = add_wgrad<H>(g, m, g->dzc, g->gc[l], LAY.Vc[l], true))) return rc;
-      if (n) spmm_kernel<<<warp_blocks(n), TPB, 0, s>>>(n, g->t_ptr, g->t_idx, g->t_Rt, g->dgc, g->dhv[cv], 1);
+      GCK(cudaEventRecord(g->ev_zc, s));
+      GCK(cudaStreamWaitEvent(side, g->ev_zc, 0));
+      if ((rc = add_wgrad2(g, m, g->dzc, g->hc[l], g->gc[l], LAY.Uc[l]))) return rc;
+      GCK(cudaEventRecord(g->ev_wc, side));
+      if (n) spmm(g, true, g->t_Rt, g->dgc, g->dhv[cv], 1);
       cc = 1 - cc;
     }
   }
   if (n) {
-    linear_bwd_kernel<<<blocks_for_rows(n), TPB, 0, s>>>(n, g->dhv[cv], g->hv[0], nullptr, nullptr, g->dzv, nullptr, nullptr);
-    if ((rc = add_wgrad<F>(g, n, g->dzv, g->Fv, LAY.Ev, true))) return rc;
+    GCK(cudaStreamWaitEvent(s, g->ev_wv, 0));
+    linear_bwd_mma_kernel<<<mma_blocks(n), MMA_WARPS * 32, 0, s>>>(n, g->dhv[cv], g->hv[0], nullptr, nullptr, g->dzv, nullptr, nullptr);
+    GCK(cudaEventRecord(g->ev_zv, s));
+    GCK(cudaStreamWaitEvent(side, g->ev_zv, 0));
+    if ((rc = add_wgrad8(g, n, g->dzv, g->Fv, LAY.Ev))) return rc;
   }
   if (m) {
-    linear_bwd_kernel<<<blocks_for_rows(m), TPB, 0, s>>>(m, g->dhc[cc], g->hc[0], nullptr, nullptr, g->dzc, nullptr, nullptr);
-    if ((rc = add_wgrad<F>(g, m, g->dzc, g->Fc, LAY.Ec, true))) return rc;
+    GCK(cudaStreamWaitEvent(s, g->ev_wc, 0));
+    linear_bwd_mma_kernel<<<mma_blocks(m), MMA_WARPS * 32, 0, s>>>(m, g->dhc[cc], g->hc[0], nullptr, nullptr, g->dzc, nullptr, nullptr);
+    GCK(cudaEventRecord(g->ev_zc, s));
+    GCK(cudaStreamWaitEvent(side, g->ev_zc, 0));
+    if ((rc = add_wgrad8(g, m, g->dzc, g->Fc, LAY.Ec))) return rc;
   }
+  GCK(cudaEventRecord(g->ev_wv, side));  // every gradient is in before the backward returns
+  GCK(cudaStreamWaitEvent(s, g->ev_wv, 0));
   GCK(cudaGetLastError());
   double lv = 0.0;
   GCK(cudaMemcpyAsync(&lv, g->loss_d, sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -1139,6 +1139,7 @@ constexpr int FB_WARPS = 16;
 constexpr int FB_TPB = FB_WARPS * LANES;
 constexpr int FB_MAX_CLUSTER = 8;     // CTAs of the cluster form (the portable cluster size)
 constexpr int FB_SLOTS_PER_CTA = 2;   // automatic cluster size: about this many slots per CTA
+constexpr int FB_SINGLE_MAX_SLOTS = 6;  // automatic: one CTA up to this many slots per copy
 
 // One product-and-step phase over every slot of M (the packed_spmv_kernel body).
 template <class Epi>
@@ -1365,11 +1366,17 @@ cudaError_t fused_body_prepare() {
   return e;
 }
 
+// Automatic size, measured on one GB300 (us per iteration, n = 2m, 8 nonzeros per column):
+// one CTA is fastest up to about 6 slots per copy (latency-bound: 8.1 us at 2 slots against
+// 11.3 separate); beyond that one SM's FP64 rate bounds it and a cluster with about two
+// slots per CTA wins narrowly (16 slots: 11.8 against 12.3 separate; 32: 15.3 against
+// 16.2); a cluster barrier costs about 2 us, so at 64 slots the separate launches win.
 int fused_cluster_ctas(const DevPacked& csc, const DevPacked& csr, int requested) {
   if (requested >= 1) return requested > FB_MAX_CLUSTER ? FB_MAX_CLUSTER : requested;
   const int slots = csc.nslots > csr.nslots ? csc.nslots : csr.nslots;
+  if (slots <= FB_SINGLE_MAX_SLOTS) return 1;
   const int c = (slots + FB_SLOTS_PER_CTA - 1) / FB_SLOTS_PER_CTA;
-  return c < 1 ? 1 : (c > FB_MAX_CLUSTER ? FB_MAX_CLUSTER : c);
+  return c > FB_MAX_CLUSTER ? FB_MAX_CLUSTER : c;
 }
 
 template <class PEpi>

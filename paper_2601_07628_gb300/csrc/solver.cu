@@ -71,7 +71,7 @@ std::map<std::string, Param> default_params() {
       {"cta_slots_primal", {4, 2, 8, true}},
       {"cta_slots_dual", {4, 2, 8, true}},
       {"fused_body", {1, 0, 1, true}},
-      {"fused_max_slots", {6, 1, FUSED_MAX_SLOTS, true}},
+      {"fused_max_slots", {40, 1, FUSED_MAX_SLOTS, true}},
       {"fused_cluster", {0, 0, 8, true}},
   };
 }
@@ -462,10 +462,10 @@ int init_fresh(dpdlp* h) {
   return 0;
 }
 
-// A small single LP runs each graph body as one fused launch (same results, fewer launches).
-// One SM issues about 2 FP64 FMAs per clock, so the fused block is bound by its FP64 work
-// once an orientation has more than a few slots: measured faster than the separate launches
-// up to 5 slots (1.4x at 1-5), slower from 8; hence fused_max_slots = 6 by default.
+// A small single LP runs each graph body as one fused launch (same results, fewer launches):
+// one thread block up to 6 slots per copy, a thread-block cluster beyond (fused_cluster_ctas);
+// measured faster than the separate launches up to about 40 slots per copy, hence
+// fused_max_slots = 40 by default.
 bool use_fused(const dpdlp* h) {
   return h->P("fused_body") != 0.0 &&
          fused_body_fits(h->csc, h->csr, h->ninst, (int)h->P("fused_max_slots"));

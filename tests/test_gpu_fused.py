@@ -130,10 +130,12 @@ def test_large_lp_does_not_fuse(Solver):
 
 
 def test_default_threshold(Solver):
-    """By default only LPs with at most 6 slots per packed copy take the fused form."""
+    """By default LPs with at most 40 slots per packed copy take the fused form (one block up
+    to 6 slots, a cluster beyond); larger ones launch separately."""
     tiny = lpgen.small_random_lp(7, n=250, m=125)  # 2 slots per copy
     small = lpgen.small_random_lp(0)  # 16 slots per copy
-    for lp, want in ((tiny, 1), (small, 0)):
+    big = lpgen.small_random_lp(1, n=8000, m=4000)  # 64 slots per copy
+    for lp, want in ((tiny, 1), (small, 1), (big, 0)):
         s = Solver()
         s.load(lp)
         assert s.info()["fused_body"] == want
