@@ -358,18 +358,20 @@ __global__ void __launch_bounds__(MMA_WARPS * 32) linear_mma_kernel(
   for (int j = 0; j < 8; ++j)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+  float2 v[2][H / 16][4];  // the warp's 16 rows of X1 and X2, all loads in flight together
+#pragma unroll
+  for (int kk = 0; kk < H / 16; ++kk) {
+    a_frag_load(X1, r0, N, kk, g, t, v[0][kk]);
+    a_frag_load(X2, r0, N, kk, g, t, v[1][kk]);
+  }
 #pragma unroll
   for (int which = 0; which < 2; ++which) {
-    const float* X = which ? X2 : X1;
     const __nv_bfloat16(*S)[WPAD] = which ? S2 : S1;
-    float2 v[H / 16][4];  // the warp's 16 rows of X, all loads in flight together
-#pragma unroll
-    for (int kk = 0; kk < H / 16; ++kk) a_frag_load(X, r0, N, kk, g, t, v[kk]);
 #pragma unroll
     for (int kk = 0; kk < H / 16; ++kk) {
       uint32_t hi[4], lo[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) split2(v[kk][q], hi[q], lo[q]);
+      for (int q = 0; q < 4; ++q) split2(v[which][kk][q], hi[q], lo[q]);
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         uint32_t b0, b1;
