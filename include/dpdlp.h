@@ -243,10 +243,13 @@ int dpdlp_set_row_bounds(dpdlp_t* h, const double* lc, const double* uc);
  *   them (they load what no kernel writes -- slot descriptors, first index batches -- while
  *   it drains, then wait for it); 0 = plain stream order.  Results do not depend on it.
  *   list_fraction (0.5, 0..2), list_warps_per_sm (0 = the most the list kernel's register
- *   budget allows): batches only.  A graph body walks the lists of slots of running
- *   instances (a persistent kernel with list_warps_per_sm resident warps per SM) when fewer
- *   than list_fraction of all slots are active, else launches over every slot (stopped
- *   instances' warps exit at once).  Launch choices only, set by the autotuner.
+ *   budget allows), list_few_slots (256): batches only.  A graph body walks the lists of
+ *   slots of running instances (a persistent kernel with list_warps_per_sm resident warps
+ *   per SM) when fewer than list_fraction of all slots are active, else launches over every
+ *   slot (stopped instances' warps exit at once); with at most list_few_slots active slots
+ *   it walks the lists with grids of about that many warps (a few stragglers do not pay for
+ *   launching a full grid each iteration).  Launch choices only; the first two are set by
+ *   the autotuner.
  * Load-time keys (block_permute, perm_block, perm_seed, precond, ruiz_passes,
  * pock_chambolle) take effect at the next dpdlp_load_lp / dpdlp_load_batch.  Unknown key or out-of-range value: DPDLP_ERR_INVALID. */
 int dpdlp_set_param(dpdlp_t* h, const char* key, double v);

@@ -75,6 +75,8 @@ struct DevPacked {
   int nlong_block = 0, nlong_warp = 0;
   int cta_slots = PK_WARPS;  // slots per block of this orientation's iteration kernel (2, 4, 8)
   int list_warps_per_sm = 0;  // resident warps per SM of the persistent list kernel (0: most)
+  int list_few_slots = 0;     // a body with at most this many active slots (list mode 2) walks
+                              // the lists with a grid of about this many warps
   const double* val = nullptr;
   const float* val32 = nullptr;  // FP32 copy of the values (nullptr: not representable)
   const uint32_t* idx = nullptr;
@@ -222,7 +224,8 @@ void build_packed(int rows, int cols, const std::vector<int64_t>& ptr,
 struct IterPlan {
   int i;              // iteration index inside the graph body
   int force_regular;  // 1: run as a regular iteration regardless of the scalars (timing)
-  int list;           // batches: 1 walk the active-slot list, 0 one launch over every slot
+  int list;           // batches: 1 walk the active-slot list, 2 the same with a small grid
+                      // (few slots active), 0 one launch over every slot
   int pdl;            // launch as a programmatic dependent of the previous kernel
   int idle;           // timing only: every instance counts as stopped (an empty slot list)
 };
@@ -251,10 +254,13 @@ cudaError_t launch_spmv(const DevPacked& M, const double* x0, const double* x1, 
 cudaError_t launch_check(const DevPacked& csr, const DevPacked& csc, const DevVecs& v,
                          DevScalars* sc, unsigned long long cond_handle, int use_cond,
                          cudaStream_t s);
-// Batches: set the graph conditional `handle` to 1 when fewer than `fraction` of the slots
-// are active (the next body walks the lists), else 0.
+// Batches: set the graph conditional `handle` (a switch over the body's three forms) to 2 when
+// at most `few` slots are active (the lists, small grids), else 1 when fewer than `fraction`
+// of the slots are active (the lists), else 0 (every slot).
 cudaError_t launch_select(const DevPacked& csr, const DevPacked& csc, unsigned long long handle,
-                          double fraction, cudaStream_t s);
+                          double fraction, int few, cudaStream_t s);
+// The same choice on the host, from the active counts.
+int select_form(long long active, long long total, double fraction, int few);
 // Most resident warps per SM of the persistent list kernel (its register budget).
 int list_max_warps_per_sm();
 // Batches: rebuild both orientations' lists of slots of running instances.

@@ -982,7 +982,10 @@ static cudaError_t launch_slots(const DevPacked& M, GatherVecs<NV> g, Epi epi, c
       const int most = (DPDLP_LIST_MIN_BLOCKS * PK_WARPS) / W;  // resident blocks per SM
       const int want = M.list_warps_per_sm > 0 ? M.list_warps_per_sm / W : most;
       const int resident = sm_count() * (want < 1 ? 1 : (want > most ? most : want));
-      const int need = (M.nslots + W - 1) / W;
+      // few slots active: a grid of about one warp per possible active slot (the warps still
+      // stride over however many there are, so any count is walked correctly)
+      const int few = epi.listed == 2 && M.list_few_slots > 0 ? (M.list_few_slots + W - 1) / W : 0;
+      const int need = few > 0 ? few : (M.nslots + W - 1) / W;
       const int grid = DPDLP_LIST_PERSISTENT && need > resident ? resident : need;
       return launch_k(packed_list_kernel<NV, W, Epi>, grid, W * LANES, s, pdl, M, g, epi);
     }
@@ -1802,18 +1805,27 @@ __global__ void __launch_bounds__(TPB) active_fill_kernel(DevVecs v, const int32
   for (int t = threadIdx.x; t < count; t += TPB) active[base + t] = first + t;
 }
 
+__host__ __device__ int select_form_of(long long active, long long total, double fraction, int few) {
+  if (few > 0 && active <= few) return 2;
+  return (double)active < fraction * (double)total ? 1 : 0;
+}
+
+int select_form(long long active, long long total, double fraction, int few) {
+  return select_form_of(active, total, fraction, few);
+}
+
 __global__ void select_kernel(const int32_t* nact_r, int nslots_r, const int32_t* nact_c,
-                              int nslots_c, unsigned long long handle, double fraction) {
+                              int nslots_c, unsigned long long handle, double fraction, int few) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const long long active = (long long)*nact_r + *nact_c, total = (long long)nslots_r + nslots_c;
   cudaGraphSetConditional((cudaGraphConditionalHandle)handle,
-                          (double)active < fraction * (double)total ? 1u : 0u);
+                          (unsigned)select_form_of(active, total, fraction, few));
 }
 
 cudaError_t launch_select(const DevPacked& csr, const DevPacked& csc, unsigned long long handle,
-                          double fraction, cudaStream_t s) {
+                          double fraction, int few, cudaStream_t s) {
   select_kernel<<<1, 32, 0, s>>>(csr.nactive, csr.nslots, csc.nactive, csc.nslots, handle,
-                                 fraction);
+                                 fraction, few);
   return cudaGetLastError();
 }
 

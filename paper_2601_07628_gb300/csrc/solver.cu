@@ -68,6 +68,7 @@ std::map<std::string, Param> default_params() {
       {"pock_chambolle", {1, 0, 1, true}},
       {"list_fraction", {0.5, 0.0, 2.0, false}},
       {"list_warps_per_sm", {0, 0, 64, true}},
+      {"list_few_slots", {256, 0, 1 << 20, true}},
       {"cta_slots_primal", {4, 2, 8, true}},
       {"cta_slots_dual", {4, 2, 8, true}},
       {"fused_body", {1, 0, 1, true}},
@@ -518,13 +519,15 @@ int build_graph(dpdlp* h, int K) {
     const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &captured);
     if (e == cudaSuccess) e = e2;
   } else {
-    // a batch: a select kernel sets the IF condition from the active-slot counts, then the
-    // body's iterations walk the lists (IF) or launch over every slot (ELSE), then the check
+    // a batch: a select kernel sets a SWITCH condition from the active-slot counts, then the
+    // body's iterations launch over every slot (0), walk the lists (1) or walk them with small
+    // grids when few slots are left (2), then the check
     cudaGraphConditionalHandle sel;
     CK(cudaGraphConditionalHandleCreate(&sel, body, 0, 0));
     e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, mode);
     if (e == cudaSuccess)
-      e = launch_select(h->csr, h->csc, (unsigned long long)sel, h->P("list_fraction"), h->cap_stream);
+      e = launch_select(h->csr, h->csc, (unsigned long long)sel, h->P("list_fraction"),
+                        (int)h->P("list_few_slots"), h->cap_stream);
     cudaGraph_t captured = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &captured);
     if (e == cudaSuccess) e = e2;
@@ -535,11 +538,12 @@ int build_graph(dpdlp* h, int K) {
       cudaGraphNodeParams ip{};
       ip.type = cudaGraphNodeTypeConditional;
       ip.conditional.handle = sel;
-      ip.conditional.type = cudaGraphCondTypeIf;
-      ip.conditional.size = 2;
+      ip.conditional.type = cudaGraphCondTypeSwitch;
+      ip.conditional.size = 3;
       CK(cudaGraphAddNode(&if_node, body, &sel_node, nullptr, 1, &ip));
-      e = capture_iters(ip.conditional.phGraph_out[0], nullptr, 0, 1);
-      if (e == cudaSuccess) e = capture_iters(ip.conditional.phGraph_out[1], nullptr, 0, 0);
+      e = capture_iters(ip.conditional.phGraph_out[0], nullptr, 0, 0);
+      if (e == cudaSuccess) e = capture_iters(ip.conditional.phGraph_out[1], nullptr, 0, 1);
+      if (e == cudaSuccess) e = capture_iters(ip.conditional.phGraph_out[2], nullptr, 0, 2);
     }
     if (e == cudaSuccess) {
       e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, &if_node, nullptr, 1, mode);
@@ -566,10 +570,8 @@ int run_host_loop(dpdlp* h) {
       CK(cudaMemcpyAsync(&na[0], h->csr.nactive, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
       CK(cudaMemcpyAsync(&na[1], h->csc.nactive, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
       CK(cudaStreamSynchronize(h->stream));
-      list = (double)(na[0] + na[1]) <
-                     h->P("list_fraction") * (double)((long long)h->csr.nslots + h->csc.nslots)
-                 ? 1
-                 : 0;
+      list = select_form(na[0] + na[1], (long long)h->csr.nslots + h->csc.nslots,
+                         h->P("list_fraction"), (int)h->P("list_few_slots"));
     }
     if (use_fused(h)) {
       CK(launch_body_fused(h->csc, h->csr, h->v, h->d_sc, K,
@@ -655,7 +657,7 @@ int dpdlp_set_param(dpdlp_t* h, const char* key, double v) {
     return fail(h, DPDLP_ERR_INVALID, k + " must be 2, 4 or 8");
   if ((k == "check_every" || k == "cta_slots_primal" || k == "cta_slots_dual" ||
        k == "fused_body" || k == "fused_max_slots" || k == "fused_cluster" || k == "pdl" ||
-       k == "list_fraction" ||
+       k == "list_fraction" || k == "list_few_slots" ||
        k == "list_warps_per_sm") && v != p.value)
     free_graph(h);  // the captured graph holds the launch shapes
   if (std::string(key) == "eta_safety" || std::string(key) == "power_iters" ||
@@ -665,6 +667,7 @@ int dpdlp_set_param(dpdlp_t* h, const char* key, double v) {
   h->csc.cta_slots = (int)h->P("cta_slots_primal");
   h->csr.cta_slots = (int)h->P("cta_slots_dual");
   h->csc.list_warps_per_sm = h->csr.list_warps_per_sm = (int)h->P("list_warps_per_sm");
+  h->csc.list_few_slots = h->csr.list_few_slots = (int)h->P("list_few_slots");
   return 0;
 }
 
@@ -815,6 +818,7 @@ int load_impl(dpdlp* h, int32_t count, const int32_t* row_off, const int32_t* co
   h->csc.cta_slots = (int)h->P("cta_slots_primal");
   h->csr.cta_slots = (int)h->P("cta_slots_dual");
   h->csc.list_warps_per_sm = h->csr.list_warps_per_sm = (int)h->P("list_warps_per_sm");
+  h->csc.list_few_slots = h->csr.list_few_slots = (int)h->P("list_few_slots");
   DevVecs& v = h->v;
   v.n = n;
   v.m = m;
