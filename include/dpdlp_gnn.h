@@ -83,6 +83,17 @@ int dpdlp_gnn_backward(dpdlp_gnn_t* g, const float* tx, const float* ty, double*
 int dpdlp_gnn_adam(dpdlp_gnn_t* g, double lr, double beta1, double beta2, double eps,
                    int64_t step);
 
+/* One whole training step on one instance: set the features fv[n][F], fc[m][F], forward pass,
+ * loss and gradient against the targets tx[n], ty[m], one Adam step -- the same kernels in the
+ * same order as dpdlp_gnn_set_features, dpdlp_gnn_forward, dpdlp_gnn_backward and
+ * dpdlp_gnn_adam, so the parameters come out bitwise the same -- as one replay of a CUDA graph
+ * captured at the first call after dpdlp_gnn_set_graph (arrays host or device per the pointer
+ * mode).  *loss (may be NULL: then the call only enqueues the step and returns without waiting
+ * for it) receives the step's loss.  Errors as the individual calls. */
+int dpdlp_gnn_train_step(dpdlp_gnn_t* g, const float* fv, const float* fc, const float* tx,
+                         const float* ty, double lr, double beta1, double beta2, double eps,
+                         int64_t step, double* loss);
+
 #ifdef __cplusplus
 }
 #endif

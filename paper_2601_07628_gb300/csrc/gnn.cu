@@ -77,19 +77,33 @@ __device__ __forceinline__ float2 spmm_range(int64_t k0, int64_t k1, const int* 
                                              const float* __restrict__ val,
                                              const float* __restrict__ in, int lane) {
   float2 acc = make_float2(0.f, 0.f);
+  int jn[SPMM_BATCH];
+  float an[SPMM_BATCH];
+#pragma unroll
+  for (int u = 0; u < SPMM_BATCH; ++u) {
+    jn[u] = k0 + u < k1 ? idx[k0 + u] : -1;
+    an[u] = k0 + u < k1 ? val[k0 + u] : 0.f;
+  }
   for (int64_t k = k0; k < k1; k += SPMM_BATCH) {
     int j[SPMM_BATCH];
     float a[SPMM_BATCH];
     float2 h[SPMM_BATCH];
 #pragma unroll
     for (int u = 0; u < SPMM_BATCH; ++u) {
-      j[u] = k + u < k1 ? idx[k + u] : -1;
-      a[u] = k + u < k1 ? val[k + u] : 0.f;
+      j[u] = jn[u];
+      a[u] = an[u];
     }
 #pragma unroll
     for (int u = 0; u < SPMM_BATCH; ++u)
       h[u] = j[u] >= 0 ? reinterpret_cast<const float2*>(in + (size_t)j[u] * H)[lane]
                        : make_float2(0.f, 0.f);
+    // the next batch's indices and values load while these gathers are in flight
+    const int64_t kn = k + SPMM_BATCH;
+#pragma unroll
+    for (int u = 0; u < SPMM_BATCH; ++u) {
+      jn[u] = kn + u < k1 ? idx[kn + u] : -1;
+      an[u] = kn + u < k1 ? val[kn + u] : 0.f;
+    }
 #pragma unroll
     for (int u = 0; u < SPMM_BATCH; ++u) {
       if (j[u] < 0) break;
@@ -285,6 +299,10 @@ __global__ void __launch_bounds__(TPB) linear_kernel(int N, const float* __restr
 // (a register holds two BF16, the lower column / row index in the low half).
 constexpr int MMA_WARPS = 8;                     // warps per block, 16 rows each
 constexpr int MMA_ROWS = MMA_WARPS * 16;         // rows per block of the dense kernels
+// Resident blocks per SM of the persistent dense kernels: they are bound by load latency
+// (ncu: long-scoreboard stalls, DRAM 17-20 % busy at two blocks per SM), so the register
+// budget is set for three.
+constexpr int MMA_BLOCKS_PER_SM = 3;
 constexpr int WPAD = H + 8;                      // shared row stride (BF16): conflict-free fragments
 
 __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
@@ -308,15 +326,30 @@ __device__ __forceinline__ void split2(float2 v, uint32_t& hi, uint32_t& lo) {
   lo = pack_bf16(__floats2bfloat162_rn(v.x - hf.x, v.y - hf.y));
 }
 
-// Stage W[H][H] (BF16) as S[n][k] = W[n][k] (transpose = false) or W[k][n] (true).
+// Stage W[H][H] (BF16) as S[n][k] = W[n][k] (transpose = false) or W[k][n] (true), eight
+// weights per 16-byte load, every thread's loads issued before its stores (W is 16-byte
+// aligned: each weight block of the parameter vector starts at a multiple of 8 entries).
 __device__ __forceinline__ void stage_w_bf16(__nv_bfloat16 (*S)[WPAD], const __nv_bfloat16* W,
                                              bool transpose) {
-  for (int e = threadIdx.x; e < H * H; e += MMA_WARPS * 32) {
-    const int r = e / H, c = e % H;
-    if (transpose) S[c][r] = W[e];
-    else S[r][c] = W[e];
+  constexpr int V = H * H / 8, PER = V / (MMA_WARPS * 32);  // 512 vectors, 2 per thread
+  const uint4* W4 = reinterpret_cast<const uint4*>(W);
+  uint4 v[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) v[u] = __ldg(W4 + threadIdx.x + u * MMA_WARPS * 32);
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int q = threadIdx.x + u * MMA_WARPS * 32, r = (8 * q) / H, c = (8 * q) % H;
+    if (!transpose) {
+      *reinterpret_cast<uint4*>(&S[r][c]) = v[u];
+    } else {
+      const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v[u]);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) S[c + j][r] = e[j];
+    }
   }
 }
+static_assert((H * H / 8) % (MMA_WARPS * 32) == 0, "weight staging: whole vectors per thread");
+static_assert((WPAD * 2) % 16 == 0, "weight staging: 16-byte aligned shared rows");
 
 // B fragments of n-tile j, k-step kk from S[n][k]
 __device__ __forceinline__ void b_frag(const __nv_bfloat16 (*S)[WPAD], int j, int kk, int g,
@@ -339,7 +372,7 @@ __device__ __forceinline__ void a_frag_load(const float* X, int r0, int N, int k
 
 // out = relu(X1 W1^T + X2 W2^T + b) for X1, X2 [N][H], W1, W2 [H][H]: each warp one 16-row
 // tile, all 64 output columns (8 n-tiles), both products into the same accumulators.
-__global__ void __launch_bounds__(MMA_WARPS * 32) linear_mma_kernel(
+__global__ void __launch_bounds__(MMA_WARPS * 32, MMA_BLOCKS_PER_SM) linear_mma_kernel(
     int N, const float* __restrict__ X1, const __nv_bfloat16* __restrict__ W1,
     const float* __restrict__ X2, const __nv_bfloat16* __restrict__ W2,
     const float* __restrict__ b, float* out) {
@@ -398,7 +431,7 @@ __global__ void __launch_bounds__(MMA_WARPS * 32) linear_mma_kernel(
 
 // Backward of out = relu(X1 W1^T + X2 W2^T + b): dZ = dOut * [out > 0] (stored), then
 // dX1 = dZ W1 and dX2 = dZ W2 ([N][H] each) on the tensor cores.
-__global__ void __launch_bounds__(MMA_WARPS * 32) linear_bwd_mma_kernel(
+__global__ void __launch_bounds__(MMA_WARPS * 32, MMA_BLOCKS_PER_SM) linear_bwd_mma_kernel(
     int N, const float* __restrict__ dOut, const float* __restrict__ Hout,
     const __nv_bfloat16* __restrict__ W1, const __nv_bfloat16* __restrict__ W2, float* dZ,
     float* dX1, float* dX2) {
@@ -785,11 +818,14 @@ __global__ void __launch_bounds__(SP_THREADS) sum_parts_kernel(int G, const floa
   }
 }
 
+// Adam's step scalars [lr, beta1, beta2, eps, 1 - beta1^step, 1 - beta2^step] are read from
+// device memory, so a captured training step can be replayed with new ones.
+constexpr int ADAM_SCALARS = 6;
 __global__ void adam_kernel(int64_t P, float* theta, float* grad, float* m1, float* m2,
-                            float lr, float b1, float b2, float eps, float bc1, float bc2,
-                            __nv_bfloat16* wbf) {
+                            const float* __restrict__ sc, __nv_bfloat16* wbf) {
   const int64_t i = blockIdx.x * (int64_t)TPB + threadIdx.x;
   if (i >= P) return;
+  const float lr = sc[0], b1 = sc[1], b2 = sc[2], eps = sc[3], bc1 = sc[4], bc2 = sc[5];
   const float g = grad[i];
   const float a = b1 * m1[i] + (1.f - b1) * g;
   const float v = b2 * m2[i] + (1.f - b2) * g * g;
@@ -817,6 +853,10 @@ struct dpdlp_gnn {
   // ev_w* after the gradient pass that reads it (side stream)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_zv = nullptr, ev_zc = nullptr, ev_wv = nullptr, ev_wc = nullptr;
+  // a whole training step (forward, backward, Adam) captured once per graph and replayed
+  cudaGraphExec_t step_exec = nullptr;
+  float* adam_sc = nullptr;  // [ADAM_SCALARS] on the device
+  float adam_host[8] = {};
   std::string err;
   int ptr_dev = 0;
   int n = 0, m = 0;
@@ -872,6 +912,8 @@ int galloc(dpdlp_gnn* g, T** p, size_t count) {
 
 void free_graph_buffers(dpdlp_gnn* g) {
   if (g->stream) cudaStreamSynchronize(g->stream);
+  if (g->step_exec) cudaGraphExecDestroy(g->step_exec);
+  g->step_exec = nullptr;
   for (void* p : g->allocs) cudaFree(p);
   g->allocs.clear();
   g->graph = false;
@@ -879,10 +921,18 @@ void free_graph_buffers(dpdlp_gnn* g) {
 }
 
 int blocks_for_rows(int rows) { return (rows + TILE - 1) / TILE; }
-// persistent dense kernels: at most two blocks per SM, each looping over 128-row tiles
+// persistent dense kernels: at most MMA_BLOCKS_PER_SM blocks per SM, each looping over
+// 128-row tiles
 int mma_blocks(int rows) {
-  const int tiles = (rows + MMA_ROWS - 1) / MMA_ROWS;
-  return tiles < WG_BLOCKS ? (tiles > 0 ? tiles : 1) : WG_BLOCKS;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int tiles = (rows + MMA_ROWS - 1) / MMA_ROWS, most = MMA_BLOCKS_PER_SM * sms;
+  return tiles < most ? (tiles > 0 ? tiles : 1) : most;
 }
 int warp_blocks(int rows) { return (int)(((size_t)rows * 32 + TPB - 1) / TPB); }
 int wg_grid(int rows) {
@@ -937,6 +987,128 @@ int add_wgrad8(dpdlp_gnn* g, int N, const float* dZ, const float* X, int64_t off
   return 0;
 }
 
+// The forward pass's kernels on g->stream (no copies, no synchronization).
+int enqueue_forward(dpdlp_gnn* g) {
+  const int n = g->n, m = g->m;
+  cudaStream_t s = g->stream;
+  const float* th = g->theta;
+  const __nv_bfloat16* w = g->wbf;
+  if (n) linear_kernel<F, false><<<blocks_for_rows(n), TPB, 0, s>>>(n, g->Fv, w + LAY.Ev, nullptr, nullptr, th + LAY.ev, g->hv[0]);
+  if (m) linear_kernel<F, false><<<blocks_for_rows(m), TPB, 0, s>>>(m, g->Fc, w + LAY.Ec, nullptr, nullptr, th + LAY.ec, g->hc[0]);
+  for (int l = 0; l < L; ++l) {
+    if (m) {
+      spmm(g, false, g->a_R, g->hv[l], g->gc[l], 0);
+      linear_mma_kernel<<<mma_blocks(m), MMA_WARPS * 32, 0, s>>>(m, g->hc[l], w + LAY.Uc[l], g->gc[l], w + LAY.Vc[l], th + LAY.bc[l], g->hc[l + 1]);
+    }
+    if (n) {
+      spmm(g, true, g->t_C, g->hc[l + 1], g->gv[l], 0);
+      linear_mma_kernel<<<mma_blocks(n), MMA_WARPS * 32, 0, s>>>(n, g->hv[l], w + LAY.Uv[l], g->gv[l], w + LAY.Vv[l], th + LAY.bv[l], g->hv[l + 1]);
+    }
+  }
+  if (n) head_kernel<<<warp_blocks(n), TPB, 0, s>>>(n, g->hv[L], w + LAY.wx, th + LAY.bx, g->xhat);
+  if (m) head_kernel<<<warp_blocks(m), TPB, 0, s>>>(m, g->hc[L], w + LAY.wy, th + LAY.by, g->yhat);
+  GCK(cudaGetLastError());
+  return 0;
+}
+
+// The backward pass's kernels (targets already in g->tx, g->ty): the data-gradient chain on
+// g->stream, the weight gradients on g->side, joined back into g->stream at the end.
+int enqueue_backward(dpdlp_gnn* g) {
+  const int n = g->n, m = g->m;
+  cudaStream_t s = g->stream;
+  const __nv_bfloat16* w = g->wbf;
+  int cv = 0, cc = 0;  // dhv[cv], dhc[cc]: gradients of the current hv, hc (the heads write all rows)
+  const int gx = n ? warp_blocks(n) : 0, gy = m ? warp_blocks(m) : 0;
+  // The weight gradients run on g->side, in order (they share `partial`); before the main
+  // stream rewrites a dZ buffer it waits for the side pass that reads it.
+  cudaStream_t side = g->side;
+  GCK(cudaEventRecord(g->ev_zv, s));  // the side stream starts after the targets are in
+  GCK(cudaStreamWaitEvent(side, g->ev_zv, 0));
+  if (n) {
+    head_bwd_kernel<<<gx, TPB, 0, s>>>(n, g->xhat, g->tx, w + LAY.wx, g->dx, g->dhv[0], g->loss_part);
+    GCK(cudaEventRecord(g->ev_zv, s));
+    GCK(cudaStreamWaitEvent(side, g->ev_zv, 0));
+    const int G = wg_grid(n);
+    head_wgrad_kernel<<<G, TPB, 0, side>>>(n, g->dx, g->hv[L], g->partial);
+    reduce_partials_kernel<<<reduce_grid(H + 1), RP_E * RP_SLICES, 0, side>>>(G, H + 1, H + 1, g->partial, g->grad + LAY.wx);
+  }
+  if (m) {
+    head_bwd_kernel<<<gy, TPB, 0, s>>>(m, g->yhat, g->ty, w + LAY.wy, g->dy, g->dhc[0], g->loss_part + gx);
+    GCK(cudaEventRecord(g->ev_zc, s));
+    GCK(cudaStreamWaitEvent(side, g->ev_zc, 0));
+    const int G = wg_grid(m);
+    head_wgrad_kernel<<<G, TPB, 0, side>>>(m, g->dy, g->hc[L], g->partial);
+    reduce_partials_kernel<<<reduce_grid(H + 1), RP_E * RP_SLICES, 0, side>>>(G, H + 1, H + 1, g->partial, g->grad + LAY.wy);
+  }
+  GCK(cudaEventRecord(g->ev_wv, side));
+  GCK(cudaEventRecord(g->ev_wc, side));
+  sum_parts_kernel<<<1, SP_THREADS, 0, s>>>(gx + gy, g->loss_part, g->loss_d);
+  int rc;
+  for (int l = L - 1; l >= 0; --l) {
+    // variable update of round l: hv[l+1] = relu(hv[l] Uv^T + gv[l] Vv^T + bv), gv = C hc[l+1]
+    if (n) {
+      GCK(cudaStreamWaitEvent(s, g->ev_wv, 0));  // the previous pass over dzv is done
+      linear_bwd_mma_kernel<<<mma_blocks(n), MMA_WARPS * 32, 0, s>>>(n, g->dhv[cv], g->hv[l + 1], w + LAY.Uv[l], w + LAY.Vv[l], g->dzv, g->dhv[1 - cv], g->dgv);
+      GCK(cudaEventRecord(g->ev_zv, s));
+      GCK(cudaStreamWaitEvent(side, g->ev_zv, 0));
+      if ((rc = add_wgrad2(g, n, g->dzv, g->hv[l], g->gv[l], LAY.Uv[l]))) return rc;
+      GCK(cudaEventRecord(g->ev_wv, side));
+      if (m) spmm(g, false, g->a_Ct, g->dgv, g->dhc[cc], 1);
+      cv = 1 - cv;
+    }
+    // constraint update of round l: hc[l+1] = relu(hc[l] Uc^T + gc[l] Vc^T + bc), gc = R hv[l]
+    if (m) {
+      GCK(cudaStreamWaitEvent(s, g->ev_wc, 0));  // the previous pass over dzc is done
+      linear_bwd_mma_kernel<<<mma_blocks(m), MMA_WARPS * 32, 0, s>>>(m, g->dhc[cc], g->hc[l + 1], w + LAY.Uc[l], w + LAY.Vc[l], g->dzc, g->dhc[1 - cc], g->dgc);
+      GCK(cudaEventRecord(g->ev_zc, s));
+      GCK(cudaStreamWaitEvent(side, g->ev_zc, 0));
+      if ((rc = add_wgrad2(g, m, g->dzc, g->hc[l], g->gc[l], LAY.Uc[l]))) return rc;
+      GCK(cudaEventRecord(g->ev_wc, side));
+      if (n) spmm(g, true, g->t_Rt, g->dgc, g->dhv[cv], 1);
+      cc = 1 - cc;
+    }
+  }
+  if (n) {
+    GCK(cudaStreamWaitEvent(s, g->ev_wv, 0));
+    linear_bwd_mma_kernel<<<mma_blocks(n), MMA_WARPS * 32, 0, s>>>(n, g->dhv[cv], g->hv[0], nullptr, nullptr, g->dzv, nullptr, nullptr);
+    GCK(cudaEventRecord(g->ev_zv, s));
+    GCK(cudaStreamWaitEvent(side, g->ev_zv, 0));
+    if ((rc = add_wgrad8(g, n, g->dzv, g->Fv, LAY.Ev))) return rc;
+  }
+  if (m) {
+    GCK(cudaStreamWaitEvent(s, g->ev_wc, 0));
+    linear_bwd_mma_kernel<<<mma_blocks(m), MMA_WARPS * 32, 0, s>>>(m, g->dhc[cc], g->hc[0], nullptr, nullptr, g->dzc, nullptr, nullptr);
+    GCK(cudaEventRecord(g->ev_zc, s));
+    GCK(cudaStreamWaitEvent(side, g->ev_zc, 0));
+    if ((rc = add_wgrad8(g, m, g->dzc, g->Fc, LAY.Ec))) return rc;
+  }
+  GCK(cudaEventRecord(g->ev_wv, side));  // every gradient is in before the backward returns
+  GCK(cudaStreamWaitEvent(s, g->ev_wv, 0));
+  GCK(cudaGetLastError());
+  return 0;
+}
+
+int enqueue_adam(dpdlp_gnn* g) {
+  const int64_t P = LAY.total;
+  adam_kernel<<<(unsigned)((P + TPB - 1) / TPB), TPB, 0, g->stream>>>(P, g->theta, g->grad, g->m1,
+                                                                      g->m2, g->adam_sc, g->wbf);
+  GCK(cudaGetLastError());
+  return 0;
+}
+
+// Adam's step scalars into the device buffer the adam kernel reads (stream-ordered).
+int set_adam_scalars(dpdlp_gnn* g, double lr, double beta1, double beta2, double eps, int64_t step) {
+  float* h = g->adam_host;
+  h[0] = (float)lr;
+  h[1] = (float)beta1;
+  h[2] = (float)beta2;
+  h[3] = (float)eps;
+  h[4] = (float)(1.0 - std::pow(beta1, (double)step));
+  h[5] = (float)(1.0 - std::pow(beta2, (double)step));
+  GCK(cudaMemcpyAsync(g->adam_sc, h, ADAM_SCALARS * sizeof(float), cudaMemcpyHostToDevice, g->stream));
+  return 0;
+}
+
 }  // namespace
 
 // ============================================================================ C ABI
@@ -950,6 +1122,8 @@ int dpdlp_gnn_create(dpdlp_gnn_t** out, int device) {
   int count = 0;
   if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
     return DPDLP_ERR_INVALID;
+  for (int l = 0; l < L; ++l)  // the dense kernels stage weights with 16-byte loads
+    if (LAY.Uc[l] % 8 || LAY.Vc[l] % 8 || LAY.Uv[l] % 8 || LAY.Vv[l] % 8) return DPDLP_ERR_INVALID;
   dpdlp_gnn* g = new (std::nothrow) dpdlp_gnn();
   if (!g) return DPDLP_ERR_OOM;
   g->device = device;
@@ -967,7 +1141,8 @@ int dpdlp_gnn_create(dpdlp_gnn_t** out, int device) {
       cudaMalloc(&g->m1, P * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&g->m2, P * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&g->wbf, P * sizeof(__nv_bfloat16)) != cudaSuccess ||
-      cudaMalloc(&g->partial, part * sizeof(float)) != cudaSuccess) {
+      cudaMalloc(&g->partial, part * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&g->adam_sc, ADAM_SCALARS * sizeof(float)) != cudaSuccess) {
     dpdlp_gnn_destroy(g);
     return DPDLP_ERR_CUDA;
   }
@@ -988,7 +1163,7 @@ void dpdlp_gnn_destroy(dpdlp_gnn_t* g) {
   if (!g) return;
   cudaSetDevice(g->device);
   free_graph_buffers(g);
-  void* ps[] = {g->theta, g->grad, g->m1, g->m2, g->wbf, g->partial};
+  void* ps[] = {g->theta, g->grad, g->m1, g->m2, g->wbf, g->partial, g->adam_sc};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (g->side) cudaStreamSynchronize(g->side);
@@ -1155,25 +1330,10 @@ int dpdlp_gnn_forward(dpdlp_gnn_t* g, float* x_hat, float* y_hat) {
   if (!g) return DPDLP_ERR_INVALID;
   if (!g->graph) return gfail(g, DPDLP_ERR_NOT_LOADED, "no graph set");
   GCK(cudaSetDevice(g->device));
+  int rc;
+  if ((rc = enqueue_forward(g))) return rc;
   const int n = g->n, m = g->m;
   cudaStream_t s = g->stream;
-  const float* th = g->theta;
-  const __nv_bfloat16* w = g->wbf;
-  if (n) linear_kernel<F, false><<<blocks_for_rows(n), TPB, 0, s>>>(n, g->Fv, w + LAY.Ev, nullptr, nullptr, th + LAY.ev, g->hv[0]);
-  if (m) linear_kernel<F, false><<<blocks_for_rows(m), TPB, 0, s>>>(m, g->Fc, w + LAY.Ec, nullptr, nullptr, th + LAY.ec, g->hc[0]);
-  for (int l = 0; l < L; ++l) {
-    if (m) {
-      spmm(g, false, g->a_R, g->hv[l], g->gc[l], 0);
-      linear_mma_kernel<<<mma_blocks(m), MMA_WARPS * 32, 0, s>>>(m, g->hc[l], w + LAY.Uc[l], g->gc[l], w + LAY.Vc[l], th + LAY.bc[l], g->hc[l + 1]);
-    }
-    if (n) {
-      spmm(g, true, g->t_C, g->hc[l + 1], g->gv[l], 0);
-      linear_mma_kernel<<<mma_blocks(n), MMA_WARPS * 32, 0, s>>>(n, g->hv[l], w + LAY.Uv[l], g->gv[l], w + LAY.Vv[l], th + LAY.bv[l], g->hv[l + 1]);
-    }
-  }
-  if (n) head_kernel<<<warp_blocks(n), TPB, 0, s>>>(n, g->hv[L], w + LAY.wx, th + LAY.bx, g->xhat);
-  if (m) head_kernel<<<warp_blocks(m), TPB, 0, s>>>(m, g->hc[L], w + LAY.wy, th + LAY.by, g->yhat);
-  GCK(cudaGetLastError());
   if (x_hat && n) GCK(cudaMemcpyAsync(x_hat, g->xhat, n * sizeof(float), out_kind(g), s));
   if (y_hat && m) GCK(cudaMemcpyAsync(y_hat, g->yhat, m * sizeof(float), out_kind(g), s));
   GCK(cudaStreamSynchronize(s));
@@ -1187,77 +1347,10 @@ int dpdlp_gnn_backward(dpdlp_gnn_t* g, const float* tx, const float* ty, double*
   GCK(cudaSetDevice(g->device));
   const int n = g->n, m = g->m;
   cudaStream_t s = g->stream;
-  const __nv_bfloat16* w = g->wbf;
   if (n) GCK(cudaMemcpyAsync(g->tx, tx, n * sizeof(float), in_kind(g), s));
   if (m) GCK(cudaMemcpyAsync(g->ty, ty, m * sizeof(float), in_kind(g), s));
-  int cv = 0, cc = 0;  // dhv[cv], dhc[cc]: gradients of the current hv, hc (the heads write all rows)
-  const int gx = n ? warp_blocks(n) : 0, gy = m ? warp_blocks(m) : 0;
-  // The weight gradients run on g->side, in order (they share `partial`); before the main
-  // stream rewrites a dZ buffer it waits for the side pass that reads it.
-  cudaStream_t side = g->side;
-  GCK(cudaEventRecord(g->ev_zv, s));  // the side stream starts after the targets are in
-  GCK(cudaStreamWaitEvent(side, g->ev_zv, 0));
-  if (n) {
-    head_bwd_kernel<<<gx, TPB, 0, s>>>(n, g->xhat, g->tx, w + LAY.wx, g->dx, g->dhv[0], g->loss_part);
-    GCK(cudaEventRecord(g->ev_zv, s));
-    GCK(cudaStreamWaitEvent(side, g->ev_zv, 0));
-    const int G = wg_grid(n);
-    head_wgrad_kernel<<<G, TPB, 0, side>>>(n, g->dx, g->hv[L], g->partial);
-    reduce_partials_kernel<<<reduce_grid(H + 1), RP_E * RP_SLICES, 0, side>>>(G, H + 1, H + 1, g->partial, g->grad + LAY.wx);
-  }
-  if (m) {
-    head_bwd_kernel<<<gy, TPB, 0, s>>>(m, g->yhat, g->ty, w + LAY.wy, g->dy, g->dhc[0], g->loss_part + gx);
-    GCK(cudaEventRecord(g->ev_zc, s));
-    GCK(cudaStreamWaitEvent(side, g->ev_zc, 0));
-    const int G = wg_grid(m);
-    head_wgrad_kernel<<<G, TPB, 0, side>>>(m, g->dy, g->hc[L], g->partial);
-    reduce_partials_kernel<<<reduce_grid(H + 1), RP_E * RP_SLICES, 0, side>>>(G, H + 1, H + 1, g->partial, g->grad + LAY.wy);
-  }
-  GCK(cudaEventRecord(g->ev_wv, side));
-  GCK(cudaEventRecord(g->ev_wc, side));
-  sum_parts_kernel<<<1, SP_THREADS, 0, s>>>(gx + gy, g->loss_part, g->loss_d);
   int rc;
-  for (int l = L - 1; l >= 0; --l) {
-    // variable update of round l: hv[l+1] = relu(hv[l] Uv^T + gv[l] Vv^T + bv), gv = C hc[l+1]
-    if (n) {
-      GCK(cudaStreamWaitEvent(s, g->ev_wv, 0));  // the previous pass over dzv is done
-      linear_bwd_mma_kernel<<<mma_blocks(n), MMA_WARPS * 32, 0, s>>>(n, g->dhv[cv], g->hv[l + 1], w + LAY.Uv[l], w + LAY.Vv[l], g->dzv, g->dhv[1 - cv], g->dgv);
-      GCK(cudaEventRecord(g->ev_zv, s));
-      GCK(cudaStreamWaitEvent(side, g->ev_zv, 0));
-      if ((rc = add_wgrad2(g, n, g->dzv, g->hv[l], g->gv[l], LAY.Uv[l]))) return rc;
-      GCK(cudaEventRecord(g->ev_wv, side));
-      if (m) spmm(g, false, g->a_Ct, g->dgv, g->dhc[cc], 1);
-      cv = 1 - cv;
-    }
-    // constraint update of round l: hc[l+1] = relu(hc[l] Uc^T + gc[l] Vc^T + bc), gc = R hv[l]
-    if (m) {
-      GCK(cudaStreamWaitEvent(s, g->ev_wc, 0));  // the previous pass over dzc is done
-      linear_bwd_mma_kernel<<<mma_blocks(m), MMA_WARPS * 32, 0, s>>>(m, g->dhc[cc], g->hc[l + 1], w + LAY.Uc[l], w + LAY.Vc[l], g->dzc, g->dhc[1 - cc], g->dgc);
-      GCK(cudaEventRecord(g->ev_zc, s));
-      GCK(cudaStreamWaitEvent(side, g->ev_zc, 0));
-      if ((rc = add_wgrad2(g, m, g->dzc, g->hc[l], g->gc[l], LAY.Uc[l]))) return rc;
-      GCK(cudaEventRecord(g->ev_wc, side));
-      if (n) spmm(g, true, g->t_Rt, g->dgc, g->dhv[cv], 1);
-      cc = 1 - cc;
-    }
-  }
-  if (n) {
-    GCK(cudaStreamWaitEvent(s, g->ev_wv, 0));
-    linear_bwd_mma_kernel<<<mma_blocks(n), MMA_WARPS * 32, 0, s>>>(n, g->dhv[cv], g->hv[0], nullptr, nullptr, g->dzv, nullptr, nullptr);
-    GCK(cudaEventRecord(g->ev_zv, s));
-    GCK(cudaStreamWaitEvent(side, g->ev_zv, 0));
-    if ((rc = add_wgrad8(g, n, g->dzv, g->Fv, LAY.Ev))) return rc;
-  }
-  if (m) {
-    GCK(cudaStreamWaitEvent(s, g->ev_wc, 0));
-    linear_bwd_mma_kernel<<<mma_blocks(m), MMA_WARPS * 32, 0, s>>>(m, g->dhc[cc], g->hc[0], nullptr, nullptr, g->dzc, nullptr, nullptr);
-    GCK(cudaEventRecord(g->ev_zc, s));
-    GCK(cudaStreamWaitEvent(side, g->ev_zc, 0));
-    if ((rc = add_wgrad8(g, m, g->dzc, g->Fc, LAY.Ec))) return rc;
-  }
-  GCK(cudaEventRecord(g->ev_wv, side));  // every gradient is in before the backward returns
-  GCK(cudaStreamWaitEvent(s, g->ev_wv, 0));
-  GCK(cudaGetLastError());
+  if ((rc = enqueue_backward(g))) return rc;
   double lv = 0.0;
   GCK(cudaMemcpyAsync(&lv, g->loss_d, sizeof(double), cudaMemcpyDeviceToHost, s));
   GCK(cudaStreamSynchronize(s));
@@ -1271,14 +1364,54 @@ int dpdlp_gnn_adam(dpdlp_gnn_t* g, double lr, double beta1, double beta2, double
       !(eps > 0))
     return gfail(g, DPDLP_ERR_INVALID, "adam: invalid hyper-parameters");
   GCK(cudaSetDevice(g->device));
-  const int64_t P = LAY.total;
-  const float bc1 = (float)(1.0 - std::pow(beta1, (double)step));
-  const float bc2 = (float)(1.0 - std::pow(beta2, (double)step));
-  adam_kernel<<<(unsigned)((P + TPB - 1) / TPB), TPB, 0, g->stream>>>(
-      P, g->theta, g->grad, g->m1, g->m2, (float)lr, (float)beta1, (float)beta2, (float)eps, bc1,
-      bc2, g->wbf);
-  GCK(cudaGetLastError());
+  int rc;
+  if ((rc = set_adam_scalars(g, lr, beta1, beta2, eps, step)) || (rc = enqueue_adam(g))) return rc;
   GCK(cudaStreamSynchronize(g->stream));
+  return 0;
+}
+
+int dpdlp_gnn_train_step(dpdlp_gnn_t* g, const float* fv, const float* fc, const float* tx,
+                         const float* ty, double lr, double beta1, double beta2, double eps,
+                         int64_t step, double* loss) {
+  if (!g || step < 1 || !(lr >= 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) ||
+      !(eps > 0))
+    return gfail(g, DPDLP_ERR_INVALID, "train_step: invalid hyper-parameters");
+  if (!g->graph) return gfail(g, DPDLP_ERR_NOT_LOADED, "no graph set");
+  const int n = g->n, m = g->m;
+  if ((n && (!fv || !tx)) || (m && (!fc || !ty)))
+    return gfail(g, DPDLP_ERR_INVALID, "train_step: NULL features or targets");
+  GCK(cudaSetDevice(g->device));
+  cudaStream_t s = g->stream;
+  if (n) GCK(cudaMemcpyAsync(g->Fv, fv, (size_t)n * F * sizeof(float), in_kind(g), s));
+  if (m) GCK(cudaMemcpyAsync(g->Fc, fc, (size_t)m * F * sizeof(float), in_kind(g), s));
+  if (n) GCK(cudaMemcpyAsync(g->tx, tx, n * sizeof(float), in_kind(g), s));
+  if (m) GCK(cudaMemcpyAsync(g->ty, ty, m * sizeof(float), in_kind(g), s));
+  int rc;
+  if ((rc = set_adam_scalars(g, lr, beta1, beta2, eps, step))) return rc;
+  if (!g->step_exec) {  // capture forward, backward (both streams) and Adam once per graph
+    cudaGraph_t graph = nullptr;
+    GCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    rc = enqueue_forward(g);
+    if (!rc) rc = enqueue_backward(g);
+    if (!rc) rc = enqueue_adam(g);
+    const cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    GCK(e);
+    const cudaError_t ei = cudaGraphInstantiate(&g->step_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    GCK(ei);
+  }
+  GCK(cudaGraphLaunch(g->step_exec, s));
+  g->fwd_done = true;
+  if (loss) {
+    double lv = 0.0;
+    GCK(cudaMemcpyAsync(&lv, g->loss_d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    GCK(cudaStreamSynchronize(s));
+    *loss = lv;
+  }
   return 0;
 }
 

@@ -31,6 +31,9 @@ EXPORTS = {
     "dpdlp_gnn_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "dpdlp_gnn_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "dpdlp_gnn_adam": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int64]),
+    "dpdlp_gnn_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_double, C.c_double, C.c_double, C.c_double, C.c_int64,
+                                       C.POINTER(C.c_double)]),
 }
 
 _declared = set()
@@ -144,6 +147,22 @@ class Network:
     def adam(self, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
         self._check(self.lib.dpdlp_gnn_adam(self.h, float(lr), float(beta1), float(beta2), float(eps), int(step)))
 
+    def train_step(self, fv, fc, tx, ty, lr, step, beta1=0.9, beta2=0.999, eps=1e-8,
+                   want_loss=True):
+        """Features, forward, backward and one Adam step as one replay of a captured CUDA
+        graph (the same kernels in the same order as the separate calls).  Returns the
+        step's loss, or None without waiting for the step when ``want_loss`` is False."""
+        if not self.dev:
+            fv = np.ascontiguousarray(fv, np.float32)
+            fc = np.ascontiguousarray(fc, np.float32)
+            tx = np.ascontiguousarray(tx, np.float32)
+            ty = np.ascontiguousarray(ty, np.float32)
+        loss = C.c_double()
+        self._check(self.lib.dpdlp_gnn_train_step(
+            self.h, _ptr(fv), _ptr(fc), _ptr(tx), _ptr(ty), float(lr), float(beta1), float(beta2),
+            float(eps), int(step), C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
 
 # ---------------------------------------------------------------- features and scales
 @dataclass
@@ -226,11 +245,8 @@ def train(net: Network, data, epochs: int, lr: float = 1e-3, seed: int = 0, log=
         tot = 0.0
         for i in rng.permutation(len(data)):
             fv, fc, tx, ty = data[i]
-            net.set_features(fv, fc)
-            net.forward()
-            tot += net.backward(tx, ty)
             step += 1
-            net.adam(lr, step)
+            tot += net.train_step(fv, fc, tx, ty, lr, step)
         hist.append(tot / len(data))
         if log:
             log(ep, hist[-1])

@@ -107,6 +107,43 @@ def test_backward_is_deterministic_and_accumulates(mods):
     net.close()
 
 
+def test_captured_train_step_equals_separate_calls(mods):
+    """dpdlp_gnn_train_step replays a captured graph of the same kernels in the same order as
+    set_features + forward + backward + adam: five steps on two alternating instances give
+    bitwise the same parameters and losses (and a new graph re-captures the step)."""
+    dpdlp, gnn = mods
+    cases = [random_case(5), random_case(6)]
+    A = cases[0][0]
+    nets = []
+    for _ in range(2):
+        net = gnn.Network()
+        net.set_params(theta_for(5, gnn))
+        net.set_graph(A.shape[1], A.shape[0], A.indptr, A.indices, A.data)
+        nets.append(net)
+    la, lb = [], []
+    for step in range(1, 6):
+        _, Fv, Fc, tx, ty = cases[step % 2]
+        la.append(nets[0].train_step(Fv, Fc, tx, ty, 1e-3, step))
+        nets[1].set_features(Fv, Fc)
+        nets[1].forward()
+        lb.append(nets[1].backward(tx, ty))
+        nets[1].adam(1e-3, step)
+    assert la == lb
+    assert np.array_equal(nets[0].params(), nets[1].params())
+    B = cases[1][0]  # another graph: the captured step is rebuilt for it
+    for net in nets:
+        net.set_graph(B.shape[1], B.shape[0], B.indptr, B.indices, B.data)
+    _, Fv, Fc, tx, ty = cases[1]
+    l0 = nets[0].train_step(Fv, Fc, tx, ty, 1e-3, 6)
+    nets[1].set_features(Fv, Fc)
+    nets[1].forward()
+    l1 = nets[1].backward(tx, ty)
+    nets[1].adam(1e-3, 6)
+    assert l0 == l1 and np.array_equal(nets[0].params(), nets[1].params())
+    for net in nets:
+        net.close()
+
+
 def test_invalid_inputs(mods):
     dpdlp, gnn = mods
     net = gnn.Network()
