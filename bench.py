@@ -676,6 +676,8 @@ def main():
                 "traffic": traffic, "kernel": dom, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6800 GB/s",
                 "bytes_per_launch": kb[dom], "ms_per_launch": kt[dom]}
+    # (launches timed back to back as the solve runs them: programmatic dependents, each
+    # launch's prologue overlapping the previous one's tail)
     kernels = {k: {"ms": kt[k], "GB/s": kb[k] / (kt[k] * 1e-3) / 1e9,
                    "hbm_frac": kb[k] / (kt[k] * 1e-3) / 1e9 / peak,
                    "fp64_Gops": fp64_ops[k] / (kt[k] * 1e-3) / 1e9,
@@ -711,6 +713,8 @@ def main():
 
     # ---- the same steps without programmatic dependent launch between the iteration kernels
     s.set_param("pdl", 0)
+    for k in kt:  # launch times without the overlap of consecutive launches
+        kernels[k]["ms_without_pdl"] = s.time_kernel(k, 50)
     Tp = T
     for _ in range(2):
         Tp += K_CHECK

@@ -225,6 +225,8 @@ struct StoreEpi1 {
   }
   struct Row {};
   __device__ Row load_row(int) const { return Row{}; }
+  __device__ Row load_row_fixed(int) const { return Row{}; }
+  __device__ void load_row_moving(int, Row&) const {}
   __device__ void apply_loaded(int r, const double* v, const Row&) { apply_direct(r, v); }
 };
 struct StoreEpi2 {
@@ -251,6 +253,8 @@ struct StoreEpi2 {
   }
   struct Row {};
   __device__ Row load_row(int) const { return Row{}; }
+  __device__ Row load_row_fixed(int) const { return Row{}; }
+  __device__ void load_row_moving(int, Row&) const {}
   __device__ void apply_loaded(int r, const double* v, const Row&) { apply_direct(r, v); }
 };
 
@@ -370,14 +374,22 @@ struct PrimalEpi {
     double a[5];
   };
   __device__ Row load_row(int j) const {
+    Row r = load_row_fixed(j);
+    load_row_moving(j, r);
+    return r;
+  }
+  // the inputs no kernel of a graph body writes (the anchor changes only at checks), and the
+  // one the iterations do (x)
+  __device__ Row load_row_fixed(int j) const {
     Row r;
     r.a[0] = ld_once(c + j);
     r.a[1] = ld_once(lv + j);
     r.a[2] = ld_once(uv + j);
-    r.a[3] = ld_once(x + j);
+    r.a[3] = 0.0;
     r.a[4] = need_anchor() ? ld_once(x0 + j) : 0.0;
     return r;
   }
+  __device__ void load_row_moving(int j, Row& r) const { r.a[3] = ld_once(x + j); }
   __device__ void apply_loaded(int j, const double* s, const Row& r) {
     step(j, s[0], r.a[0], r.a[1], r.a[2], r.a[3], r.a[4]);
   }
@@ -480,13 +492,19 @@ struct DualEpi {
     double a[4];
   };
   __device__ Row load_row(int i) const {
+    Row r = load_row_fixed(i);
+    load_row_moving(i, r);
+    return r;
+  }
+  __device__ Row load_row_fixed(int i) const {
     Row r;
     r.a[0] = ld_once(lo + i);
     r.a[1] = ld_once(hi + i);
-    r.a[2] = ld_once(y + i);
+    r.a[2] = 0.0;
     r.a[3] = need_anchor() ? ld_once(y0 + i) : 0.0;
     return r;
   }
+  __device__ void load_row_moving(int i, Row& r) const { r.a[2] = ld_once(y + i); }
   __device__ void apply_loaded(int i, const double* s, const Row& r) {
     step(i, s[0], r.a[0], r.a[1], r.a[2], r.a[3]);
   }
@@ -800,27 +818,43 @@ __global__ void __launch_bounds__(W * LANES, (DPDLP_PK_MIN_BLOCKS * PK_WARPS) / 
 // of the additions is that of the plain loop.
 // L2: read the sums from L2 (ld.global.cg), for sums another SM of the cluster wrote.
 constexpr int PIECE_BATCH = 8;
+// Piece ids of the batch starting at q (q, q + step, ...; -1 past q1).
+__device__ __forceinline__ void piece_ids(const DevPacked& M, int q, int q1, int step,
+                                          int (&pid)[PIECE_BATCH]) {
+#pragma unroll
+  for (int u = 0; u < PIECE_BATCH; ++u) {
+    const int qq = q + u * step;
+    pid[u] = qq < q1 ? M.long_piece[qq] : -1;
+  }
+}
+// The same sum with the first batch's ids already loaded (`first`, from piece_ids(q)).
 template <bool L2 = false>
-__device__ __forceinline__ double strided_piece_sum(const DevPacked& M, int k, int q, int q1,
-                                                    int step) {
+__device__ __forceinline__ double strided_piece_sum_from(const DevPacked& M, int k, int q, int q1,
+                                                         int step, const int (&first)[PIECE_BATCH]) {
   const double* ps = M.piece_sum + (size_t)k * M.npieces;
   double a = 0.0;
-  for (; q < q1; q += PIECE_BATCH * step) {
-    int pid[PIECE_BATCH];
-    double v[PIECE_BATCH];
+  int pid[PIECE_BATCH];
 #pragma unroll
-    for (int u = 0; u < PIECE_BATCH; ++u) {
-      const int qq = q + u * step;
-      pid[u] = qq < q1 ? M.long_piece[qq] : -1;
-    }
+  for (int u = 0; u < PIECE_BATCH; ++u) pid[u] = first[u];
+  for (; q < q1; q += PIECE_BATCH * step) {
+    double v[PIECE_BATCH];
 #pragma unroll
     for (int u = 0; u < PIECE_BATCH; ++u)
       v[u] = pid[u] >= 0 ? (L2 ? __ldcg(ps + pid[u]) : ps[pid[u]]) : 0.0;
+    const int qn = q + PIECE_BATCH * step;
+    if (qn < q1) piece_ids(M, qn, q1, step, pid);  // the next batch's ids during these loads
 #pragma unroll
     for (int u = 0; u < PIECE_BATCH; ++u)
-      if (pid[u] >= 0) a += v[u];
+      if (q + u * step < q1) a += v[u];  // the batch's pieces in order (pid is the next batch's)
   }
   return a;
+}
+template <bool L2 = false>
+__device__ __forceinline__ double strided_piece_sum(const DevPacked& M, int k, int q, int q1,
+                                                    int step) {
+  int first[PIECE_BATCH];
+  piece_ids(M, q, q1, step, first);
+  return strided_piece_sum_from<L2>(M, k, q, q1, step, first);
 }
 
 // Long rows: add each row's pieces, then its epilogue.  Rows come longest first: the first
@@ -831,21 +865,31 @@ __global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_i
   __shared__ double red[TPB / 32];
   Epi epi = epi_in;
   pdl_trigger();
-  pdl_wait();  // the pieces and scalars come from the kernels before
-  if (!epi.begin()) return;
+  // Before waiting for the kernel that wrote the pieces, load what no kernel of a graph body
+  // writes: the scalars and the anchor (checks only), the rows' indices, piece ranges, first
+  // piece ids and fixed step inputs.  The row's iterate (x or y, written by the previous
+  // iteration's pass, which with programmatic launches may still be running) and the piece
+  // sums load after the wait.
+  const bool go = epi.begin();  // uniform over the launch
   const int nb = M.nlong_block, nw = M.nlong_warp;
   const int wblocks = (nw + TPB / 32 - 1) / (TPB / 32);
   int b = blockIdx.x;
   double v[NV];
+  int first[PIECE_BATCH];
   if (b < nb) {
     const int i = b;
-    if (!epi.inst(M.long_inst[i])) return;  // uniform over the block
+    const bool act = go && epi.inst(M.long_inst[i]);  // uniform over the block
     const int row = M.long_row[i];
-    typename Epi::Row in{};
-    if (threadIdx.x == 0) in = epi.load_row(row);  // in flight during the sums
     const int q0 = M.long_ptr[i], q1 = M.long_ptr[i + 1];
+    piece_ids(M, q0 + threadIdx.x, q1, TPB, first);
+    typename Epi::Row in{};
+    if (act && threadIdx.x == 0) in = epi.load_row_fixed(row);
+    pdl_wait();  // the pieces come from the kernel before
+    if (!act) return;
+    if (threadIdx.x == 0) epi.load_row_moving(row, in);  // in flight during the sums
 #pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = block_sum(strided_piece_sum(M, k, q0 + threadIdx.x, q1, TPB), red);
+    for (int k = 0; k < NV; ++k)
+      v[k] = block_sum(strided_piece_sum_from(M, k, q0 + threadIdx.x, q1, TPB, first), red);
     if (threadIdx.x == 0) {
       epi.prepare(M.long_inst[i]);
       epi.apply_loaded(row, v, in);
@@ -856,15 +900,22 @@ __global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_i
   if (b < wblocks) {
     const int i = nb + b * (TPB / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (i >= nb + nw) return;
-    if (!epi.inst(M.long_inst[i])) return;  // uniform over the warp
+    if (i >= nb + nw) {
+      pdl_wait();
+      return;
+    }
+    const bool act = go && epi.inst(M.long_inst[i]);  // uniform over the warp
     const int row = M.long_row[i];
-    typename Epi::Row in{};
-    if (lane == 0) in = epi.load_row(row);
     const int q0 = M.long_ptr[i], q1 = M.long_ptr[i + 1];
+    piece_ids(M, q0 + lane, q1, LANES, first);
+    typename Epi::Row in{};
+    if (act && lane == 0) in = epi.load_row_fixed(row);
+    pdl_wait();
+    if (!act) return;
+    if (lane == 0) epi.load_row_moving(row, in);
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      double a = strided_piece_sum(M, k, q0 + lane, q1, LANES);
+      double a = strided_piece_sum_from(M, k, q0 + lane, q1, LANES, first);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
       v[k] = a;
@@ -877,13 +928,21 @@ __global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_i
   }
   b -= wblocks;
   const int i = nb + nw + b * TPB + threadIdx.x;
-  if (i >= M.nlong) return;
-  if (!epi.inst(M.long_inst[i])) return;
+  if (i >= M.nlong) {
+    pdl_wait();
+    return;
+  }
+  const bool act = go && epi.inst(M.long_inst[i]);
   const int row = M.long_row[i];
-  const typename Epi::Row in = epi.load_row(row);
   const int q0 = M.long_ptr[i], q1 = M.long_ptr[i + 1];
+  piece_ids(M, q0, q1, 1, first);
+  typename Epi::Row in{};
+  if (act) in = epi.load_row_fixed(row);
+  pdl_wait();
+  if (!act) return;
+  epi.load_row_moving(row, in);
 #pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = strided_piece_sum(M, k, q0, q1, 1);
+  for (int k = 0; k < NV; ++k) v[k] = strided_piece_sum_from(M, k, q0, q1, 1, first);
   epi.prepare(M.long_inst[i]);
   epi.apply_loaded(row, v, in);
 }

@@ -1307,7 +1307,8 @@ int dpdlp_time_kernel(dpdlp_t* h, const char* which, int32_t reps, double* avg_m
   bool primal = w == "primal";
   // batches also time the iteration kernels as the solve may run them: walking the
   // active-slot lists (*_list), and with every instance stopped (*_idle, *_list_idle)
-  IterPlan p{0, 1, 0, 0, 0};
+  // launched as the solve launches them (programmatic dependents when pdl is on)
+  IterPlan p{0, 1, 0, (int)h->P("pdl"), 0};
   const std::string side0 = w.substr(0, w.find('_'));
   const std::string rest = w.find('_') == std::string::npos ? "" : w.substr(w.find('_') + 1);
   if ((side0 == "primal" || side0 == "dual") &&
