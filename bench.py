@@ -684,14 +684,19 @@ def main():
                    "fp64_frac": fp64_ops[k] / (kt[k] * 1e-3) / 1e9 / fp64_peak}
                for k in kt}
     # ---- access ceilings of the packed layout: each kernel's loads without its arithmetic
-    # (gather: indices + random x[col] gathers; access: + values; stream: indices + values)
+    # (gather: indices + random x[col] gathers; access: + values; stream: indices + values;
+    # memory: access + the epilogue's row-vector loads and stores)
     stored = {"primal": info["nnz_padded_csc"], "dual": info["nnz_padded_csr"]}
     for k in kt:
-        pr = {mode: s.time_kernel(f"{mode}_{k}", 50) for mode in ("gather", "access", "stream")}
+        # the slot kernel alone (without the long-row pass), the part the probes mirror
+        kernels[k]["ms_slots_only"] = s.time_kernel(f"{k}_slots", 50)
+        pr = {mode: s.time_kernel(f"{mode}_{k}", 50)
+              for mode in ("gather", "access", "stream", "memory")}
         kernels[k]["ceilings"] = {
             mode: {"ms": t, "stored_entries": stored[k],
                    "G_entries_per_s": stored[k] / (t * 1e-3) / 1e9,
-                   "kernel_frac": t / kt[k]} for mode, t in pr.items()}
+                   "kernel_frac": t / kt[k], "slot_kernel_frac": t / kernels[k]["ms_slots_only"]}
+            for mode, t in pr.items()}
         kernels[k]["ceilings"]["stream"]["GB/s"] = 12 * stored[k] / (pr["stream"] * 1e-3) / 1e9
         kernels[k]["ceilings"]["gather"]["L2_sectors_per_s"] = stored[k] / (pr["gather"] * 1e-3)
     roofline["access_ceiling"] = {
@@ -700,7 +705,11 @@ def main():
         "ms_per_launch": kernels[dom]["ceilings"]["access"]["ms"],
         "kernel_frac": kernels[dom]["ceilings"]["access"]["kernel_frac"],
         "gather_only_ms": kernels[dom]["ceilings"]["gather"]["ms"],
-        "stream_only_ms": kernels[dom]["ceilings"]["stream"]["ms"]}
+        "stream_only_ms": kernels[dom]["ceilings"]["stream"]["ms"],
+        "with_row_vectors_ms": kernels[dom]["ceilings"]["memory"]["ms"],
+        "with_row_vectors_kernel_frac": kernels[dom]["ceilings"]["memory"]["kernel_frac"],
+        "slot_kernel_ms": kernels[dom]["ms_slots_only"],
+        "with_row_vectors_slot_kernel_frac": kernels[dom]["ceilings"]["memory"]["slot_kernel_frac"]}
 
     # ---- library reference point: cuSPARSE CSR SpMV (through torch) on the same matrix,
     # A x and A^T y in FP64, timed like the fused kernels (which do more: the product plus

@@ -307,9 +307,13 @@ int dpdlp_apply_AT(dpdlp_t* h, const double* y, double* out);
  * primal update, "dual": fused CSR SpMV + dual update) on the handle's stream with CUDA
  * events, on the current state (the state is left as it was).  *avg_ms = mean duration of
  * one launch.  Needs a solve or dpdlp_set_start beforehand.  Other names:
- *   "gather_primal", "access_primal", "stream_primal" (and _dual): access probes of the
- *   orientation's product -- its index stream and x[col] gathers; plus its value stream;
- *   its two streams alone -- without arithmetic (ceilings of the access pattern);
+ *   "primal_slots", "dual_slots": the same without the long-row pass (the slot kernel);
+ *   "gather_primal", "access_primal", "stream_primal", "memory_primal" (and _dual):
+ *   access probes of the orientation's product -- its index stream and x[col] gathers;
+ *   plus its value stream; its two streams alone; the product's loads plus the loads and
+ *   stores of the epilogue's row vectors (every access of the kernel's slots) -- without
+ *   arithmetic (ceilings of the access pattern), launched like the kernels (programmatic
+ *   dependents when the "pdl" parameter is on);
  *   "primal_list", "primal_idle", "primal_list_idle" (and dual_), batches only: the
  *   persistent kernel walking the list of every slot, a launch over every slot with all
  *   instances stopped, the list kernel over an empty list (costs the autotuner compares). */

@@ -228,6 +228,7 @@ struct IterPlan {
                       // (few slots active), 0 one launch over every slot
   int pdl;            // launch as a programmatic dependent of the previous kernel
   int idle;           // timing only: every instance counts as stopped (an empty slot list)
+  int slots_only;     // timing only: the slot kernel without the long-row pass
 };
 
 cudaError_t launch_primal(const DevPacked& csc, const DevVecs& v, const DevScalars* sc,
@@ -275,8 +276,11 @@ cudaError_t launch_scatter(const double* in, const int32_t* perm, const double* 
                            double* out, int len, cudaStream_t s);
 cudaError_t launch_fill(double* p, double v, int len, cudaStream_t s);
 // Access probes of one packed orientation (no arithmetic, for the roofline): mode 0 the
-// index stream and the gathers of x, mode 1 plus the value stream, mode 2 the streams only.
+// index stream and the gathers of x, mode 1 plus the value stream, mode 2 the streams only,
+// mode 3 mode 1 plus the loads and stores of the epilogue's row vectors of `v` (primal: the
+// A^T y orientation's; else the dual's), which it overwrites.
 cudaError_t launch_access_probe(const DevPacked& M, const double* x, int mode,
+                                const DevVecs& v, bool primal, bool pdl,
                                 unsigned long long* sink, cudaStream_t s);
 // One power-iteration round for every instance: w = A v, lam_i = w_i.w_i, u = A^T w,
 // v_i = u_i / ||u_i||; pw[4 i] = lam_i, pw[4 i + 1] = ||u_i||.

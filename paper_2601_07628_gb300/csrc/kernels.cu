@@ -860,8 +860,14 @@ __device__ __forceinline__ double strided_piece_sum(const DevPacked& M, int k, i
 // Long rows: add each row's pieces, then its epilogue.  Rows come longest first: the first
 // nlong_block rows get a thread block each, the next nlong_warp rows a warp each (fixed
 // strided sums and fixed reduction trees), the rest a thread each (pieces in order).
+// Resident blocks per SM the register allocation targets: the pass is latency-bound, and on
+// the power-law LP its ~880 blocks fit one wave only from 6 blocks per SM (at most 40
+// registers; 56 without the bound, 4 blocks per SM: 1.44 waves).
+#ifndef DPDLP_LONG_MIN_BLOCKS
+#define DPDLP_LONG_MIN_BLOCKS 6
+#endif
 template <int NV, class Epi>
-__global__ void __launch_bounds__(TPB) finish_long_kernel(DevPacked M, Epi epi_in) {
+__global__ void __launch_bounds__(TPB, DPDLP_LONG_MIN_BLOCKS) finish_long_kernel(DevPacked M, Epi epi_in) {
   __shared__ double red[TPB / 32];
   Epi epi = epi_in;
   pdl_trigger();
@@ -1032,6 +1038,11 @@ static bool pdl_of(const Epi& epi) {
   if constexpr (Epi::kTunable) return epi.plan.pdl != 0;
   return false;
 }
+template <class Epi>
+static bool slots_only_of(const Epi& epi) {
+  if constexpr (Epi::kTunable) return epi.plan.slots_only != 0;
+  return false;
+}
 
 template <int NV, int W, class Epi>
 static cudaError_t launch_slots(const DevPacked& M, GatherVecs<NV> g, Epi epi, cudaStream_t s) {
@@ -1069,7 +1080,7 @@ static cudaError_t launch_packed(const DevPacked& M, GatherVecs<NV> g, Epi epi, 
       e = launch_slots<NV, PK_WARPS>(M, g, epi, s);
     }
   }
-  if (e == cudaSuccess && M.nlong > 0) {
+  if (e == cudaSuccess && M.nlong > 0 && !slots_only_of(epi)) {
     const int rest = M.nlong - M.nlong_block - M.nlong_warp;
     const int grid = M.nlong_block + (M.nlong_warp + TPB / 32 - 1) / (TPB / 32) + (rest + TPB - 1) / TPB;
     e = launch_k(finish_long_kernel<NV, Epi>, grid, TPB, s, pdl_of(epi), M, epi);
@@ -1115,13 +1126,23 @@ cudaError_t launch_spmv(const DevPacked& M, const double* x0, const double* x1, 
 //   mode 0  the index stream and the x[col] gathers (random 8-byte gathers, each its own
 //           32-byte L2 sector: the gather ceiling of this layout);
 //   mode 1  mode 0 plus the value stream (every load the product makes per stored entry);
-//   mode 2  the index and value streams without gathers (the coalesced-stream ceiling).
-// Same slots, warps, cache policies and pipeline depth as packed_spmv_kernel.  Loaded words
-// are folded with integer xor (no FP64 work) and the fold is stored only if it equals a
-// constant it practically never takes, so every load stays live.
+//   mode 2  the index and value streams without gathers (the coalesced-stream ceiling);
+//   mode 3  mode 1 plus the epilogue's per-row vector loads and stores (every memory access
+//           of the iteration kernel's slots, the `ProbeRows` vectors).
+// Same slots, warps, cache policies and pipeline depth as packed_spmv_kernel, and launched
+// as it is (a programmatic dependent that loads its first index batches before the wait).
+// Loaded words are folded with integer xor (no FP64 work) and the fold is stored only if it
+// equals a constant it practically never takes, so every load stays live; mode 3 stores
+// its folds into the epilogue's output vectors (the caller keeps a copy of them).
+struct ProbeRows {
+  const double* ld[5];  // the epilogue's per-row inputs (nld of them)
+  double* st[2];        // its per-row outputs (nst of them)
+  int nld, nst;
+};
 template <int Mode>
 __global__ void __launch_bounds__(PK_TPB, DPDLP_PK_MIN_BLOCKS)
-    access_probe_kernel(DevPacked M, const double* __restrict__ x, unsigned long long* sink) {
+    access_probe_kernel(DevPacked M, const double* __restrict__ x, ProbeRows E,
+                        unsigned long long* sink) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = blockIdx.x * PK_WARPS + w;
   if (s >= M.nslots) return;  // uniform over the warp
@@ -1135,6 +1156,8 @@ __global__ void __launch_bounds__(PK_TPB, DPDLP_PK_MIN_BLOCKS)
   uint32_t c0[B], c1[B];
   load_idx<B>(ip, 0, c0, pol);
   load_idx<B>(ip, 1, c1, pol);
+  pdl_trigger();
+  pdl_wait();
   unsigned long long g0[B];
   double v0[B];
   if (Mode >= 1) Vals<double>::load<B>(vp, 0, v0, pol);
@@ -1168,20 +1191,48 @@ __global__ void __launch_bounds__(PK_TPB, DPDLP_PK_MIN_BLOCKS)
       }
     }
   }
+  if (Mode == 3) {  // the epilogue's rows as apply_rows reads them: every load, then stores
+    const SlotDesc sd = M.slots[s];
+    constexpr int R = MAX_SLOT_ROWS / LANES;
+    unsigned long long f[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int r = lane + k * LANES;
+      f[k] = 0;
+      if (r < sd.nrows)
+        for (int q = 0; q < E.nld; ++q)
+          f[k] ^= (unsigned long long)__double_as_longlong(ld_once(E.ld[q] + sd.row_base + r));
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int r = lane + k * LANES;
+      if (r < sd.nrows)
+        for (int q = 0; q < E.nst; ++q)
+          st_once(E.st[q] + sd.row_base + r, __longlong_as_double((long long)(f[k] ^ acc)));
+    }
+  }
   if (acc == 0x9e3779b97f4a7c15ull) sink[0] = acc;
 }
 
 cudaError_t launch_access_probe(const DevPacked& M, const double* x, int mode,
+                                const DevVecs& v, bool primal, bool pdl,
                                 unsigned long long* sink, cudaStream_t s) {
   if (M.nslots <= 0) return cudaSuccess;
   const int grid = (M.nslots + PK_WARPS - 1) / PK_WARPS;
+  // the rows' vectors of a regular (Halpern) iteration's epilogue: PrimalEpi reads c, the
+  // bounds, x and the anchor and writes x_bar and x; DualEpi reads the -S box, y and the
+  // anchor and writes y
+  const ProbeRows E = primal ? ProbeRows{{v.c, v.lv, v.uv, v.x, v.x0}, {v.xbar, v.x}, 5, 2}
+                             : ProbeRows{{v.lo, v.hi, v.y, v.y0, nullptr}, {v.y, nullptr}, 4, 1};
+  cudaError_t e;
   switch (mode) {
-    case 0: access_probe_kernel<0><<<grid, PK_TPB, 0, s>>>(M, x, sink); break;
-    case 1: access_probe_kernel<1><<<grid, PK_TPB, 0, s>>>(M, x, sink); break;
-    case 2: access_probe_kernel<2><<<grid, PK_TPB, 0, s>>>(M, x, sink); break;
+    case 0: e = launch_k(access_probe_kernel<0>, grid, PK_TPB, s, pdl, M, x, E, sink); break;
+    case 1: e = launch_k(access_probe_kernel<1>, grid, PK_TPB, s, pdl, M, x, E, sink); break;
+    case 2: e = launch_k(access_probe_kernel<2>, grid, PK_TPB, s, pdl, M, x, E, sink); break;
+    case 3: e = launch_k(access_probe_kernel<3>, grid, PK_TPB, s, pdl, M, x, E, sink); break;
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- fused body (small LPs)

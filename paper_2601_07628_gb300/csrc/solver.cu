@@ -1300,9 +1300,10 @@ int dpdlp_time_kernel(dpdlp_t* h, const char* which, int32_t reps, double* avg_m
   if (!h || !which || reps <= 0 || !avg_ms) return DPDLP_ERR_INVALID;
   if (!h->loaded) return fail(h, DPDLP_ERR_NOT_LOADED, "no LP loaded");
   const std::string w(which);
-  // the iteration kernels, or an access probe of one orientation's product (its loads
-  // without arithmetic): gather_* indices + gathers, access_* plus values, stream_* the
-  // index and value streams only
+  // the iteration kernels (*_slots: without the long-row pass), or an access probe of one
+  // orientation's product (its loads without arithmetic): gather_* indices + gathers,
+  // access_* plus values, stream_* the index and value streams only, memory_* access_* plus
+  // the epilogue's row vectors
   int probe = -1;
   bool primal = w == "primal";
   // batches also time the iteration kernels as the solve may run them: walking the
@@ -1311,8 +1312,11 @@ int dpdlp_time_kernel(dpdlp_t* h, const char* which, int32_t reps, double* avg_m
   IterPlan p{0, 1, 0, (int)h->P("pdl"), 0};
   const std::string side0 = w.substr(0, w.find('_'));
   const std::string rest = w.find('_') == std::string::npos ? "" : w.substr(w.find('_') + 1);
-  if ((side0 == "primal" || side0 == "dual") &&
-      (rest == "list" || rest == "idle" || rest == "list_idle")) {
+  if ((side0 == "primal" || side0 == "dual") && rest == "slots") {
+    primal = side0 == "primal";
+    p.slots_only = 1;
+  } else if ((side0 == "primal" || side0 == "dual") &&
+             (rest == "list" || rest == "idle" || rest == "list_idle")) {
     if (h->ninst < 2) return fail(h, DPDLP_ERR_INVALID, "list and idle timings need a batch");
     primal = side0 == "primal";
     p.list = rest != "idle";
@@ -1321,10 +1325,12 @@ int dpdlp_time_kernel(dpdlp_t* h, const char* which, int32_t reps, double* avg_m
     const size_t us = w.find('_');
     const std::string kind = us == std::string::npos ? w : w.substr(0, us);
     const std::string side = us == std::string::npos ? "" : w.substr(us + 1);
-    probe = kind == "gather" ? 0 : kind == "access" ? 1 : kind == "stream" ? 2 : -1;
+    probe = kind == "gather" ? 0 : kind == "access" ? 1 : kind == "stream" ? 2
+          : kind == "memory" ? 3 : -1;
     if (probe < 0 || (side != "primal" && side != "dual"))
       return fail(h, DPDLP_ERR_INVALID,
-                  "kernel must be primal, dual, or gather_/access_/stream_ + primal or dual");
+                  "kernel must be primal, dual, primal_slots, dual_slots, or "
+                  "gather_/access_/stream_/memory_ + primal or dual");
     primal = side == "primal";
   }
   if (!h->has_state) return fail(h, DPDLP_ERR_INVALID, "solve or set a start first");
@@ -1341,6 +1347,7 @@ int dpdlp_time_kernel(dpdlp_t* h, const char* which, int32_t reps, double* avg_m
     if (probe >= 0) {
       // the primal product gathers y over the rows of A^T, the dual one x_bar over A
       CK(launch_access_probe(primal ? h->csc : h->csr, primal ? h->v.y : h->v.xbar, probe,
+                             h->v, primal, p.pdl != 0,
                              reinterpret_cast<unsigned long long*>(h->v.pw), h->stream));
     } else if (primal) {
       CK(launch_primal(h->csc, h->v, h->d_sc, p, h->stream));

@@ -264,9 +264,23 @@ def test_time_kernel_keeps_state(Solver):
     s.solve(0.0, 64)
     before = s.get_state()
     assert s.time_kernel("primal", 5) > 0 and s.time_kernel("dual", 5) > 0
+    assert s.time_kernel("primal_slots", 5) > 0 and s.time_kernel("dual_slots", 5) > 0
+    # the access probes, including the one that stores into the epilogue's output vectors
+    for probe in ("gather", "access", "stream", "memory"):
+        for side in ("primal", "dual"):
+            assert s.time_kernel(f"{probe}_{side}", 3) > 0
     after = s.get_state()
     for k in ("x", "y", "x0", "y0"):
         assert np.array_equal(before[k], after[k])
+    # and the solve continues exactly as one that was never timed
+    s.solve(0.0, 128)
+    t = Solver()
+    t.load(lp)
+    t.set_param("eta", 0.1)
+    t.solve(0.0, 64)
+    t.solve(0.0, 128)
+    for a, b in zip(s.solution(), t.solution()):
+        assert np.array_equal(a, b)
 
 
 def test_invalid_inputs_are_rejected(Solver):
