@@ -243,9 +243,11 @@ bool fused_body_fits(const DevPacked& csc, const DevPacked& csr, int ninst, int 
 // Sets the fused kernel's shared-memory limit; called before the first launch or capture.
 cudaError_t fused_body_prepare();
 // cluster > 1: the body spread over a thread-block cluster of that many CTAs (at most 8),
-// bitwise the same results.
+// bitwise the same results.  slot_cache: each CTA copies its slots into shared memory once
+// per launch when they fit (bitwise the same results).
 cudaError_t launch_body_fused(const DevPacked& csc, const DevPacked& csr, const DevVecs& v,
-                              const DevScalars* sc, int K, int cluster, cudaStream_t s);
+                              const DevScalars* sc, int K, int cluster, int slot_cache,
+                              cudaStream_t s);
 // CTAs of the cluster form: `requested` (>= 1), or 0 = about two slots per CTA, at most 8.
 int fused_cluster_ctas(const DevPacked& csc, const DevPacked& csr, int requested);
 // out0 = M x0 (and out1 = M x1 when x1 != nullptr) for one packed orientation M; with

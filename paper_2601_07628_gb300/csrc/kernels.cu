@@ -596,7 +596,8 @@ __device__ __forceinline__ double gather(const double* p) {
 
 // Values and indices of batch b (positions B*b .. B*b+B-1) of this lane: 16-byte loads,
 // each covering 512 contiguous bytes across the warp.  FP64 values are stored in pairs per
-// lane, FP32 values and indices in fours.
+// lane, FP32 values and indices in fours.  Gen: plain (generic) loads, for a copy of the
+// slot in shared memory; otherwise streaming global loads with the given L2 policy.
 template <typename V>
 struct Vals;
 template <>
@@ -605,12 +606,13 @@ struct Vals<double> {
   static __device__ __forceinline__ const double2* base(const DevPacked& M, size_t off, int lane) {
     return reinterpret_cast<const double2*>(M.val + off) + lane;
   }
-  template <int B>
+  template <int B, bool Gen = false>
   static __device__ __forceinline__ void load(const double2* vp, int b, double (&v)[B],
                                               unsigned long long pol) {
 #pragma unroll
     for (int q = 0; q < B / 2; ++q) {
-      const double2 d = ld_stream(vp + ((B / 2) * b + q) * LANES, pol);
+      const double2* a = vp + ((B / 2) * b + q) * LANES;
+      const double2 d = Gen ? *a : ld_stream(a, pol);
       v[2 * q] = d.x;
       v[2 * q + 1] = d.y;
     }
@@ -623,12 +625,13 @@ struct Vals<float> {
   static __device__ __forceinline__ const float4* base(const DevPacked& M, size_t off, int lane) {
     return reinterpret_cast<const float4*>(M.val32 + off) + lane;
   }
-  template <int B>
+  template <int B, bool Gen = false>
   static __device__ __forceinline__ void load(const float4* vp, int b, float (&v)[B],
                                               unsigned long long pol) {
 #pragma unroll
     for (int q = 0; q < B / 4; ++q) {
-      const float4 d = ld_stream(vp + ((B / 4) * b + q) * LANES, pol);
+      const float4* a = vp + ((B / 4) * b + q) * LANES;
+      const float4 d = Gen ? *a : ld_stream(a, pol);
       v[4 * q] = d.x;
       v[4 * q + 1] = d.y;
       v[4 * q + 2] = d.z;
@@ -646,12 +649,13 @@ struct Vals<float> {
   }
 };
 
-template <int B>
+template <int B, bool Gen = false>
 __device__ __forceinline__ void load_idx(const uint4* ip, int b, uint32_t (&c)[B],
                                          unsigned long long pol) {
 #pragma unroll
   for (int q = 0; q < B / 4; ++q) {
-    const uint4 d = ld_stream(ip + ((B / 4) * b + q) * LANES, pol);
+    const uint4* a = ip + ((B / 4) * b + q) * LANES;
+    const uint4 d = Gen ? *a : ld_stream(a, pol);
     c[4 * q] = d.x;
     c[4 * q + 1] = d.y;
     c[4 * q + 2] = d.z;
@@ -663,8 +667,9 @@ __device__ __forceinline__ void load_idx(const uint4* ip, int b, uint32_t (&c)[B
 // in FP64 from values of type V); at every end flag the finished sum goes to the slot's row
 // sums (short rows) or to the piece array (long-row pieces).  Three-stage pipeline of
 // batches: indices two batches ahead, values and the x[col] gathers one batch ahead, so
-// gathers are in flight while the FMA chain runs.
-template <typename V, int NV, int B, bool Coh = false>
+// gathers are in flight while the FMA chain runs.  Gen: the slot's values and indices are a
+// copy in shared memory (M.val / M.idx point there).
+template <typename V, int NV, int B, bool Coh = false, bool Gen = false>
 __device__ __forceinline__ void lane_sums(const DevPacked& M, const GatherVecs<NV>& g, size_t off,
                                           int lane, int rl, int pid,
                                           double (*srow)[MAX_SLOT_ROWS], const uint4* ip,
@@ -677,7 +682,7 @@ __device__ __forceinline__ void lane_sums(const DevPacked& M, const GatherVecs<N
   for (int k = 0; k < NV; ++k) acc[k] = 0.0;
   V v0[B];
   double x0v[NV][B];
-  Vals<V>::template load<B>(vp, 0, v0, pol);
+  Vals<V>::template load<B, Gen>(vp, 0, v0, pol);
 #pragma unroll
   for (int j = 0; j < B; ++j) {
 #pragma unroll
@@ -688,9 +693,9 @@ __device__ __forceinline__ void lane_sums(const DevPacked& M, const GatherVecs<N
     uint32_t c2[B];
     V v1[B];
     double x1v[NV][B];
-    if (b + 2 < NB) load_idx<B>(ip, b + 2, c2, pol);
+    if (b + 2 < NB) load_idx<B, Gen>(ip, b + 2, c2, pol);
     if (b + 1 < NB) {
-      Vals<V>::template load<B>(vp, b + 1, v1, pol);
+      Vals<V>::template load<B, Gen>(vp, b + 1, v1, pol);
 #pragma unroll
       for (int j = 0; j < B; ++j) {
 #pragma unroll
@@ -860,11 +865,18 @@ __device__ __forceinline__ double strided_piece_sum(const DevPacked& M, int k, i
 // Long rows: add each row's pieces, then its epilogue.  Rows come longest first: the first
 // nlong_block rows get a thread block each, the next nlong_warp rows a warp each (fixed
 // strided sums and fixed reduction trees), the rest a thread each (pieces in order).
-// Resident blocks per SM the register allocation targets: the pass is latency-bound, and on
-// the power-law LP its ~880 blocks fit one wave only from 6 blocks per SM (at most 40
-// registers; 56 without the bound, 4 blocks per SM: 1.44 waves).
+// Resident blocks per SM the register allocation targets: on the power-law LP the pass's
+// ~880 blocks fit one wave from 6 blocks per SM (at most 40 registers; 56 without the
+// bound, 4 blocks per SM: 1.44 waves).  Measured on one GB300, the pass added to the dual
+// slot kernel: 13.7 us at 6 blocks per SM, 13.2-13.7 at 4, 16.4 at 8 (32 registers, spills):
+// its cost is its dependent loads and its launch, not waves.
 #ifndef DPDLP_LONG_MIN_BLOCKS
 #define DPDLP_LONG_MIN_BLOCKS 6
+#endif
+// DPDLP_LONG_PDL  launch the pass as a programmatic dependent of the slot kernel (measured:
+// 13.7 us per pass with, 16.2 without)
+#ifndef DPDLP_LONG_PDL
+#define DPDLP_LONG_PDL 1
 #endif
 template <int NV, class Epi>
 __global__ void __launch_bounds__(TPB, DPDLP_LONG_MIN_BLOCKS) finish_long_kernel(DevPacked M, Epi epi_in) {
@@ -1083,7 +1095,7 @@ static cudaError_t launch_packed(const DevPacked& M, GatherVecs<NV> g, Epi epi, 
   if (e == cudaSuccess && M.nlong > 0 && !slots_only_of(epi)) {
     const int rest = M.nlong - M.nlong_block - M.nlong_warp;
     const int grid = M.nlong_block + (M.nlong_warp + TPB / 32 - 1) / (TPB / 32) + (rest + TPB - 1) / TPB;
-    e = launch_k(finish_long_kernel<NV, Epi>, grid, TPB, s, pdl_of(epi), M, epi);
+    e = launch_k(finish_long_kernel<NV, Epi>, grid, TPB, s, pdl_of(epi) && DPDLP_LONG_PDL, M, epi);
   }
   return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -1254,24 +1266,91 @@ constexpr int FB_MAX_CLUSTER = 8;     // CTAs of the cluster form (the portable 
 constexpr int FB_SLOTS_PER_CTA = 2;   // automatic cluster size: about this many slots per CTA
 constexpr int FB_SINGLE_MAX_SLOTS = 6;  // automatic: one CTA up to this many slots per copy
 
-// One product-and-step phase over every slot of M (the packed_spmv_kernel body).
-template <class Epi>
-__device__ __forceinline__ void fused_slots(const DevPacked& M, const GatherVecs<1>& g, Epi& epi,
-                                            double (*srow)[MAX_SLOT_ROWS], int w, int lane) {
+// A CTA's copy of its slots of one packed orientation in shared memory (the slots rank,
+// rank + C, rank + 2 C, ... of a C-CTA cluster, in that order): values, indices, lane
+// metadata and descriptors, filled once per launch and read by every iteration of the body
+// (the matrix does not change inside a graph body).  FP32 values are not copied: that form
+// reads the global slot.
+struct SlotCache {
+  double* val;      // SLOT_ITEMS per cached slot, the global layout
+  uint32_t* idx;    // likewise
+  LaneMeta* lanes;  // LANES per cached slot
+  SlotDesc* desc;
+};
+// Bytes of the copies of `slots` slots (values, indices, lane metadata, descriptor).
+constexpr size_t SLOT_CACHE_BYTES = SLOT_ITEMS * (sizeof(double) + sizeof(uint32_t)) +
+                                    LANES * sizeof(LaneMeta) + sizeof(SlotDesc);
+// Carves the copies of kc primal and kr dual slots out of shared memory at `base` (16-byte
+// aligned).
+__device__ __forceinline__ void carve_slot_caches(char* base, int kc, int kr, SlotCache& cc,
+                                                  SlotCache& cr) {
+  cc.val = reinterpret_cast<double*>(base);
+  cr.val = cc.val + (size_t)kc * SLOT_ITEMS;
+  cc.idx = reinterpret_cast<uint32_t*>(cr.val + (size_t)kr * SLOT_ITEMS);
+  cr.idx = cc.idx + (size_t)kc * SLOT_ITEMS;
+  cc.lanes = reinterpret_cast<LaneMeta*>(cr.idx + (size_t)kr * SLOT_ITEMS);
+  cr.lanes = cc.lanes + (size_t)kc * LANES;
+  cc.desc = reinterpret_cast<SlotDesc*>(cr.lanes + (size_t)kr * LANES);
+  cr.desc = cc.desc + kc;
+}
+// Every thread of the CTA copies (16 bytes at a time) this CTA's slots of M.
+__device__ __forceinline__ void fill_slot_cache(const DevPacked& M, const SlotCache& c, int rank,
+                                                int C) {
+  const int nk = rank < M.nslots ? (M.nslots - rank + C - 1) / C : 0;
+  constexpr int V16 = SLOT_ITEMS * (int)sizeof(double) / 16, I16 = SLOT_ITEMS * (int)sizeof(uint32_t) / 16;
+  constexpr int L16 = LANES * (int)sizeof(LaneMeta) / 16;
+  for (int t = threadIdx.x; t < nk * V16; t += blockDim.x) {
+    const int k = t / V16, u = t % V16;
+    reinterpret_cast<uint4*>(c.val + (size_t)k * SLOT_ITEMS)[u] =
+        reinterpret_cast<const uint4*>(M.val + (size_t)(rank + C * k) * SLOT_ITEMS)[u];
+  }
+  for (int t = threadIdx.x; t < nk * I16; t += blockDim.x) {
+    const int k = t / I16, u = t % I16;
+    reinterpret_cast<uint4*>(c.idx + (size_t)k * SLOT_ITEMS)[u] =
+        reinterpret_cast<const uint4*>(M.idx + (size_t)(rank + C * k) * SLOT_ITEMS)[u];
+  }
+  for (int t = threadIdx.x; t < nk * L16; t += blockDim.x) {
+    const int k = t / L16, u = t % L16;
+    reinterpret_cast<uint4*>(c.lanes + (size_t)k * LANES)[u] =
+        reinterpret_cast<const uint4*>(M.lanes + (size_t)(rank + C * k) * LANES)[u];
+  }
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) c.desc[k] = M.slots[rank + C * k];
+}
+
+// One product-and-step phase over this CTA's slots of M (the packed_spmv_kernel body): CTA
+// `rank` of C takes the slots rank, rank + C, ..., its warps striding over them.  Cache: the
+// slots are read from this CTA's shared-memory copy.
+template <bool Cache, class Epi>
+__device__ __forceinline__ void body_slots(const DevPacked& M, const SlotCache& cache,
+                                           const GatherVecs<1>& g, Epi& epi,
+                                           double (*srow)[MAX_SLOT_ROWS], int w, int lane,
+                                           int rank, int C) {
   constexpr int B = DPDLP_PK_BATCH;
   const unsigned long long pol = l2_evict_first_policy();
-  for (int s = w; s < M.nslots; s += FB_WARPS) {  // uniform over the warp
-    const SlotDesc sd = M.slots[s];
-    const LaneMeta lm = M.lanes[(size_t)s * LANES + lane];
-    const size_t off = (size_t)s * SLOT_ITEMS;
-    const uint4* ip = reinterpret_cast<const uint4*>(M.idx + off) + lane;
+  DevPacked Mv = M;  // the view the FP64 product reads: the copy when cached
+  if constexpr (Cache) {
+    Mv.val = cache.val;
+    Mv.idx = cache.idx;
+  }
+  for (int k = w, s = rank + C * w; s < M.nslots; k += FB_WARPS, s += C * FB_WARPS) {
+    // uniform over the warp
+    const SlotDesc sd = Cache ? cache.desc[k] : M.slots[s];
+    const LaneMeta lm = Cache ? cache.lanes[(size_t)k * LANES + lane] : M.lanes[(size_t)s * LANES + lane];
     uint32_t c0[B], c1[B];
-    load_idx<B>(ip, 0, c0, pol);
-    load_idx<B>(ip, 1, c1, pol);
-    if (epi.fp32() && M.val32)
+    if (epi.fp32() && M.val32) {  // FP32 values: the global slot
+      const size_t off = (size_t)s * SLOT_ITEMS;
+      const uint4* ip = reinterpret_cast<const uint4*>(M.idx + off) + lane;
+      load_idx<B>(ip, 0, c0, pol);
+      load_idx<B>(ip, 1, c1, pol);
       lane_sums<float, 1, B, true>(M, g, off, lane, lm.row_local, lm.piece_base, srow, ip, pol, c0, c1);
-    else
-      lane_sums<double, 1, B, true>(M, g, off, lane, lm.row_local, lm.piece_base, srow, ip, pol, c0, c1);
+    } else {
+      const size_t off = (size_t)(Cache ? k : s) * SLOT_ITEMS;
+      const uint4* ip = reinterpret_cast<const uint4*>(Mv.idx + off) + lane;
+      load_idx<B, Cache>(ip, 0, c0, pol);
+      load_idx<B, Cache>(ip, 1, c1, pol);
+      lane_sums<double, 1, B, true, Cache>(Mv, g, off, lane, lm.row_local, lm.piece_base, srow, ip,
+                                           pol, c0, c1);
+    }
     __syncwarp();
     epi.prepare(sd.inst);
     epi.apply_rows(sd.row_base, sd.nrows, lane, srow);
@@ -1306,15 +1385,56 @@ __device__ __forceinline__ void fused_long(const DevPacked& M, Epi& epi, int w, 
   }
 }
 
-template <class PEpi>
+// Per-body constants of one LP in shared memory: the solver and instance scalars and the
+// Halpern weights of the body's K iterations (same layout as the global table), which the
+// epilogues read at every phase; only the check and control kernels between bodies change
+// them.
+struct BodyConsts {
+  DevScalars sc;
+  InstScalars inst;
+  double w[2 * KMAX];
+};
+__device__ __forceinline__ void load_body_consts(BodyConsts& b, const DevScalars* sc,
+                                                 const InstScalars* itab, const double* wtab, int K) {
+  if (threadIdx.x == 0) {
+    b.sc = *sc;
+    b.inst = itab[0];
+  }
+  for (int t = threadIdx.x; t < K; t += blockDim.x) {
+    b.w[t] = wtab[t];
+    b.w[KMAX + t] = wtab[KMAX + t];
+  }
+}
+template <class Epi>
+__device__ __forceinline__ void use_body_consts(Epi& e, const BodyConsts& b) {
+  e.sc = &b.sc;
+  e.itab = &b.inst;
+  e.wtab = b.w;
+}
+
+// Offset of the slot copies in the dynamic shared memory, after y and x_bar (16-byte aligned).
+__host__ __device__ inline size_t fb_cache_offset(int rows_total) {
+  return ((size_t)rows_total * sizeof(double) + 15) / 16 * 16;
+}
+
+template <class PEpi, bool Cache>
 __global__ void __launch_bounds__(FB_TPB, 1)
-    fused_body_kernel(DevPacked Mc, DevPacked Mr, PEpi pe_in, DualEpi<true, 1> de_in, int K) {
+    fused_body_kernel(DevPacked Mc, DevPacked Mr, PEpi pe_in, DualEpi<true, 1> de_in, int K,
+                      int kc, int kr) {
   __shared__ double srow[FB_WARPS][1][MAX_SLOT_ROWS];
-  extern __shared__ double fb_vecs[];  // y [m], then x_bar [n]
+  extern __shared__ __align__(16) double fb_vecs[];  // y [m], x_bar [n], (Cache) slot copies
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m = Mr.rows, n = Mc.rows;
   double* ys = fb_vecs;
   double* xs = fb_vecs + m;
+  __shared__ BodyConsts consts;
+  load_body_consts(consts, pe_in.sc, pe_in.itab, pe_in.wtab, K);
+  SlotCache cc{}, cr{};
+  if constexpr (Cache) {
+    carve_slot_caches(reinterpret_cast<char*>(fb_vecs) + fb_cache_offset(m + n), kc, kr, cc, cr);
+    fill_slot_cache(Mc, cc, 0, 1);
+    fill_slot_cache(Mr, cr, 0, 1);
+  }
   for (int i = threadIdx.x; i < m; i += FB_TPB) ys[i] = de_in.y[i];
   __syncthreads();
   // x_bar lives only in shared memory (nothing after the body reads it); y is written to
@@ -1326,8 +1446,9 @@ __global__ void __launch_bounds__(FB_TPB, 1)
     PEpi pe = pe_in;
     pe.plan.i = i;
     pe.xbar = xs;
+    use_body_consts(pe, consts);
     if (!pe.begin()) break;
-    fused_slots(Mc, gp, pe, srow[w], w, lane);
+    body_slots<Cache>(Mc, cc, gp, pe, srow[w], w, lane, 0, 1);
     __syncthreads();
     if (Mc.nlong > 0) {
       fused_long(Mc, pe, w, lane);
@@ -1336,8 +1457,9 @@ __global__ void __launch_bounds__(FB_TPB, 1)
     DualEpi<true, 1> de = de_in;
     de.plan.i = i;
     de.ys = ys;
+    use_body_consts(de, consts);
     if (!de.begin()) break;
-    fused_slots(Mr, gd, de, srow[w], w, lane);
+    body_slots<Cache>(Mr, cr, gd, de, srow[w], w, lane, 0, 1);
     __syncthreads();
     if (Mr.nlong > 0) {
       fused_long(Mr, de, w, lane);
@@ -1355,31 +1477,6 @@ __global__ void __launch_bounds__(FB_TPB, 1)
 // separate the phases (and order the piece sums of long rows, which cross SMs through L2).
 // Each slot's lane sums, each epilogue and each long row's sum are the same code as the
 // separate launches, so results are bitwise theirs.
-template <class Epi>
-__device__ __forceinline__ void cluster_slots(const DevPacked& M, const GatherVecs<1>& g, Epi& epi,
-                                              double (*srow)[MAX_SLOT_ROWS], int w, int lane,
-                                              int rank, int C) {
-  constexpr int B = DPDLP_PK_BATCH;
-  const unsigned long long pol = l2_evict_first_policy();
-  for (int s = rank + C * w; s < M.nslots; s += C * FB_WARPS) {  // uniform over the warp
-    const SlotDesc sd = M.slots[s];
-    const LaneMeta lm = M.lanes[(size_t)s * LANES + lane];
-    const size_t off = (size_t)s * SLOT_ITEMS;
-    const uint4* ip = reinterpret_cast<const uint4*>(M.idx + off) + lane;
-    uint32_t c0[B], c1[B];
-    load_idx<B>(ip, 0, c0, pol);
-    load_idx<B>(ip, 1, c1, pol);
-    if (epi.fp32() && M.val32)
-      lane_sums<float, 1, B, true>(M, g, off, lane, lm.row_local, lm.piece_base, srow, ip, pol, c0, c1);
-    else
-      lane_sums<double, 1, B, true>(M, g, off, lane, lm.row_local, lm.piece_base, srow, ip, pol, c0, c1);
-    __syncwarp();
-    epi.prepare(sd.inst);
-    epi.apply_rows(sd.row_base, sd.nrows, lane, srow);
-    __syncwarp();
-  }
-}
-
 template <class Epi>
 __device__ __forceinline__ void cluster_long(const DevPacked& M, Epi& epi, int w, int lane,
                                              int rank, int C) {
@@ -1411,17 +1508,28 @@ __device__ __forceinline__ void cluster_sync_pieces(cooperative_groups::cluster_
   cl.sync();
 }
 
-template <class PEpi>
+template <class PEpi, bool Cache>
 __global__ void __launch_bounds__(FB_TPB, 1)
-    cluster_body_kernel(DevPacked Mc, DevPacked Mr, PEpi pe_in, DualEpi<true, 2> de_in, int K) {
+    cluster_body_kernel(DevPacked Mc, DevPacked Mr, PEpi pe_in, DualEpi<true, 2> de_in, int K,
+                        int kc, int kr) {
   cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
   const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   __shared__ double srow[FB_WARPS][1][MAX_SLOT_ROWS];
-  extern __shared__ double fb_vecs[];  // y [m], then x_bar [n]: this CTA's copies
+  // y [m], then x_bar [n]: this CTA's copies (same offsets in every CTA), then (Cache) the
+  // copies of this CTA's slots
+  extern __shared__ __align__(16) double fb_vecs[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m = Mr.rows, n = Mc.rows;
   double* ys = fb_vecs;
   double* xs = fb_vecs + m;
+  __shared__ BodyConsts consts;
+  load_body_consts(consts, pe_in.sc, pe_in.itab, pe_in.wtab, K);
+  SlotCache cc{}, cr{};
+  if constexpr (Cache) {
+    carve_slot_caches(reinterpret_cast<char*>(fb_vecs) + fb_cache_offset(m + n), kc, kr, cc, cr);
+    fill_slot_cache(Mc, cc, rank, C);
+    fill_slot_cache(Mr, cr, rank, C);
+  }
   for (int i = threadIdx.x; i < m; i += FB_TPB) ys[i] = de_in.y[i];
   cl.sync();  // every CTA of the cluster runs before any stores into another's copies
   const GatherVecs<1> gp{{ys}}, gd{{xs}};
@@ -1431,8 +1539,9 @@ __global__ void __launch_bounds__(FB_TPB, 1)
     pe.plan.i = i;
     pe.xbar = xs;
     pe.ncta = (unsigned)C;
+    use_body_consts(pe, consts);
     if (!pe.begin()) break;
-    cluster_slots(Mc, gp, pe, srow[w], w, lane, rank, C);
+    body_slots<Cache>(Mc, cc, gp, pe, srow[w], w, lane, rank, C);
     if (Mc.nlong > 0) {
       cluster_sync_pieces(cl);
       cluster_long(Mc, pe, w, lane, rank, C);
@@ -1442,8 +1551,9 @@ __global__ void __launch_bounds__(FB_TPB, 1)
     de.plan.i = i;
     de.ys = ys;
     de.ncta = (unsigned)C;
+    use_body_consts(de, consts);
     if (!de.begin()) break;
-    cluster_slots(Mr, gd, de, srow[w], w, lane, rank, C);
+    body_slots<Cache>(Mr, cr, gd, de, srow[w], w, lane, rank, C);
     if (Mr.nlong > 0) {
       cluster_sync_pieces(cl);
       cluster_long(Mr, de, w, lane, rank, C);
@@ -1454,9 +1564,15 @@ __global__ void __launch_bounds__(FB_TPB, 1)
   (void)n;
 }
 
-// x_bar and y in shared memory: at most FB_VEC_MAX entries together
+// x_bar and y in shared memory: at most FB_VEC_MAX entries together; with the slot copies
+// at most FB_DYN_CACHE_MAX bytes of dynamic shared memory (a block may hold 227 KB; the
+// static row sums and the body constants take about 32 KB)
 constexpr int FB_VEC_MAX = 20480;
 constexpr int FB_DYN_MAX = FB_VEC_MAX * (int)sizeof(double);
+constexpr int FB_DYN_CACHE_MAX = 192 * 1024;
+static_assert(FB_DYN_CACHE_MAX + FB_WARPS * MAX_SLOT_ROWS * sizeof(double) + sizeof(BodyConsts) <=
+                  227 * 1024,
+              "slot copies, vectors, row sums and body constants fit one block's shared memory");
 
 bool fused_body_fits(const DevPacked& csc, const DevPacked& csr, int ninst, int max_slots) {
   return ninst == 1 && max_slots <= FUSED_MAX_SLOTS && csc.nslots <= max_slots &&
@@ -1464,18 +1580,22 @@ bool fused_body_fits(const DevPacked& csc, const DevPacked& csr, int ninst, int 
          (long long)csc.rows + csr.rows <= FB_VEC_MAX;
 }
 
+template <class Kern>
+static cudaError_t set_dyn_smem(Kern kernel, int bytes, cudaError_t e) {
+  return e != cudaSuccess ? e
+                          : cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 cudaError_t fused_body_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(fused_body_kernel<PrimalEpi<true>>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, FB_DYN_MAX);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(fused_body_kernel<PrimalEpi<true, true>>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, FB_DYN_MAX);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(cluster_body_kernel<PrimalEpi<true, false, true>>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, FB_DYN_MAX);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(cluster_body_kernel<PrimalEpi<true, true, true>>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, FB_DYN_MAX);
+  cudaError_t e = cudaSuccess;
+  e = set_dyn_smem(fused_body_kernel<PrimalEpi<true>, false>, FB_DYN_MAX, e);
+  e = set_dyn_smem(fused_body_kernel<PrimalEpi<true, true>, false>, FB_DYN_MAX, e);
+  e = set_dyn_smem(cluster_body_kernel<PrimalEpi<true, false, true>, false>, FB_DYN_MAX, e);
+  e = set_dyn_smem(cluster_body_kernel<PrimalEpi<true, true, true>, false>, FB_DYN_MAX, e);
+  e = set_dyn_smem(fused_body_kernel<PrimalEpi<true>, true>, FB_DYN_CACHE_MAX, e);
+  e = set_dyn_smem(fused_body_kernel<PrimalEpi<true, true>, true>, FB_DYN_CACHE_MAX, e);
+  e = set_dyn_smem(cluster_body_kernel<PrimalEpi<true, false, true>, true>, FB_DYN_CACHE_MAX, e);
+  e = set_dyn_smem(cluster_body_kernel<PrimalEpi<true, true, true>, true>, FB_DYN_CACHE_MAX, e);
   return e;
 }
 
@@ -1492,9 +1612,10 @@ int fused_cluster_ctas(const DevPacked& csc, const DevPacked& csr, int requested
   return c > FB_MAX_CLUSTER ? FB_MAX_CLUSTER : c;
 }
 
-template <class PEpi>
+template <class PEpi, bool Cache>
 static cudaError_t launch_cluster(const DevPacked& csc, const DevPacked& csr, PEpi pe,
-                                  DualEpi<true, 2> de, int K, int C, size_t dyn, cudaStream_t s) {
+                                  DualEpi<true, 2> de, int K, int C, size_t dyn, int kc, int kr,
+                                  cudaStream_t s) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(C);
   cfg.blockDim = dim3(FB_TPB);
@@ -1507,27 +1628,45 @@ static cudaError_t launch_cluster(const DevPacked& csc, const DevPacked& csr, PE
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, cluster_body_kernel<PEpi>, csc, csr, pe, de, K);
+  return cudaLaunchKernelEx(&cfg, cluster_body_kernel<PEpi, Cache>, csc, csr, pe, de, K, kc, kr);
+}
+
+template <class PEpi>
+static cudaError_t launch_single(const DevPacked& csc, const DevPacked& csr, PEpi pe,
+                                 DualEpi<true, 1> de, int K, bool cache, size_t dyn, int kc,
+                                 int kr, cudaStream_t s) {
+  if (cache)
+    fused_body_kernel<PEpi, true><<<1, FB_TPB, dyn, s>>>(csc, csr, pe, de, K, kc, kr);
+  else
+    fused_body_kernel<PEpi, false><<<1, FB_TPB, dyn, s>>>(csc, csr, pe, de, K, kc, kr);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_body_fused(const DevPacked& csc, const DevPacked& csr, const DevVecs& v,
-                              const DevScalars* sc, int K, int cluster, cudaStream_t s) {
+                              const DevScalars* sc, int K, int cluster, int slot_cache,
+                              cudaStream_t s) {
   if (v.ninst != 1 || csc.rows + csr.rows > FB_VEC_MAX) return cudaErrorInvalidValue;
   const IterPlan p{0, 0, 0};
-  const size_t dyn = (size_t)(csc.rows + csr.rows) * sizeof(double);
-  if (cluster > 1) {
-    const int C = cluster > FB_MAX_CLUSTER ? FB_MAX_CLUSTER : cluster;
+  const int C = cluster > 1 ? (cluster > FB_MAX_CLUSTER ? FB_MAX_CLUSTER : cluster) : 1;
+  // the slots of CTA 0 (the most of any CTA) copied into shared memory, when they fit
+  const int kc = (csc.nslots + C - 1) / C, kr = (csr.nslots + C - 1) / C;
+  const size_t cached = fb_cache_offset(csc.rows + csr.rows) + (size_t)(kc + kr) * SLOT_CACHE_BYTES;
+  const bool cache = slot_cache && cached <= (size_t)FB_DYN_CACHE_MAX;
+  const size_t dyn = cache ? cached : (size_t)(csc.rows + csr.rows) * sizeof(double);
+  if (C > 1) {
     const DualEpi<true, 2> de{sc, v.inst, v.wtab, p, 0, v.lo, v.hi, v.y0, v.y, v.yh, {}, nullptr, 0};
+    const PrimalEpi<true, true, true> pq{sc, v.inst, v.wtab, p, 0, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, v.q, {}, 0};
+    const PrimalEpi<true, false, true> pl{sc, v.inst, v.wtab, p, 0, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, nullptr, {}, 0};
     if (v.q)
-      return launch_cluster(csc, csr, PrimalEpi<true, true, true>{sc, v.inst, v.wtab, p, 0, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, v.q, {}, 0}, de, K, C, dyn, s);
-    return launch_cluster(csc, csr, PrimalEpi<true, false, true>{sc, v.inst, v.wtab, p, 0, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, nullptr, {}, 0}, de, K, C, dyn, s);
+      return cache ? launch_cluster<PrimalEpi<true, true, true>, true>(csc, csr, pq, de, K, C, dyn, kc, kr, s)
+                   : launch_cluster<PrimalEpi<true, true, true>, false>(csc, csr, pq, de, K, C, dyn, kc, kr, s);
+    return cache ? launch_cluster<PrimalEpi<true, false, true>, true>(csc, csr, pl, de, K, C, dyn, kc, kr, s)
+                 : launch_cluster<PrimalEpi<true, false, true>, false>(csc, csr, pl, de, K, C, dyn, kc, kr, s);
   }
   const DualEpi<true, 1> de{sc, v.inst, v.wtab, p, 0, v.lo, v.hi, v.y0, v.y, v.yh, {}, nullptr};
   if (v.q)
-    fused_body_kernel<<<1, FB_TPB, dyn, s>>>(csc, csr, PrimalEpi<true, true>{sc, v.inst, v.wtab, p, 0, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, v.q, {}}, de, K);
-  else
-    fused_body_kernel<<<1, FB_TPB, dyn, s>>>(csc, csr, PrimalEpi<true>{sc, v.inst, v.wtab, p, 0, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, nullptr, {}}, de, K);
-  return cudaGetLastError();
+    return launch_single(csc, csr, PrimalEpi<true, true>{sc, v.inst, v.wtab, p, 0, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, v.q, {}}, de, K, cache, dyn, kc, kr, s);
+  return launch_single(csc, csr, PrimalEpi<true>{sc, v.inst, v.wtab, p, 0, v.c, v.lv, v.uv, v.x0, v.x, v.xbar, v.xh, v.dx, nullptr, {}}, de, K, cache, dyn, kc, kr, s);
 }
 
 // ---------------------------------------------------------------- check reductions

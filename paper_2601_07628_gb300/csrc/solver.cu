@@ -74,6 +74,7 @@ std::map<std::string, Param> default_params() {
       {"fused_body", {1, 0, 1, true}},
       {"fused_max_slots", {40, 1, FUSED_MAX_SLOTS, true}},
       {"fused_cluster", {0, 0, 8, true}},
+      {"fused_slot_cache", {1, 0, 1, true}},
   };
 }
 
@@ -506,7 +507,7 @@ int build_graph(dpdlp* h, int K) {
       if (e == cudaSuccess)
         e = launch_body_fused(h->csc, h->csr, h->v, h->d_sc, K,
                               fused_cluster_ctas(h->csc, h->csr, (int)h->P("fused_cluster")),
-                              h->cap_stream);
+                              (int)h->P("fused_slot_cache"), h->cap_stream);
     } else {
       for (int i = 0; i < K && e == cudaSuccess; ++i) {
         e = launch_primal(h->csc, h->v, h->d_sc, IterPlan{i, 0, 0, pdl}, h->cap_stream);
@@ -575,7 +576,8 @@ int run_host_loop(dpdlp* h) {
     }
     if (use_fused(h)) {
       CK(launch_body_fused(h->csc, h->csr, h->v, h->d_sc, K,
-                           fused_cluster_ctas(h->csc, h->csr, (int)h->P("fused_cluster")), h->stream));
+                           fused_cluster_ctas(h->csc, h->csr, (int)h->P("fused_cluster")),
+                           (int)h->P("fused_slot_cache"), h->stream));
     } else {
       for (int i = 0; i < K; ++i) {
         CK(launch_primal(h->csc, h->v, h->d_sc, IterPlan{i, 0, list, pdl}, h->stream));
@@ -657,6 +659,7 @@ int dpdlp_set_param(dpdlp_t* h, const char* key, double v) {
     return fail(h, DPDLP_ERR_INVALID, k + " must be 2, 4 or 8");
   if ((k == "check_every" || k == "cta_slots_primal" || k == "cta_slots_dual" ||
        k == "fused_body" || k == "fused_max_slots" || k == "fused_cluster" || k == "pdl" ||
+       k == "fused_slot_cache" ||
        k == "list_fraction" || k == "list_few_slots" ||
        k == "list_warps_per_sm") && v != p.value)
     free_graph(h);  // the captured graph holds the launch shapes

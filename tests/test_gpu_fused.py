@@ -89,6 +89,24 @@ def test_fused_body_is_bitwise_the_separate_path(Solver, case, cluster):
     assert [r["restart"] for r in a["trace"]] == [r["restart"] for r in b["trace"]]
 
 
+@pytest.mark.parametrize("cluster", [1, 2, 8])
+@pytest.mark.parametrize("case", ["tiny", "small", "cross", "fp32_values"])
+def test_slot_cache_is_bitwise_the_uncached_body(Solver, case, cluster):
+    """Each block's copy of its slots in shared memory (``fused_slot_cache``, on by default
+    where it fits) changes where the product reads the matrix, not what it adds: bitwise the
+    same results as reading the global slots."""
+    lp = {"tiny": lambda: lpgen.small_random_lp(3, n=250, m=125), "small": lpgen.small_random_lp,
+          "cross": cross_lp, "fp32_values": lpgen.small_random_lp}[case]()
+    params = dict(spmv_fp32=2) if case == "fp32_values" else {}
+    a = run(Solver, lp, 1, 333, fused_cluster=cluster, fused_slot_cache=1, **params)
+    b = run(Solver, lp, 1, 333, fused_cluster=cluster, fused_slot_cache=0, **params)
+    assert a["info"]["fused_body"] == 1 and a["status"] == b["status"]
+    assert np.array_equal(bits(a["x"]), bits(b["x"]))
+    assert np.array_equal(bits(a["y"]), bits(b["y"]))
+    for key in ("iterations", "restarts", "checks", "r_primal", "r_dual", "r_gap", "omega"):
+        assert a["kkt"][key] == b["kkt"][key], key
+
+
 def test_fused_body_long_rows_present(Solver):
     info = run(Solver, cross_lp(), 1, 1)["info"]
     assert info["long_rows"] >= 2 and info["long_cols"] >= 1
