@@ -21,6 +21,11 @@
 //                     CUDA-graph loop condition.
 //  apply_kernel       after a check: restart (anchor and iterate <- PDHG output) or the
 //                     Halpern step of the check iteration.
+//  fused_body_kernel, cluster_body_kernel
+//                     a small LP's whole graph body (K iterations) in one launch of one
+//                     block or of one thread-block cluster, from the same device code.
+//  access_probe_kernel the packed kernels' memory accesses without their arithmetic (the
+//                     roofline's access ceilings).
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
