@@ -66,6 +66,10 @@ def parse():
                    help="warm start: training instances of the transportation family")
     p.add_argument("--ws-test", type=int, default=32, help="warm start: held-out instances")
     p.add_argument("--ws-epochs", type=int, default=8, help="warm start: training epochs")
+    p.add_argument("--gnn-only", type=int, default=0, metavar="N",
+                   help="time N training steps of the warm-start network on the transportation "
+                        "family's graph (seeded targets) and exit: one JSON line of its own "
+                        "(for profiling the network's kernels)")
     p.add_argument("--x3-full", action="store_true",
                    help="learned warm start with 2,000 training and 200 held-out instances of "
                         "the transportation family (default: --ws-train / --ws-test); several minutes")
@@ -278,6 +282,44 @@ def cusparse_reference(lp, dev, kb, reps=30):
     out["note"] = ("torch.sparse_csr_tensor @ dense (cuSPARSE SpMV); the solver's primal / dual "
                    "kernels compute A^T y / A x_bar plus the whole primal / dual step")
     return out
+
+
+def run_gnn_only(args, dev):
+    """The warm-start network's training step alone: ``--gnn-only`` captured steps
+    (``dpdlp_gnn_train_step``: features, forward, backward, Adam) on the 300 x 300
+    transportation family's graph, two instances alternating, seeded random targets, after
+    3 untimed steps."""
+    import numpy as np
+    import torch
+
+    import lpgen
+    from paper_2601_07628_gb300 import gnn
+
+    fam = lpgen.transport_family(seed=4)
+    lps = [lpgen.transport_lp(fam, 100 + i) for i in range(2)]
+    rng = np.random.default_rng(0)
+    xs = [rng.random(lp.n) for lp in lps]
+    ys = [rng.standard_normal(lp.m) for lp in lps]
+    sc = gnn.fit_scales(lps, xs, ys)
+    net = gnn.Network(dev)
+    net.set_params(gnn.init_params(0))
+    net.set_graph(lps[0].n, lps[0].m, lps[0].row_ptr, lps[0].col, lps[0].val)
+    net.device_arrays(True)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(f"cuda:{dev}")
+    data = [(t(fv), t(fc), t(x / sc.x_scale), t(y / sc.y_scale))
+            for lp, x, y in zip(lps, xs, ys) for fv, fc in [gnn.features(lp, sc)]]
+    for step in range(1, 4):
+        net.train_step(*data[step % 2], 1e-3, step)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for step in range(4, 4 + args.gnn_only):
+        net.train_step(*data[step % 2], 1e-3, step, want_loss=False)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / max(args.gnn_only, 1)
+    net.close()
+    print(json.dumps({"gnn_train_step_ms": ms, "steps": args.gnn_only,
+                      "graph": f"transportation 300 x 300 + 20000 side rows (n={lps[0].n:,}, "
+                               f"m={lps[0].m:,}, nnz={lps[0].nnz:,})"}), flush=True)
 
 
 def run_reference(args, world, rank):
@@ -638,6 +680,10 @@ def main():
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream().cuda_stream
     dev = torch.cuda.current_device()
+    if args.gnn_only:
+        if rank == 0:
+            run_gnn_only(args, dev)
+        return
 
     lp = make_lp(args.workload)
     s = Solver(dev)
