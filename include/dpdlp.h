@@ -239,9 +239,9 @@ int dpdlp_set_row_bounds(dpdlp_t* h, const double* lc, const double* uc);
  *   order are those of the separate launches, so results are bitwise the same in every
  *   form; fused_body = 0 always launches the kernels separately.  dpdlp_get_info reports
  *   which form the next solve takes.  fused_slot_cache (1): each block of that form copies
- *   its slots (values, indices, lane metadata) into shared memory once per launch, when
- *   they fit next to the shared copies of x_bar and y (210 KB in all), and every iteration
- *   of the body reads them there; same results.
+ *   its slots (values, indices, lane metadata) and their rows' epilogue inputs into shared
+ *   memory once per launch, when they fit next to the shared copies of x_bar and y (192 KB
+ *   in all), and every iteration of the body reads them there; same results.
  *   pdl (1): the iteration kernels launch as programmatic dependents of the kernel before
  *   them (they load what no kernel writes -- slot descriptors, first index batches -- while
  *   it drains, then wait for it); 0 = plain stream order.  Results do not depend on it.

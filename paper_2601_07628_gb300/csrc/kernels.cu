@@ -422,6 +422,41 @@ struct PrimalEpi {
       if (r < nr) step(r0 + r, sr[0][r], cj[k], lj[k], uj[k], xj[k], aj[k]);
     }
   }
+  // The fused bodies' epilogue: the slot's row inputs from the block's shared copy (field f of
+  // row r at rc[f * fs + r]: c, lv, uv, x0, x, and for a QP the diagonal of Q), the updates
+  // to the global rows r0 + r with step()'s arithmetic; a regular iteration's new x also goes
+  // to the copy, which the next iteration reads.
+  __device__ void apply_rows_copied(int r0, int nr, int lane, const double (*sr)[MAX_SLOT_ROWS],
+                                    double* rc, int fs) {
+    constexpr int R = MAX_SLOT_ROWS / LANES;
+    const bool na = need_anchor();
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int r = lane + k * LANES;
+      if (r < nr) {
+        const int j = r0 + r;
+        const double xj = rc[4 * fs + r], x0j = na ? rc[3 * fs + r] : 0.0;
+        double t = fma(-q.step, rc[r] - sr[0][r], xj);
+        if constexpr (QP) t = t / fma(q.step, rc[5 * fs + r], 1.0);
+        const double xhj = clampd_int(t, rc[fs + r], rc[2 * fs + r]);
+        const double xb = fma(2.0, xhj, -xj);
+        if constexpr (Bcast) st_cluster_all(xbar + j, xb, ncta);
+        else st_keep(xbar + j, xb);
+        if (q.check) {
+          xh[j] = xhj;
+          dx[j] = xj - xhj;
+        } else {
+          double xn = xhj;
+          if (q.halpern) {
+            const double rr = q.gamma_one ? xb : fma(1.0 + q.gamma, xhj, -q.gamma * xj);
+            xn = fma(q.w1, rr, q.w0 * x0j);
+          }
+          st_once(x + j, xn);
+          rc[4 * fs + r] = xn;
+        }
+      }
+    }
+  }
 };
 
 // Dual step per row i, given z = (A x_bar)_i:
@@ -532,6 +567,20 @@ struct DualEpi {
     for (int k = 0; k < R; ++k) {
       const int r = lane + k * LANES;
       if (r < nr) step(r0 + r, sr[0][r], lj[k], hj[k], yj[k], aj[k]);
+    }
+  }
+  // The fused bodies' epilogue: the slot's row inputs from the block's shared copy (lo, hi,
+  // y0 at rc[f * fs + r]) and y from the shared mirror ys, then step().
+  __device__ void apply_rows_copied(int r0, int nr, int lane, const double (*sr)[MAX_SLOT_ROWS],
+                                    double* rc, int fs) {
+    static_assert(Mirror >= 1, "y is read from the shared mirror");
+    constexpr int R = MAX_SLOT_ROWS / LANES;
+    const bool na = need_anchor();
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int r = lane + k * LANES;
+      if (r < nr)
+        step(r0 + r, sr[0][r], rc[r], rc[fs + r], ys[r0 + r], na ? rc[2 * fs + r] : 0.0);
     }
   }
 };
@@ -1281,10 +1330,18 @@ struct SlotCache {
   uint32_t* idx;    // likewise
   LaneMeta* lanes;  // LANES per cached slot
   SlotDesc* desc;
+  // the epilogue's row inputs of the cached slots: field f of row r of cached slot k at
+  // rows[f * fs + k * MAX_SLOT_ROWS + r] (primal: c, lv, uv, x0, x, Q diagonal; dual: lo, hi,
+  // y0); none of them changes inside a body but x, which the epilogue keeps current
+  double* rows;
+  int fs;
 };
-// Bytes of the copies of `slots` slots (values, indices, lane metadata, descriptor).
+// Bytes of the copies of one slot (values, indices, lane metadata, descriptor), and of its
+// rows' epilogue inputs (ROW_FIELDS_PRIMAL / _DUAL fields).
 constexpr size_t SLOT_CACHE_BYTES = SLOT_ITEMS * (sizeof(double) + sizeof(uint32_t)) +
                                     LANES * sizeof(LaneMeta) + sizeof(SlotDesc);
+constexpr int ROW_FIELDS_PRIMAL = 6, ROW_FIELDS_DUAL = 3;
+constexpr size_t ROW_COPY_BYTES = MAX_SLOT_ROWS * sizeof(double);
 // Carves the copies of kc primal and kr dual slots out of shared memory at `base` (16-byte
 // aligned).
 __device__ __forceinline__ void carve_slot_caches(char* base, int kc, int kr, SlotCache& cc,
@@ -1297,6 +1354,23 @@ __device__ __forceinline__ void carve_slot_caches(char* base, int kc, int kr, Sl
   cr.lanes = cc.lanes + (size_t)kc * LANES;
   cc.desc = reinterpret_cast<SlotDesc*>(cr.lanes + (size_t)kr * LANES);
   cr.desc = cc.desc + kc;
+  cc.rows = reinterpret_cast<double*>(cr.desc + kr);
+  cc.fs = kc * MAX_SLOT_ROWS;
+  cr.rows = cc.rows + (size_t)ROW_FIELDS_PRIMAL * cc.fs;
+  cr.fs = kr * MAX_SLOT_ROWS;
+}
+// Every thread of the CTA copies the epilogue inputs `src[0..nf)` of the rows of this CTA's
+// slots of M into c.rows.
+__device__ __forceinline__ void fill_row_copies(const DevPacked& M, const SlotCache& c,
+                                                const double* const* src, int nf, int rank,
+                                                int C) {
+  const int nk = rank < M.nslots ? (M.nslots - rank + C - 1) / C : 0;
+  for (int t = threadIdx.x; t < nk * MAX_SLOT_ROWS; t += blockDim.x) {
+    const int k = t / MAX_SLOT_ROWS, r = t % MAX_SLOT_ROWS;
+    const SlotDesc d = M.slots[rank + C * k];
+    if (r < d.nrows)
+      for (int f = 0; f < nf; ++f) c.rows[(size_t)f * c.fs + t] = src[f][d.row_base + r];
+  }
 }
 // Every thread of the CTA copies (16 bytes at a time) this CTA's slots of M.
 __device__ __forceinline__ void fill_slot_cache(const DevPacked& M, const SlotCache& c, int rank,
@@ -1358,7 +1432,11 @@ __device__ __forceinline__ void body_slots(const DevPacked& M, const SlotCache& 
     }
     __syncwarp();
     epi.prepare(sd.inst);
-    epi.apply_rows(sd.row_base, sd.nrows, lane, srow);
+    if constexpr (Cache)
+      epi.apply_rows_copied(sd.row_base, sd.nrows, lane, srow, cache.rows + (size_t)k * MAX_SLOT_ROWS,
+                            cache.fs);
+    else
+      epi.apply_rows(sd.row_base, sd.nrows, lane, srow);
     __syncwarp();  // the row sums are read before the warp's next slot writes them
   }
 }
@@ -1439,6 +1517,10 @@ __global__ void __launch_bounds__(FB_TPB, 1)
     carve_slot_caches(reinterpret_cast<char*>(fb_vecs) + fb_cache_offset(m + n), kc, kr, cc, cr);
     fill_slot_cache(Mc, cc, 0, 1);
     fill_slot_cache(Mr, cr, 0, 1);
+    const double* const ps[ROW_FIELDS_PRIMAL] = {pe_in.c, pe_in.lv, pe_in.uv, pe_in.x0, pe_in.x, pe_in.qd};
+    const double* const ds[ROW_FIELDS_DUAL] = {de_in.lo, de_in.hi, de_in.y0};
+    fill_row_copies(Mc, cc, ps, pe_in.qd ? 6 : 5, 0, 1);
+    fill_row_copies(Mr, cr, ds, ROW_FIELDS_DUAL, 0, 1);
   }
   for (int i = threadIdx.x; i < m; i += FB_TPB) ys[i] = de_in.y[i];
   __syncthreads();
@@ -1534,6 +1616,10 @@ __global__ void __launch_bounds__(FB_TPB, 1)
     carve_slot_caches(reinterpret_cast<char*>(fb_vecs) + fb_cache_offset(m + n), kc, kr, cc, cr);
     fill_slot_cache(Mc, cc, rank, C);
     fill_slot_cache(Mr, cr, rank, C);
+    const double* const ps[ROW_FIELDS_PRIMAL] = {pe_in.c, pe_in.lv, pe_in.uv, pe_in.x0, pe_in.x, pe_in.qd};
+    const double* const ds[ROW_FIELDS_DUAL] = {de_in.lo, de_in.hi, de_in.y0};
+    fill_row_copies(Mc, cc, ps, pe_in.qd ? 6 : 5, rank, C);
+    fill_row_copies(Mr, cr, ds, ROW_FIELDS_DUAL, rank, C);
   }
   for (int i = threadIdx.x; i < m; i += FB_TPB) ys[i] = de_in.y[i];
   cl.sync();  // every CTA of the cluster runs before any stores into another's copies
@@ -1655,7 +1741,8 @@ cudaError_t launch_body_fused(const DevPacked& csc, const DevPacked& csr, const 
   const int C = cluster > 1 ? (cluster > FB_MAX_CLUSTER ? FB_MAX_CLUSTER : cluster) : 1;
   // the slots of CTA 0 (the most of any CTA) copied into shared memory, when they fit
   const int kc = (csc.nslots + C - 1) / C, kr = (csr.nslots + C - 1) / C;
-  const size_t cached = fb_cache_offset(csc.rows + csr.rows) + (size_t)(kc + kr) * SLOT_CACHE_BYTES;
+  const size_t cached = fb_cache_offset(csc.rows + csr.rows) + (size_t)(kc + kr) * SLOT_CACHE_BYTES +
+                        (size_t)(ROW_FIELDS_PRIMAL * kc + ROW_FIELDS_DUAL * kr) * ROW_COPY_BYTES;
   const bool cache = slot_cache && cached <= (size_t)FB_DYN_CACHE_MAX;
   const size_t dyn = cache ? cached : (size_t)(csc.rows + csr.rows) * sizeof(double);
   if (C > 1) {
