@@ -227,7 +227,7 @@ int dpdlp_set_row_bounds(dpdlp_t* h, const double* lc, const double* uc);
  *   cta_slots_primal, cta_slots_dual (4): warp slots per thread block of the primal (A^T y)
  *   and dual (A x_bar) iteration kernels, 2, 4 or 8 (64, 128 or 256 threads); a launch
  *   shape only, results do not depend on it (set by the autotuner).
- *   fused_body (1), fused_max_slots (40, at most 64), fused_cluster (0): a single LP whose
+ *   fused_body (1), fused_max_slots (48, at most 64), fused_cluster (0): a single LP whose
  *   packed copies have at most fused_max_slots warp slots each (a slot holds 1,024 stored
  *   nonzeros) runs each graph body -- check_every iterations -- as one launch instead of two
  *   or three launches per iteration: one thread block with block barriers between the

@@ -1690,11 +1690,13 @@ cudaError_t fused_body_prepare() {
   return e;
 }
 
-// Automatic size, measured on one GB300 (us per iteration, n = 2m, 8 nonzeros per column):
-// one CTA is fastest up to about 6 slots per copy (latency-bound: 8.1 us at 2 slots against
-// 11.3 separate); beyond that one SM's FP64 rate bounds it and a cluster with about two
-// slots per CTA wins narrowly (16 slots: 11.8 against 12.3 separate; 32: 15.3 against
-// 16.2); a cluster barrier costs about 2 us, so at 64 slots the separate launches win.
+// Automatic size, measured on one GB300 with the shared-memory copies (us per iteration,
+// n = 2m, 8 nonzeros per column): one CTA is fastest up to about 6 slots per copy
+// (latency-bound: 7.9 us at 2-3 slots, 9.2 for two CTAs, 11.8 separate); beyond that one
+// SM's FP64 rate bounds it and a cluster with about two slots per CTA wins (8 slots: 10.2,
+// 10.0 with two CTAs, 12.6 separate; 16: 9.5 against 12.3; 32: 10.5 against 13.0); its two
+// barriers per iteration cost about 3.5 us, so from about 50 slots the separate launches
+// win (48: 13.1 against 13.5; 64: 14.6 against 13.7).
 int fused_cluster_ctas(const DevPacked& csc, const DevPacked& csr, int requested) {
   if (requested >= 1) return requested > FB_MAX_CLUSTER ? FB_MAX_CLUSTER : requested;
   const int slots = csc.nslots > csr.nslots ? csc.nslots : csr.nslots;

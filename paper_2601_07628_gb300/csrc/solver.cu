@@ -72,7 +72,7 @@ std::map<std::string, Param> default_params() {
       {"cta_slots_primal", {4, 2, 8, true}},
       {"cta_slots_dual", {4, 2, 8, true}},
       {"fused_body", {1, 0, 1, true}},
-      {"fused_max_slots", {40, 1, FUSED_MAX_SLOTS, true}},
+      {"fused_max_slots", {48, 1, FUSED_MAX_SLOTS, true}},
       {"fused_cluster", {0, 0, 8, true}},
       {"fused_slot_cache", {1, 0, 1, true}},
   };
@@ -466,8 +466,8 @@ int init_fresh(dpdlp* h) {
 
 // A small single LP runs each graph body as one fused launch (same results, fewer launches):
 // one thread block up to 6 slots per copy, a thread-block cluster beyond (fused_cluster_ctas);
-// measured faster than the separate launches up to about 40 slots per copy, hence
-// fused_max_slots = 40 by default.
+// measured faster than the separate launches up to about 50 slots per copy (48: 13.1 against
+// 13.5 us per iteration; 64: 14.6 against 13.7), hence fused_max_slots = 48 by default.
 bool use_fused(const dpdlp* h) {
   return h->P("fused_body") != 0.0 &&
          fused_body_fits(h->csc, h->csr, h->ninst, (int)h->P("fused_max_slots"));
