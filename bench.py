@@ -107,10 +107,10 @@ def peaks():
 
 
 def _code_only(text):
-    """C++ source without comments and blank lines (string literals are left alone: the
-    kernel sources hold no comment markers inside them)."""
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    lines = (re.sub(r"//.*", "", line).rstrip() for line in text.splitlines())
+    """C++ source without comments, blank lines and whitespace differences (string literals
+    are left alone: the kernel sources hold no comment markers inside them)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    lines = (" ".join(re.sub(r"//.*", "", line).split()) for line in text.splitlines())
     return "\n".join(line for line in lines if line)
 
 

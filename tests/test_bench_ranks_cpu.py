@@ -89,3 +89,15 @@ def test_reference_arm_prints_the_contract_line():
     assert d["e2e"] == {"value": d["value"], "unit": "iter/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+
+
+def test_kernel_source_hash_ignores_comments():
+    """The DRAM traffic recorded from ncu is keyed to the kernels' code: comments and blank
+    lines do not change the key, code does."""
+    import bench
+
+    a = "int f(int x) {  // one\n  /* two\n three */ return x + 1;\n\n}\n"
+    b = "int f(int x) {\n  return x + 1;\n}\n"
+    assert bench._code_only(a) == bench._code_only(b)
+    assert bench._code_only(a) != bench._code_only(b.replace("+ 1", "+ 2"))
+    assert len(bench.kernel_source_hash()) == 16
