@@ -343,9 +343,9 @@ int dpdlp_get_info(dpdlp_t* h, dpdlp_info_t* out);
  * concurrently on the GPU (different streams without ordering) race and must not overlap;
  * each call rewrites every slot it reads, so nothing needs clearing between calls.  The
  * first call on a device looks up the array's device address (once per device, with that
- * device current) and keeps it for the life of the process; make that first call before
- * any stream capture.  A device reset (cudaDeviceReset) unloads the array and leaves the
- * kept address stale: do not call this entry point on a device after resetting it.
+ * device current) and keeps it for the life of the process.  A device reset
+ * (cudaDeviceReset) unloads the array and leaves the kept address stale: do not call this
+ * entry point on a device after resetting it.
  * Limits: nnz <= 2^30 (DPDLP_ERR_TOO_LARGE beyond it); negative sizes or NULL pointers:
  * DPDLP_ERR_INVALID; a failed launch or lookup: DPDLP_ERR_CUDA.  Results are deterministic
  * (fixed summation order) and agree with dpdlp_apply_A to rounding. */
