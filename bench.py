@@ -366,8 +366,11 @@ def run_reference(args, world, rank):
 
 
 def time_to_tol(s, tol, max_iter, fp32_mode=0):
-    """Fresh solve to ``tol`` on a loaded handle (power iteration and graph build done by a
-    64-iteration solve before the timed one)."""
+    """Fresh solve to ``tol`` from the default start (x = proj_X(0), y = 0) on a loaded
+    handle (power iteration and graph build done by a 64-iteration solve before the timed
+    one).  A start point set earlier on the handle stays set until cleared, so it is
+    cleared here."""
+    s.set_start(None, None)
     s.set_param("resume", 0)
     s.set_param("spmv_fp32", fp32_mode)
     s.solve(tol, 64)

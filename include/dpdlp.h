@@ -261,7 +261,9 @@ int dpdlp_set_param(dpdlp_t* h, const char* key, double v);
 int dpdlp_get_param(const dpdlp_t* h, const char* key, double* v);
 
 /* Warm start: x0[n], y0[m] (host or device per ptr_mode_device; either may be NULL for the
- * default x = proj_X(0), y = 0).  Used by the next non-resumed solve. */
+ * default x = proj_X(0), y = 0).  The start stays set: every later solve that starts fresh
+ * (not resumed) begins there, until the next dpdlp_set_start replaces it (NULL, NULL
+ * restores the default start) or an LP is loaded. */
 int dpdlp_set_start(dpdlp_t* h, const double* x0, const double* y0);
 
 /* Run PDHG until max(r_primal, r_dual, r_gap) <= tol at a check, or until the total

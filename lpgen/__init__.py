@@ -137,8 +137,11 @@ def small_random_lp(seed: int = 0, n: int = 2000, m: int = 1000, nnz_per_col: in
     if n_eq is None:
         n_eq = (m * 6) // 10
     k = min(nnz_per_col, m)
-    rows = np.argpartition(rng.random((n, m)), k - 1, axis=1)[:, :k].reshape(-1) if m > 0 \
-        else np.zeros(0, dtype=np.int64)
+    # the k rows of smallest key per column, in increasing row order: argpartition leaves
+    # the order of the selected entries to the implementation (it differs between numpy's
+    # SIMD and generic selection), and the values below are assigned in this order
+    rows = np.sort(np.argpartition(rng.random((n, m)), k - 1, axis=1)[:, :k], axis=1).reshape(-1) \
+        if m > 0 else np.zeros(0, dtype=np.int64)
     cols = np.repeat(np.arange(n), k) if m > 0 else np.zeros(0, dtype=np.int64)
     vals = rng.standard_normal(rows.shape[0])
     row_ptr, col, val = _csr_from_coo(m, n, rows.astype(np.int64), cols.astype(np.int64), vals)

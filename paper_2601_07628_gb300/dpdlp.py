@@ -328,6 +328,8 @@ class Solver:
         return v.value
 
     def set_start(self, x0=None, y0=None):
+        """Start point of every later fresh solve until replaced; ``set_start()`` restores
+        the default start (x = proj_X(0), y = 0)."""
         dev = self._mode(x0, y0)
         if not dev:
             x0 = None if x0 is None else _host_f64(x0, self.n)

@@ -7,6 +7,16 @@ The parity bar compares the GPU's iterates with the oracle's two ways:
 """
 import numpy as np
 
+# KKT values (relative residuals and gap) are compared at 1e-6 relative, or within KKT_ABS
+# absolutely.  The gap |obj_p - obj_d| / (1 + max |obj|) is a difference of two objectives,
+# each a sum of n (or m) products that the two sides add in different orders: each sum is
+# off by up to about n u sum|terms| (u = 1.1e-16), which at these sizes (n up to a few
+# thousand, sum|terms| a few times |obj|) is 1e-13 to 1e-12 of 1 + max |obj|.  Once the
+# gap itself is near 1e-8 that rounding is all that separates the two sides, so the
+# relative bar alone would demand more than FP64 gives; the residual norms are bounded the
+# same way.
+KKT_ABS = 1e-12
+
 
 def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))

@@ -148,8 +148,8 @@ def test_large_lp_does_not_fuse(Solver):
 
 
 def test_default_threshold(Solver):
-    """By default LPs with at most 40 slots per packed copy take the fused form (one block up
-    to 6 slots, a cluster beyond); larger ones launch separately."""
+    """By default LPs with at most 48 slots per packed copy (``fused_max_slots``) take the
+    fused form (one block up to 6 slots, a cluster beyond); larger ones launch separately."""
     tiny = lpgen.small_random_lp(7, n=250, m=125)  # 2 slots per copy
     small = lpgen.small_random_lp(0)  # 16 slots per copy
     big = lpgen.small_random_lp(1, n=8000, m=4000)  # 64 slots per copy

@@ -10,7 +10,7 @@ import pytest
 
 import lpgen
 from oracle import pdhg as O
-from parity_util import assert_xy_parity, rel
+from parity_util import KKT_ABS, assert_xy_parity, rel
 from oracle import precond as P
 
 pytestmark = pytest.mark.gpu
@@ -46,7 +46,7 @@ def test_precond_matches_oracle(Solver, T):
     assert_xy_parity(x, y, res.x, res.y, 1e-9)
     k = s.kkt()
     for key in ("r_primal", "r_dual", "r_gap", "obj_p", "obj_d"):
-        assert k[key] == pytest.approx(res.kkt[key], rel=1e-6, abs=1e-14), key
+        assert k[key] == pytest.approx(res.kkt[key], rel=1e-6, abs=KKT_ABS), key
     s.close()
 
 

@@ -11,7 +11,7 @@ import pytest
 
 import lpgen
 from oracle import pdhg as O
-from parity_util import assert_xy_parity, rel
+from parity_util import KKT_ABS, assert_xy_parity, rel
 from oracle import precond as P
 
 pytestmark = pytest.mark.gpu
@@ -53,7 +53,7 @@ def test_qp_matches_oracle(Solver, case, T):
     assert_xy_parity(x, y, res.x, res.y, 1e-9)
     k = s.kkt()
     for key in ("r_primal", "r_dual", "r_gap", "obj_p", "obj_d"):
-        assert k[key] == pytest.approx(res.kkt[key], rel=1e-6, abs=1e-13), key
+        assert k[key] == pytest.approx(res.kkt[key], rel=1e-6, abs=KKT_ABS), key
     s.close()
 
 
