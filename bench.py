@@ -387,6 +387,28 @@ def time_to_tol(s, tol, max_iter, fp32_mode=0):
             "fp64_from_iteration": switch}
 
 
+def solution_and_objective(s):
+    import numpy as np
+
+    x, y = s.solution()
+    return np.array(x, copy=True), np.array(y, copy=True), s.kkt()["obj_p"]
+
+
+def error_vs_fp64(mixed, fp64, p_star):
+    """How far a mixed-precision answer lies from the FP64 answer to the same tolerance
+    (the FP64 path is the one that matches the oracle iterate for iterate): relative
+    2-norm distances of x and y, and each objective's error against the planted optimum
+    value p*, relative to 1 + |p*|."""
+    import numpy as np
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    return {"x_rel": rel(mixed[0], fp64[0]), "y_rel": rel(mixed[1], fp64[1]),
+            "obj_p_err_mixed": abs(mixed[2] - p_star) / (1.0 + abs(p_star)),
+            "obj_p_err_fp64": abs(fp64[2] - p_star) / (1.0 + abs(p_star))}
+
+
 def _uneven(args):
     import lpgen
 
@@ -888,10 +910,15 @@ def main():
 
         sm = Solver(dev)
         sm.set_stream(stream)
-        sm.load(lpgen.small_random_lp(0))
+        slp = lpgen.small_random_lp(0)
+        sm.load(slp)
         for tol in (1e-4, 1e-8):
+            answers = []
             for mode in (0, 1):
                 ttt[f"small_lp_{tol:.0e}_{['fp64', 'mixed_fp32'][mode]}"] = time_to_tol(sm, tol, 1_000_000, mode)
+                answers.append(solution_and_objective(sm))
+            ttt[f"small_lp_{tol:.0e}_mixed_fp32"]["error_vs_fp64"] = error_vs_fp64(answers[1], answers[0],
+                                                                                   slp.p_star)
         sm.close()
         # a tiny LP (n=250, m=125, 2 warp slots per packed copy) takes the fused body (one
         # launch per 64 iterations); the same solve with separate primal / dual launches
