@@ -299,9 +299,11 @@ int dpdlp_set_state(dpdlp_t* h, const double* x, const double* y, const double* 
                     const double* y0, const dpdlp_scalar_state_t* s);
 
 /* Parity mode: restart decisions of checks 0..count-1 (0 none, 1..3 restart kinds) are
- * taken from `kinds` (HOST) instead of the restart test; count = 0 switches it off.  For a
- * batch of N instances count = N * L and kinds[i * L + c] is instance i's decision at
- * check c (count not a multiple of N: DPDLP_ERR_INVALID). */
+ * taken from `kinds` (HOST) instead of the restart test; checks past the schedule make no
+ * restart.  The schedule stays in force for every later solve until count = 0 switches it
+ * off (a fresh solve counts its checks from 0, a resumed one continues the count).  For a batch of N instances
+ * count = N * L and kinds[i * L + c] is instance i's decision at check c (count not a
+ * multiple of N: DPDLP_ERR_INVALID). */
 int dpdlp_set_schedule(dpdlp_t* h, const int8_t* kinds, int32_t count);
 
 /* Operator application with the solver's SpMV kernels: out[m] = A x[n], out[n] = A^T y[m]. */
