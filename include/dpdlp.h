@@ -156,11 +156,12 @@ int dpdlp_set_stream(dpdlp_t* h, void* cuda_stream);
  *                       2: lc = b, uc = +inf ('>=').  Both may be NULL (rows free until
  *                       dpdlp_set_row_bounds).
  *   lv[n], uv[n]        variable bounds, -INFINITY / +INFINITY allowed, lv <= uv
- * Validates the input (DPDLP_ERR_INVALID on failure; n and m must be below 2^30), then on
- * the host applies the optional block-wise random permutation (Section 4.2), builds the CSC
- * copy of A, packs the rows of both copies into warp lanes (nonzero-aware partitioning,
- * Section 4.3, at lane granularity), and copies everything to the device.  Replaces any LP loaded before
- * and resets the solver state. */
+ * Validates the input (DPDLP_ERR_INVALID on failure; 1 <= n and 0 <= m, both below 2^30:
+ * an LP needs a variable, while m = 0 leaves only the bounds), then on the host applies
+ * the optional block-wise random permutation (Section 4.2), builds the CSC copy of A,
+ * packs the rows of both copies into warp lanes (nonzero-aware partitioning, Section 4.3,
+ * at lane granularity), and copies everything to the device.  Replaces any LP loaded
+ * before and resets the solver state. */
 int dpdlp_load_lp(dpdlp_t* h, int32_t n, int32_t m, const double* c, const int64_t* row_ptr,
                   const int32_t* col_idx, const double* val, const double* b,
                   const double* lv, const double* uv, const int8_t* ctype);
@@ -170,8 +171,9 @@ int dpdlp_load_lp(dpdlp_t* h, int32_t n, int32_t m, const double* c, const int64
  * arguments are those of dpdlp_load_lp for the block-diagonal LP that stacks the
  * instances, plus HOST ranges row_off[count+1] and col_off[count+1]: instance i owns rows
  * [row_off[i], row_off[i+1]) and columns [col_off[i], col_off[i+1]) (row_off[0] =
- * col_off[0] = 0, non-decreasing, row_off[count] = m, col_off[count] = n), and every
- * nonzero of its rows must lie in its columns (else DPDLP_ERR_INVALID).  Each instance
+ * col_off[0] = 0, row_off non-decreasing, col_off increasing: every instance has at
+ * least one variable, row_off[count] = m, col_off[count] = n), and every nonzero of its
+ * rows must lie in its columns (else DPDLP_ERR_INVALID).  Each instance
  * gets its own step size (power iteration on its own block), primal weight, restart
  * epoch, PID state, mixed-precision switch and status; the iteration counter, the check
  * period and the parameters are shared.  An instance that converges stops iterating (its

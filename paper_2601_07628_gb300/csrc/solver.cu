@@ -703,9 +703,14 @@ int load_impl(dpdlp* h, int32_t count, const int32_t* row_off, const int32_t* co
   if (count < 1 || !row_off || !col_off) return fail(h, DPDLP_ERR_INVALID, "invalid instance count or ranges");
   if (row_off[0] != 0 || col_off[0] != 0 || row_off[count] != m || col_off[count] != n)
     return fail(h, DPDLP_ERR_INVALID, "instance ranges must start at 0 and end at m and n");
-  for (int i = 0; i < count; ++i)
+  for (int i = 0; i < count; ++i) {
     if (row_off[i + 1] < row_off[i] || col_off[i + 1] < col_off[i])
       return fail(h, DPDLP_ERR_INVALID, "instance ranges must be non-decreasing");
+    // An empty row is stored as one zero entry gathering column 0 of its instance, which
+    // must exist (in the fused body's shared copies as much as in global memory).
+    if (col_off[i + 1] == col_off[i])
+      return fail(h, DPDLP_ERR_INVALID, "an LP (each instance of a batch) needs at least one variable");
+  }
   std::string e = validate_csr(m, n, row_ptr, col_idx, val);
   if (!e.empty()) return fail(h, DPDLP_ERR_INVALID, e);
   for (int i = 0; i < count; ++i)

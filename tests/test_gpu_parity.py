@@ -337,6 +337,14 @@ def test_invalid_inputs_are_rejected(Solver):
     bad.val[3] = np.nan
     with pytest.raises(DpdlpError):
         s.load(bad)
+    novar = lpgen.LP(0, 3, np.zeros(0), np.zeros(4, np.int64), np.zeros(0, np.int32), np.zeros(0),
+                     np.zeros(3), np.zeros(3), np.zeros(0), np.zeros(0), name="no variables")
+    with pytest.raises(DpdlpError) as e:  # an LP needs a variable: rejected before any upload
+        s.load(novar)
+    assert e.value.code == -1
+    with pytest.raises(DpdlpError) as e:  # so does each instance of a batch
+        s.load_batch([lp, novar])
+    assert e.value.code == -1
     with pytest.raises(DpdlpError):
         s.set_param("no_such_key", 1.0)
     with pytest.raises(DpdlpError):
