@@ -256,7 +256,8 @@ int dpdlp_set_row_bounds(dpdlp_t* h, const double* lc, const double* uc);
  *   launching a full grid each iteration).  Launch choices only; the first two are set by
  *   the autotuner.
  * Load-time keys (block_permute, perm_block, perm_seed, precond, ruiz_passes,
- * pock_chambolle) take effect at the next dpdlp_load_lp / dpdlp_load_batch.  Unknown key or out-of-range value: DPDLP_ERR_INVALID. */
+ * pock_chambolle, trace_capacity) take effect at the next dpdlp_load_lp /
+ * dpdlp_load_batch.  Unknown key or out-of-range value: DPDLP_ERR_INVALID. */
 int dpdlp_set_param(dpdlp_t* h, const char* key, double v);
 
 /* Read a parameter's current value. */
