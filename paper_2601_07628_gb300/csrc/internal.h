@@ -219,6 +219,10 @@ void build_packed(int rows, int cols, const std::vector<int64_t>& ptr,
                   const std::vector<int32_t>& idx, const std::vector<double>& val,
                   const PackPlan& plan, const std::vector<int32_t>& col_new_of_old,
                   HostPacked& out);
+// A batch: padding and empty rows of instance i's slots gather offsets[i], the instance's
+// own first entry of the gathered vector (its entry 0 when solved alone), not entry 0 of
+// the stack, which belongs to instance 0.
+void own_instance_zero_gathers(HostPacked& packed, const std::vector<int32_t>& offsets);
 
 // ---------------------------------------------------------------- kernel launchers
 struct IterPlan {

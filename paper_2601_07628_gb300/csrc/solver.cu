@@ -686,25 +686,6 @@ int dpdlp_get_param(const dpdlp_t* h, const char* key, double* v) {
 
 namespace {
 
-// Padding entries and the stored zero of an empty row gather entry 0 of the other
-// orientation's vector (value 0 times a finite entry).  In a batch entry 0 belongs to
-// instance 0, so a non-finite iterate there would reach the other instances' rows through
-// 0 * inf = NaN.  Each slot of instance i instead gathers offsets[i], the instance's own
-// first entry: its entry 0 in a solve of its own, so the batch still mirrors that solve.
-// An entry of such a slot with index 0 is never a real nonzero unless offsets[i] is 0
-// (load checks that nonzeros lie in their instance's range), when nothing changes.  An
-// instance with no entries in that orientation keeps index 0.
-void own_instance_zero_gathers(HostPacked& H, const std::vector<int32_t>& offsets) {
-  for (int s = 0; s < H.nslots; ++s) {
-    const int inst = H.slots[s].inst;
-    if (offsets[inst + 1] == offsets[inst]) continue;
-    const uint32_t base = (uint32_t)offsets[inst];
-    uint32_t* si = H.idx.data() + (size_t)s * SLOT_ITEMS;
-    for (int k = 0; k < SLOT_ITEMS; ++k)
-      if ((si[k] & IDX_MASK) == 0) si[k] |= base;
-  }
-}
-
 // Loads `count` instances: instance i owns rows [row_off[i], row_off[i+1]) and columns
 // [col_off[i], col_off[i+1]) of one block-diagonal matrix.
 int load_impl(dpdlp* h, int32_t count, const int32_t* row_off, const int32_t* col_off,

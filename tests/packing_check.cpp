@@ -38,15 +38,27 @@ int main(int argc, char** argv) {
   if (cols && std::fread(x.data(), 8, cols, f) != (size_t)cols) return fail("x");
   std::fclose(f);
 
+  auto parse_offsets = [](const char* q) {
+    std::vector<int32_t> o;
+    while (*q) {
+      o.push_back((int32_t)std::strtol(q, (char**)&q, 10));
+      if (*q == ',') ++q;
+    }
+    return o;
+  };
   // optional argv[2]: instance row offsets (comma separated, first 0, last rows) -> batch
   std::vector<int32_t> offsets;
   if (argc > 2) {
-    const char* q = argv[2];
-    while (*q) {
-      offsets.push_back((int32_t)std::strtol(q, (char**)&q, 10));
-      if (*q == ',') ++q;
-    }
+    offsets = parse_offsets(argv[2]);
     if (offsets.size() < 2 || offsets.front() != 0 || offsets.back() != rows) return fail("offsets");
+  }
+  // optional argv[3] (a batch): the instances' column offsets; padding and empty rows then
+  // gather their own instance's first column, as the solver packs a batch
+  std::vector<int32_t> col_offsets;
+  if (argc > 3) {
+    col_offsets = parse_offsets(argv[3]);
+    if (col_offsets.size() != offsets.size() || col_offsets.front() != 0 || col_offsets.back() != cols)
+      return fail("column offsets");
   }
   PackPlan P;
   if (offsets.empty()) plan_packing(rows, ptr, P);
@@ -55,6 +67,7 @@ int main(int argc, char** argv) {
   for (int j = 0; j < cols; ++j) ident[j] = j;
   HostPacked H;
   build_packed(rows, cols, ptr, idx, val, P, ident, H);
+  if (!col_offsets.empty()) own_instance_zero_gathers(H, col_offsets);
 
   // permutation
   std::vector<int> seen(rows, 0);
@@ -107,6 +120,17 @@ int main(int argc, char** argv) {
     for (int i = 1; i < H.nlong; ++i)
       if (H.long_ptr[i + 1] - H.long_ptr[i] > H.long_ptr[i] - H.long_ptr[i - 1])
         return fail("long rows not longest first", i, 0);
+    // every stored entry of an instance's slots, padding and empty rows included, gathers
+    // a column of that instance (index 0 for an instance without columns)
+    for (int s = 0; s < H.nslots && !col_offsets.empty(); ++s) {
+      const int i = H.slots[s].inst;
+      const bool own = col_offsets[i + 1] > col_offsets[i];
+      for (int k = 0; k < SLOT_ITEMS; ++k) {
+        const int c = (int)(H.idx[(size_t)s * SLOT_ITEMS + k] & IDX_MASK);
+        if (own ? (c < col_offsets[i] || c >= col_offsets[i + 1]) : c != 0)
+          return fail("gather outside its instance", s, c);
+      }
+    }
   }
   // replay the lanes
   std::vector<double> out(rows, NAN), piece(H.npieces, NAN);

@@ -31,7 +31,7 @@ def checker(tmp_path_factory):
     return exe, d
 
 
-def run(checker, row_ptr, col, val, ncols, seed=0, offsets=None, threads=None):
+def run(checker, row_ptr, col, val, ncols, seed=0, offsets=None, threads=None, col_offsets=None):
     exe, d = checker
     rows = len(row_ptr) - 1
     x = np.random.default_rng(seed).standard_normal(ncols)
@@ -43,6 +43,7 @@ def run(checker, row_ptr, col, val, ncols, seed=0, offsets=None, threads=None):
         np.asarray(val, dtype=np.float64).tofile(f)
         x.tofile(f)
     cmd = [exe, path] + ([",".join(str(int(o)) for o in offsets)] if offsets is not None else [])
+    cmd += [",".join(str(int(o)) for o in col_offsets)] if col_offsets is not None else []
     env = dict(os.environ)
     if threads is not None:
         env["DPDLP_HOST_THREADS"] = str(threads)
@@ -105,6 +106,13 @@ def test_batch_packing(checker):
     offs = np.concatenate([[0], np.cumsum([p.m for p in parts])])
     st = run(checker, B.indptr, B.indices, B.data, B.shape[1], seed=7, offsets=offs)
     assert int(st["nlong"]) > 0
+    # as the solver packs a batch: padding and empty rows gather their own instance's
+    # first column (the checker verifies every stored index lies in its instance's
+    # columns), and the products are unchanged
+    coffs = np.concatenate([[0], np.cumsum([p.n for p in parts])])
+    st2 = run(checker, B.indptr, B.indices, B.data, B.shape[1], seed=7, offsets=offs,
+              col_offsets=coffs)
+    assert st2["nlong"] == st["nlong"]
 
 
 def test_cross_stress_fits_the_fused_body(checker):
