@@ -58,7 +58,7 @@ def assert_parity(ores, x, y, tol=TOL):
 
 
 # --------------------------------------------------------------------------- small LP
-@pytest.mark.parametrize("T", [1, 2, 63, 64, 65, 200, 1000])
+@pytest.mark.parametrize("T", [1, 2, 63, 64, 65, 200, 1000, 5000])
 def test_small_lp_fixed_iterations(Solver, T):
     lp = lpgen.small_random_lp(0)
     ores, s, status, x, y = run_pair(Solver, lp, T)
