@@ -169,6 +169,19 @@ int dalloc(dpdlp* h, T** p, size_t count) {
   return 0;
 }
 
+// Releases one buffer of the handle's allocations; the caller has drained the stream and
+// no captured graph refers to it.
+void dfree(dpdlp* h, void* p) {
+  for (size_t k = 0; k < h->allocs.size(); ++k) {
+    if (h->allocs[k].first != p) continue;
+    if (h->release_fn) h->release_fn(p, h->allocs[k].second, h->alloc_ctx);
+    else cudaFree(p);
+    h->dev_bytes -= (int64_t)h->allocs[k].second;
+    h->allocs.erase(h->allocs.begin() + (std::ptrdiff_t)k);
+    return;
+  }
+}
+
 void free_graph(dpdlp* h) {
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->graph) cudaGraphDestroy(h->graph);
@@ -1278,12 +1291,15 @@ int dpdlp_set_schedule(dpdlp_t* h, const int8_t* kinds, int32_t count) {
   for (int i = 0; i < count; ++i)
     if (kinds[i] < 0 || kinds[i] > 3) return fail(h, DPDLP_ERR_INVALID, "restart kind must be 0..3");
   CK(cudaStreamSynchronize(h->stream));
-  // reallocate the schedule buffer (it is not part of the captured graph's pointers
-  // except through DevVecs, so the graph is rebuilt)
+  // a new schedule buffer replaces the old one; the captured graph holds the old pointer
+  // (through DevVecs), so it is rebuilt
   free_graph(h);
   int rc;
-  if ((rc = dalloc(h, &h->v.sched, count > 0 ? count : 1))) return rc;
-  if (count > 0) CK(cudaMemcpy(h->v.sched, kinds, count, cudaMemcpyHostToDevice));
+  int8_t* fresh = nullptr;
+  if ((rc = dalloc(h, &fresh, count > 0 ? count : 1))) return rc;
+  if (count > 0) CK(cudaMemcpy(fresh, kinds, count, cudaMemcpyHostToDevice));
+  dfree(h, h->v.sched);
+  h->v.sched = fresh;
   h->h_sc.sched_len = count / h->ninst;  // per instance: kinds[i * len + check]
   return 0;
 }

@@ -235,6 +235,24 @@ def test_fresh_solve_on_a_used_handle_is_a_new_handle(Solver):
     used.close()
 
 
+def test_schedule_replacement_frees_the_old_buffer(Solver):
+    """Each dpdlp_set_schedule replaces the device buffer of the previous schedule: the
+    handle's device memory stays the same over many calls, and the last schedule is the
+    one in force."""
+    lp = lpgen.small_random_lp(3, n=200, m=100)
+    s = Solver()
+    s.load(lp)
+    s.set_schedule([0, 3, 0])
+    before = s.info()["device_bytes"]
+    for _ in range(50):
+        s.set_schedule([0, 3, 0])
+    assert s.info()["device_bytes"] == before
+    s.set_schedule([3, 0, 0, 3])
+    s.solve(0.0, 4 * 64)
+    assert [r["restart"] for r in s.trace()] == [3, 0, 0, 3]
+    s.close()
+
+
 def test_checkpoint_resume_is_exact(Solver):
     lp = lpgen.small_random_lp(7, n=1000, m=500)
     a = Solver()
