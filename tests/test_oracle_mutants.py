@@ -210,3 +210,90 @@ def test_mutant_is_caught(name, monkeypatch):
             caught = (getattr(check, "__name__", "check"), type(e).__name__)
             break
     assert caught, f"no pin caught the planted mistake: {name}"
+
+
+# ----------------------------------------------------------------------------- diagonal QP
+# Plausible slips in the QP variant (Section "Extensions to Diagonal QPs"), each caught by
+# one of the QP pins of ``test_qp_oracle.py`` (the prox step by hand, the separable box QP's
+# closed form, the KKT values at an equality QP's optimum, ...).
+import test_qp_oracle as qpins  # noqa: E402
+
+QP_CHECKS = [qpins.test_prox_step_by_hand, qpins.test_separable_box_qp_closed_form,
+             qpins.test_equality_qp_matches_kkt_system, qpins.test_bounded_qp_matches_slsqp]
+
+
+def _qp_step_variant(tau_in_prox=True, clamp_first=False):
+    def f(lp, x, y, tau, sigma):
+        g = lp.c - lp.ATy(y)
+        if lp.q is None:
+            xh = O.proj_X(x - tau * g, lp.lv, lp.uv)
+        else:
+            den = 1.0 + (tau if tau_in_prox else 1.0) * lp.q
+            xh = (O.proj_X(x - tau * g, lp.lv, lp.uv) / den if clamp_first
+                  else O.proj_X((x - tau * g) / den, lp.lv, lp.uv))
+        xbar = 2.0 * xh - x
+        z = lp.Ax(xbar)
+        w = y / sigma - z
+        return xh, sigma * (w - O.proj_negS(w, lp.lc, lp.uc)), xbar, z
+    return f
+
+
+def _qp_kkt_variant(grad_has_qx=True, dual_quad=-0.5, primal_quad=0.5):
+    def f(lp, x, y, tau, bnorm=None, cnorm=None, row_w=None, col_w=None):
+        if bnorm is None:
+            bnorm = O.finite_bound_norm(lp.lc, lp.uc)
+        if cnorm is None:
+            cnorm = float(np.linalg.norm(lp.c))
+        ax = lp.Ax(x)
+        quad = 0.0 if lp.q is None else float(np.dot(lp.q * x, x))
+        rp = ax - O.proj_S(ax, lp.lc, lp.uc)
+        if row_w is not None:
+            rp = rp * row_w
+        r_p = float(np.linalg.norm(rp)) / (1.0 + bnorm)
+        g = lp.c + lp.q * x - lp.ATy(y) if (lp.q is not None and grad_has_qx) else lp.c - lp.ATy(y)
+        xt = x - tau * g
+        px = O.proj_X(xt, lp.lv, lp.uv)
+        rd = px - x
+        if col_w is not None:
+            rd = rd * col_w
+        r_d = float(np.linalg.norm(rd)) / tau / (1.0 + cnorm)
+        s = (px - xt) / tau
+        obj_p = float(np.dot(lp.c, x)) + primal_quad * quad
+        obj_d = -O.p_fun(-y, lp.lc, lp.uc) + float(np.dot(s, x)) + dual_quad * quad
+        r_g = abs(obj_p - obj_d) / (1.0 + max(abs(obj_p), abs(obj_d)))
+        return dict(r_primal=r_p, r_dual=r_d, r_gap=r_g, obj_p=obj_p, obj_d=obj_d)
+    return f
+
+
+QP_MUTANTS = {
+    "QP prox step without tau": ("pdhg_step", _qp_step_variant(tau_in_prox=False)),
+    "QP prox step clamped before the division": ("pdhg_step", _qp_step_variant(clamp_first=True)),
+    "QP dual residual without Q x in the gradient": ("kkt", _qp_kkt_variant(grad_has_qx=False)),
+    "QP dual objective adds 1/2 x^T Q x": ("kkt", _qp_kkt_variant(dual_quad=0.5)),
+    "QP primal objective without the 1/2": ("kkt", _qp_kkt_variant(primal_quad=1.0)),
+}
+
+
+def test_qp_kkt_and_step_variants_match_the_oracle():
+    """The unmutated variants reproduce the oracle's QP step and KKT exactly, so each mutant
+    above differs from the oracle by its one planted change only."""
+    o = qpins.qp(np.array([[1.0, 2.0], [0.0, 1.0]]), [1.0, -1.0], [0.0, -np.inf], [1.0, 2.0],
+                 [0.0, -1.0], [3.0, np.inf], [0.5, 2.0])
+    x, y = np.array([0.3, -0.2]), np.array([0.1, -0.4])
+    assert all(np.array_equal(a, b) for a, b in
+               zip(_qp_step_variant()(o, x, y, 0.3, 0.7), O.pdhg_step(o, x, y, 0.3, 0.7)))
+    assert _qp_kkt_variant()(o, x, y, 0.3) == O.kkt(o, x, y, 0.3)
+
+
+@pytest.mark.parametrize("name", sorted(QP_MUTANTS))
+def test_qp_mutant_is_caught(name, monkeypatch):
+    attr, fn = QP_MUTANTS[name]
+    monkeypatch.setattr(O, attr, fn)
+    caught = None
+    for check in QP_CHECKS:
+        try:
+            check()
+        except Exception as e:
+            caught = (check.__name__, type(e).__name__)
+            break
+    assert caught, f"no pin caught the planted mistake: {name}"
