@@ -297,3 +297,102 @@ def test_qp_mutant_is_caught(name, monkeypatch):
             caught = (check.__name__, type(e).__name__)
             break
     assert caught, f"no pin caught the planted mistake: {name}"
+
+
+# ----------------------------------------------------------------------------- preconditioning
+# Plausible slips in the optional preconditioning (reading O15), each caught by one of the
+# pins of ``test_precond_oracle.py``.
+import scipy.sparse as sp  # noqa: E402
+
+from oracle import precond as P  # noqa: E402
+import test_precond_oracle as ppins  # noqa: E402
+
+PRECOND_CHECKS = [ppins.test_pow2_nearest, ppins.test_factors_are_powers_of_two_and_scaling_is_exact,
+                  ppins.test_ruiz_equilibrates, ppins.test_kkt_is_reported_for_the_original_lp,
+                  ppins.test_identity_scaling_is_the_plain_solve,
+                  ppins.test_preconditioned_solve_reaches_planted_optimum,
+                  ppins.test_preconditioned_answer_satisfies_the_original_kkt]
+
+_orig_scaled_lp = P.scaled_lp
+_orig_precond_solve = P.solve
+_orig_pow2 = P.pow2_nearest
+
+
+def _scaled_variant(bounds="div", rows="mul", cost="mul"):
+    def f(lp, dr, dc):
+        A = (sp.diags(dr) @ lp.A @ sp.diags(dc)).tocsr()
+        A.sort_indices()
+        rw = dr if rows == "mul" else 1.0 / dr
+        cc = dc * lp.c if cost == "mul" else lp.c / dc
+        lv, uv = (lp.lv / dc, lp.uv / dc) if bounds == "div" else (lp.lv * dc, lp.uv * dc)
+        return O.OracleLP(lp.n, lp.m, cc, A.indptr, A.indices, A.data, rw * lp.lc, rw * lp.uc,
+                          lv, uv, None if lp.q is None else dc * dc * lp.q)
+    return f
+
+
+def _precond_solve_variant(y_back="mul", weights="inv"):
+    def f(lp, eps=1e-8, max_iter=100_000, params=None, x_start=None, y_start=None,
+          ruiz_passes=10, pock_chambolle=True):
+        dr, dc = P.scale_factors(lp, ruiz_passes, pock_chambolle)
+        S = P.scaled_lp(lp, dr, dc)
+        wr, wc = (1.0 / dr, 1.0 / dc) if weights == "inv" else (dr, dc)
+        w = (wr, wc, O.finite_bound_norm(lp.lc, lp.uc), float(np.linalg.norm(lp.c)))
+        res = O.solve(S, eps, max_iter, params,
+                      None if x_start is None else np.asarray(x_start) / dc,
+                      None if y_start is None else np.asarray(y_start) / dr, kkt_weights=w)
+        res.x = dc * res.x
+        res.y = dr * res.y if y_back == "mul" else res.y / dr
+        return res
+    return f
+
+
+def m_ruiz_without_sqrt(norms):
+    norms = np.asarray(norms, np.float64).ravel()
+    out = np.ones_like(norms)
+    pos = norms > 0
+    out[pos] = _orig_pow2(1.0 / norms[pos])
+    return out
+
+
+def m_pow2_arithmetic_midpoint(v):
+    m, e = np.frexp(np.asarray(v, np.float64))
+    return np.ldexp(1.0, np.where(m >= 0.75, e, e - 1))
+
+
+PRECOND_MUTANTS = {
+    "scaled variable bounds multiplied by D_c": ("scaled_lp", _scaled_variant(bounds="mul")),
+    "scaled row bounds divided by D_r": ("scaled_lp", _scaled_variant(rows="div")),
+    "scaled cost divided by D_c": ("scaled_lp", _scaled_variant(cost="div")),
+    "dual answer divided by D_r on the way back": ("solve", _precond_solve_variant(y_back="div")),
+    "KKT weights D_r, D_c instead of their inverses": ("solve", _precond_solve_variant(weights="dir")),
+    "Ruiz factor without the square root": ("_factors", m_ruiz_without_sqrt),
+    "power-of-two rounding at the arithmetic midpoint": ("pow2_nearest", m_pow2_arithmetic_midpoint),
+}
+
+
+def test_precond_variants_match_the_oracle():
+    """The unmutated variants reproduce the oracle's scaled LP and preconditioned solve
+    exactly, so each mutant differs from the oracle by its one planted change only."""
+    import lpgen
+
+    o = O.OracleLP.from_lpgen(lpgen.small_random_lp(2, n=120, m=60))
+    dr, dc = P.scale_factors(o)
+    a, b = _scaled_variant()(o, dr, dc), _orig_scaled_lp(o, dr, dc)
+    for k in ("c", "lc", "uc", "lv", "uv"):
+        assert np.array_equal(getattr(a, k), getattr(b, k)), k
+    ra, rb = _precond_solve_variant()(o, 0.0, 100), _orig_precond_solve(o, 0.0, 100)
+    assert np.array_equal(ra.x, rb.x) and np.array_equal(ra.y, rb.y) and ra.kkt == rb.kkt
+
+
+@pytest.mark.parametrize("name", sorted(PRECOND_MUTANTS))
+def test_precond_mutant_is_caught(name, monkeypatch):
+    attr, fn = PRECOND_MUTANTS[name]
+    monkeypatch.setattr(P, attr, fn)
+    caught = None
+    for check in PRECOND_CHECKS:
+        try:
+            check()
+        except Exception as e:
+            caught = (check.__name__, type(e).__name__)
+            break
+    assert caught, f"no pin caught the planted mistake: {name}"

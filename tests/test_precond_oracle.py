@@ -109,3 +109,23 @@ def test_preconditioned_solve_reaches_planted_optimum():
     ax = o.Ax(res.x)
     assert np.linalg.norm(ax - O.proj_S(ax, o.lc, o.uc)) <= 1e-6 * (1 + np.linalg.norm(lp.b))
     assert np.all(res.x >= o.lv - 1e-12) and np.all(res.x <= o.uv + 1e-12)
+
+
+def test_preconditioned_answer_satisfies_the_original_kkt():
+    """The pair returned by the preconditioned solve, mapped back (x = D_c xs, y = D_r ys), is
+    optimal for the original LP: its KKT errors evaluated on the original LP, with nothing
+    of the scaling, are at the solve's tolerance (an optimal pair has zero projected-gradient
+    residual for every step size, so the step size of this check is free)."""
+    lp = lpgen.small_random_lp(1)
+    o = O.OracleLP.from_lpgen(lp)
+    res = P.solve(o, eps=1e-8, max_iter=200_000)
+    assert res.status == 0
+    for tau in (0.1, 1.0):
+        k = O.kkt(o, res.x, res.y, tau)
+        assert max(k["r_primal"], k["r_dual"], k["r_gap"]) <= 1e-7, (tau, k)
+    # the reported primal residual and primal objective are the original LP's: the factors
+    # are powers of two, so the scaled residual divided by D_r is the original one exactly
+    dr, dc = P.scale_factors(o)
+    assert not np.all(dr == 1.0)  # the check below would not see inverted row weights
+    assert res.kkt["r_primal"] == pytest.approx(k["r_primal"], rel=1e-12)
+    assert res.kkt["obj_p"] == pytest.approx(k["obj_p"], rel=1e-12)
