@@ -160,3 +160,42 @@ def test_bf16_rounding():
     assert r["Ev"][0, 2] == 1.0 + 2.0 ** -7
     assert r["Ev"][0, 3] == -(1.0 + 2.0 ** -7)
     assert r["ev"][0] == 1.0 + 2.0 ** -9
+
+
+def _routing_theta(block_constraints=False):
+    """Weights that route one channel: hv0 = Fv[:, 0], then per round c = R v (channel 0 of
+    the constraint update) and v = v + C c (channel 0 of the variable update), heads read
+    channel 0.  With block_constraints a bias of -1e6 zeroes every constraint state."""
+    P = G.unpack(np.zeros(G.param_count()))
+    P["Ev"][0, 0] = 1.0
+    for l in range(G.L):
+        P[f"Vc{l}"][0, 0] = 1.0
+        if block_constraints:
+            P[f"bc{l}"][0] = -1e6
+        P[f"Uv{l}"][0, 0] = 1.0
+        P[f"Vv{l}"][0, 0] = 1.0
+    P["wx"][0] = 1.0
+    P["wy"][0] = 1.0
+    return G.pack(P)
+
+
+def test_routed_channel_closed_form():
+    """With non-negative entries and inputs every ReLU passes its argument, and the network
+    reduces to the linear recurrence c <- R v, v <- v + C c over its L rounds: x_hat =
+    (I + C R)^L v0 and y_hat = R (I + C R)^(L-1) v0.  A variable update that read the
+    constraint state from before the round, an aggregation applied the wrong way, a round
+    too many or too few, or heads on the wrong state would each change these."""
+    rng = np.random.default_rng(11)
+    n, m = 7, 5
+    A = abs(random_graph(rng, n, m))
+    R, C = G.aggregation(n, m, A.indptr, A.indices, A.data)
+    Fv = np.abs(rng.standard_normal((n, G.F)))
+    Fc = rng.standard_normal((m, G.F))
+    v0 = Fv[:, 0]
+    M = np.eye(n) + (C @ R).toarray()
+    x, y, _ = G.forward(_routing_theta(), R, C, Fv, Fc)
+    np.testing.assert_allclose(x, np.linalg.matrix_power(M, G.L) @ v0, rtol=1e-13)
+    np.testing.assert_allclose(y, R @ (np.linalg.matrix_power(M, G.L - 1) @ v0), rtol=1e-13)
+    # a large negative bias in the constraint update: its ReLU stops every message
+    x, y, _ = G.forward(_routing_theta(block_constraints=True), R, C, Fv, Fc)
+    assert np.array_equal(x, v0) and np.all(y == 0.0)

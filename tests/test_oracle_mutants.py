@@ -397,3 +397,90 @@ def test_precond_mutant_is_caught(name, monkeypatch):
                 caught = (check.__name__, type(e).__name__)
                 break
     assert caught, f"no pin caught the planted mistake: {name}"
+
+
+# ----------------------------------------------------------------------------- warm-start network
+# Slips in the network's forward pass, each caught by a forward pin of ``test_gnn_oracle.py``
+# (closed forms and invariants).  The finite-difference pins are left out here: a slip made
+# the same way in the forward and the backward pass would pass them.
+from oracle import gnn as G  # noqa: E402
+import test_gnn_oracle as gpins  # noqa: E402
+
+GNN_FORWARD_CHECKS = [gpins.test_aggregation_by_hand, gpins.test_zero_weights_closed_form,
+                      gpins.test_routed_channel_closed_form, gpins.test_no_messages_is_node_local,
+                      gpins.test_components_are_independent, gpins.test_permutation_equivariance]
+
+_orig_gnn_forward = G.forward
+_orig_aggregation = G.aggregation
+
+
+def _forward_variant(stale_constraints=False, relu_constraints=True, head_first=False, rounds=None):
+    def f(theta, R, C, Fv, Fc):
+        P = G.unpack(np.asarray(theta, np.float64))
+        hv = G.relu(Fv @ P["Ev"].T + P["ev"])
+        hc = G.relu(Fc @ P["Ec"].T + P["ec"])
+        hv0, hc0 = hv, hc
+        cache = {"hv": [hv], "hc": [hc], "gv": [], "gc": []}
+        for l in range(G.L if rounds is None else rounds):
+            gc = R @ hv
+            zc = hc @ P[f"Uc{l}"].T + gc @ P[f"Vc{l}"].T + P[f"bc{l}"]
+            hc_new = G.relu(zc) if relu_constraints else zc
+            gv = C @ (hc if stale_constraints else hc_new)
+            hc = hc_new
+            hv = G.relu(hv @ P[f"Uv{l}"].T + gv @ P[f"Vv{l}"].T + P[f"bv{l}"])
+            cache["gc"].append(gc)
+            cache["hc"].append(hc)
+            cache["gv"].append(gv)
+            cache["hv"].append(hv)
+        hx, hy = (hv0, hc0) if head_first else (hv, hc)
+        return hx @ P["wx"] + P["bx"], hy @ P["wy"] + P["by"], cache
+    return f
+
+
+def _aggregation_variant(by_count=False, swapped=False):
+    def f(n, m, row_ptr, col, val):
+        A = sp.csr_matrix((np.asarray(val, np.float64), np.asarray(col), np.asarray(row_ptr)),
+                          shape=(m, n))
+        W = (A != 0).astype(np.float64) if by_count else abs(A)
+        rs = np.maximum(1.0, np.asarray(W.sum(axis=1)).ravel())
+        cs = np.maximum(1.0, np.asarray(W.sum(axis=0)).ravel())
+        if swapped:  # each side normalised by the other side's sums
+            return (A @ sp.diags(1.0 / cs)).tocsr(), (A.T @ sp.diags(1.0 / rs)).tocsr()
+        return (sp.diags(1.0 / rs) @ A).tocsr(), (sp.diags(1.0 / cs) @ A.T).tocsr()
+    return f
+
+
+GNN_MUTANTS = {
+    "variable update reads the constraint state from before the round":
+        ("forward", _forward_variant(stale_constraints=True)),
+    "no ReLU in the constraint update": ("forward", _forward_variant(relu_constraints=False)),
+    "heads read the encoder output, not the last round": ("forward", _forward_variant(head_first=True)),
+    "one message-passing round too few": ("forward", _forward_variant(rounds=G.L - 1)),
+    "aggregation normalised by neighbour counts": ("aggregation", _aggregation_variant(by_count=True)),
+    "aggregation normalised by the other side's sums": ("aggregation", _aggregation_variant(swapped=True)),
+}
+
+
+def test_gnn_variants_match_the_oracle():
+    """The unmutated variants reproduce the oracle's forward pass and aggregation exactly."""
+    rng, A, R, C, Fv, Fc, _, _ = gpins.setup(3)
+    th = gpins.random_theta(rng)
+    a, b = _forward_variant()(th, R, C, Fv, Fc), _orig_gnn_forward(th, R, C, Fv, Fc)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for p, q in zip(_aggregation_variant()(A.shape[1], A.shape[0], A.indptr, A.indices, A.data),
+                    _orig_aggregation(A.shape[1], A.shape[0], A.indptr, A.indices, A.data)):
+        assert (p != q).nnz == 0
+
+
+@pytest.mark.parametrize("name", sorted(GNN_MUTANTS))
+def test_gnn_mutant_is_caught(name, monkeypatch):
+    attr, fn = GNN_MUTANTS[name]
+    monkeypatch.setattr(G, attr, fn)
+    caught = None
+    for check in GNN_FORWARD_CHECKS:
+        try:
+            check()
+        except Exception as e:
+            caught = (check.__name__, type(e).__name__)
+            break
+    assert caught, f"no forward pin caught the planted mistake: {name}"
