@@ -20,6 +20,7 @@ ALL_CHECKS = [
     pins.check_pid, pins.check_box_only, pins.check_knapsack,
     pins.check_eta_closed_form, pins.check_default_omega, pins.check_epoch_hand,
     lambda: pins.check_brute_force(seeds=range(2)), pins.check_epoch_trace,
+    pins.check_check_point,
 ]
 
 
@@ -196,6 +197,64 @@ MUTANTS = {
     "infinite bounds counted in ||b||": ("finite_bound_norm", m_bound_norm_with_infinities),
     "eta without the safety factor": ("default_eta", m_eta_no_safety),
 }
+
+
+# Slips inside the solve loop itself, planted in a copy of ``solve`` built from its source
+# with one snippet replaced (the loop has no smaller function to swap).
+import inspect  # noqa: E402
+import textwrap  # noqa: E402
+
+_SOLVE_SRC = textwrap.dedent(inspect.getsource(O.solve))
+
+
+def _solve_with(old, new):
+    assert old in _SOLVE_SRC, old
+    ns = dict(vars(O))
+    exec(compile(_SOLVE_SRC.replace(old, new), "<planted solve>", "exec"), ns)
+    return ns["solve"]
+
+
+SOLVE_MUTANTS = {
+    "restart leaves the anchor where it was": ("            x0, y0 = xh.copy(), yh.copy()\n", ""),
+    "restart continues from the Halpern iterate":
+        ("            x, y = xh.copy(), yh.copy()\n            new_epoch(S)",
+         "            x, y = xn, yn\n            new_epoch(S)"),
+    "tau and sigma swapped": ("tau, sigma = eta / omega, eta * omega", "tau, sigma = eta * omega, eta / omega"),
+    "KKT evaluated at the Halpern iterate": ("last_kkt = kkt(lp, xh, yh,", "last_kkt = kkt(lp, xn, yn,"),
+    "step sizes not refreshed after the PID update":
+        ("            new_epoch(S)\n            tau, sigma = eta / omega, eta * omega\n", "            new_epoch(S)\n"),
+    "fixed-point residual measured from the anchor":
+        ("fixed_point_residual(lp, x, y, xh, yh,", "fixed_point_residual(lp, x0, y0, xh, yh,"),
+    "solution returned at the Halpern iterate": ("OracleResult(x=xh, y=yh,", "OracleResult(x=x, y=y,"),
+    "artificial restart against the check count": ('S["k"], S["T"],\n', 'S["k"], S["checks"],\n'),
+    "inner count not advanced": ('S["k"] = k + 1', 'S["k"] = k'),
+    "check one iteration late": ('if S["T"] % K != 0 and', 'if (S["T"] - 1) % K != 0 and'),
+}
+
+
+def test_unplanted_solve_copy_is_the_oracle():
+    """The copy built from the source, with nothing replaced, solves bit for bit as the
+    oracle does, so each planted copy differs by its one snippet only."""
+    import lpgen
+
+    o = O.OracleLP.from_lpgen(lpgen.small_random_lp(3, n=300, m=150))
+    a = _solve_with("", "")(o, eps=0.0, max_iter=300)
+    b = O.solve(o, eps=0.0, max_iter=300)
+    assert np.array_equal(a.x, b.x) and np.array_equal(a.y, b.y) and a.trace == b.trace
+
+
+@pytest.mark.parametrize("name", sorted(SOLVE_MUTANTS))
+def test_solve_mutant_is_caught(name, monkeypatch):
+    monkeypatch.setattr(O, "solve", _solve_with(*SOLVE_MUTANTS[name]))
+    caught = None
+    with np.errstate(all="ignore"):
+        for check in ALL_CHECKS:
+            try:
+                check()
+            except Exception as e:
+                caught = (getattr(check, "__name__", "check"), type(e).__name__)
+                break
+    assert caught, f"no pin caught the planted mistake: {name}"
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))

@@ -523,3 +523,36 @@ def test_diverging_step_is_reported_at_the_first_check():
     assert bad.status == 2 and bad.iterations == 64
     ok = O.solve(o, eps=1e-4, max_iter=100_000, params=dict(eta=O.default_eta(o)))
     assert ok.status == 0
+
+
+# --------------------------------------------------------------------------- check point (O11)
+def check_check_point():
+    """Reading O11: a check evaluates the KKT errors and the fixed-point residual at the PDHG
+    output T(z) of its iteration, and a restart sets both the anchor and the iterate to T(z).
+    So at a check without a restart the reported KKT values are kkt() of the returned
+    (x^, y^); at a check with a restart the state continues from (x^, y^) with k = 0, and
+    the next iteration is the PDHG step from (x^, y^) with the updated step sizes."""
+    lp = lpgen.small_random_lp(3, n=300, m=150)
+    o = O.OracleLP.from_lpgen(lp)
+    prm = dict(eta=O.default_eta(o))
+    kinds = [r["restart"] for r in O.solve(o, eps=0.0, max_iter=640, params=prm).trace]
+    t_keep = 64 * (kinds.index(0) + 1)
+    t_restart = 64 * (next(i for i, k in enumerate(kinds) if k) + 1)
+    a = O.solve(o, eps=0.0, max_iter=t_keep, params=prm)
+    assert a.trace[-1]["restart"] == 0
+    assert a.kkt == O.kkt(o, a.x, a.y, a.eta / a.omega)
+    b = O.solve(o, eps=0.0, max_iter=t_restart, params=prm)
+    assert b.trace[-1]["restart"] != 0
+    S = b.state
+    for key in ("x", "x0"):
+        assert np.array_equal(S[key], b.x), key
+    for key in ("y", "y0"):
+        assert np.array_equal(S[key], b.y), key
+    assert S["k"] == 0
+    c = O.solve(o, eps=0.0, max_iter=t_restart + 1, params=prm, state=S)
+    xh, yh, _, _ = O.pdhg_step(o, b.x, b.y, b.eta / b.omega, b.eta * b.omega)
+    assert np.array_equal(c.x, xh) and np.array_equal(c.y, yh)
+
+
+def test_check_point_and_restart_point():
+    check_check_point()
