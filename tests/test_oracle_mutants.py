@@ -257,6 +257,56 @@ def test_solve_mutant_is_caught(name, monkeypatch):
     assert caught, f"no pin caught the planted mistake: {name}"
 
 
+# Slips inside the KKT formulas (Appendix B.4), planted the same way in copies of ``kkt``.
+_KKT_SRC = textwrap.dedent(inspect.getsource(O.kkt))
+
+
+def _kkt_with(old, new):
+    assert old in _KKT_SRC, old
+    ns = dict(vars(O))
+    exec(compile(_KKT_SRC.replace(old, new), "<planted kkt>", "exec"), ns)
+    return ns["kkt"]
+
+
+KKT_MUTANTS = {
+    "r_primal without the 1 + in its denominator":
+        ("r_p = float(np.linalg.norm(rp_vec)) / (1.0 + bnorm)",
+         "r_p = float(np.linalg.norm(rp_vec)) / max(bnorm, 1e-300)"),
+    "r_primal normalised by ||c||":
+        ("r_p = float(np.linalg.norm(rp_vec)) / (1.0 + bnorm)",
+         "r_p = float(np.linalg.norm(rp_vec)) / (1.0 + cnorm)"),
+    "r_dual without the 1 + in its denominator": ("/ tau / (1.0 + cnorm)", "/ tau / max(cnorm, 1e-300)"),
+    "gap denominator with min": ("(1.0 + max(abs(obj_p), abs(obj_d)))", "(1.0 + min(abs(obj_p), abs(obj_d)))"),
+    "reduced cost s with its sign flipped": ("s = (px - xt) / tau", "s = (xt - px) / tau"),
+    "dual objective without s^T x": ("+ float(np.dot(s, x)) - 0.5 * quad", "- 0.5 * quad"),
+    "primal residual against -S": ("rp_vec = ax - proj_S(ax, lp.lc, lp.uc)",
+                                   "rp_vec = ax + proj_negS(ax, lp.lc, lp.uc)"),
+}
+
+
+def test_unplanted_kkt_copy_is_the_oracle():
+    import lpgen
+
+    lp = lpgen.small_random_lp(3, n=300, m=150)
+    o = O.OracleLP.from_lpgen(lp)
+    x, y = lp.x_star + 0.1, lp.y_star - 0.2
+    assert _kkt_with("", "")(o, x, y, 0.3) == O.kkt(o, x, y, 0.3)
+
+
+@pytest.mark.parametrize("name", sorted(KKT_MUTANTS))
+def test_kkt_mutant_is_caught(name, monkeypatch):
+    monkeypatch.setattr(O, "kkt", _kkt_with(*KKT_MUTANTS[name]))
+    caught = None
+    with np.errstate(all="ignore"):
+        for check in ALL_CHECKS:
+            try:
+                check()
+            except Exception as e:
+                caught = (getattr(check, "__name__", "check"), type(e).__name__)
+                break
+    assert caught, f"no pin caught the planted mistake: {name}"
+
+
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_mutant_is_caught(name, monkeypatch):
     attr, fn = MUTANTS[name]

@@ -166,6 +166,12 @@ def check_kkt_hand():
     k = O.kkt(one_var_lp(-1.0), np.array([5.0]), np.array([0.0]), 0.5)
     assert (k["r_primal"], k["r_dual"], k["r_gap"]) == (0.0, 0.0, 0.0)
     assert (k["obj_p"], k["obj_d"]) == (-5.0, -5.0)
+    # min 3x with ||c|| = 3 != ||b|| = 1, at x = 1/2, y = 2, tau = 1/2: r_p = (1/2)/(1+1) = 1/4;
+    # g = 3 - 2 = 1, x - tau g = 0 = proj_X -> r_d = (1/2)/(1/2)/(1+3) = 1/4, s = 0;
+    # obj_p = 3/2, obj_d = 2, r_gap = (1/2)/(1+2)
+    k = O.kkt(one_var_lp(3.0), np.array([0.5]), np.array([2.0]), 0.5)
+    assert (k["r_primal"], k["r_dual"], k["r_gap"]) == (0.25, 0.25, 0.5 / 3.0)
+    assert (k["obj_p"], k["obj_d"]) == (1.5, 2.0)
 
 
 def test_kkt_hand_computed():
