@@ -204,14 +204,18 @@ MUTANTS = {
 import inspect  # noqa: E402
 import textwrap  # noqa: E402
 
-_SOLVE_SRC = textwrap.dedent(inspect.getsource(O.solve))
+def _planted(name, old, new):
+    """A copy of the oracle function ``name`` built from its source with ``old`` replaced
+    by ``new`` (both empty: the function itself)."""
+    src = textwrap.dedent(inspect.getsource(getattr(O, name)))
+    assert old in src, old
+    ns = dict(vars(O))
+    exec(compile(src.replace(old, new), f"<planted {name}>", "exec"), ns)
+    return ns[name]
 
 
 def _solve_with(old, new):
-    assert old in _SOLVE_SRC, old
-    ns = dict(vars(O))
-    exec(compile(_SOLVE_SRC.replace(old, new), "<planted solve>", "exec"), ns)
-    return ns["solve"]
+    return _planted("solve", old, new)
 
 
 SOLVE_MUTANTS = {
@@ -258,14 +262,8 @@ def test_solve_mutant_is_caught(name, monkeypatch):
 
 
 # Slips inside the KKT formulas (Appendix B.4), planted the same way in copies of ``kkt``.
-_KKT_SRC = textwrap.dedent(inspect.getsource(O.kkt))
-
-
 def _kkt_with(old, new):
-    assert old in _KKT_SRC, old
-    ns = dict(vars(O))
-    exec(compile(_KKT_SRC.replace(old, new), "<planted kkt>", "exec"), ns)
-    return ns["kkt"]
+    return _planted("kkt", old, new)
 
 
 KKT_MUTANTS = {
@@ -296,6 +294,38 @@ def test_unplanted_kkt_copy_is_the_oracle():
 @pytest.mark.parametrize("name", sorted(KKT_MUTANTS))
 def test_kkt_mutant_is_caught(name, monkeypatch):
     monkeypatch.setattr(O, "kkt", _kkt_with(*KKT_MUTANTS[name]))
+    caught = None
+    with np.errstate(all="ignore"):
+        for check in ALL_CHECKS:
+            try:
+                check()
+            except Exception as e:
+                caught = (getattr(check, "__name__", "check"), type(e).__name__)
+                break
+    assert caught, f"no pin caught the planted mistake: {name}"
+
+
+# Slips inside the restart rules (Appendix B.2) and the PID update (Appendix B.3).
+RULE_MUTANTS = {
+    "necessary decay allowed at the epoch's first check":
+        ("restart_decision", "if (not first_check) and r <=", "if r <="),
+    "sufficient decay with <": ("restart_decision", "if r <= beta_s * r_anchor:", "if r < beta_s * r_anchor:"),
+    "artificial restart with >": ("restart_decision", "if k >= beta_a * T:", "if k > beta_a * T:"),
+    "artificial restart against a fixed length": ("restart_decision", "if k >= beta_a * T:", "if k >= beta_a * 64:"),
+    "necessary decay against beta_sufficient":
+        ("restart_decision", "r <= beta_n * r_anchor and", "r <= beta_s * r_anchor and"),
+    "PID integral without the current error": ("pid_omega", "e_sum = e_sum + e", "e_sum = e_sum"),
+    "PID derivative sign": ("pid_omega", "de = 0.0 if e_prev is None else (e - e_prev)",
+                            "de = 0.0 if e_prev is None else (e_prev - e)"),
+    "PID error without the sqrt(omega) weights":
+        ("pid_omega", "e = math.log((so * d_x) / (d_y / so))", "e = math.log(d_x / d_y)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(RULE_MUTANTS))
+def test_rule_mutant_is_caught(name, monkeypatch):
+    fn, old, new = RULE_MUTANTS[name]
+    monkeypatch.setattr(O, fn, _planted(fn, old, new))
     caught = None
     with np.errstate(all="ignore"):
         for check in ALL_CHECKS:
