@@ -43,3 +43,19 @@ def assert_vec_parity(a, b, tol, what=""):
 def assert_xy_parity(x, y, xr, yr, tol, what=""):
     assert_vec_parity(x, xr, tol, f"{what} x")
     assert_vec_parity(y, yr, tol, f"{what} y")
+
+
+def first_divergence(gpu_trace, oracle_trace):
+    """Parity report of free-running solves (reading O21): the first check at which the GPU's
+    and the oracle's restart decisions (or check iterations) differ, as a dict with the
+    check index, both records' iteration, decision and KKT values, or None when both traces
+    agree and have the same length.  GPU records name the fixed-point residual r_fp, the
+    oracle's r."""
+    keys = ("T", "restart", "r_primal", "r_dual", "r_gap")
+    for i, (g, o) in enumerate(zip(gpu_trace, oracle_trace)):
+        if g["restart"] != o["restart"] or g["T"] != o["T"]:
+            return {"check": i, "gpu": {k: g[k] for k in keys}, "oracle": {k: o[k] for k in keys}}
+    if len(gpu_trace) != len(oracle_trace):
+        return {"check": min(len(gpu_trace), len(oracle_trace)), "gpu_checks": len(gpu_trace),
+                "oracle_checks": len(oracle_trace)}
+    return None

@@ -20,7 +20,7 @@ import pytest
 import lpgen
 from oracle import pdhg as O
 from oracle import precond as P
-from parity_util import KKT_ABS, assert_xy_parity
+from parity_util import KKT_ABS, assert_xy_parity, first_divergence
 
 pytestmark = pytest.mark.gpu
 
@@ -152,7 +152,8 @@ def test_free_running_with_own_step_matches_oracle(Solver, seed):
     tr = s.trace()
     k = s.kkt()
     s.close()
-    assert [r["restart"] for r in tr] == [r["restart"] for r in ores.trace]
+    rep = first_divergence(tr, ores.trace)  # the first differing decision, if any
+    assert rep is None, rep
     assert close(k["eta"], ores.eta)
     assert abs(k["omega"] - ores.omega) <= 1e-9 * ores.omega
     assert_xy_parity(x, y, ores.x, ores.y, 1e-9)
