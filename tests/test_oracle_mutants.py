@@ -305,8 +305,19 @@ def test_kkt_mutant_is_caught(name, monkeypatch):
     assert caught, f"no pin caught the planted mistake: {name}"
 
 
-# Slips inside the restart rules (Appendix B.2) and the PID update (Appendix B.3).
+# Slips inside the PDHG step (Section 2.2), the Halpern step (Appendix B.1), the restart
+# rules (Appendix B.2) and the PID update (Appendix B.3).
 RULE_MUTANTS = {
+    "extrapolation 2 x^ + x": ("pdhg_step", "xbar = 2.0 * xh - x", "xbar = 2.0 * xh + x"),
+    "dual argument y * sigma": ("pdhg_step", "w = y / sigma - z", "w = y * sigma - z"),
+    "dual step without the sigma factor": ("pdhg_step", "yh = sigma * (w - proj_negS(w, lp.lc, lp.uc))",
+                                           "yh = (w - proj_negS(w, lp.lc, lp.uc))"),
+    "dual box with its bounds swapped": ("pdhg_step", "proj_negS(w, lp.lc, lp.uc)", "proj_negS(w, lp.uc, lp.lc)"),
+    "primal step with sigma": ("pdhg_step", "xh = proj_X(x - tau * g, lp.lv, lp.uv)",
+                               "xh = proj_X(x - sigma * g, lp.lv, lp.uv)"),
+    "reflection with 1 - gamma": ("halpern", "((1.0 + gamma) * zh - gamma * z)", "((1.0 - gamma) * zh + gamma * z)"),
+    "Halpern weight k / (k + 1)": ("halpern", "w1 = (k + 1.0) / (k + 2.0)", "w1 = k / (k + 1.0)"),
+    "anchor weight 1 / (k + 1)": ("halpern", "w0 = 1.0 / (k + 2.0)", "w0 = 1.0 / (k + 1.0)"),
     "necessary decay allowed at the epoch's first check":
         ("restart_decision", "if (not first_check) and r <=", "if r <="),
     "sufficient decay with <": ("restart_decision", "if r <= beta_s * r_anchor:", "if r < beta_s * r_anchor:"),
