@@ -101,3 +101,19 @@ def test_kernel_source_hash_ignores_comments():
     assert bench._code_only(a) == bench._code_only(b)
     assert bench._code_only(a) != bench._code_only(b.replace("+ 1", "+ 2"))
     assert len(bench.kernel_source_hash()) == 16
+
+
+def test_error_vs_fp64_definitions():
+    """The mixed-precision error report: relative 2-norm distances of x and y from the FP64
+    answer, and each objective's error against p* relative to 1 + |p*|."""
+    import numpy as np
+
+    import bench
+
+    fp64 = (np.array([3.0, 4.0]), np.array([1.0, 0.0]), -10.0)
+    same = bench.error_vs_fp64(fp64, fp64, -10.0)
+    assert same == {"x_rel": 0.0, "y_rel": 0.0, "obj_p_err_mixed": 0.0, "obj_p_err_fp64": 0.0}
+    mixed = (np.array([3.0, 4.5]), np.array([1.0, 0.0]), -9.0)
+    r = bench.error_vs_fp64(mixed, fp64, -10.5)
+    assert r["x_rel"] == 0.5 / 5.0 and r["y_rel"] == 0.0
+    assert r["obj_p_err_mixed"] == 1.5 / 11.5 and r["obj_p_err_fp64"] == 0.5 / 11.5
