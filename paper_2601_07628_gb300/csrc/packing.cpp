@@ -346,14 +346,16 @@ void build_chunks(const std::vector<int32_t>& offsets, int chunk, std::vector<in
 // (load checks that nonzeros lie in their instance's range), when nothing changes.  An
 // instance with no entries in that orientation keeps index 0.
 void own_instance_zero_gathers(HostPacked& H, const std::vector<int32_t>& offsets) {
-  for (int s = 0; s < H.nslots; ++s) {
-    const int inst = H.slots[s].inst;
-    if (offsets[inst + 1] == offsets[inst]) continue;
-    const uint32_t base = (uint32_t)offsets[inst];
-    uint32_t* si = H.idx.data() + (size_t)s * SLOT_ITEMS;
-    for (int k = 0; k < SLOT_ITEMS; ++k)
-      if ((si[k] & IDX_MASK) == 0) si[k] |= base;
-  }
+  run_parts(even_parts(H.nslots, host_threads()), [&](int, int64_t s0, int64_t s1) {
+    for (int64_t s = s0; s < s1; ++s) {  // slots are independent
+      const int inst = H.slots[s].inst;
+      if (offsets[inst + 1] == offsets[inst]) continue;
+      const uint32_t base = (uint32_t)offsets[inst];
+      uint32_t* si = H.idx.data() + (size_t)s * SLOT_ITEMS;
+      for (int k = 0; k < SLOT_ITEMS; ++k)
+        if ((si[k] & IDX_MASK) == 0) si[k] |= base;
+    }
+  });
 }
 
 }  // namespace pdhg

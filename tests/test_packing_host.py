@@ -148,7 +148,7 @@ def test_results_do_not_depend_on_host_threads(checker, case):
     output is the same, bit for bit, with 1, 3 and 7 threads."""
     import scipy.sparse as sp
 
-    offs = None
+    offs = coffs = None
     if case == "stress":
         lp = lpgen.row_length_stress_lp(11, LENGTHS, n=12000)
         A = sp.csr_matrix((lp.val, lp.col, lp.row_ptr), shape=(lp.m, lp.n))
@@ -158,6 +158,7 @@ def test_results_do_not_depend_on_host_threads(checker, case):
                            for p in parts]).tocsr()
         A.sort_indices()
         offs = np.concatenate([[0], np.cumsum([p.m for p in parts])])
+        coffs = np.concatenate([[0], np.cumsum([p.n for p in parts])])  # per-instance gathers
     else:
         lp = lpgen.scaled_powerlaw_lp(1, 0.01)
         A = sp.csr_matrix((lp.val, lp.col, lp.row_ptr), shape=(lp.m, lp.n))
@@ -165,6 +166,6 @@ def test_results_do_not_depend_on_host_threads(checker, case):
     for t in (1, 3, 7):
         for M, off in ((A, offs), (A.T.tocsr(), None)):
             st = run(checker, M.indptr, M.indices, M.data, M.shape[1], seed=40 + t, offsets=off,
-                     threads=t)
+                     threads=t, col_offsets=coffs if off is not None else None)
             hashes.add((M.shape, st["hash"]))
     assert len(hashes) == 2, hashes
