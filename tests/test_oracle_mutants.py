@@ -20,7 +20,7 @@ ALL_CHECKS = [
     pins.check_pid, pins.check_box_only, pins.check_knapsack,
     pins.check_eta_closed_form, pins.check_default_omega, pins.check_epoch_hand,
     lambda: pins.check_brute_force(seeds=range(2)), pins.check_epoch_trace,
-    pins.check_check_point,
+    pins.check_check_point, pins.check_power_rounds_by_hand, pins.check_power_stop_rule,
 ]
 
 
@@ -318,6 +318,12 @@ RULE_MUTANTS = {
     "reflection with 1 - gamma": ("halpern", "((1.0 + gamma) * zh - gamma * z)", "((1.0 - gamma) * zh + gamma * z)"),
     "Halpern weight k / (k + 1)": ("halpern", "w1 = (k + 1.0) / (k + 2.0)", "w1 = k / (k + 1.0)"),
     "anchor weight 1 / (k + 1)": ("halpern", "w0 = 1.0 / (k + 2.0)", "w0 = 1.0 / (k + 1.0)"),
+    "power iteration from an unnormalised start":
+        ("power_sigma_max", "v = np.full(n, 1.0 / math.sqrt(n))", "v = np.full(n, 1.0)"),
+    "power iteration from 1/n": ("power_sigma_max", "v = np.full(n, 1.0 / math.sqrt(n))", "v = np.full(n, 1.0 / n)"),
+    "Rayleigh quotient as ||A v||": ("power_sigma_max", "lam = float(np.dot(w, w))", "lam = float(np.linalg.norm(w))"),
+    "power iteration stops on the absolute change":
+        ("power_sigma_max", "if abs(lam - lam_prev) <= tol * lam:", "if abs(lam - lam_prev) <= tol:"),
     "necessary decay allowed at the epoch's first check":
         ("restart_decision", "if (not first_check) and r <=", "if r <="),
     "sufficient decay with <": ("restart_decision", "if r <= beta_s * r_anchor:", "if r < beta_s * r_anchor:"),

@@ -332,6 +332,51 @@ def test_power_iteration_matches_svd():
     check_power_iteration()
 
 
+def check_power_rounds_by_hand():
+    """The first rounds of the power iteration (reading O8) worked by hand on A = diag(3, 4):
+    from v = (1, 1)/sqrt(2), w = A v = (3, 4)/sqrt(2) and lam = w^T w = 25/2; then v = A^T w /
+    ||A^T w|| = (9, 16)/sqrt(337), w = (27, 64)/sqrt(337), lam = 4825/337.  With power_tol = 0
+    the iteration runs exactly the given number of rounds."""
+    lp = O.OracleLP(2, 2, [1.0, 1.0], [0, 1, 2], [0, 1], [3.0, 4.0], [0.0, 0.0], [1.0, 1.0],
+                    [0.0, 0.0], [1.0, 1.0])
+    s1 = O.power_sigma_max(lp, iters=1, tol=0.0)
+    s2 = O.power_sigma_max(lp, iters=2, tol=0.0)
+    assert abs(s1 - math.sqrt(25.0 / 2.0)) <= 1e-15 * s1, s1
+    assert abs(s2 - math.sqrt(4825.0 / 337.0)) <= 1e-15 * s2, s2
+
+
+def test_power_rounds_by_hand():
+    check_power_rounds_by_hand()
+
+
+def check_power_stop_rule():
+    """The stopping rule |lam - lam_prev| <= tol * lam (reading O8) on A = diag(2a, a),
+    a = 1000: from v = (1, 1)/sqrt(2) round k gives lam_k = a^2 (4 16^(k-1) + 1) /
+    (16^(k-1) + 1) in closed form (v_k is proportional to (4^k, 1)).  The relative rule is
+    blind to the scale a, so the stopping round and sigma = sqrt(lam_K) follow from exact
+    fractions; a rule on the absolute change would run on far longer at this scale."""
+    from fractions import Fraction as Fr
+
+    a = 1000
+    lp = O.OracleLP(2, 2, [1.0, 1.0], [0, 1, 2], [0, 1], [2.0 * a, float(a)], [0.0, 0.0],
+                    [1.0, 1.0], [0.0, 0.0], [1.0, 1.0])
+    lam = lambda k: Fr(a * a) * (4 * 16 ** (k - 1) + 1) / (16 ** (k - 1) + 1)
+    tol, prev, k = Fr(1, 10 ** 8), Fr(0), 0
+    while True:
+        k += 1
+        cur = lam(k)
+        if abs(cur - prev) <= tol * cur:
+            break
+        prev = cur
+    assert k == 9  # stops with a margin of about 4 on either side of the threshold
+    s = O.power_sigma_max(lp)
+    assert abs(s - math.sqrt(float(lam(k)))) <= 1e-14 * s, (s, math.sqrt(float(lam(k))))
+
+
+def test_power_stop_rule():
+    check_power_stop_rule()
+
+
 def check_eta_closed_form():
     """eta = safety / sigma_max(A) (the step-size condition eta ||A||_2 < 1 of Section 2.2,
     with the documented safety factor 0.998): on A = diag(3, 4) sigma_max is 4, so
