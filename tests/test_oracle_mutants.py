@@ -324,6 +324,16 @@ RULE_MUTANTS = {
     "Rayleigh quotient as ||A v||": ("power_sigma_max", "lam = float(np.dot(w, w))", "lam = float(np.linalg.norm(w))"),
     "power iteration stops on the absolute change":
         ("power_sigma_max", "if abs(lam - lam_prev) <= tol * lam:", "if abs(lam - lam_prev) <= tol:"),
+    "equality rows counted twice in ||b||":
+        ("finite_bound_norm", "eq = np.isfinite(lc) & np.isfinite(uc) & (lc == uc)",
+         "eq = np.zeros_like(lc, dtype=bool)"),
+    "p() without its lower-bound term": ("p_fun", "return float(np.sum(tu) - np.sum(tl))", "return float(np.sum(tu))"),
+    "p() with its lower-bound term added": ("p_fun", "return float(np.sum(tu) - np.sum(tl))",
+                                            "return float(np.sum(tu) + np.sum(tl))"),
+    "p() forming 0 * inf": ("p_fun", "    nz = yp > 0\n    tu[nz] = u[nz] * yp[nz]\n    nz = ym > 0\n"
+                                     "    tl[nz] = l[nz] * ym[nz]", "    tu = u * yp\n    tl = l * ym"),
+    "projection onto -S with its bounds swapped":
+        ("proj_negS", "return np.minimum(np.maximum(v, -uc), -lc)", "return np.minimum(np.maximum(v, -lc), -uc)"),
     "necessary decay allowed at the epoch's first check":
         ("restart_decision", "if (not first_check) and r <=", "if r <="),
     "sufficient decay with <": ("restart_decision", "if r <= beta_s * r_anchor:", "if r < beta_s * r_anchor:"),
