@@ -204,12 +204,12 @@ MUTANTS = {
 import inspect  # noqa: E402
 import textwrap  # noqa: E402
 
-def _planted(name, old, new):
-    """A copy of the oracle function ``name`` built from its source with ``old`` replaced
-    by ``new`` (both empty: the function itself)."""
-    src = textwrap.dedent(inspect.getsource(getattr(O, name)))
+def _planted(name, old, new, module=O):
+    """A copy of the oracle function ``name`` (of ``module``) built from its source with
+    ``old`` replaced by ``new`` (both empty: the function itself)."""
+    src = textwrap.dedent(inspect.getsource(getattr(module, name)))
     assert old in src, old
-    ns = dict(vars(O))
+    ns = dict(vars(module))
     exec(compile(src.replace(old, new), f"<planted {name}>", "exec"), ns)
     return ns[name]
 
@@ -650,3 +650,42 @@ def test_gnn_mutant_is_caught(name, monkeypatch):
             caught = (check.__name__, type(e).__name__)
             break
     assert caught, f"no forward pin caught the planted mistake: {name}"
+
+
+# Slips in the network's backward pass, each caught by the finite-difference pins (every bias
+# and head entry, and entries of every weight block).
+GNN_FD_CHECKS = [lambda: gpins.test_gradient_matches_finite_differences(0),
+                 lambda: gpins.test_gradient_matches_finite_differences(1)]
+
+GNN_BACKWARD_MUTANTS = {
+    "a weight gradient transposed": ('G[f"Uv{l}"] = dz.T @ K["hv"][l]', 'G[f"Uv{l}"] = (dz.T @ K["hv"][l]).T'),
+    "ReLU mask of the round's input": ('dz = dhv * (K["hv"][l + 1] > 0)', 'dz = dhv * (K["hv"][l] > 0)'),
+    "message gradient through C^T dropped": ("dhc = dhc + C.T @ dgv", "dhc = dhc"),
+    "message gradient through R^T dropped": ("dhv = dhv + R.T @ dgc", "dhv = dhv"),
+    "Vc gradient from the next round's messages":
+        ('G[f"Vc{l}"] = dz.T @ K["gc"][l]', 'G[f"Vc{l}"] = dz.T @ K["gc"][min(l + 1, L - 1)]'),
+    "encoder gradient without its ReLU mask": ('dz = dhv * (K["hv"][0] > 0)\n    G["Ev"]', 'dz = dhv\n    G["Ev"]'),
+    "loss gradient without the 1/n": ("dx = 2.0 * (x_hat - tx) / n", "dx = 2.0 * (x_hat - tx)"),
+    "encoder gradient against permuted features": ('G["Ec"] = dz.T @ Fc', 'G["Ec"] = dz.T @ Fc[::-1]'),
+}
+
+
+def test_unplanted_backward_copy_is_the_oracle():
+    rng, A, R, C, Fv, Fc, tx, ty = gpins.setup(4)
+    th = gpins.random_theta(rng)
+    a = _planted("backward", "", "", module=G)(th, R, C, Fv, Fc, tx, ty)
+    b = G.backward(th, R, C, Fv, Fc, tx, ty)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("name", sorted(GNN_BACKWARD_MUTANTS))
+def test_gnn_backward_mutant_is_caught(name, monkeypatch):
+    monkeypatch.setattr(G, "backward", _planted("backward", *GNN_BACKWARD_MUTANTS[name], module=G))
+    caught = None
+    for check in GNN_FD_CHECKS:
+        try:
+            check()
+        except Exception as e:
+            caught = type(e).__name__
+            break
+    assert caught, f"no pin caught the planted mistake: {name}"
