@@ -22,6 +22,13 @@ static int fail(const char* what, long a = 0, long b = 0) {
 }
 
 int main(int argc, char** argv) {
+  if (argc == 5 && std::strcmp(argv[1], "--perm") == 0) {  // the block permutation alone
+    const std::vector<int32_t> p =
+        block_permutation(std::atoi(argv[2]), std::atoi(argv[3]), std::strtoull(argv[4], nullptr, 10), true);
+    for (size_t i = 0; i < p.size(); ++i) std::printf("%d%c", p[i], i + 1 < p.size() ? ',' : '\n');
+    if (p.empty()) std::printf("\n");
+    return 0;
+  }
   if (argc < 2) return fail("usage");
   FILE* f = std::fopen(argv[1], "rb");
   if (!f) return fail("open");

@@ -169,3 +169,50 @@ def test_results_do_not_depend_on_host_threads(checker, case):
                      threads=t, col_offsets=coffs if off is not None else None)
             hashes.add((M.shape, st["hash"]))
     assert len(hashes) == 2, hashes
+
+
+_M64 = (1 << 64) - 1
+
+
+def _splitmix64(state):
+    """SplitMix64 (Steele, Lea and Flood, 2014): advance the state by the golden-ratio
+    increment, then two xor-shift-multiply rounds and a final xor-shift."""
+    state = (state + 0x9E3779B97F4A7C15) & _M64
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return state, z ^ (z >> 31)
+
+
+def _block_permutation(length, block, seed):
+    """Reading O17: Fisher-Yates over the whole blocks (i from the last block down to 1, j =
+    the next SplitMix64 output mod (i + 1)), rows keeping their order inside a block, the
+    trailing partial block in place; new position k holds old row perm[k]."""
+    perm = list(range(length))
+    if length <= block:
+        return perm
+    nfull = length // block
+    order = list(range(nfull))
+    state = seed
+    for i in range(nfull - 1, 0, -1):
+        state, r = _splitmix64(state)
+        j = r % (i + 1)
+        order[i], order[j] = order[j], order[i]
+    for b in range(nfull):
+        for t in range(block):
+            perm[b * block + t] = order[b] * block + t
+    return perm
+
+
+def test_block_permutation_is_splitmix64_fisher_yates(checker):
+    """The solver's block permutation (host C++) against the reading written out in Python
+    from the published SplitMix64 definition, whose first output from state 0 is
+    0xE220A8397B1DCDAF; row and column seeds of a single LP and of batch instances."""
+    assert _splitmix64(0)[1] == 0xE220A8397B1DCDAF
+    exe, _ = checker
+    for length, block, seed in ((1000, 256, 1), (1000, 256, 2), (100_003, 256, 1), (100_003, 256, 8),
+                                (512, 256, 5), (255, 256, 1), (7, 3, 7)):
+        out = subprocess.run([exe, "--perm", str(length), str(block), str(seed)], capture_output=True,
+                             text=True, check=True).stdout.strip()
+        got = [int(v) for v in out.split(",")] if out else []
+        assert got == _block_permutation(length, block, seed), (length, block, seed)
