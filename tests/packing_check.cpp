@@ -270,6 +270,13 @@ int main(int argc, char** argv) {
     }
     if (std::memcmp(v.data(), sval.data(), nnz * sizeof(double)) != 0 || er != dr || ec != dc)
       return fail("preconditioning");
+    if (const char* path = std::getenv("PACKING_CHECK_SCALING")) {  // D_r then D_c, float64
+      FILE* g = std::fopen(path, "wb");
+      if (!g || std::fwrite(dr.data(), 8, dr.size(), g) != dr.size() ||
+          std::fwrite(dc.data(), 8, dc.size(), g) != dc.size())
+        return fail("scaling dump");
+      std::fclose(g);
+    }
   }
 
   unsigned long long h = 1469598103934665603ull;  // FNV-1a over every output

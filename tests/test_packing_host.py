@@ -31,7 +31,8 @@ def checker(tmp_path_factory):
     return exe, d
 
 
-def run(checker, row_ptr, col, val, ncols, seed=0, offsets=None, threads=None, col_offsets=None):
+def run(checker, row_ptr, col, val, ncols, seed=0, offsets=None, threads=None, col_offsets=None,
+        scaling_to=None):
     exe, d = checker
     rows = len(row_ptr) - 1
     x = np.random.default_rng(seed).standard_normal(ncols)
@@ -47,6 +48,8 @@ def run(checker, row_ptr, col, val, ncols, seed=0, offsets=None, threads=None, c
     env = dict(os.environ)
     if threads is not None:
         env["DPDLP_HOST_THREADS"] = str(threads)
+    if scaling_to is not None:
+        env["PACKING_CHECK_SCALING"] = str(scaling_to)
     out = subprocess.run(cmd, capture_output=True, text=True, env=env).stdout.strip()
     assert out.startswith("ok"), out
     return dict(kv.split("=") for kv in out.split()[1:])
@@ -216,3 +219,25 @@ def test_block_permutation_is_splitmix64_fisher_yates(checker):
                              text=True, check=True).stdout.strip()
         got = [int(v) for v in out.split(",")] if out else []
         assert got == _block_permutation(length, block, seed), (length, block, seed)
+
+
+def test_host_preconditioner_matches_the_oracle(checker, tmp_path):
+    """The solver's host preconditioner (C++) computes the oracle's factors exactly: 10 Ruiz
+    passes, then one Pock-Chambolle pass, each factor the power of two nearest to
+    1/sqrt(row or column norm) (reading O15), on a matrix whose entries span twelve
+    decades."""
+    from oracle import pdhg as O
+    from oracle import precond as P
+    import test_precond_oracle as pp
+
+    A = pp.badly_scaled(5)
+    m, n = A.shape
+    path = tmp_path / "scaling.bin"
+    run(checker, A.indptr, A.indices, A.data, n, seed=50, scaling_to=path)
+    d = np.fromfile(path, dtype=np.float64)
+    lp = O.OracleLP(n, m, np.ones(n), A.indptr, A.indices, A.data, -np.ones(m), np.ones(m),
+                    np.zeros(n), np.full(n, 3.0))
+    dr, dc = P.scale_factors(lp)
+    assert d.shape == (m + n,)
+    assert np.array_equal(d[:m], dr) and np.array_equal(d[m:], dc)
+    assert dr.min() < 1e-2 and dr.max() > 1e2  # the factors do vary
