@@ -102,7 +102,9 @@ def tune(solver, cache: str | None = DEFAULT_CACHE, reps: int = 20, rounds: int 
     Needs a solver state (after ``solve`` or ``set_state``; a fresh handle gets one from a
     zero-iteration solve).  Returns ``{"key", "cached", "ms", <parameter>: <value>...}``;
     ``ms`` holds the timings (best of ``rounds`` x ``reps`` launches) when they were taken
-    now.
+    now.  Timing the fused body of a single LP runs graph bodies from a saved state and
+    puts that state back with ``set_state``, so, as after any ``set_state``, the next
+    ``solve`` continues from it whatever ``resume`` says.
     """
     info = solver.info()
     ninst = len(solver.row_off) - 1
