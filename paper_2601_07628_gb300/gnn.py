@@ -293,11 +293,11 @@ def guard_starts(solver, lps, starts, probe_iters: int = 64):
     ``solver`` holds ``lps`` as a batch (``load_batch``).  Both start sets are run for
     ``probe_iters`` iterations on that handle; an instance keeps its predicted start when
     its relative KKT error after them is at most that of the cold start, else it falls back
-    to the cold start (plain PDHG from zero stays the fallback and the judge of the
-    prediction).  The handle is left with the chosen start set and ``resume`` = 0, ready for
-    the real solve.  Returns (chosen starts, kept mask, KKT from the prediction, KKT cold)."""
+    to the cold start (plain PDHG from zero stays the fallback and the yardstick for the
+    prediction).  The handle is left with the chosen start set and ``resume`` = 0, so the
+    next solve starts from the chosen starts.  Returns (chosen starts, kept mask, KKT from
+    the prediction, KKT cold)."""
     cold = [cold_start(lp) for lp in lps]
-    resume0 = solver.get_param("resume")
     solver.set_param("resume", 0)
     errs = []
     for st in (starts, cold):
@@ -307,5 +307,4 @@ def guard_starts(solver, lps, starts, probe_iters: int = 64):
     keep = [w <= c for w, c in zip(*errs)]
     chosen = [s if k else c for s, k, c in zip(starts, keep, cold)]
     solver.set_start(np.concatenate([x for x, _ in chosen]), np.concatenate([y for _, y in chosen]))
-    solver.set_param("resume", resume0)
     return chosen, keep, errs[0], errs[1]
